@@ -1,0 +1,227 @@
+/*
+ * rs.h -- C ABI of librs, a B300 (sm_103a) engine for streaming pipelines whose
+ * input is cut into variably sized regions (Timcheck & Buhler, "Streaming
+ * Computations with Region-Based State on SIMD Architectures").
+ *
+ * The problem, as the paper states it:
+ *   - Section 4: the input is a stream of composite objects ("parents"); parent r
+ *     holds L_r elements (findCount() in Figure 4).  Enumeration opens each parent
+ *     into the stream of its elements i = 0..L_r-1; downstream nodes can consult the
+ *     parent (getParent()).  Aggregation closes it again: one result per parent,
+ *     including parents none of whose elements survive.
+ *   - Section 2.1: the computation is a linear pipeline of nodes joined by
+ *     fixed-size queues; each input makes a node emit 0..k outputs, k known a
+ *     priori per node (Section 3.2 uses it to decide fireability).
+ *   - Section 2.2: one pipeline instance per SIMD processor; processors compete for
+ *     the common input with atomics; a node consumes ensembles of up to W items.
+ *   - Section 3: region boundaries travel as signals on a separate queue per edge,
+ *     synchronised with the data by credits (Lemma 1: precise delivery), and no
+ *     ensemble mixes items from both sides of a signal (Section 3.3).  The
+ *     alternative of Section 2.3 / Section 5 tags every item with its region instead.
+ *
+ * Conventions (every entry point):
+ *   - returns rs_status; nothing else crosses the ABI on failure;
+ *   - pointers named "device" must be device memory of the current CUDA device,
+ *     owned by the caller and kept alive until the work enqueued on the given CUDA
+ *     stream has finished (the same rule as cudaMemcpyAsync);
+ *   - the library allocates no device memory: scratch space is a caller-owned
+ *     workspace sized by rs_workspace_size();
+ *   - a pipeline object is not thread-safe; use one per host thread;
+ *   - CUDA streams are passed as rs_cuda_stream (the same handle as cudaStream_t);
+ *     NULL means the legacy default stream.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rs_cuda_stream;
+typedef struct rs_pipeline rs_pipeline;
+
+typedef enum {
+    RS_OK = 0,
+    RS_ERR_INVALID = 1,     /* bad argument, stage list, option or stream description */
+    RS_ERR_NOMEM = 2,       /* host allocation failed                                 */
+    RS_ERR_CUDA = 3,        /* a CUDA runtime call failed (see rs_last_cuda_error)    */
+    RS_ERR_NOT_READY = 4,   /* nothing submitted / not captured yet                   */
+    RS_ERR_STALL = 5,       /* a device loop ran out of its iteration budget          */
+    RS_ERR_CAPACITY = 6,    /* workspace too small, or a size beyond a stated limit   */
+    RS_ERR_STATE = 7,       /* call out of order (e.g. submit while a graph is live)  */
+    RS_ERR_DEVICE_INPUT = 8 /* the device found inconsistent input (offsets, bounds)  */
+} rs_status;
+
+/* ---- stages (Section 2.1 nodes; Section 4 enumeration / aggregation) ---------- */
+
+typedef enum {
+    RS_ENUM_HASH = 1,   /* enumerate: element i of parent r is hash32(p_r, i)             */
+    RS_ENUM_LOAD = 2,   /* enumerate: element i of parent r is elements[off_r + i]        */
+    RS_FILTER = 3,      /* 0 or 1 output per input                                        */
+    RS_MAP = 4,         /* exactly 1 output per input                                     */
+    RS_EXPAND = 5,      /* 0..max_fanout outputs per input                                */
+    RS_AGGREGATE = 6    /* per-region count / sum / min of the surviving values           */
+} rs_stage_kind;
+
+/* Operations.  hash32(a, b) = fmix32(a XOR fmix32(b XOR 0x9E3779B9)) where fmix32 is
+ * the MurmurHash3 32-bit finalizer; all arithmetic is modulo 2^32.  t_r is the
+ * parent's context word (ctx[r], 0 when no ctx array is given) and p_r its id. */
+typedef enum {
+    RS_OP_NONE = 0,
+    RS_OP_MOD_EQ = 1,       /* FILTER: keep x mod params[0] == params[1]  (params[0] > 0) */
+    RS_OP_HASH_CTX_LT = 2,  /* FILTER: keep (hash32(x, params[0]) XOR t_r) < params[1]    */
+    RS_OP_WEIGHT_LT = 3,    /* FILTER: keep hash32(x, params[0]) < hash32(p_r, params[0]) */
+    RS_OP_MUL_ADD = 4,      /* MAP:    x <- params[0] * x + params[1]                     */
+    RS_OP_HASH_FANOUT = 5   /* EXPAND: n = hash32(x, params[0]) mod (max_fanout + 1)
+                               outputs hash32(x, params[0] + 1 + j), j = 0..n-1           */
+} rs_op;
+
+typedef struct {
+    uint32_t kind;          /* rs_stage_kind                                    */
+    uint32_t op;            /* rs_op (RS_OP_NONE for enumerate / aggregate)     */
+    uint32_t max_fanout;    /* a-priori maximum outputs per input (Section 3.2) */
+    uint32_t params[4];
+} rs_stage_desc;
+
+#define RS_MAX_STAGES 6     /* enumerate + up to 4 element stages + aggregate */
+
+/* ---- options ----------------------------------------------------------------- */
+
+typedef enum {
+    RS_STRATEGY_SIGNAL = 0, /* signal-delimited ensembles: Begin/End signals with credits
+                               (Sections 3-4); ensembles never cross a region boundary   */
+    RS_STRATEGY_TAG = 1,    /* per-item region tags (Section 2.3 / Section 5): ensembles
+                               stay full across region boundaries                        */
+    RS_STRATEGY_AUTO = 2    /* pick by mean region length at run time (see rs_autotune)  */
+} rs_strategy;
+
+typedef struct {
+    uint32_t ensemble_width;    /* W, lanes per ensemble; 32 (one warp = one SIMD processor) */
+    uint32_t queue_capacity;    /* data-queue slots per edge; power of two,
+                                   >= W * (max fan-out + 1) so a blocked node always leaves
+                                   room for one full ensemble downstream; 0 = the smallest
+                                   legal power of two >= 64                                  */
+    uint32_t signal_capacity;   /* signal-queue slots per edge; power of two >= 4; 0 = 32     */
+    uint32_t strategy;          /* rs_strategy                                                 */
+    uint32_t regions_per_unit;  /* parents claimed per atomic step, <= 256; 0 = from the mean
+                                   region length (about 2048 elements per claim)              */
+    uint32_t tile_elements;     /* elements per bulk-copy tile for RS_ENUM_LOAD, a power of
+                                   two in 64..4096; 0 = 256                                   */
+    uint32_t tiles_in_flight;   /* staging tiles per processor, 2 or 4; 0 = 4                 */
+    uint32_t warps_per_block;   /* processors per CTA, 1..16; 0 = 4                           */
+    uint32_t grid;              /* CTAs; 0 = a persistent grid (SMs x resident CTAs per SM)   */
+    uint32_t reserved;
+    uint64_t device_budget;     /* scheduler sweeps allowed per claimed unit before the device
+                                   reports RS_ERR_STALL; 0 = 2^22                            */
+} rs_pipeline_opts;
+
+/* Fill *opts with the defaults above (strategy = RS_STRATEGY_TAG). */
+rs_status rs_default_opts(rs_pipeline_opts *opts);
+
+/* Create a pipeline from a stage list: stages[0] is RS_ENUM_HASH or RS_ENUM_LOAD,
+ * stages[n-1] is RS_AGGREGATE, the ones between are FILTER / MAP / EXPAND.
+ * Checks (RS_ERR_INVALID): 2 <= n <= RS_MAX_STAGES; kinds/ops/params legal; FILTER
+ * and MAP have max_fanout 1, EXPAND 1..8; the queue capacity holds one ensemble's
+ * worst-case output (Section 3.2).  No CUDA call is made. */
+rs_status rs_pipeline_create(const rs_stage_desc *stages, uint32_t n_stages,
+                             const rs_pipeline_opts *opts, rs_pipeline **out);
+rs_status rs_pipeline_destroy(rs_pipeline *p);
+/* Replace the options of an existing pipeline (same checks as create). */
+rs_status rs_pipeline_set_opts(rs_pipeline *p, const rs_pipeline_opts *opts);
+rs_status rs_pipeline_get_opts(const rs_pipeline *p, rs_pipeline_opts *opts);
+
+/* ---- streams (Section 4 composite objects) ------------------------------------- */
+
+typedef struct {
+    uint64_t n_regions;             /* R, < 2^32                                             */
+    const uint32_t *parents;        /* device, R ids p_r; NULL means p_r = r                 */
+    const uint32_t *region_len;     /* device, R lengths L_r; or NULL when offsets are given */
+    const uint32_t *region_offsets; /* device, R+1 non-decreasing CSR offsets (element index
+                                       of each parent's first element); NULL = from lengths */
+    const uint32_t *elements;       /* device, element array for RS_ENUM_LOAD, else NULL     */
+    uint64_t n_elements;            /* entries in `elements` (bounds check), < 2^32          */
+    const uint32_t *ctx;            /* device, R context words t_r, or NULL (t_r = 0)        */
+    uint32_t *out_count;            /* device, R; count of survivors per region (or NULL)    */
+    uint64_t *out_sum;              /* device, R; sum of survivors per region (or NULL)      */
+    uint32_t *out_min;              /* device, R; min survivor, 0xFFFFFFFF if none (or NULL) */
+    uint64_t total_elements_hint;   /* sum of L_r if the caller knows it, else 0; only used to
+                                       size work units (regions_per_unit = 0)               */
+} rs_stream_desc;
+
+/* Register a stream with the pipeline; it is processed by every later rs_run until
+ * rs_clear_streams.  Only pointers are recorded; nothing is read now.  Empty streams
+ * (R = 0) are accepted.  *stream_id is the index used by rs_fetch_region_results. */
+rs_status rs_stream_submit(rs_pipeline *p, const rs_stream_desc *s, uint64_t *stream_id);
+rs_status rs_clear_streams(rs_pipeline *p);
+
+/* Bytes of caller-owned device workspace rs_run needs for the streams submitted so
+ * far (work cursor, look-back words, stream table, counters, status word). */
+rs_status rs_workspace_size(const rs_pipeline *p, uint64_t *bytes);
+
+/* Enqueue one pass over every submitted stream on `stream`: one persistent kernel
+ * launch (plus a memset of the workspace header).  Asynchronous; results land in
+ * each stream's out_* arrays.  RS_ERR_CAPACITY if workspace_bytes is too small,
+ * RS_ERR_NOT_READY if nothing is submitted, RS_ERR_CUDA on a launch failure. */
+rs_status rs_run(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream);
+
+typedef struct {
+    uint32_t *count;    /* destination (host or device), R entries, or NULL */
+    uint64_t *sum;
+    uint32_t *min;
+} rs_region_results;
+
+/* Enqueue copies of stream `stream_id`'s per-region results into dst (any memory
+ * cudaMemcpyAsync accepts).  Asynchronous like rs_run. */
+rs_status rs_fetch_region_results(rs_pipeline *p, uint64_t stream_id, const rs_region_results *dst,
+                                  rs_cuda_stream stream);
+
+/* ---- statistics and device status ---------------------------------------------- */
+
+typedef struct {
+    uint32_t device_status;            /* bit 0 stall, 1 look-back timeout, 2 copy timeout,
+                                          3 bad offsets/bounds, 4 internal queue overflow   */
+    uint32_t n_nodes;
+    uint64_t units;                    /* work units claimed                                */
+    uint64_t ensembles[RS_MAX_STAGES]; /* ensembles fired per node (node 0 = enumerate)     */
+    uint64_t items[RS_MAX_STAGES];     /* items consumed per node (active lanes)            */
+    uint64_t signals[RS_MAX_STAGES];   /* signals consumed per node                         */
+    uint64_t firings[RS_MAX_STAGES];   /* scheduler firings per node                        */
+} rs_stats;
+
+/* Synchronise `stream`, read the workspace counters of the last rs_run and return
+ * RS_ERR_STALL / RS_ERR_DEVICE_INPUT if the device flagged a problem (stats filled
+ * either way).  Active-lane fraction of node i = items[i] / (W * ensembles[i]). */
+rs_status rs_get_stats(rs_pipeline *p, const void *workspace, rs_cuda_stream stream, rs_stats *out);
+
+/* ---- batching in a CUDA graph (many streams, one launch, replayed) ------------- */
+
+/* Capture rs_run for the submitted streams into a CUDA graph owned by the pipeline. */
+rs_status rs_graph_capture(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream);
+/* Replay the captured graph on `stream`. */
+rs_status rs_graph_launch(rs_pipeline *p, rs_cuda_stream stream);
+rs_status rs_graph_release(rs_pipeline *p);
+
+/* ---- autotuning (Section 5: choose per workload, from measurements) ------------ */
+
+/* Time candidate configurations (strategy x regions_per_unit x queue capacity x
+ * warps_per_block) on the submitted streams with CUDA events, `trials` timed runs
+ * each after one warm-up, keep the fastest in the pipeline and return it in *best
+ * (and its mean milliseconds in *best_ms).  Overwrites the streams' outputs. */
+rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream,
+                      uint32_t trials, rs_pipeline_opts *best, float *best_ms);
+
+/* ---- misc ---------------------------------------------------------------------- */
+
+const char *rs_status_string(rs_status s);
+/* Last CUDA error code seen by the library on this thread (0 if none). */
+int rs_last_cuda_error(void);
+/* Library version, for the binding's load check. */
+uint32_t rs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RS_H */

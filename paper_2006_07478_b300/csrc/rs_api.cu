@@ -1,0 +1,738 @@
+// rs_api.cu -- host side of the C ABI declared in include/rs.h.
+//
+// Validates stage lists and streams, sizes the caller's workspace, lays out each
+// processor's shared memory, picks the persistent grid, launches the kernel of
+// rs_kernel.cu, reads counters back, captures runs into CUDA graphs and times
+// candidate configurations for the autotuner (Section 5: the strategy should be
+// chosen from measurements of the workload).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "rs_internal.h"
+
+#define RS_VERSION 1u
+
+static thread_local int g_last_cuda = 0;
+
+static rs_status cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return RS_ERR_CUDA;
+}
+
+struct rs_pipeline {
+    rs_stage_desc stages[RS_MAX_STAGES];
+    uint32_t n_stages;
+    rs_pipeline_opts opts;
+    std::vector<rs_stream_desc> streams;
+    std::vector<uint32_t> stream_K;
+    // pinned copy of the device stream table
+    DevStream *table_host = nullptr;
+    size_t table_cap = 0;
+    bool table_dirty = true;
+    cudaEvent_t upload_done = nullptr;
+    bool upload_pending = false;
+    // graph
+    cudaGraphExec_t graph = nullptr;
+    // device facts
+    int n_sm = 0;
+};
+
+static uint32_t host_fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+static bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+static uint32_t max_fanout_of(const rs_stage_desc *st, uint32_t n)
+{
+    uint32_t k = 1;
+    for (uint32_t i = 1; i + 1 < n; ++i)
+        if (st[i].max_fanout > k) k = st[i].max_fanout;
+    return k;
+}
+
+static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
+{
+    if (o->ensemble_width == 0) o->ensemble_width = RS_W;
+    if (o->queue_capacity == 0) {
+        uint32_t c = 64;
+        while (c < RS_W * (fan + 1)) c <<= 1;
+        o->queue_capacity = c;
+    }
+    if (o->signal_capacity == 0) o->signal_capacity = 32;
+    if (o->tile_elements == 0) o->tile_elements = 256;
+    if (o->tiles_in_flight == 0) o->tiles_in_flight = 4;
+    if (o->warps_per_block == 0) o->warps_per_block = 4;
+    if (o->device_budget == 0) o->device_budget = 1ull << 22;
+    return RS_OK;
+}
+
+static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
+{
+    if (o->ensemble_width != RS_W) return RS_ERR_INVALID;
+    if (!is_pow2(o->queue_capacity) || o->queue_capacity < RS_W * (fan + 1) || o->queue_capacity > 4096)
+        return RS_ERR_INVALID;
+    if (!is_pow2(o->signal_capacity) || o->signal_capacity < 4 || o->signal_capacity > 1024)
+        return RS_ERR_INVALID;
+    if (o->strategy > RS_STRATEGY_AUTO) return RS_ERR_INVALID;
+    if (o->regions_per_unit > RS_MAX_K) return RS_ERR_INVALID;
+    if (!is_pow2(o->tile_elements) || o->tile_elements < 64 || o->tile_elements > 4096) return RS_ERR_INVALID;
+    if (o->tiles_in_flight != 2 && o->tiles_in_flight != 4) return RS_ERR_INVALID;
+    if (o->warps_per_block < 1 || o->warps_per_block > 16) return RS_ERR_INVALID;
+    return RS_OK;
+}
+
+static rs_status check_stages(const rs_stage_desc *st, uint32_t n)
+{
+    if (!st || n < 2 || n > RS_MAX_STAGES) return RS_ERR_INVALID;
+    if (st[0].kind != RS_ENUM_HASH && st[0].kind != RS_ENUM_LOAD) return RS_ERR_INVALID;
+    if (st[n - 1].kind != RS_AGGREGATE) return RS_ERR_INVALID;
+    for (uint32_t i = 1; i + 1 < n; ++i) {
+        const rs_stage_desc &s = st[i];
+        switch (s.kind) {
+        case RS_FILTER:
+            if (s.max_fanout != 1) return RS_ERR_INVALID;
+            if (s.op == RS_OP_MOD_EQ) {
+                if (s.params[0] == 0) return RS_ERR_INVALID;
+            } else if (s.op != RS_OP_HASH_CTX_LT && s.op != RS_OP_WEIGHT_LT) {
+                return RS_ERR_INVALID;
+            }
+            break;
+        case RS_MAP:
+            if (s.max_fanout != 1 || s.op != RS_OP_MUL_ADD) return RS_ERR_INVALID;
+            break;
+        case RS_EXPAND:
+            if (s.op != RS_OP_HASH_FANOUT || s.max_fanout < 1 || s.max_fanout > 8) return RS_ERR_INVALID;
+            break;
+        default:
+            return RS_ERR_INVALID;
+        }
+    }
+    return RS_OK;
+}
+
+static DevStage to_dev(const rs_stage_desc &s)
+{
+    DevStage d;
+    memset(&d, 0, sizeof d);
+    d.fanout = s.max_fanout ? s.max_fanout : 1;
+    d.p0 = s.params[0];
+    d.p1 = s.params[1];
+    d.c0 = host_fmix32(s.params[0] ^ RS_GOLD);
+    switch (s.kind) {
+    case RS_ENUM_HASH: d.op = D_ENUM_HASH; break;
+    case RS_ENUM_LOAD: d.op = D_ENUM_LOAD; break;
+    case RS_AGGREGATE: d.op = D_AGG; break;
+    case RS_MAP: d.op = D_MAP_MULADD; break;
+    case RS_EXPAND: d.op = D_EXPAND; break;
+    case RS_FILTER:
+        if (s.op == RS_OP_MOD_EQ) {
+            if (is_pow2(s.params[0])) {
+                d.op = D_FILT_MASK;
+                d.p0 = s.params[0] - 1u;
+                // x mod m == c with c >= m can never hold; keep the comparison exact
+                d.p1 = s.params[1] < s.params[0] ? s.params[1] : 0xFFFFFFFFu;
+            } else {
+                d.op = D_FILT_MOD;
+            }
+        } else if (s.op == RS_OP_HASH_CTX_LT) {
+            d.op = D_FILT_HASH_CTX;
+        } else {
+            d.op = D_FILT_WEIGHT;
+        }
+        break;
+    }
+    return d;
+}
+
+extern "C" {
+
+const char *rs_status_string(rs_status s)
+{
+    switch (s) {
+    case RS_OK: return "ok";
+    case RS_ERR_INVALID: return "invalid argument";
+    case RS_ERR_NOMEM: return "host out of memory";
+    case RS_ERR_CUDA: return "CUDA error";
+    case RS_ERR_NOT_READY: return "not ready";
+    case RS_ERR_STALL: return "device iteration budget exhausted";
+    case RS_ERR_CAPACITY: return "capacity exceeded";
+    case RS_ERR_STATE: return "call out of order";
+    case RS_ERR_DEVICE_INPUT: return "device found inconsistent input";
+    }
+    return "unknown status";
+}
+
+int rs_last_cuda_error(void) { return g_last_cuda; }
+
+uint32_t rs_version(void) { return RS_VERSION; }
+
+rs_status rs_default_opts(rs_pipeline_opts *o)
+{
+    if (!o) return RS_ERR_INVALID;
+    memset(o, 0, sizeof *o);
+    o->strategy = RS_STRATEGY_TAG;
+    fill_defaults(o, 1);
+    return RS_OK;
+}
+
+rs_status rs_pipeline_create(const rs_stage_desc *stages, uint32_t n_stages, const rs_pipeline_opts *opts,
+                             rs_pipeline **out)
+{
+    if (!out) return RS_ERR_INVALID;
+    *out = nullptr;
+    rs_status st = check_stages(stages, n_stages);
+    if (st != RS_OK) return st;
+    rs_pipeline_opts o;
+    if (opts) o = *opts; else { memset(&o, 0, sizeof o); o.strategy = RS_STRATEGY_TAG; }
+    uint32_t fan = max_fanout_of(stages, n_stages);
+    fill_defaults(&o, fan);
+    st = check_opts(&o, fan);
+    if (st != RS_OK) return st;
+    rs_pipeline *p = new (std::nothrow) rs_pipeline();
+    if (!p) return RS_ERR_NOMEM;
+    memcpy(p->stages, stages, n_stages * sizeof(rs_stage_desc));
+    p->n_stages = n_stages;
+    p->opts = o;
+    *out = p;
+    return RS_OK;
+}
+
+rs_status rs_pipeline_destroy(rs_pipeline *p)
+{
+    if (!p) return RS_ERR_INVALID;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->upload_done) {
+        if (p->upload_pending) cudaEventSynchronize(p->upload_done);
+        cudaEventDestroy(p->upload_done);
+    }
+    if (p->table_host) cudaFreeHost(p->table_host);
+    delete p;
+    return RS_OK;
+}
+
+rs_status rs_pipeline_set_opts(rs_pipeline *p, const rs_pipeline_opts *opts)
+{
+    if (!p || !opts) return RS_ERR_INVALID;
+    rs_pipeline_opts o = *opts;
+    uint32_t fan = max_fanout_of(p->stages, p->n_stages);
+    fill_defaults(&o, fan);
+    rs_status st = check_opts(&o, fan);
+    if (st != RS_OK) return st;
+    p->opts = o;
+    p->table_dirty = true;   // regions_per_unit may change the unit split
+    return RS_OK;
+}
+
+rs_status rs_pipeline_get_opts(const rs_pipeline *p, rs_pipeline_opts *opts)
+{
+    if (!p || !opts) return RS_ERR_INVALID;
+    *opts = p->opts;
+    return RS_OK;
+}
+
+rs_status rs_stream_submit(rs_pipeline *p, const rs_stream_desc *s, uint64_t *stream_id)
+{
+    if (!p || !s) return RS_ERR_INVALID;
+    if (p->graph) return RS_ERR_STATE;
+    if (s->n_regions >= (1ull << 32)) return RS_ERR_CAPACITY;
+    if (s->n_regions > 0) {
+        if (!s->region_len && !s->region_offsets) return RS_ERR_INVALID;
+        if (p->stages[0].kind == RS_ENUM_LOAD && (!s->elements || s->n_elements == 0)) return RS_ERR_INVALID;
+        if (s->n_elements >= (1ull << 32)) return RS_ERR_CAPACITY;
+        for (uint32_t i = 1; i + 1 < p->n_stages; ++i)
+            if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_HASH_CTX_LT) {
+                // ctx may be NULL (t_r = 0)
+            }
+    }
+    try {
+        p->streams.push_back(*s);
+    } catch (...) {
+        return RS_ERR_NOMEM;
+    }
+    p->table_dirty = true;
+    if (stream_id) *stream_id = p->streams.size() - 1;
+    return RS_OK;
+}
+
+rs_status rs_clear_streams(rs_pipeline *p)
+{
+    if (!p) return RS_ERR_INVALID;
+    if (p->graph) return RS_ERR_STATE;
+    p->streams.clear();
+    p->table_dirty = true;
+    return RS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+
+static uint32_t choose_K(const rs_pipeline *p, const rs_stream_desc &s)
+{
+    if (p->opts.regions_per_unit) return p->opts.regions_per_unit;
+    if (s.n_regions == 0) return 1;
+    uint64_t tot = s.total_elements_hint;
+    if (!tot && p->stages[0].kind == RS_ENUM_LOAD) tot = s.n_elements;
+    double mean = tot ? (double)tot / (double)s.n_regions : 32.0;
+    double want = 2048.0 / (mean > 1e-9 ? mean : 1e-9);
+    uint32_t K = 1;
+    while (K * 2 <= want && K * 2 <= RS_MAX_K) K *= 2;
+    return K;
+}
+
+struct Plan {
+    uint64_t total_units;
+    uint32_t Kmax;
+    size_t hdr_bytes, lb_off, lb_bytes, table_off, table_bytes, total;
+};
+
+static Plan make_plan(const rs_pipeline *p)
+{
+    Plan pl;
+    memset(&pl, 0, sizeof pl);
+    pl.Kmax = 1;
+    for (const auto &s : p->streams) {
+        uint32_t K = choose_K(p, s);
+        if (K > pl.Kmax) pl.Kmax = K;
+        pl.total_units += (s.n_regions + K - 1) / K;
+    }
+    pl.hdr_bytes = (sizeof(WsHeader) + 255) & ~(size_t)255;
+    pl.lb_off = pl.hdr_bytes;
+    pl.lb_bytes = ((pl.total_units * 8) + 255) & ~(size_t)255;
+    pl.table_off = pl.lb_off + pl.lb_bytes;
+    pl.table_bytes = ((p->streams.size() * sizeof(DevStream)) + 255) & ~(size_t)255;
+    pl.total = pl.table_off + pl.table_bytes;
+    return pl;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
+
+static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax, bool any_load, bool need_ctx,
+                              bool need_par)
+{
+    const rs_pipeline_opts &o = p->opts;
+    SmemLayout L;
+    memset(&L, 0, sizeof L);
+    size_t off = 0;
+    L.o_mbar = (uint32_t)off;
+    off += any_load ? 8 * o.tiles_in_flight : 0;
+    off = align_up(off, 16);
+    L.o_scr = (uint32_t)off;
+    off += 32 * 4;
+    off = align_up(off, 128);
+    L.o_tiles = (uint32_t)off;
+    off += any_load ? (size_t)o.tiles_in_flight * o.tile_elements * 4 : 0;
+    L.o_rs = (uint32_t)off;
+    off += (size_t)Kmax * 8;
+    L.o_off = (uint32_t)off;
+    off += (size_t)(Kmax + 1) * 4;
+    off = align_up(off, 16);
+    L.o_ctx = (uint32_t)off;
+    off += need_ctx ? (size_t)Kmax * 4 : 0;
+    L.o_par = (uint32_t)off;
+    off += need_par ? (size_t)Kmax * 4 : 0;
+    L.o_rc = (uint32_t)off;
+    off += (size_t)Kmax * 4;
+    L.o_rm = (uint32_t)off;
+    off += (size_t)Kmax * 4;
+    off = align_up(off, 16);
+    const uint32_t ne = p->n_stages - 1;
+    L.o_qv = (uint32_t)off;
+    off += (size_t)ne * o.queue_capacity * 4;
+    L.o_qt = (uint32_t)off;
+    off += strategy == RS_STRATEGY_TAG ? (size_t)ne * o.queue_capacity * 4 : 0;
+    L.o_sq = (uint32_t)off;
+    off += strategy == RS_STRATEGY_SIGNAL ? (size_t)ne * o.signal_capacity * 8 : 0;
+    L.per_warp = (uint32_t)align_up(off, 128);
+    return L;
+}
+
+static int resolve_strategy(const rs_pipeline *p)
+{
+    if (p->opts.strategy != RS_STRATEGY_AUTO) return (int)p->opts.strategy;
+    // mean region length across the submitted streams; long regions favour signals
+    uint64_t R = 0, N = 0;
+    for (const auto &s : p->streams) {
+        R += s.n_regions;
+        uint64_t t = s.total_elements_hint;
+        if (!t && p->stages[0].kind == RS_ENUM_LOAD) t = s.n_elements;
+        N += t;
+    }
+    double mean = R ? (double)N / (double)R : 0.0;
+    return mean >= 1024.0 ? RS_STRATEGY_SIGNAL : RS_STRATEGY_TAG;
+}
+
+extern "C" rs_status rs_workspace_size(const rs_pipeline *p, uint64_t *bytes)
+{
+    if (!p || !bytes) return RS_ERR_INVALID;
+    *bytes = make_plan(p).total;
+    return RS_OK;
+}
+
+struct Launch {
+    KParams P;
+    Plan pl;
+    int grid, block;
+    size_t smem;
+};
+
+// Host-only preparation: stream table in pinned memory, kernel parameters, grid.
+// Makes no stream-ordered call, so it may run before a stream capture begins.
+static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *out)
+{
+    if (!p || !ws) return RS_ERR_INVALID;
+    if (p->streams.empty()) return RS_ERR_NOT_READY;
+    Launch &Lc = *out;
+    Lc.pl = make_plan(p);
+    const Plan &pl = Lc.pl;
+    if (ws_bytes < pl.total) return RS_ERR_CAPACITY;
+    if (((uintptr_t)ws & 255) != 0) return RS_ERR_INVALID;
+    if (pl.total_units >= (1ull << 31)) return RS_ERR_CAPACITY;
+    cudaError_t e;
+    if (!p->n_sm) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    const int strategy = resolve_strategy(p);
+    const rs_pipeline_opts &o = p->opts;
+    unsigned char *wsb = (unsigned char *)ws;
+
+    // ---- stream table (pinned host copy, uploaded by every run) ----
+    const size_t ns = p->streams.size();
+    if (p->table_dirty || !p->table_host) {
+        if (p->upload_pending) {
+            if ((e = cudaEventSynchronize(p->upload_done)) != cudaSuccess) return cuda_fail(e);
+            p->upload_pending = false;
+        }
+        if (p->table_cap < ns) {
+            if (p->table_host) cudaFreeHost(p->table_host);
+            p->table_host = nullptr;
+            p->table_cap = 0;
+            size_t cap = ns < 16 ? 16 : ns;
+            if ((e = cudaMallocHost((void **)&p->table_host, cap * sizeof(DevStream))) != cudaSuccess)
+                return cuda_fail(e);
+            p->table_cap = cap;
+        }
+        uint32_t base = 0;
+        for (size_t i = 0; i < ns; ++i) {
+            const rs_stream_desc &s = p->streams[i];
+            DevStream &d = p->table_host[i];
+            memset(&d, 0, sizeof d);
+            uint32_t K = choose_K(p, s);
+            d.parents = s.parents;
+            d.len = s.region_len;
+            d.offsets = s.region_offsets;
+            d.elements = s.elements;
+            d.ctx = s.ctx;
+            d.out_count = s.out_count;
+            d.out_sum = (unsigned long long *)s.out_sum;
+            d.out_min = s.out_min;
+            d.n_elements = s.n_elements;
+            d.R = (uint32_t)s.n_regions;
+            d.K = K;
+            d.n_units = (uint32_t)((s.n_regions + K - 1) / K);
+            d.unit_base = base;
+            d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
+            base += d.n_units;
+        }
+        p->table_dirty = false;
+    }
+
+    // ---- kernel parameters ----
+    KParams &P = Lc.P;
+    memset(&P, 0, sizeof P);
+    bool need_ctx = false, need_par = p->stages[0].kind == RS_ENUM_HASH;
+    for (uint32_t i = 0; i < p->n_stages; ++i) {
+        P.st[i] = to_dev(p->stages[i]);
+        if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_HASH_CTX_LT) need_ctx = true;
+        if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_WEIGHT_LT) need_par = true;
+    }
+    P.n_stages = (int)p->n_stages;
+    P.strategy = strategy;
+    P.n_streams = (uint32_t)ns;
+    P.total_units = (uint32_t)pl.total_units;
+    P.streams = (const DevStream *)(wsb + pl.table_off);
+    P.hdr = (WsHeader *)wsb;
+    P.lookback = (unsigned long long *)(wsb + pl.lb_off);
+    P.C = o.queue_capacity;
+    P.SC = o.signal_capacity;
+    P.TE = o.tile_elements;
+    P.NT = o.tiles_in_flight;
+    P.need_ctx = need_ctx;
+    P.need_par = need_par;
+    bool wc = false, wsum = false, wm = false;
+    for (const auto &s : p->streams) {
+        wc |= s.out_count != nullptr;
+        wsum |= s.out_sum != nullptr;
+        wm |= s.out_min != nullptr;
+    }
+    // every non-empty stream must provide each output any stream asks for
+    for (const auto &s : p->streams) {
+        if (s.n_regions == 0) continue;
+        if ((wc && !s.out_count) || (wsum && !s.out_sum) || (wm && !s.out_min)) return RS_ERR_INVALID;
+    }
+    P.want_count = wc;
+    P.want_sum = wsum;
+    P.want_min = wm;
+    P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
+    P.budget = o.device_budget;
+    P.spin_limit = 2000000000ull;   // 2 s on the global timer
+    P.L = make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par);
+
+    Lc.block = (int)o.warps_per_block * 32;
+    Lc.smem = (size_t)P.L.per_warp * o.warps_per_block;
+    Lc.grid = (int)o.grid;
+    if (pl.total_units == 0) return RS_OK;
+    if (Lc.grid == 0) {
+        int bps = 0;
+        int ce = rs_kernel_occupancy(strategy, Lc.block, Lc.smem, &bps);
+        if (ce != 0) return cuda_fail((cudaError_t)ce);
+        if (bps == 0) return RS_ERR_CAPACITY;
+        Lc.grid = bps * p->n_sm;
+        uint64_t warps = (uint64_t)Lc.grid * o.warps_per_block;   // no more processors than units
+        if (warps > pl.total_units) {
+            Lc.grid = (int)((pl.total_units + o.warps_per_block - 1) / o.warps_per_block);
+            if (Lc.grid < 1) Lc.grid = 1;
+        }
+    } else {
+        int ce = rs_kernel_max_smem_optin(Lc.smem);
+        (void)ce;
+    }
+    return RS_OK;
+}
+
+// Stream-ordered part: workspace reset, table upload, kernel launch.
+static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_t stream, bool capturing)
+{
+    if (Lc.pl.total_units == 0) return RS_OK;   // only empty streams: nothing to launch
+    cudaError_t e;
+    unsigned char *wsb = (unsigned char *)ws;
+    if ((e = cudaMemsetAsync(wsb, 0, Lc.pl.table_off, stream)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(wsb + Lc.pl.table_off, p->table_host, p->streams.size() * sizeof(DevStream),
+                             cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail(e);
+    if (!capturing) {
+        if (!p->upload_done) {
+            if ((e = cudaEventCreateWithFlags(&p->upload_done, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e);
+        }
+        if ((e = cudaEventRecord(p->upload_done, stream)) != cudaSuccess) return cuda_fail(e);
+        p->upload_pending = true;
+    }
+    int le = rs_launch_kernel(Lc.P, Lc.grid, Lc.block, Lc.smem, (void *)stream);
+    if (le != 0) return cuda_fail((cudaError_t)le);
+    return RS_OK;
+}
+
+static rs_status run_impl(rs_pipeline *p, void *ws, uint64_t ws_bytes, cudaStream_t stream)
+{
+    Launch Lc;
+    rs_status st = prepare(p, ws, ws_bytes, &Lc);
+    if (st != RS_OK) return st;
+    return enqueue(p, ws, Lc, stream, false);
+}
+
+extern "C" {
+
+rs_status rs_run(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream)
+{
+    return run_impl(p, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+rs_status rs_fetch_region_results(rs_pipeline *p, uint64_t stream_id, const rs_region_results *dst,
+                                  rs_cuda_stream stream)
+{
+    if (!p || !dst || stream_id >= p->streams.size()) return RS_ERR_INVALID;
+    const rs_stream_desc &s = p->streams[stream_id];
+    const size_t R = s.n_regions;
+    if (R == 0) return RS_OK;
+    cudaError_t e;
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (dst->count) {
+        if (!s.out_count) return RS_ERR_INVALID;
+        if (dst->count != s.out_count &&
+            (e = cudaMemcpyAsync(dst->count, s.out_count, R * 4, cudaMemcpyDefault, cs)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    if (dst->sum) {
+        if (!s.out_sum) return RS_ERR_INVALID;
+        if (dst->sum != s.out_sum &&
+            (e = cudaMemcpyAsync(dst->sum, s.out_sum, R * 8, cudaMemcpyDefault, cs)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    if (dst->min) {
+        if (!s.out_min) return RS_ERR_INVALID;
+        if (dst->min != s.out_min &&
+            (e = cudaMemcpyAsync(dst->min, s.out_min, R * 4, cudaMemcpyDefault, cs)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    return RS_OK;
+}
+
+rs_status rs_get_stats(rs_pipeline *p, const void *workspace, rs_cuda_stream stream, rs_stats *out)
+{
+    if (!p || !workspace || !out) return RS_ERR_INVALID;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e);
+    WsHeader h;
+    if ((e = cudaMemcpy(&h, workspace, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
+    memset(out, 0, sizeof *out);
+    out->device_status = h.status;
+    out->n_nodes = p->n_stages;
+    out->units = h.units;
+    for (uint32_t i = 0; i < p->n_stages; ++i) {
+        out->ensembles[i] = h.counters[4 * i + 0];
+        out->items[i] = h.counters[4 * i + 1];
+        out->signals[i] = h.counters[4 * i + 2];
+        out->firings[i] = h.counters[4 * i + 3];
+    }
+    if (h.status & (ST_STALL | ST_LOOKBACK_TIMEOUT | ST_COPY_TIMEOUT | ST_OVERFLOW)) return RS_ERR_STALL;
+    if (h.status & ST_BAD_INPUT) return RS_ERR_DEVICE_INPUT;
+    return RS_OK;
+}
+
+rs_status rs_graph_capture(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream)
+{
+    if (!p || !stream) return RS_ERR_INVALID;
+    if (p->graph) return RS_ERR_STATE;
+    cudaError_t e;
+    // the table upload inside the graph reads the pinned buffer at every replay:
+    // build it now, outside the capture
+    if (p->upload_pending) {
+        if ((e = cudaEventSynchronize(p->upload_done)) != cudaSuccess) return cuda_fail(e);
+        p->upload_pending = false;
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    Launch Lc;
+    rs_status st = prepare(p, workspace, workspace_bytes, &Lc);
+    if (st != RS_OK) return st;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_fail(e);
+    st = enqueue(p, workspace, Lc, cs, true);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    if (st != RS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e);
+    p->graph = ex;
+    return RS_OK;
+}
+
+rs_status rs_graph_launch(rs_pipeline *p, rs_cuda_stream stream)
+{
+    if (!p) return RS_ERR_INVALID;
+    if (!p->graph) return RS_ERR_NOT_READY;
+    cudaError_t e = cudaGraphLaunch(p->graph, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return RS_OK;
+}
+
+rs_status rs_graph_release(rs_pipeline *p)
+{
+    if (!p) return RS_ERR_INVALID;
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    return RS_OK;
+}
+
+rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream,
+                      uint32_t trials, rs_pipeline_opts *best, float *best_ms)
+{
+    if (!p || !workspace) return RS_ERR_INVALID;
+    if (p->graph) return RS_ERR_STATE;
+    if (p->streams.empty()) return RS_ERR_NOT_READY;
+    if (trials == 0) trials = 3;
+    const rs_pipeline_opts base = p->opts;
+    // units sized from the mean (K0) and half / double of it
+    rs_pipeline_opts probe = base;
+    probe.regions_per_unit = 0;
+    p->opts = probe;
+    uint32_t K0 = 1;
+    for (const auto &s : p->streams) {
+        uint32_t k = choose_K(p, s);
+        if (k > K0) K0 = k;
+    }
+    std::vector<rs_pipeline_opts> cand;
+    const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
+    const uint32_t Ks[3] = {K0 > 1 ? K0 / 2 : 1, K0, K0 * 2 <= RS_MAX_K ? K0 * 2 : K0};
+    const uint32_t wpbs[2] = {4, 8};
+    try {
+        for (uint32_t si = 0; si < 2; ++si)
+            for (uint32_t ki = 0; ki < 3; ++ki)
+                for (uint32_t wi = 0; wi < 2; ++wi) {
+                    if (ki > 0 && Ks[ki] == Ks[ki - 1]) continue;
+                    rs_pipeline_opts c = base;
+                    c.strategy = strategies[si];
+                    c.regions_per_unit = Ks[ki];
+                    c.warps_per_block = wpbs[wi];
+                    c.grid = 0;
+                    cand.push_back(c);
+                }
+    } catch (...) {
+        p->opts = base;
+        return RS_ERR_NOMEM;
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&ev0)) != cudaSuccess) { p->opts = base; return cuda_fail(e); }
+    if ((e = cudaEventCreate(&ev1)) != cudaSuccess) { cudaEventDestroy(ev0); p->opts = base; return cuda_fail(e); }
+    float best_t = 1e30f;
+    rs_pipeline_opts best_o = base;
+    rs_status result = RS_OK;
+    for (const auto &c : cand) {
+        p->opts = c;
+        p->table_dirty = true;
+        uint64_t need = make_plan(p).total;
+        if (need > workspace_bytes) continue;
+        rs_status st = run_impl(p, workspace, workspace_bytes, (cudaStream_t)stream);
+        if (st == RS_ERR_CAPACITY) continue;
+        if (st != RS_OK) { result = st; break; }
+        cudaEventRecord(ev0, (cudaStream_t)stream);
+        for (uint32_t t = 0; t < trials && st == RS_OK; ++t)
+            st = run_impl(p, workspace, workspace_bytes, (cudaStream_t)stream);
+        cudaEventRecord(ev1, (cudaStream_t)stream);
+        if (st != RS_OK) { result = st; break; }
+        if ((e = cudaEventSynchronize(ev1)) != cudaSuccess) { result = cuda_fail(e); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        ms /= (float)trials;
+        rs_stats stt;
+        rs_status ss = rs_get_stats(p, workspace, stream, &stt);
+        if (ss != RS_OK) continue;   // a configuration that stalls is never chosen
+        if (ms < best_t) {
+            best_t = ms;
+            best_o = c;
+        }
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    p->opts = best_o;
+    p->table_dirty = true;
+    if (result != RS_OK) return result;
+    if (best) *best = best_o;
+    if (best_ms) *best_ms = best_t;
+    return RS_OK;
+}
+
+}  // extern "C"

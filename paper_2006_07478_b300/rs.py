@@ -1,0 +1,369 @@
+"""ctypes binding of librs (include/rs.h): argument marshalling only.
+
+Every step of the pipeline runs in the CUDA library; this module turns stage
+tuples into rs_stage_desc records, torch CUDA tensors into device pointers and
+the current torch CUDA stream into an rs_cuda_stream.  torch is used for device
+memory and streams only.  There is no CPU path: if librs.so is missing or no GPU
+is present, calls raise.
+
+Stage tuples (the same names the workload module uses):
+    ("enum_hash",)                   element i of parent r = hash32(p_r, i)
+    ("enum_load",)                   element i of parent r = elements[off_r + i]
+    ("filter_mod", m, c)             keep x mod m == c
+    ("filter_hash_ctx", salt, theta) keep (hash32(x, salt) ^ t_r) < theta
+    ("filter_weight_lt", salt)       keep hash32(x, salt) < hash32(p_r, salt)
+    ("map_mul", a, b)                x <- a*x + b mod 2^32
+    ("expand", k, salt)              0..k outputs per input
+    ("aggregate",)                   count / sum / min per region
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+RS_OK, RS_ERR_INVALID, RS_ERR_NOMEM, RS_ERR_CUDA, RS_ERR_NOT_READY = 0, 1, 2, 3, 4
+RS_ERR_STALL, RS_ERR_CAPACITY, RS_ERR_STATE, RS_ERR_DEVICE_INPUT = 5, 6, 7, 8
+RS_ENUM_HASH, RS_ENUM_LOAD, RS_FILTER, RS_MAP, RS_EXPAND, RS_AGGREGATE = 1, 2, 3, 4, 5, 6
+RS_OP_NONE, RS_OP_MOD_EQ, RS_OP_HASH_CTX_LT, RS_OP_WEIGHT_LT, RS_OP_MUL_ADD, RS_OP_HASH_FANOUT = 0, 1, 2, 3, 4, 5
+STRATEGIES = {"signal": 0, "tag": 1, "auto": 2}
+RS_MAX_STAGES = 6
+
+EXPORTS = [
+    "rs_default_opts", "rs_pipeline_create", "rs_pipeline_destroy", "rs_pipeline_set_opts",
+    "rs_pipeline_get_opts", "rs_stream_submit", "rs_clear_streams", "rs_workspace_size", "rs_run",
+    "rs_fetch_region_results", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
+    "rs_graph_release", "rs_autotune", "rs_status_string", "rs_last_cuda_error", "rs_version",
+]
+
+
+class StageDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("op", ctypes.c_uint32), ("max_fanout", ctypes.c_uint32),
+                ("params", ctypes.c_uint32 * 4)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("ensemble_width", ctypes.c_uint32), ("queue_capacity", ctypes.c_uint32),
+                ("signal_capacity", ctypes.c_uint32), ("strategy", ctypes.c_uint32),
+                ("regions_per_unit", ctypes.c_uint32), ("tile_elements", ctypes.c_uint32),
+                ("tiles_in_flight", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
+                ("grid", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("device_budget", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class StreamDesc(ctypes.Structure):
+    _fields_ = [("n_regions", ctypes.c_uint64), ("parents", ctypes.c_void_p), ("region_len", ctypes.c_void_p),
+                ("region_offsets", ctypes.c_void_p), ("elements", ctypes.c_void_p),
+                ("n_elements", ctypes.c_uint64), ("ctx", ctypes.c_void_p), ("out_count", ctypes.c_void_p),
+                ("out_sum", ctypes.c_void_p), ("out_min", ctypes.c_void_p),
+                ("total_elements_hint", ctypes.c_uint64)]
+
+
+class RegionResults(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_void_p), ("sum", ctypes.c_void_p), ("min", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("device_status", ctypes.c_uint32), ("n_nodes", ctypes.c_uint32), ("units", ctypes.c_uint64),
+                ("ensembles", ctypes.c_uint64 * RS_MAX_STAGES), ("items", ctypes.c_uint64 * RS_MAX_STAGES),
+                ("signals", ctypes.c_uint64 * RS_MAX_STAGES), ("firings", ctypes.c_uint64 * RS_MAX_STAGES)]
+
+    def as_dict(self):
+        n = self.n_nodes
+        ens = list(self.ensembles)[:n]
+        items = list(self.items)[:n]
+        return {
+            "device_status": self.device_status, "units": self.units,
+            "ensembles": ens, "items": items,
+            "signals": list(self.signals)[:n], "firings": list(self.firings)[:n],
+            "active_lane_fraction": [(it / (32.0 * e)) if e else 0.0 for it, e in zip(items, ens)],
+        }
+
+
+class RsError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load librs.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"librs.so not found at {_build.LIB}; the CUDA library is required")
+        L = ctypes.CDLL(_build.LIB)
+        P, U32, U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        sig = {
+            "rs_default_opts": ([ctypes.POINTER(Opts)], ctypes.c_int),
+            "rs_pipeline_create": ([ctypes.POINTER(StageDesc), U32, ctypes.POINTER(Opts), ctypes.POINTER(P)],
+                                   ctypes.c_int),
+            "rs_pipeline_destroy": ([P], ctypes.c_int),
+            "rs_pipeline_set_opts": ([P, ctypes.POINTER(Opts)], ctypes.c_int),
+            "rs_pipeline_get_opts": ([P, ctypes.POINTER(Opts)], ctypes.c_int),
+            "rs_stream_submit": ([P, ctypes.POINTER(StreamDesc), ctypes.POINTER(U64)], ctypes.c_int),
+            "rs_clear_streams": ([P], ctypes.c_int),
+            "rs_workspace_size": ([P, ctypes.POINTER(U64)], ctypes.c_int),
+            "rs_run": ([P, P, U64, P], ctypes.c_int),
+            "rs_fetch_region_results": ([P, U64, ctypes.POINTER(RegionResults), P], ctypes.c_int),
+            "rs_get_stats": ([P, P, P, ctypes.POINTER(Stats)], ctypes.c_int),
+            "rs_graph_capture": ([P, P, U64, P], ctypes.c_int),
+            "rs_graph_launch": ([P, P], ctypes.c_int),
+            "rs_graph_release": ([P], ctypes.c_int),
+            "rs_autotune": ([P, P, U64, P, U32, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_float)],
+                            ctypes.c_int),
+            "rs_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "rs_last_cuda_error": ([], ctypes.c_int),
+            "rs_version": ([], U32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def status_string(st: int) -> str:
+    return lib().rs_status_string(int(st)).decode()
+
+
+def check(st: int, what: str):
+    if st != RS_OK:
+        if st == RS_ERR_CUDA:
+            raise RsError(st, f"{what} (cuda error {lib().rs_last_cuda_error()})")
+        raise RsError(st, what)
+
+
+def stage_desc(st) -> StageDesc:
+    name, a = st[0], [int(x) & 0xFFFFFFFF for x in st[1:]]
+    d = StageDesc()
+    d.max_fanout = 1
+    if name == "enum_hash":
+        d.kind = RS_ENUM_HASH
+    elif name == "enum_load":
+        d.kind = RS_ENUM_LOAD
+    elif name == "aggregate":
+        d.kind = RS_AGGREGATE
+    elif name == "filter_mod":
+        d.kind, d.op = RS_FILTER, RS_OP_MOD_EQ
+        d.params[0], d.params[1] = a[0], a[1]
+    elif name == "filter_hash_ctx":
+        d.kind, d.op = RS_FILTER, RS_OP_HASH_CTX_LT
+        d.params[0], d.params[1] = a[0], a[1]
+    elif name == "filter_weight_lt":
+        d.kind, d.op = RS_FILTER, RS_OP_WEIGHT_LT
+        d.params[0] = a[0]
+    elif name == "map_mul":
+        d.kind, d.op = RS_MAP, RS_OP_MUL_ADD
+        d.params[0], d.params[1] = a[0], a[1]
+    elif name == "expand":
+        d.kind, d.op = RS_EXPAND, RS_OP_HASH_FANOUT
+        d.max_fanout = a[0]
+        d.params[0] = a[1]
+    else:
+        raise ValueError(f"unknown stage {name!r}")
+    return d
+
+
+def make_opts(strategy="tag", **kw) -> Opts:
+    o = Opts()
+    check(lib().rs_default_opts(ctypes.byref(o)), "rs_default_opts")
+    o.queue_capacity = 0
+    o.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _cur_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Pipeline:
+    """A stage list bound to options; streams are submitted as torch CUDA tensors."""
+
+    def __init__(self, stages, strategy="tag", **opts):
+        self.stages = list(stages)
+        arr = (StageDesc * len(self.stages))(*[stage_desc(s) for s in self.stages])
+        o = make_opts(strategy, **opts)
+        h = ctypes.c_void_p()
+        check(lib().rs_pipeline_create(arr, len(self.stages), ctypes.byref(o), ctypes.byref(h)),
+              "rs_pipeline_create")
+        self._h = h
+        self._keep = []          # tensors referenced by submitted streams
+        self._ws = None
+        self.streams = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rs_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def opts(self) -> dict:
+        o = Opts()
+        check(lib().rs_pipeline_get_opts(self._h, ctypes.byref(o)), "rs_pipeline_get_opts")
+        return o.as_dict()
+
+    def set_opts(self, strategy=None, **kw):
+        o = Opts()
+        check(lib().rs_pipeline_get_opts(self._h, ctypes.byref(o)), "rs_pipeline_get_opts")
+        if strategy is not None:
+            o.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        for k, v in kw.items():
+            setattr(o, k, int(v))
+        check(lib().rs_pipeline_set_opts(self._h, ctypes.byref(o)), "rs_pipeline_set_opts")
+
+    def submit(self, dev: dict, outputs=("count", "sum", "min")) -> dict:
+        """Register a device stream (dict of torch CUDA tensors: parents, len, offsets,
+        elements, ctx; any may be None).  Allocates its result tensors and returns
+        them in a dict with the stream id."""
+        import torch
+        R = int(dev["R"])
+        dvc = torch.device("cuda")
+        out = {
+            "count": torch.empty(R, dtype=torch.int32, device=dvc) if "count" in outputs else None,
+            "sum": torch.empty(R, dtype=torch.int64, device=dvc) if "sum" in outputs else None,
+            "min": torch.empty(R, dtype=torch.int32, device=dvc) if "min" in outputs else None,
+        }
+        d = StreamDesc()
+        d.n_regions = R
+        d.parents = _ptr(dev.get("parents"))
+        d.region_len = _ptr(dev.get("len"))
+        d.region_offsets = _ptr(dev.get("offsets"))
+        el = dev.get("elements")
+        d.elements = _ptr(el)
+        d.n_elements = 0 if el is None else int(el.numel())
+        d.ctx = _ptr(dev.get("ctx"))
+        d.out_count = _ptr(out["count"])
+        d.out_sum = _ptr(out["sum"])
+        d.out_min = _ptr(out["min"])
+        d.total_elements_hint = int(dev.get("total_elements", 0))
+        sid = ctypes.c_uint64()
+        check(lib().rs_stream_submit(self._h, ctypes.byref(d), ctypes.byref(sid)), "rs_stream_submit")
+        self._keep.append((dev, out))
+        out["id"] = int(sid.value)
+        self.streams.append(out)
+        return out
+
+    def clear(self):
+        check(lib().rs_clear_streams(self._h), "rs_clear_streams")
+        self._keep = []
+        self.streams = []
+
+    def workspace_bytes(self) -> int:
+        n = ctypes.c_uint64()
+        check(lib().rs_workspace_size(self._h, ctypes.byref(n)), "rs_workspace_size")
+        return int(n.value)
+
+    def workspace(self):
+        import torch
+        need = max(256, self.workspace_bytes())
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+        # 256-byte aligned view
+        off = (-self._ws.data_ptr()) % 256
+        return self._ws[off:]
+
+    def run(self):
+        ws = self.workspace()
+        check(lib().rs_run(self._h, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _cur_stream()), "rs_run")
+
+    def stats(self, raise_on_error=True) -> dict:
+        ws = self.workspace()
+        s = Stats()
+        st = lib().rs_get_stats(self._h, ctypes.c_void_p(ws.data_ptr()), _cur_stream(), ctypes.byref(s))
+        if raise_on_error:
+            check(st, "rs_get_stats")
+        d = s.as_dict()
+        d["status"] = st
+        return d
+
+    def fetch(self, sid: int, count=None, sum=None, min=None):
+        r = RegionResults(_ptr(count), _ptr(sum), _ptr(min))
+        check(lib().rs_fetch_region_results(self._h, sid, ctypes.byref(r), _cur_stream()),
+              "rs_fetch_region_results")
+
+    def graph_capture(self):
+        ws = self.workspace()
+        check(lib().rs_graph_capture(self._h, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _cur_stream()),
+              "rs_graph_capture")
+
+    def graph_launch(self):
+        check(lib().rs_graph_launch(self._h, _cur_stream()), "rs_graph_launch")
+
+    def graph_release(self):
+        check(lib().rs_graph_release(self._h), "rs_graph_release")
+
+    def autotune(self, trials=3):
+        ws = self.workspace()
+        best = Opts()
+        ms = ctypes.c_float()
+        check(lib().rs_autotune(self._h, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _cur_stream(), trials,
+                                ctypes.byref(best), ctypes.byref(ms)), "rs_autotune")
+        return best.as_dict(), float(ms.value)
+
+
+def to_device(stream: dict) -> dict:
+    """Copy a host stream (numpy uint32 arrays) to CUDA tensors (int32 views of the bits)."""
+    import numpy as np
+    import torch
+    dev = {"R": int(stream["R"])}
+    for k in ("parents", "len", "offsets", "elements", "ctx"):
+        a = stream.get(k)
+        dev[k] = None if a is None else torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    if stream.get("len") is not None:
+        dev["total_elements"] = int(np.asarray(stream["len"], dtype=np.uint64).sum())
+    elif stream.get("offsets") is not None:
+        o = stream["offsets"]
+        dev["total_elements"] = int(o[-1]) - int(o[0]) if len(o) else 0
+    return dev
+
+
+def results_to_numpy(out: dict) -> dict:
+    """Device result tensors -> numpy with the unsigned types of the ABI."""
+    import numpy as np
+    res = {}
+    if out.get("count") is not None:
+        res["count"] = out["count"].cpu().numpy().view(np.uint32)
+    if out.get("sum") is not None:
+        res["sum"] = out["sum"].cpu().numpy().view(np.uint64)
+    if out.get("min") is not None:
+        res["min"] = out["min"].cpu().numpy().view(np.uint32)
+    return res
+
+
+def run_stream(stages, stream: dict, strategy="tag", outputs=("count", "sum", "min"), **opts):
+    """One-shot helper: upload a host stream, run the pipeline once, return numpy
+    results and the run's statistics."""
+    import torch
+    p = Pipeline(stages, strategy=strategy, **opts)
+    dev = to_device(stream)
+    out = p.submit(dev, outputs=outputs)
+    p.run()
+    st = p.stats()
+    torch.cuda.synchronize()
+    res = results_to_numpy(out)
+    p.close()
+    return res, st

@@ -1,0 +1,122 @@
+"""The C ABI without a GPU: the library loads, exports every symbol include/rs.h
+declares, and its host-side validation behaves as documented (no kernel runs)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2006_07478_b300 import rs
+from paper_2006_07478_b300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rs_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    L = rs.lib()
+    declared = _declared()
+    assert "rs_run" in declared and "rs_pipeline_create" in declared
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(rs.EXPORTS) <= declared
+
+
+def test_version_and_status_strings():
+    assert rs.lib().rs_version() >= 1
+    assert rs.status_string(rs.RS_OK) == "ok"
+    assert "invalid" in rs.status_string(rs.RS_ERR_INVALID)
+
+
+def _create(stages, **opts):
+    arr = (rs.StageDesc * len(stages))(*[rs.stage_desc(s) for s in stages])
+    o = rs.make_opts(**opts)
+    h = ctypes.c_void_p()
+    st = rs.lib().rs_pipeline_create(arr, len(stages), ctypes.byref(o), ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("pipe", [wl.pipeline_hash_filter_map(), wl.pipeline_cascade(), wl.pipeline_graph_edges(),
+                                  [("enum_hash",), ("expand", 3, 7), ("aggregate",)]])
+def test_valid_pipelines_create(pipe):
+    st, h = _create(pipe)
+    assert st == rs.RS_OK
+    assert rs.lib().rs_pipeline_destroy(h) == rs.RS_OK
+
+
+@pytest.mark.parametrize("pipe", [
+    [("aggregate",)],                                                    # too short
+    [("enum_hash",), ("filter_mod", 2, 0)],                              # no aggregate last
+    [("filter_mod", 2, 0), ("aggregate",)],                              # no enumeration first
+    [("enum_hash",), ("filter_mod", 0, 0), ("aggregate",)],              # modulus 0
+    [("enum_hash",)] + [("map_mul", 1, 0)] * 5 + [("aggregate",)],       # too many stages
+    [("enum_hash",), ("expand", 9, 1), ("aggregate",)],                  # fan-out > 8
+])
+def test_invalid_pipelines_rejected(pipe):
+    st, h = _create(pipe)
+    assert st == rs.RS_ERR_INVALID
+
+
+def test_queue_capacity_must_hold_worst_case_output():
+    # fan-out 4 needs >= 32 * 5 slots; 128 is too small, 256 is fine
+    st, _ = _create([("enum_hash",), ("expand", 4, 1), ("aggregate",)], queue_capacity=128)
+    assert st == rs.RS_ERR_INVALID
+    st, h = _create([("enum_hash",), ("expand", 4, 1), ("aggregate",)], queue_capacity=256)
+    assert st == rs.RS_OK
+    rs.lib().rs_pipeline_destroy(h)
+    st, _ = _create(wl.pipeline_cascade(), queue_capacity=96)      # not a power of two
+    assert st == rs.RS_ERR_INVALID
+    st, _ = _create(wl.pipeline_cascade(), tiles_in_flight=3)
+    assert st == rs.RS_ERR_INVALID
+    st, _ = _create(wl.pipeline_cascade(), ensemble_width=64)
+    assert st == rs.RS_ERR_INVALID
+
+
+def test_stream_submit_validation_and_workspace_size():
+    st, h = _create(wl.pipeline_cascade())
+    assert st == rs.RS_OK
+    L = rs.lib()
+    d = rs.StreamDesc()
+    d.n_regions = 10
+    sid = ctypes.c_uint64()
+    # no lengths and no offsets
+    assert L.rs_stream_submit(h, ctypes.byref(d), ctypes.byref(sid)) == rs.RS_ERR_INVALID
+    d.region_len = ctypes.c_void_p(0x1000)
+    # loading enumeration without elements
+    assert L.rs_stream_submit(h, ctypes.byref(d), ctypes.byref(sid)) == rs.RS_ERR_INVALID
+    d.elements = ctypes.c_void_p(0x2000)
+    d.n_elements = 1 << 32
+    assert L.rs_stream_submit(h, ctypes.byref(d), ctypes.byref(sid)) == rs.RS_ERR_CAPACITY
+    d.n_elements = 1000
+    d.out_count = ctypes.c_void_p(0x3000)
+    assert L.rs_stream_submit(h, ctypes.byref(d), ctypes.byref(sid)) == rs.RS_OK
+    assert sid.value == 0
+    n = ctypes.c_uint64()
+    assert L.rs_workspace_size(h, ctypes.byref(n)) == rs.RS_OK
+    # header + one look-back word per unit + the stream table, each 256-byte aligned
+    assert n.value >= 256 and n.value % 256 == 0
+    # running without a workspace is an argument error, caught before any CUDA call
+    assert L.rs_run(h, None, 0, None) == rs.RS_ERR_INVALID
+    assert L.rs_clear_streams(h) == rs.RS_OK
+    assert L.rs_graph_launch(h, None) == rs.RS_ERR_NOT_READY
+    assert L.rs_pipeline_destroy(h) == rs.RS_OK
+
+
+def test_opts_round_trip():
+    p = rs.Pipeline(wl.pipeline_cascade(), strategy="signal", queue_capacity=128, regions_per_unit=16)
+    o = p.opts
+    assert o["strategy"] == 0 and o["queue_capacity"] == 128 and o["regions_per_unit"] == 16
+    p.set_opts(strategy="tag", warps_per_block=8)
+    assert p.opts["strategy"] == 1 and p.opts["warps_per_block"] == 8
+    with pytest.raises(rs.RsError):
+        p.set_opts(regions_per_unit=1000)
+    p.close()

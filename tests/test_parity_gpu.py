@@ -1,0 +1,202 @@
+"""GPU path vs the CPU oracle, bit-exact (all arithmetic is integer).
+
+Every test calls the CUDA library through its C ABI (via the ctypes binding) and
+compares per-region count / sum / min element by element with oracle.run on the
+same seeded input.  Sizes are small enough for the oracle, yet span many work
+units, tiles and ragged tails; the bench-size cases compare sampled regions."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2006_07478_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+STRATEGIES = ("tag", "signal")
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2006_07478_b300 import rs as _rs
+    _rs.lib()
+    return _rs
+
+
+def _check(rs, pipe, stream, strategy, outputs=("count", "sum", "min"), **opts):
+    want = oracle.run(pipe, stream)
+    got, st = rs.run_stream(pipe, stream, strategy=strategy, outputs=outputs, **opts)
+    assert st["device_status"] == 0, st
+    for k in outputs:
+        bad = np.flatnonzero(got[k] != want[k])
+        assert bad.size == 0, (k, strategy, bad[:5], got[k][bad[:5]], want[k][bad[:5]])
+    return got, st
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_hashed_uniform_10k(rs, strategy):
+    s = wl.hashed_uniform_stream()
+    got, st = _check(rs, wl.pipeline_hash_filter_map(), s, strategy)
+    N = int(s["len"].astype(np.int64).sum())
+    assert st["items"][0] == N and st["items"][1] == N          # enumerate emits N, filter consumes N
+    assert st["items"][2] == int(got["count"].astype(np.int64).sum())  # map sees the survivors
+    assert st["items"][3] == st["items"][2]                      # aggregate consumes what map pushed
+    if strategy == "signal":
+        R = s["R"]
+        for node in (1, 2, 3):
+            assert st["signals"][node] == 2 * R                  # Begin and End reach every node
+        # no ensemble spans a region boundary: at least sum ceil(L/32) ensembles at node 1
+        assert st["ensembles"][1] >= int(np.sum((s["len"].astype(np.int64) + 31) // 32))
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+@pytest.mark.parametrize("mean", [1, 4, 32, 256, 4096])
+def test_cascade_geometric(rs, strategy, mean):
+    s = wl.cascade_stream(n_total=1 << 18, mean=mean, seed=7)
+    _check(rs, wl.pipeline_cascade(), s, strategy, outputs=("count", "sum"))
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_graph_csr(rs, strategy):
+    g = wl.graph_stream(V=1 << 14, E=1 << 18, cap=1 << 12, seed=7)
+    _check(rs, wl.pipeline_graph_edges(), g, strategy, outputs=("count", "min"))
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_expand_fanout_and_general_modulus(rs, strategy):
+    s = wl.hashed_uniform_stream(3000, 40, 5)
+    pipe = [("enum_hash",), ("expand", 3, 77), ("filter_mod", 3, 1), ("map_mul", 7, 11), ("aggregate",)]
+    _check(rs, pipe, s, strategy)
+    pipe = [("enum_hash",), ("expand", 4, 9), ("expand", 2, 5), ("aggregate",)]
+    _check(rs, pipe, s, strategy)
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_empty_and_degenerate_regions(rs, strategy):
+    rng = np.random.default_rng(4)
+    pipe = [("enum_load",), ("filter_hash_ctx", 1, 3 << 30), ("aggregate",)]
+    # all regions empty
+    L = np.zeros(1000, dtype=np.uint32)
+    s = wl.make_stream(L, elements=np.arange(16, dtype=np.uint32), ctx=np.zeros(1000, dtype=np.uint32))
+    _check(rs, pipe, s, strategy)
+    # one huge region, lengths that are exact multiples of 32, runs of empties
+    L = np.array([1 << 18], dtype=np.uint32)
+    s = wl.make_stream(L, elements=rng.integers(0, 1 << 32, 1 << 18, dtype=np.uint64).astype(np.uint32),
+                       ctx=np.array([123], dtype=np.uint32))
+    _check(rs, pipe, s, strategy)
+    L = (rng.integers(0, 5, 5000) * 32).astype(np.uint32)
+    L[100:400] = 0
+    n = int(L.sum())
+    s = wl.make_stream(L, elements=rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32),
+                       ctx=rng.integers(0, 1 << 32, 5000, dtype=np.uint64).astype(np.uint32))
+    _check(rs, pipe, s, strategy)
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+@pytest.mark.parametrize("opts", [
+    dict(regions_per_unit=1), dict(regions_per_unit=256), dict(queue_capacity=128, signal_capacity=4),
+    dict(tile_elements=64, tiles_in_flight=2), dict(tile_elements=4096, tiles_in_flight=2),
+    dict(warps_per_block=1, grid=1), dict(warps_per_block=16), dict(grid=3),
+])
+def test_option_sweep(rs, strategy, opts):
+    s = wl.cascade_stream(n_total=100_003, mean=20, seed=9)
+    _check(rs, wl.pipeline_cascade(), s, strategy, **opts)
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_unaligned_elements_pointer(rs, strategy):
+    """elements not 16-byte aligned: the kernel reads them without bulk copies."""
+    import torch
+    s = wl.cascade_stream(n_total=50_001, mean=8, seed=3)
+    pipe = wl.pipeline_cascade()
+    want = oracle.run(pipe, s)
+    p = rs.Pipeline(pipe, strategy=strategy)
+    dev = rs.to_device(s)
+    big = torch.empty(dev["elements"].numel() + 1, dtype=torch.int32, device="cuda")
+    big[1:] = dev["elements"]
+    dev["elements"] = big[1:]
+    out = p.submit(dev, outputs=("count", "sum", "min"))
+    p.run()
+    st = p.stats()
+    res = rs.results_to_numpy(out)
+    for k in res:
+        assert np.array_equal(res[k], want[k]), k
+    assert st["device_status"] == 0
+    p.close()
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_batched_streams_one_launch_and_graph_replay(rs, strategy):
+    import torch
+    streams = wl.batched_streams(n_streams=48, median=2 ** 10, sigma=1.5, cap=1 << 14, seed=11)
+    streams.append(wl.make_stream(np.zeros(0, dtype=np.uint32)))                # an empty stream
+    pipe = wl.pipeline_hash_filter_map()
+    p = rs.Pipeline(pipe, strategy=strategy)
+    outs = [p.submit(rs.to_device(s)) for s in streams]
+    p.run()
+    assert p.stats()["device_status"] == 0
+    first = [rs.results_to_numpy(o) for o in outs]
+    for s, res in zip(streams, first):
+        want = oracle.run(pipe, s)
+        for k in res:
+            assert np.array_equal(res[k], want[k]), k
+    # replay the same work from a captured graph on a side stream, after clobbering outputs
+    for o in outs:
+        for k in ("count", "sum", "min"):
+            o[k].fill_(-1)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        p.graph_capture()
+        p.graph_launch()
+        p.graph_launch()
+    side.synchronize()
+    for res, o in zip(first, outs):
+        again = rs.results_to_numpy(o)
+        for k in res:
+            assert np.array_equal(again[k], res[k]), k
+    p.graph_release()
+    p.close()
+
+
+def test_fetch_to_host_and_autotune(rs):
+    import torch
+    s = wl.cascade_stream(n_total=1 << 18, mean=64, seed=5)
+    pipe = wl.pipeline_cascade()
+    want = oracle.run(pipe, s)
+    p = rs.Pipeline(pipe, strategy="tag")
+    out = p.submit(rs.to_device(s), outputs=("count", "sum"))
+    best, ms = p.autotune(trials=2)
+    assert best["strategy"] in (0, 1) and ms > 0
+    p.run()
+    hc = torch.empty(s["R"], dtype=torch.int32).pin_memory()
+    hs = torch.empty(s["R"], dtype=torch.int64).pin_memory()
+    p.fetch(out["id"], count=hc, sum=hs)
+    torch.cuda.synchronize()
+    assert np.array_equal(hc.numpy().view(np.uint32), want["count"])
+    assert np.array_equal(hs.numpy().view(np.uint64), want["sum"])
+    p.close()
+
+
+@pytest.mark.parametrize("mean", [1, 4096])
+def test_bench_size_sampled(rs, mean):
+    """The bench's full-size stream (2^26 elements) in the bench's launch
+    configuration: sampled regions against the oracle one by one, plus the
+    cascade's pass rate over the whole stream."""
+    s = wl.cascade_stream(n_total=1 << 26, mean=mean, seed=7)
+    pipe = wl.pipeline_cascade()
+    for strategy in STRATEGIES:
+        if strategy == "signal" and mean == 1:
+            continue      # covered at 2^18; the full-size signal run at mean 1 is slow by design
+        got, st = rs.run_stream(pipe, s, strategy=strategy, outputs=("count", "sum"))
+        assert st["device_status"] == 0
+        rng = np.random.default_rng(mean)
+        idx = np.unique(np.concatenate([rng.integers(0, s["R"], 4000), [0, s["R"] - 1]]))
+        want = oracle.run_sampled(pipe, s, idx)
+        assert np.array_equal(got["count"][idx], want["count"])
+        assert np.array_equal(got["sum"][idx], want["sum"])
+        p = 0.5 * 0.3 * 0.1
+        frac = got["count"].astype(np.int64).sum() / (1 << 26)
+        assert abs(frac - p) < 6 * np.sqrt(p * (1 - p) / (1 << 26))
+        assert st["items"][1] == 1 << 26
