@@ -1,0 +1,448 @@
+"""Benchmark: input items/s of the region-segmented cascade on B300, with the
+fraction of HBM peak per mean region size.
+
+One step = one pass of the pipeline (enumerate -> three context-dependent hash
+filters -> per-region count+sum) over five seeded streams of 2^26 uint32 elements
+each, cut into geometric regions of mean 1, 4, 32, 256 and 4096 (seed 7); each
+stream runs with the region strategy and unit size the library's autotuner picked
+for it.  Inputs are device-resident and each stream's 256 MiB element array is
+larger than L2, and the five streams alternate, so no launch reuses the previous
+launch's lines.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs the same five streams on
+its own GPU (weak scaling, no data-path collective); value = all ranks' items /
+the slowest rank's time.  `--impl reference` times the CPU oracle (the plain
+sequential definition) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2006_07478_b300 import workloads as wl  # noqa: E402
+
+METRIC = "input items/s & fraction of HBM peak vs mean region size; p50/p99 stream latency"
+MEANS = (1, 4, 32, 256, 4096)
+N_ELEM = 1 << 26
+SEED = 7
+SPEC_HBM_GBS = 8000.0
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def alg_bytes(stream) -> int:
+    """Algorithmic HBM bytes of one pass: every element read once (4 B), and per
+    region its length and context word read and its count (4 B) and sum (8 B)
+    written."""
+    return 4 * N_ELEM + 20 * int(stream["R"])
+
+
+def make_streams():
+    return [wl.cascade_stream(n_total=N_ELEM, mean=m, seed=SEED) for m in MEANS]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._reader, daemon=True)
+        self.thread.start()
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = []
+        for t, line in self.samples:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            rows.append((t, parts))
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        used = inside if inside else [r for r in rows if t0 - 0.5 <= r[0] <= t1 + 0.5]
+        if not used:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(p[0]) for _, p in used if p[0].replace(".", "", 1).isdigit()]
+        smax = [float(p[1]) for _, p in used if p[1].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, p in used:
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(used), "samples_in_timed_region": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+
+def time_oracle(streams, threads: int, budget_s: float = 20.0):
+    """Run the CPU oracle over the streams (whole streams, in order) until the
+    budget is spent; returns (items, seconds, streams_done)."""
+    from oracle import oracle
+    pipe = wl.pipeline_cascade()
+    items, secs, done = 0, 0.0, 0
+    for s in streams:
+        t = time.perf_counter()
+        oracle.run(pipe, s, threads=threads)
+        secs += time.perf_counter() - t
+        items += N_ELEM
+        done += 1
+        if secs > budget_s:
+            break
+    return items, secs, done
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    streams = make_streams()
+    threads = os.cpu_count() or 1
+    from oracle import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        time_oracle(streams[:1], threads, budget_s=0.0)
+    times, items = [], 0
+    for _ in range(args.steps):
+        it, secs, done = time_oracle(streams, threads, budget_s=1e9)
+        times.append(secs)
+        items += it
+    total = sum(times)
+    value = items / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "items/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded)",
+        "config": {"workload": "cascade: 5 streams x 2^26 u32 elements, geometric regions mean 1/4/32/256/4096, "
+                               "3 context hash filters (pass 0.5/0.3/0.1), count+sum per region", "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": "items/s", "cores": threads, "kind": "oracle",
+                         "sample": "the whole workload each step (5 x 2^26 elements)"},
+        "e2e": {"value": value, "unit": "items/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("rs_kernel.cu", "rs_internal.h"):
+        with open(os.path.join(ROOT, "paper_2006_07478_b300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """Per-launch DRAM bytes of the timed kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_cascade.txt")
+    try:
+        rows = {}
+        src = None
+        with open(path) as f:
+            for line in f:
+                line = line.strip()
+                if line.startswith("kernel_source"):
+                    src = line.split()[1]
+                elif line.startswith("mean="):
+                    kv = dict(tok.split("=") for tok in line.split())
+                    rows[(int(kv["mean"]), kv["strategy"])] = float(kv["dram_bytes"])
+        if src != kernel_source_hash():
+            return None
+        return rows
+    except Exception:
+        return None
+
+
+def run_case(args, rs, torch):
+    """One stream, one fixed strategy: warm-up launches then `steps` timed launches.
+    Used to give profilers a small, fixed launch sequence."""
+    parts = args.case.split(":")
+    mean, strat = float(parts[0]), parts[1]
+    n = 1 << int(parts[2]) if len(parts) > 2 else N_ELEM
+    s = wl.cascade_stream(n_total=n, mean=mean, seed=SEED)
+    p = rs.Pipeline(wl.pipeline_cascade(), strategy=strat)
+    out = p.submit(rs.to_device(s), outputs=("count", "sum"))
+    p.timing_enable(args.steps + args.warmup)
+    for _ in range(args.warmup):
+        p.run()
+    torch.cuda.synchronize()
+    p.timing_read()
+    for _ in range(args.steps):
+        p.run()
+    ms = p.timing_read()
+    st = p.stats()
+    kms = statistics.median(ms)
+    ab = 4 * n + 20 * int(s["R"])
+    print(json.dumps({"case": args.case, "n": n, "regions": int(s["R"]), "kernel_ms": kms,
+                      "items_per_s": n / (kms * 1e-3), "alg_gbs": ab / (kms * 1e-3) / 1e9,
+                      "opts": p.opts, "active_lane_fraction": st["active_lane_fraction"],
+                      "ensembles": st["ensembles"], "firings": st["firings"]}), flush=True)
+    del out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--case", default=None,
+                    help="MEAN:STRATEGY[:N_LOG2] -- run one stream with a fixed strategy (for profilers)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2006_07478_b300 import rs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    if args.case:
+        run_case(args, rs, torch)
+        return
+
+    streams = make_streams()
+    pipe = wl.pipeline_cascade()
+
+    # ---- device-resident inputs, one pipeline per stream, tuned per stream ----
+    pipes, outs, tuned = [], [], []
+    for s in streams:
+        p = rs.Pipeline(pipe, strategy="tag")
+        dev = rs.to_device(s)
+        out = p.submit(dev, outputs=("count", "sum"))
+        pipes.append(p)
+        outs.append(out)
+    per_mean = []
+    for m, s, p in zip(MEANS, streams, pipes):
+        best, best_ms = p.autotune(trials=3)
+        tuned.append(best)
+        row = {"mean": m, "regions": int(s["R"]), "alg_bytes": alg_bytes(s),
+               "chosen": {"strategy": "signal" if best["strategy"] == 0 else "tag",
+                          "regions_per_unit": best["regions_per_unit"], "warps_per_block": best["warps_per_block"]}}
+        # both strategies at the tuned unit size, kernel-only event timing
+        for strat in ("tag", "signal"):
+            p.set_opts(strategy=strat)
+            p.timing_enable(8)
+            for _ in range(2):
+                p.run()
+            torch.cuda.synchronize()
+            p.timing_read()
+            for _ in range(5):
+                p.run()
+            ms = p.timing_read()
+            st = p.stats()
+            kms = statistics.median(ms)
+            gbs = alg_bytes(s) / (kms * 1e-3) / 1e9
+            row[strat] = {"kernel_ms": kms, "items_per_s": N_ELEM / (kms * 1e-3), "alg_gbs": gbs,
+                          "active_lane_fraction": [round(x, 4) for x in st["active_lane_fraction"]]}
+        p.set_opts(**{k: v for k, v in best.items() if k != "strategy"}, strategy=best["strategy"])
+        per_mean.append(row)
+
+    # correctness spot check of the tuned configuration (oracle, sampled regions)
+    from oracle import oracle
+    for s, p, out in zip(streams, pipes, outs):
+        p.run()
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(1)
+        idx = np.unique(rng.integers(0, s["R"], 2000))
+        want = oracle.run_sampled(pipe, s, idx)
+        got = rs.results_to_numpy(out)
+        assert np.array_equal(got["count"][idx], want["count"]) and np.array_equal(got["sum"][idx], want["sum"])
+
+    for p in pipes:
+        p.timing_enable(args.steps + 8)
+
+    # ---- warm-up, then exactly K timed steps ----
+    for _ in range(args.warmup):
+        for p in pipes:
+            p.run()
+    torch.cuda.synchronize()
+    for p in pipes:
+        p.timing_read()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for p in pipes:
+            p.run()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_end = time.perf_counter()
+    barrier()
+    time.sleep(0.2)
+    sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    kernel_ms = [p.timing_read() for p in pipes]
+    statuses = [p.stats()["device_status"] for p in pipes]
+    assert all(s == 0 for s in statuses), statuses
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    items_step = N_ELEM * len(MEANS)
+    value = items_step * args.steps * world / (elapsed_ms * 1e-3)
+
+    # ---- roofline of the timed kernel: algorithmic bytes / kernel time, all launches ----
+    peak, peak_kind = load_peaks()
+    tot_bytes = sum(alg_bytes(s) * len(k) for s, k in zip(streams, kernel_ms))
+    tot_kms = sum(sum(k) for k in kernel_ms)
+    achieved = tot_bytes / (tot_kms * 1e-3) / 1e9
+    traffic_rows = read_traffic()
+    traffic = None
+    if traffic_rows:
+        try:
+            traffic = sum(traffic_rows[(m, "signal" if t["strategy"] == 0 else "tag")]
+                          for m, t in zip(MEANS, tuned)) / len(MEANS)
+        except KeyError:
+            traffic = None
+    for row, k in zip(per_mean, kernel_ms):
+        kms = statistics.median(k)
+        row["timed_kernel_ms_median"] = kms
+        row["timed_alg_gbs"] = row["alg_bytes"] / (kms * 1e-3) / 1e9
+        row["frac_of_measured_hbm"] = row["timed_alg_gbs"] / peak
+        row["frac_of_8tbs_spec"] = row["timed_alg_gbs"] / SPEC_HBM_GBS
+
+    # ---- end to end: host buffers, copies inside the timed region ----
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in, dev_in = [], []
+        for p in pipes:
+            dev, _ = p._keep[0]
+            hi = {k: dev[k].cpu().pin_memory() for k in ("len", "elements", "ctx") if dev.get(k) is not None}
+            host_in.append(hi)
+            dev_in.append(dev)
+        host_out = [{"count": torch.empty_like(o["count"], device="cpu").pin_memory(),
+                     "sum": torch.empty_like(o["sum"], device="cpu").pin_memory()} for o in outs]
+        h2d = sum(t.numel() * t.element_size() for hi in host_in for t in hi.values())
+        d2h = sum(t.numel() * t.element_size() for ho in host_out for t in ho.values())
+        for rep in range(args.e2e_steps + 1):
+            if rep == 1:
+                torch.cuda.synchronize()
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            for p, hi, dev, out, ho in zip(pipes, host_in, dev_in, outs, host_out):
+                for k, t in hi.items():
+                    dev[k].copy_(t, non_blocking=True)
+                p.run()
+                p.fetch(out["id"], count=ho["count"], sum=ho["sum"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": items_step * world / (e2e_ms * 1e-3), "unit": "items/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+
+    # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        items, secs, done = time_oracle(streams, threads, budget_s=20.0)
+        cpu = {"value": items / secs, "unit": "items/s", "cores": threads, "kind": "oracle",
+               "sample": f"{done} of the 5 streams, whole ({items} elements), {threads} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "items/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+            "config": {"workload": "cascade: 5 streams x 2^26 u32 elements, geometric regions mean 1/4/32/256/4096, "
+                                   "3 context hash filters (pass 0.5/0.3/0.1), count+sum per region",
+                       "seed": SEED, "l2": "inputs larger than L2 (256 MiB per stream), streams alternate",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                         "frac_of_8tbs_spec": achieved / SPEC_HBM_GBS,
+                         "kernel": "rs_pipeline_kernel (all launches of the timed region)"},
+            "per_mean": per_mean,
+            "clocks": sampler.summary(t_start, t_end),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": sum(len(k) for k in kernel_ms),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

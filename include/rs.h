@@ -213,6 +213,17 @@ rs_status rs_graph_release(rs_pipeline *p);
 rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream,
                       uint32_t trials, rs_pipeline_opts *best, float *best_ms);
 
+/* ---- per-launch kernel timing --------------------------------------------------- */
+
+/* When enabled (capacity > 0), every rs_run records a pair of CUDA events on its
+ * stream immediately before and after its kernel launch, into a ring of `capacity`
+ * slots owned by the pipeline (capacity 0 disables and frees them).  Not recorded
+ * inside rs_graph_capture. */
+rs_status rs_timing_enable(rs_pipeline *p, uint32_t capacity);
+/* Wait for the recorded events, write up to `max` kernel durations in milliseconds
+ * (launch order) to ms[], their number to *n, and empty the ring. */
+rs_status rs_timing_read(rs_pipeline *p, float *ms, uint32_t max, uint32_t *n);
+
 /* ---- misc ---------------------------------------------------------------------- */
 
 const char *rs_status_string(rs_status s);

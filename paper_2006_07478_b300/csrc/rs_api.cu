@@ -40,7 +40,18 @@ struct rs_pipeline {
     cudaGraphExec_t graph = nullptr;
     // device facts
     int n_sm = 0;
+    // per-launch timing ring
+    std::vector<cudaEvent_t> tev;   // 2 events per slot
+    uint32_t t_cap = 0, t_count = 0;
 };
+
+static void timing_free(rs_pipeline *p)
+{
+    for (cudaEvent_t e : p->tev)
+        if (e) cudaEventDestroy(e);
+    p->tev.clear();
+    p->t_cap = p->t_count = 0;
+}
 
 static uint32_t host_fmix32(uint32_t h)
 {
@@ -218,6 +229,7 @@ rs_status rs_pipeline_destroy(rs_pipeline *p)
         cudaEventDestroy(p->upload_done);
     }
     if (p->table_host) cudaFreeHost(p->table_host);
+    timing_free(p);
     delete p;
     return RS_OK;
 }
@@ -533,8 +545,15 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
         if ((e = cudaEventRecord(p->upload_done, stream)) != cudaSuccess) return cuda_fail(e);
         p->upload_pending = true;
     }
+    const bool timed = !capturing && p->t_cap > 0;
+    const uint32_t slot = timed ? (p->t_count % p->t_cap) : 0;
+    if (timed && (e = cudaEventRecord(p->tev[2 * slot], stream)) != cudaSuccess) return cuda_fail(e);
     int le = rs_launch_kernel(Lc.P, Lc.grid, Lc.block, Lc.smem, (void *)stream);
     if (le != 0) return cuda_fail((cudaError_t)le);
+    if (timed) {
+        if ((e = cudaEventRecord(p->tev[2 * slot + 1], stream)) != cudaSuccess) return cuda_fail(e);
+        p->t_count++;
+    }
     return RS_OK;
 }
 
@@ -653,6 +672,51 @@ rs_status rs_graph_release(rs_pipeline *p)
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
     }
+    return RS_OK;
+}
+
+rs_status rs_timing_enable(rs_pipeline *p, uint32_t capacity)
+{
+    if (!p) return RS_ERR_INVALID;
+    timing_free(p);
+    if (capacity == 0) return RS_OK;
+    try {
+        p->tev.assign(2 * (size_t)capacity, nullptr);
+    } catch (...) {
+        return RS_ERR_NOMEM;
+    }
+    for (auto &e : p->tev) {
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) {
+            timing_free(p);
+            return cuda_fail(ce);
+        }
+    }
+    p->t_cap = capacity;
+    p->t_count = 0;
+    return RS_OK;
+}
+
+rs_status rs_timing_read(rs_pipeline *p, float *ms, uint32_t max, uint32_t *n)
+{
+    if (!p || !n) return RS_ERR_INVALID;
+    *n = 0;
+    if (p->t_cap == 0) return RS_ERR_NOT_READY;
+    uint32_t cnt = p->t_count < p->t_cap ? p->t_count : p->t_cap;
+    uint32_t first = p->t_count - cnt;
+    uint32_t w = 0;
+    for (uint32_t i = 0; i < cnt && w < max; ++i) {
+        uint32_t slot = (first + i) % p->t_cap;
+        cudaError_t e = cudaEventSynchronize(p->tev[2 * slot + 1]);
+        if (e != cudaSuccess) return cuda_fail(e);
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, p->tev[2 * slot], p->tev[2 * slot + 1]);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (ms) ms[w] = t;
+        ++w;
+    }
+    *n = w;
+    p->t_count = 0;
     return RS_OK;
 }
 

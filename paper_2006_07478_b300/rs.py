@@ -34,7 +34,8 @@ EXPORTS = [
     "rs_default_opts", "rs_pipeline_create", "rs_pipeline_destroy", "rs_pipeline_set_opts",
     "rs_pipeline_get_opts", "rs_stream_submit", "rs_clear_streams", "rs_workspace_size", "rs_run",
     "rs_fetch_region_results", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
-    "rs_graph_release", "rs_autotune", "rs_status_string", "rs_last_cuda_error", "rs_version",
+    "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_status_string",
+    "rs_last_cuda_error", "rs_version",
 ]
 
 
@@ -121,6 +122,8 @@ def lib(build_if_missing: bool = True):
             "rs_graph_release": ([P], ctypes.c_int),
             "rs_autotune": ([P, P, U64, P, U32, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_float)],
                             ctypes.c_int),
+            "rs_timing_enable": ([P, U32], ctypes.c_int),
+            "rs_timing_read": ([P, ctypes.POINTER(ctypes.c_float), U32, ctypes.POINTER(U32)], ctypes.c_int),
             "rs_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "rs_last_cuda_error": ([], ctypes.c_int),
             "rs_version": ([], U32),
@@ -315,6 +318,15 @@ class Pipeline:
 
     def graph_release(self):
         check(lib().rs_graph_release(self._h), "rs_graph_release")
+
+    def timing_enable(self, capacity: int):
+        check(lib().rs_timing_enable(self._h, int(capacity)), "rs_timing_enable")
+
+    def timing_read(self, max_n: int = 65536) -> list:
+        buf = (ctypes.c_float * max_n)()
+        n = ctypes.c_uint32()
+        check(lib().rs_timing_read(self._h, buf, max_n, ctypes.byref(n)), "rs_timing_read")
+        return [float(buf[i]) for i in range(n.value)]
 
     def autotune(self, trials=3):
         ws = self.workspace()
