@@ -99,7 +99,8 @@ typedef enum {
 } rs_strategy;
 
 typedef struct {
-    uint32_t ensemble_width;    /* W, lanes per ensemble; 32 (one warp = one SIMD processor) */
+    uint32_t ensemble_width;    /* W, items per ensemble: 32, 64 or 128; a warp is one SIMD
+                                   processor and each lane takes W/32 items; 0 = 128         */
     uint32_t queue_capacity;    /* data-queue slots per edge; power of two,
                                    >= W * (max fan-out + 1) so a blocked node always leaves
                                    room for one full ensemble downstream; 0 = the smallest
@@ -109,9 +110,9 @@ typedef struct {
     uint32_t regions_per_unit;  /* parents claimed per atomic step, <= 256; 0 = from the mean
                                    region length (about 2048 elements per claim)              */
     uint32_t tile_elements;     /* elements per bulk-copy tile for RS_ENUM_LOAD, a power of
-                                   two in 64..4096; 0 = 256                                   */
+                                   two in W..4096; 0 = 256                                    */
     uint32_t tiles_in_flight;   /* staging tiles per processor, 2 or 4; 0 = 4                 */
-    uint32_t warps_per_block;   /* processors per CTA, 1..16; 0 = 4                           */
+    uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = 4                            */
     uint32_t grid;              /* CTAs; 0 = a persistent grid (SMs x resident CTAs per SM)   */
     uint32_t reserved;
     uint64_t device_budget;     /* scheduler sweeps allowed per claimed unit before the device

@@ -75,10 +75,10 @@ static uint32_t max_fanout_of(const rs_stage_desc *st, uint32_t n)
 
 static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
 {
-    if (o->ensemble_width == 0) o->ensemble_width = RS_W;
+    if (o->ensemble_width == 0) o->ensemble_width = 4 * RS_W;
     if (o->queue_capacity == 0) {
         uint32_t c = 64;
-        while (c < RS_W * (fan + 1)) c <<= 1;
+        while (c < o->ensemble_width * (fan + 1)) c <<= 1;
         o->queue_capacity = c;
     }
     if (o->signal_capacity == 0) o->signal_capacity = 32;
@@ -91,16 +91,17 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
 
 static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
 {
-    if (o->ensemble_width != RS_W) return RS_ERR_INVALID;
-    if (!is_pow2(o->queue_capacity) || o->queue_capacity < RS_W * (fan + 1) || o->queue_capacity > 4096)
+    const uint32_t W = o->ensemble_width;
+    if (W != RS_W && W != 2 * RS_W && W != 4 * RS_W) return RS_ERR_INVALID;
+    if (!is_pow2(o->queue_capacity) || o->queue_capacity < W * (fan + 1) || o->queue_capacity > 4096)
         return RS_ERR_INVALID;
     if (!is_pow2(o->signal_capacity) || o->signal_capacity < 4 || o->signal_capacity > 1024)
         return RS_ERR_INVALID;
     if (o->strategy > RS_STRATEGY_AUTO) return RS_ERR_INVALID;
     if (o->regions_per_unit > RS_MAX_K) return RS_ERR_INVALID;
-    if (!is_pow2(o->tile_elements) || o->tile_elements < 64 || o->tile_elements > 4096) return RS_ERR_INVALID;
+    if (!is_pow2(o->tile_elements) || o->tile_elements < W || o->tile_elements > 4096) return RS_ERR_INVALID;
     if (o->tiles_in_flight != 2 && o->tiles_in_flight != 4) return RS_ERR_INVALID;
-    if (o->warps_per_block < 1 || o->warps_per_block > 16) return RS_ERR_INVALID;
+    if (o->warps_per_block < 1 || o->warps_per_block > 8) return RS_ERR_INVALID;
     return RS_OK;
 }
 
@@ -360,13 +361,16 @@ static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax,
     L.o_rm = (uint32_t)off;
     off += (size_t)Kmax * 4;
     off = align_up(off, 16);
-    const uint32_t ne = p->n_stages - 1;
+    // rings for edges 1..n-2 (edge 0 carries element positions, staged in the tiles)
+    const uint32_t nr = p->n_stages - 2;
     L.o_qv = (uint32_t)off;
-    off += (size_t)ne * o.queue_capacity * 4;
+    off += (size_t)nr * o.queue_capacity * 4;
     L.o_qt = (uint32_t)off;
-    off += strategy == RS_STRATEGY_TAG ? (size_t)ne * o.queue_capacity * 4 : 0;
+    off += strategy == RS_STRATEGY_TAG ? (size_t)nr * o.queue_capacity * 2 : 0;
+    off = align_up(off, 16);
+    // signal rings for edges 0..n-2
     L.o_sq = (uint32_t)off;
-    off += strategy == RS_STRATEGY_SIGNAL ? (size_t)ne * o.signal_capacity * 8 : 0;
+    off += strategy == RS_STRATEGY_SIGNAL ? (size_t)(p->n_stages - 1) * o.signal_capacity * 8 : 0;
     L.per_warp = (uint32_t)align_up(off, 128);
     return L;
 }
@@ -480,6 +484,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.streams = (const DevStream *)(wsb + pl.table_off);
     P.hdr = (WsHeader *)wsb;
     P.lookback = (unsigned long long *)(wsb + pl.lb_off);
+    P.V = o.ensemble_width / RS_W;
     P.C = o.queue_capacity;
     P.SC = o.signal_capacity;
     P.TE = o.tile_elements;
@@ -511,7 +516,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     if (pl.total_units == 0) return RS_OK;
     if (Lc.grid == 0) {
         int bps = 0;
-        int ce = rs_kernel_occupancy(strategy, Lc.block, Lc.smem, &bps);
+        int ce = rs_kernel_occupancy(strategy, (int)P.V, Lc.block, Lc.smem, &bps);
         if (ce != 0) return cuda_fail((cudaError_t)ce);
         if (bps == 0) return RS_ERR_CAPACITY;
         Lc.grid = bps * p->n_sm;
@@ -521,8 +526,8 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
             if (Lc.grid < 1) Lc.grid = 1;
         }
     } else {
-        int ce = rs_kernel_max_smem_optin(Lc.smem);
-        (void)ce;
+        int ce = rs_kernel_max_smem_optin(strategy, (int)P.V, Lc.smem);
+        if (ce != 0) return cuda_fail((cudaError_t)ce);
     }
     return RS_OK;
 }

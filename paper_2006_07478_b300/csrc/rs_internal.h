@@ -5,7 +5,7 @@
 
 #include "rs.h"
 
-#define RS_W 32                       // lanes per ensemble: one warp is one SIMD processor
+#define RS_W 32                       // lanes of one SIMD processor (a warp)
 #define RS_MAX_EDGES (RS_MAX_STAGES - 1)
 #define RS_MAX_K 256                  // parents per work unit
 #define RS_GOLD 0x9E3779B9u
@@ -84,6 +84,7 @@ struct KParams {
     const DevStream *streams;
     WsHeader *hdr;
     unsigned long long *lookback; // one word per unit
+    uint32_t V;                   // items per lane per ensemble (W = 32 V)
     uint32_t C, SC, TE, NT;       // queue slots, signal slots, tile elements, tiles
     uint32_t need_ctx, need_par, want_count, want_sum, want_min;
     uint32_t any_load;
@@ -94,5 +95,5 @@ struct KParams {
 
 // Launch helper implemented in rs_kernel.cu.
 int rs_launch_kernel(const KParams &P, int grid, int block, size_t smem, void *stream);
-int rs_kernel_max_smem_optin(size_t smem);
-int rs_kernel_occupancy(int strategy, int block, size_t smem, int *blocks_per_sm);
+int rs_kernel_max_smem_optin(int strategy, int V, size_t smem);
+int rs_kernel_occupancy(int strategy, int V, int block, size_t smem, int *blocks_per_sm);

@@ -146,14 +146,16 @@ __device__ __forceinline__ unsigned long long warp_sum_u32_wide(uint32_t v)
 }
 
 // ---------------------------------------------------------------------------
-// per-warp state
+// per-warp (per-processor) state, all warp-uniform, held in registers
 
 struct Warp {
-    // queue cursors (free-running; slot = cursor & (C-1))
+    // queue cursors (free-running).  Edge 0 (enumerate -> node 1) carries element
+    // positions of the unit: qh[0] is node 1's next position, qt[0] the enumerated limit.
+    // Edges e >= 1 are shared-memory rings of C slots (slot = cursor & (C-1)).
     uint32_t qh[RS_MAX_EDGES], qt[RS_MAX_EDGES];
     // signal rings and the sender's emitted-since-last-signal counter (Section 3.1)
     uint32_t sh[RS_MAX_EDGES], st[RS_MAX_EDGES], em[RS_MAX_EDGES];
-    // receiver state: current credit counter and current parent (local index)
+    // receiver state per node: current credit counter and current parent (local index)
     uint32_t credit[RS_MAX_STAGES], ctxk[RS_MAX_STAGES];
     // aggregate accumulator (signal strategy)
     uint32_t acc_c, acc_m;
@@ -165,7 +167,8 @@ struct Warp {
 
 struct Smem {
     unsigned long long *mbar;
-    uint32_t *tiles, *moff, *mctx, *mpar, *rc, *rm, *qv, *qtag, *sq, *scr;
+    uint32_t *tiles, *moff, *mctx, *mpar, *rc, *rm, *qv, *sq, *scr;
+    uint16_t *qtag;
     unsigned long long *rs;
 };
 
@@ -181,27 +184,30 @@ struct Stage {
 
 // ---------------------------------------------------------------------------
 
-template <int STRAT>
-struct Kern {
+template <int STRAT, int V>
+struct Proc {
+    static constexpr uint32_t W = 32u * V;   // ensemble width (items per firing)
     const KParams &P;
     Smem &M;
     Warp &w;
     Stage &g;
-    uint32_t lane;
-    // unit
-    uint32_t nk, total, E0, r0;
+    const uint32_t lane;
+    // current unit
+    uint32_t nk, total, E0;
+    uint32_t ek;     // enumerate: next parent to open (signal strategy)
+    uint32_t ek1;    // node 1: parent containing its next position (tag strategy)
     bool stop;
 
-    __device__ __forceinline__ Kern(const KParams &P_, Smem &M_, Warp &w_, Stage &g_, uint32_t lane_)
-        : P(P_), M(M_), w(w_), g(g_), lane(lane_), nk(0), total(0), E0(0), r0(0), stop(false) {}
+    __device__ __forceinline__ Proc(const KParams &P_, Smem &M_, Warp &w_, Stage &g_, uint32_t lane_)
+        : P(P_), M(M_), w(w_), g(g_), lane(lane_), nk(0), total(0), E0(0), ek(0), ek1(0), stop(false) {}
+
+    __device__ __forceinline__ bool loading() const { return P.st[0].op == D_ENUM_LOAD; }
 
     // ---- tile staging (TMA bulk copies into a ring of NT*TE elements) ----
     __device__ __forceinline__ void issue_tiles()
     {
         const uint32_t TE = P.TE, NT = P.NT;
-        bool any = false;
         while (g.t_issued < g.ntiles && g.t_issued < g.t_freed + NT) {
-            any = true;
             uint32_t t = g.t_issued;
             uint32_t start = g.A + t * TE;
             uint32_t cnt = min(TE, g.B - start);
@@ -213,10 +219,9 @@ struct Kern {
             }
             g.t_issued++;
         }
-        (void)any;
     }
 
-    // make elements [.., e_hi) (absolute) readable from the ring
+    // make elements below e_hi (absolute) readable from the ring
     __device__ __forceinline__ void ensure_ready(uint32_t e_hi)
     {
         if (!g.tma) return;
@@ -245,7 +250,7 @@ struct Kern {
         }
     }
 
-    // the enumerating node has read everything below e_read (absolute)
+    // node 1 has consumed every element below e_read (absolute): recycle tiles
     __device__ __forceinline__ void release_below(uint32_t e_read)
     {
         if (!g.tma) return;
@@ -267,8 +272,6 @@ struct Kern {
         return __ldg(g.elements + e);
     }
 
-    // drain outstanding copies (they must land before the shared memory is reused or
-    // the CTA exits); bounded like every wait
     __device__ __forceinline__ void finish_tiles()
     {
         if (!g.tma) return;
@@ -276,367 +279,454 @@ struct Kern {
         g.t_freed = g.t_ready;
     }
 
-    // ---- signal ring helpers ----
-    __device__ __forceinline__ void push_signal(int e, uint32_t word)
+    // ---- signal rings: slot j of edge e holds {word, credit} ----
+    __device__ __forceinline__ uint32_t sidx(int e, uint32_t cursor) const
     {
-        // Section 3.1 sender rules: empty signal queue -> credit = items queued now;
-        // else -> items emitted since the previous signal.
-        uint32_t credit = (w.sh[e] == w.st[e]) ? (w.qt[e] - w.qh[e]) : w.em[e];
-        if (lane == 0) {
-            uint32_t idx = e * P.SC + (w.st[e] & (P.SC - 1));
-            M.sq[2 * idx] = word;
-            M.sq[2 * idx + 1] = credit;
-        }
-        w.st[e]++;
-        w.em[e] = 0;
+        return 2u * (e * P.SC + (cursor & (P.SC - 1)));
     }
 
-    // ---- enumeration, tag strategy ----
-    // fills queue 0 with (element, local region) pairs, ensembles cut only by space
-    __device__ __forceinline__ void enum_tag(uint32_t &epos, uint32_t &ek)
+    // ---- enumeration (Section 4.2) ----
+    // Signal strategy: for each parent k, Begin(k), its L_k element positions, End(k).
+    // A batch of up to 32 parents is emitted at once, lane j handling parent ek + j; the
+    // credits follow the sender rules of Section 3.1 exactly as if emitted one by one:
+    // the first signal gets |Q| if the signal queue was empty, else the items emitted
+    // since the previous signal; a Begin after an End carries 0; End(k) carries L_k.
+    __device__ __forceinline__ void enum_signal()
     {
-        const uint32_t C = P.C, cm = C - 1;
-        const DevStage &s0 = P.st[0];
-        while (epos < total && !stop) {
-            uint32_t space = C - (w.qt[0] - w.qh[0]);
-            if (space == 0) break;
-            uint32_t take = min(min((uint32_t)RS_W, space), total - epos);
-            // window of the next 32 region ends after ek
-            uint32_t kk = ek + lane + 1;
-            uint32_t endj = M.moff[min(kk, nk)];
-            uint32_t end31 = __shfl_sync(FULLMASK, endj, 31);
-            if (ek + 32 <= nk) take = min(take, end31 - epos);
-            uint32_t nxt = __shfl_down_sync(FULLMASK, endj, 1);
-            uint32_t pj = endj - epos;
-            bool valid = (pj < take) && (lane == 31 || endj != nxt);
-            if (valid) M.scr[pj] = lane + 1;
-            uint32_t D = __reduce_or_sync(FULLMASK, valid ? (1u << pj) : 0u);
-            __syncwarp();
-            uint32_t myk = ek;
-            uint32_t mk = D & ((2u << lane) - 1u);
-            if (lane < take && mk) myk = ek + M.scr[31 - __clz(mk)];
-            uint32_t pos = epos + lane;
-            uint32_t x = 0;
-            if (s0.op == D_ENUM_HASH) {
-                if (lane < take) x = fmix32(M.mpar[myk] ^ fmix32((pos - M.moff[myk]) ^ RS_GOLD));
-            } else {
-                ensure_ready(E0 + epos + take);
-                if (stop) return;
-                if (lane < take) x = load_elem(E0 + pos);
-            }
-            if (lane < take) {
-                uint32_t slot = (w.qt[0] + lane) & cm;
-                M.qv[slot] = x;
-                M.qtag[slot] = myk;
+        const uint32_t SC = P.SC;
+        while (ek < nk) {
+            uint32_t room = (SC - (w.st[0] - w.sh[0])) >> 1;
+            uint32_t m = min(min(32u, room), nk - ek);
+            if (m == 0) break;
+            uint32_t k = ek + lane;
+            bool mine = lane < m;
+            uint32_t L = mine ? (M.moff[k + 1] - M.moff[k]) : 0u;
+            uint32_t Lsum = __reduce_add_sync(FULLMASK, L);
+            uint32_t first = (w.sh[0] == w.st[0]) ? (w.qt[0] - w.qh[0]) : w.em[0];
+            if (mine) {
+                uint32_t b = sidx(0, w.st[0] + 2 * lane), e = sidx(0, w.st[0] + 2 * lane + 1);
+                M.sq[b] = k;
+                M.sq[b + 1] = lane == 0 ? first : 0u;
+                M.sq[e] = SIG_END | k;
+                M.sq[e + 1] = L;
             }
             __syncwarp();
-            w.qt[0] += take;
-            epos += take;
+            w.st[0] += 2 * m;
+            w.qt[0] += Lsum;
+            w.em[0] = 0;
+            ek += m;
             w.c_ens[0]++;
-            w.c_items[0] += take;
-            ek = __shfl_sync(FULLMASK, myk, take - 1);
-            if (epos < total) {
-                // advance to the region containing epos (skipping empty regions)
-                for (;;) {
-                    uint32_t e2 = M.moff[min(ek + lane + 1, nk)];
-                    uint32_t cnt = __popc(__ballot_sync(FULLMASK, e2 <= epos));
-                    ek += cnt;
-                    if (cnt < 32) break;
-                }
-            }
-            if (s0.op == D_ENUM_LOAD) release_below(E0 + epos);
+            w.c_items[0] += Lsum;
         }
     }
 
-    // ---- enumeration, signal strategy ----
-    // per parent: Begin(k), its elements, End(k) (Section 4.2)
-    __device__ __forceinline__ void enum_signal(uint32_t &epos, uint32_t &ek, bool &begun)
+    // ---- parent of each of the positions [P0, P0+n) (tag strategy, node 1) ----
+    // ek1 contains P0.  Every non-empty parent starting inside the window marks its
+    // start; each lane takes the last mark at or before its position.
+    __device__ __forceinline__ uint32_t assign_parents(uint32_t P0, uint32_t n)
     {
-        const uint32_t C = P.C, cm = C - 1, SC = P.SC;
-        const DevStage &s0 = P.st[0];
-        while (ek < nk && !stop) {
-            if (!begun) {
-                if (w.st[0] - w.sh[0] >= SC) return;
-                push_signal(0, ek);
-                begun = true;
-            }
-            uint32_t re = M.moff[ek + 1];
-            while (epos < re) {
-                uint32_t space = C - (w.qt[0] - w.qh[0]);
-                if (space == 0) return;
-                uint32_t take = min(min((uint32_t)RS_W, space), re - epos);
-                uint32_t pos = epos + lane;
-                uint32_t x = 0;
-                if (s0.op == D_ENUM_HASH) {
-                    if (lane < take) x = fmix32(M.mpar[ek] ^ fmix32((pos - M.moff[ek]) ^ RS_GOLD));
-                } else {
-                    ensure_ready(E0 + epos + take);
-                    if (stop) return;
-                    if (lane < take) x = load_elem(E0 + pos);
-                }
-                if (lane < take) M.qv[(w.qt[0] + lane) & cm] = x;
-                __syncwarp();
-                w.qt[0] += take;
-                w.em[0] += take;
-                epos += take;
-                w.c_ens[0]++;
-                w.c_items[0] += take;
-                if (s0.op == D_ENUM_LOAD) release_below(E0 + epos);
-            }
-            if (w.st[0] - w.sh[0] >= SC) return;
-            push_signal(0, SIG_END | ek);
-            __syncwarp();
-            ek++;
-            begun = false;
+        uint32_t end0 = M.moff[ek1 + 1];
+        if (end0 >= P0 + n) return ek1;   // the whole window lies in one parent
+        uint32_t D = 0;
+        uint32_t base = ek1 + 1;
+        for (;;) {
+            uint32_t k = base + lane;
+            bool in = k < nk;
+            uint32_t st = in ? M.moff[k] : total;
+            uint32_t en = in ? M.moff[k + 1] : total;
+            bool mark = in && en > st && st < P0 + n;
+            if (mark) M.scr[st - P0] = k;
+            D |= __reduce_or_sync(FULLMASK, mark ? (1u << (st - P0)) : 0u);
+            uint32_t st31 = __shfl_sync(FULLMASK, st, 31);
+            if (!(base + 32 < nk && st31 < P0 + n)) break;
+            base += 32;
+        }
+        __syncwarp();
+        uint32_t mk = D & ((2u << lane) - 1u);
+        uint32_t myk = mk ? M.scr[31 - __clz(mk)] : ek1;
+        __syncwarp();
+        return myk;
+    }
+
+    // advance ek1 from parent `from` to the parent containing position pos (< total)
+    __device__ __forceinline__ void advance_ek1(uint32_t from, uint32_t pos)
+    {
+        ek1 = from;
+        for (;;) {
+            uint32_t e2 = M.moff[min(ek1 + lane + 1, nk)];
+            uint32_t cnt = __popc(__ballot_sync(FULLMASK, e2 <= pos));
+            ek1 += cnt;
+            if (cnt < 32) break;
         }
     }
 
-    // ---- one ensemble through an element stage (filter / map / expand) ----
+    // ---- gather one ensemble of node I: x[s], k[s] for lane's items 32 s + lane ----
     template <int I>
-    __device__ __forceinline__ void run_element_stage(uint32_t take)
+    __device__ __forceinline__ void gather(uint32_t take, uint32_t (&x)[V], uint32_t (&k)[V])
     {
-        const DevStage &s = P.st[I];
-        const uint32_t C = P.C, cm = C - 1;
-        const bool active = lane < take;
-        const uint32_t islot = (I - 1) * C + ((w.qh[I - 1] + lane) & cm);
-        uint32_t x = active ? M.qv[islot] : 0u;
-        uint32_t k = (STRAT == RS_STRATEGY_TAG) ? (active ? M.qtag[islot] : 0u) : w.ctxk[I];
-        if (s.op == D_EXPAND) {
-            uint32_t nout = active ? fmix32(x ^ s.c0) % (s.fanout + 1u) : 0u;
-            uint32_t incl = warp_incl_scan_u32(nout, lane);
-            uint32_t tot = __shfl_sync(FULLMASK, incl, 31);
-            uint32_t base = w.qt[I] + incl - nout;
-            for (uint32_t j = 0; j < nout; ++j) {
-                uint32_t y = fmix32(x ^ fmix32((s.p0 + 1u + j) ^ RS_GOLD));
-                uint32_t slot = I * C + ((base + j) & cm);
-                M.qv[slot] = y;
-                if (STRAT == RS_STRATEGY_TAG) M.qtag[slot] = k;
+        if constexpr (I == 1) {
+            const uint32_t q0 = w.qh[0];
+            const bool hashed = P.st[0].op == D_ENUM_HASH;
+            if (!hashed) {
+                ensure_ready(E0 + q0 + take);
             }
-            w.qt[I] += tot;
-            w.em[I] += tot;
+#pragma unroll
+            for (int s = 0; s < V; ++s) {
+                const uint32_t sb = 32u * s;
+                k[s] = 0;
+                x[s] = 0;
+                if (sb < take) {
+                    const uint32_t n = min(32u, take - sb);
+                    const uint32_t pos = q0 + sb + lane;
+                    uint32_t kk;
+                    if (STRAT == RS_STRATEGY_TAG) {
+                        kk = assign_parents(q0 + sb, n);
+                        uint32_t klast = __shfl_sync(FULLMASK, kk, n - 1);
+                        if (q0 + sb + n < total && M.moff[klast + 1] <= q0 + sb + n)
+                            advance_ek1(klast, q0 + sb + n);
+                        else
+                            ek1 = klast;
+                    } else {
+                        kk = w.ctxk[1];
+                    }
+                    k[s] = kk;
+                    if (lane < n) {
+                        if (hashed)
+                            x[s] = fmix32(M.mpar[kk] ^ fmix32((pos - M.moff[kk]) ^ RS_GOLD));
+                        else
+                            x[s] = load_elem(E0 + pos);
+                    }
+                }
+            }
         } else {
-            bool keep;
-            uint32_t y = x;
-            switch (s.op) {
-            case D_FILT_MASK: keep = (x & s.p0) == s.p1; break;
-            case D_FILT_MOD: keep = (x % s.p0) == s.p1; break;
-            case D_FILT_HASH_CTX: keep = (fmix32(x ^ s.c0) ^ M.mctx[k]) < s.p1; break;
-            case D_FILT_WEIGHT: keep = fmix32(x ^ s.c0) < fmix32(M.mpar[k] ^ s.c0); break;
-            case D_MAP_MULADD: y = x * s.p0 + s.p1; keep = true; break;
-            default: keep = false; break;
+            const uint32_t C = P.C, cm = C - 1;
+            const uint32_t rb = (I - 2) * C;   // input edge I-1 is ring I-2
+#pragma unroll
+            for (int s = 0; s < V; ++s) {
+                const uint32_t q = 32u * s + lane;
+                x[s] = 0;
+                k[s] = (STRAT == RS_STRATEGY_TAG) ? 0u : w.ctxk[I];
+                if (q < take) {
+                    const uint32_t slot = rb + ((w.qh[I - 1] + q) & cm);
+                    x[s] = M.qv[slot];
+                    if (STRAT == RS_STRATEGY_TAG) k[s] = M.qtag[slot];
+                }
             }
-            keep = keep && active;
-            uint32_t b = __ballot_sync(FULLMASK, keep);
-            if (keep) {
-                uint32_t slot = I * C + ((w.qt[I] + __popc(b & lanemask_lt())) & cm);
-                M.qv[slot] = y;
-                if (STRAT == RS_STRATEGY_TAG) M.qtag[slot] = k;
-            }
-            uint32_t np = __popc(b);
-            w.qt[I] += np;
-            w.em[I] += np;
         }
     }
 
-    // ---- one ensemble into the aggregate ----
+    // ---- one ensemble through element stage I (filter / map / expand) ----
     template <int I>
-    __device__ __forceinline__ void run_aggregate(uint32_t take)
+    __device__ __forceinline__ void element_stage(uint32_t take)
     {
+        const DevStage &sd = P.st[I];
         const uint32_t C = P.C, cm = C - 1;
-        const bool active = lane < take;
-        const uint32_t islot = (I - 1) * C + ((w.qh[I - 1] + lane) & cm);
-        uint32_t v = active ? M.qv[islot] : 0u;
+        const uint32_t orb = (I - 1) * C;   // output edge I is ring I-1
+        uint32_t x[V], k[V];
+        gather<I>(take, x, k);
+        if (sd.op == D_EXPAND) {
+#pragma unroll
+            for (int s = 0; s < V; ++s) {
+                if (32u * s < take) {
+                    const bool act = 32u * s + lane < take;
+                    uint32_t nout = act ? fmix32(x[s] ^ sd.c0) % (sd.fanout + 1u) : 0u;
+                    uint32_t incl = warp_incl_scan_u32(nout, lane);
+                    uint32_t tot = __shfl_sync(FULLMASK, incl, 31);
+                    uint32_t base = w.qt[I] + incl - nout;
+                    for (uint32_t j = 0; j < nout; ++j) {
+                        uint32_t y = fmix32(x[s] ^ fmix32((sd.p0 + 1u + j) ^ RS_GOLD));
+                        uint32_t slot = orb + ((base + j) & cm);
+                        M.qv[slot] = y;
+                        if (STRAT == RS_STRATEGY_TAG) M.qtag[slot] = (uint16_t)k[s];
+                    }
+                    w.qt[I] += tot;
+                    w.em[I] += tot;
+                }
+            }
+            return;
+        }
+        bool keep[V];
+        uint32_t y[V];
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            const uint32_t xs = x[s];
+            bool kp;
+            uint32_t ys = xs;
+            switch (sd.op) {
+            case D_FILT_MASK: kp = (xs & sd.p0) == sd.p1; break;
+            case D_FILT_MOD: kp = (xs % sd.p0) == sd.p1; break;
+            case D_FILT_HASH_CTX: kp = (fmix32(xs ^ sd.c0) ^ M.mctx[k[s]]) < sd.p1; break;
+            case D_FILT_WEIGHT: kp = fmix32(xs ^ sd.c0) < fmix32(M.mpar[k[s]] ^ sd.c0); break;
+            case D_MAP_MULADD: ys = xs * sd.p0 + sd.p1; kp = true; break;
+            default: kp = false; break;
+            }
+            keep[s] = kp && (32u * s + lane < take);
+            y[s] = ys;
+        }
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            if (32u * s < take) {
+                uint32_t b = __ballot_sync(FULLMASK, keep[s]);
+                if (keep[s]) {
+                    uint32_t slot = orb + ((w.qt[I] + __popc(b & lt)) & cm);
+                    M.qv[slot] = y[s];
+                    if (STRAT == RS_STRATEGY_TAG) M.qtag[slot] = (uint16_t)k[s];
+                }
+                uint32_t np = __popc(b);
+                w.qt[I] += np;
+                w.em[I] += np;
+            }
+        }
+    }
+
+    // ---- one ensemble into the aggregate (node I = n-1) ----
+    template <int I>
+    __device__ __forceinline__ void aggregate(uint32_t take)
+    {
+        uint32_t x[V], k[V];
+        gather<I>(take, x, k);
         if (STRAT == RS_STRATEGY_SIGNAL) {
-            // every item of the ensemble belongs to the current parent (Section 3.3)
+            // the whole ensemble belongs to the current parent (Section 3.3)
+            unsigned long long part = 0;
+            uint32_t mn = 0xFFFFFFFFu;
+#pragma unroll
+            for (int s = 0; s < V; ++s) {
+                if (32u * s + lane < take) {
+                    part += x[s];
+                    mn = min(mn, x[s]);
+                }
+            }
+            uint32_t lo = __reduce_add_sync(FULLMASK, (uint32_t)(part & 0xFFFFu));
+            uint32_t hi = __reduce_add_sync(FULLMASK, (uint32_t)(part >> 16));
             w.acc_c += take;
-            w.acc_s += warp_sum_u32_wide(v);
-            w.acc_m = min(w.acc_m, __reduce_min_sync(FULLMASK, active ? v : 0xFFFFFFFFu));
-        } else {
-            uint32_t k = active ? M.qtag[islot] : 0xFFFFFFFFu;
-            uint32_t kprev = __shfl_up_sync(FULLMASK, k, 1);
-            uint32_t knext = __shfl_down_sync(FULLMASK, k, 1);
-            bool head = (lane == 0) || (k != kprev);
-            bool tail = (lane == 31) || (k != knext);
-            uint32_t heads = __ballot_sync(FULLMASK, head);
-            uint32_t k0 = __shfl_sync(FULLMASK, k, 0);
-            uint32_t amask = (take >= 32) ? FULLMASK : ((1u << take) - 1u);
-            if ((heads & amask) == 1u) {
-                // one region in the whole ensemble
-                unsigned long long s = warp_sum_u32_wide(v);
-                uint32_t m = __reduce_min_sync(FULLMASK, active ? v : 0xFFFFFFFFu);
+            w.acc_s += ((unsigned long long)hi << 16) + lo;
+            w.acc_m = min(w.acc_m, __reduce_min_sync(FULLMASK, mn));
+            return;
+        }
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            const uint32_t sb = 32u * s;
+            if (sb >= take) break;
+            const uint32_t n = min(32u, take - sb);
+            const bool act = lane < n;
+            const uint32_t v = act ? x[s] : 0u;
+            const uint32_t kk = act ? k[s] : 0xFFFFFFFFu;
+            const uint32_t k0 = __shfl_sync(FULLMASK, kk, 0);
+            const uint32_t kl = __shfl_sync(FULLMASK, kk, n - 1);
+            if (k0 == kl) {
+                // one parent in the whole sub-ensemble (tags are non-decreasing)
+                unsigned long long sm = warp_sum_u32_wide(v);
+                uint32_t mn = __reduce_min_sync(FULLMASK, act ? v : 0xFFFFFFFFu);
                 if (lane == 0) {
-                    M.rc[k0] += take;
-                    M.rs[k0] += s;
-                    M.rm[k0] = min(M.rm[k0], m);
+                    M.rc[k0] += n;
+                    M.rs[k0] += sm;
+                    M.rm[k0] = min(M.rm[k0], mn);
                 }
             } else {
+                uint32_t kprev = __shfl_up_sync(FULLMASK, kk, 1);
+                uint32_t knext = __shfl_down_sync(FULLMASK, kk, 1);
+                bool head = (lane == 0) || (kk != kprev);
+                bool tail = (lane == 31) || (kk != knext);
+                uint32_t heads = __ballot_sync(FULLMASK, head);
                 uint32_t hl = 31 - __clz(heads & ((2u << lane) - 1u));
                 unsigned long long ps = v;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
-                    unsigned long long y = __shfl_up_sync(FULLMASK, ps, d);
-                    if (lane >= (uint32_t)d) ps += y;
+                    unsigned long long t = __shfl_up_sync(FULLMASK, ps, d);
+                    if (lane >= (uint32_t)d) ps += t;
                 }
                 unsigned long long before = __shfl_sync(FULLMASK, ps, hl > 0 ? hl - 1 : 0);
                 if (hl == 0) before = 0;
-                uint32_t m = active ? v : 0xFFFFFFFFu;
+                uint32_t m = act ? v : 0xFFFFFFFFu;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
-                    uint32_t y = __shfl_up_sync(FULLMASK, m, d);
-                    if (lane >= (uint32_t)d && lane - d >= hl) m = min(m, y);
+                    uint32_t t = __shfl_up_sync(FULLMASK, m, d);
+                    if (lane >= (uint32_t)d && lane - d >= hl) m = min(m, t);
                 }
-                if (active && tail) {
-                    M.rc[k] += lane - hl + 1;
-                    M.rs[k] += ps - before;
-                    M.rm[k] = min(M.rm[k], m);
+                if (act && tail) {
+                    M.rc[kk] += lane - hl + 1;
+                    M.rs[kk] += ps - before;
+                    M.rm[kk] = min(M.rm[kk], m);
                 }
             }
+            __syncwarp();
         }
-        __syncwarp();
     }
 
-    // ---- fire node I (1 <= I < n): data phase(s) and signal phase(s) ----
+    // ---- signal phase of node I (Section 3.2), receiver rule 2b ----
+    // While the counter is 0: if the head signal carries credit, move it to the counter
+    // and stop; otherwise consume the run of zero-credit signals at the head, up to 32
+    // at a time, one lane each.  Consuming a run in parallel gives the same state as
+    // consuming it one by one: the parent context is the last Begin's; the aggregate's
+    // End(k) reports the running accumulator unless a Begin precedes it in the run (an
+    // empty parent: identity); forwarded signals carry fresh credit by the sender rules
+    // (the first one |Q_out| or the items emitted since the last signal, the rest 0).
+    template <int I>
+    __device__ __forceinline__ bool signal_phase(bool last)
+    {
+        const uint32_t SC = P.SC;
+        bool progress = false;
+        while (w.credit[I] == 0 && w.sh[I - 1] != w.st[I - 1]) {
+            const uint32_t h = sidx(I - 1, w.sh[I - 1]);
+            const uint32_t hcr = M.sq[h + 1];
+            if (hcr > 0) {
+                w.credit[I] = hcr;
+                __syncwarp();
+                if (lane == 0) M.sq[h + 1] = 0;
+                __syncwarp();
+                progress = true;
+                break;
+            }
+            uint32_t room = 32u;
+            if constexpr (I + 1 < RS_MAX_STAGES) {
+                if (!last) room = SC - (w.st[I] - w.sh[I]);
+            }
+            const uint32_t mmax = min(min(32u, w.st[I - 1] - w.sh[I - 1]), room);
+            if (mmax == 0) break;
+            const bool in = lane < mmax;
+            const uint32_t j = sidx(I - 1, w.sh[I - 1] + lane);
+            const uint32_t word = in ? M.sq[j] : 0u;
+            const uint32_t cr = in ? M.sq[j + 1] : 1u;
+            const uint32_t nz = __ballot_sync(FULLMASK, cr != 0u);
+            const uint32_t m = nz ? (uint32_t)(__ffs(nz) - 1) : 32u;
+            const bool mine = lane < m;
+            const bool is_begin = mine && !(word & SIG_END);
+            const uint32_t begins = __ballot_sync(FULLMASK, is_begin);
+            if (begins) {
+                const uint32_t lb = 31 - __clz(begins);
+                w.ctxk[I] = __shfl_sync(FULLMASK, word, lb);
+            }
+            if (last) {
+                if (mine && (word & SIG_END)) {
+                    const uint32_t kk = word & ~SIG_END;
+                    const bool fresh = (begins & lanemask_lt()) != 0u;
+                    M.rc[kk] = fresh ? 0u : w.acc_c;
+                    M.rs[kk] = fresh ? 0ull : w.acc_s;
+                    M.rm[kk] = fresh ? 0xFFFFFFFFu : w.acc_m;
+                }
+                if (begins) {
+                    w.acc_c = 0;
+                    w.acc_s = 0;
+                    w.acc_m = 0xFFFFFFFFu;
+                }
+            } else {
+                if constexpr (I + 1 < RS_MAX_STAGES) {
+                    const uint32_t c0 = (w.sh[I] == w.st[I]) ? (w.qt[I] - w.qh[I]) : w.em[I];
+                    if (mine) {
+                        const uint32_t o = sidx(I, w.st[I] + lane);
+                        M.sq[o] = word;
+                        M.sq[o + 1] = lane == 0 ? c0 : 0u;
+                    }
+                    w.st[I] += m;
+                    w.em[I] = 0;
+                }
+            }
+            __syncwarp();
+            w.sh[I - 1] += m;
+            w.c_sig[I] += m;
+            progress = true;
+        }
+        return progress;
+    }
+
+    // ---- fire node I (1 <= I < n) ----
+    // drain: nothing more will arrive on node I's input (everything upstream is done),
+    // so partial ensembles are fired; otherwise only full ensembles, or ensembles cut
+    // by a pending signal's credit.
     template <int I>
     __device__ __forceinline__ void fire(bool drain)
     {
         if (I >= P.n_stages || stop) return;
-        const DevStage &s = P.st[I];
-        constexpr bool can_push = I + 1 < RS_MAX_STAGES;   // node I has an output queue slot
+        constexpr bool can_push = I + 1 < RS_MAX_STAGES;
         const bool last = !can_push || (I == P.n_stages - 1);
-        const uint32_t C = P.C, SC = P.SC;
+        const uint32_t fan = P.st[I].fanout;
         bool fired = false;
         for (;;) {
-            bool progress = false;
-            const bool sig_pending = (STRAT == RS_STRATEGY_SIGNAL) && (w.sh[I - 1] != w.st[I - 1]);
-            uint32_t avail = w.qt[I - 1] - w.qh[I - 1];
-            bool ready = drain ? (avail > 0 || sig_pending) : (avail >= RS_W || sig_pending);
-            if (!ready) break;
+            const bool sigp = (STRAT == RS_STRATEGY_SIGNAL) && (w.sh[I - 1] != w.st[I - 1]);
+            const uint32_t avail0 = w.qt[I - 1] - w.qh[I - 1];
+            if (!(drain ? (avail0 > 0 || sigp) : (avail0 >= W || sigp))) break;
             if (!fired) {
                 w.c_fire[I]++;
                 fired = true;
             }
-            // data phase (Section 3.2): min(queued, downstream space, credit if a signal is pending)
+            bool progress = false;
+            // data phase: min(queued, downstream space, credit while a signal is pending)
             for (;;) {
-                avail = w.qt[I - 1] - w.qh[I - 1];
-                uint32_t lim = sig_pending ? w.credit[I] : avail;
-                uint32_t take = min(min(avail, lim), (uint32_t)RS_W);
+                uint32_t want = min(w.qt[I - 1] - w.qh[I - 1], W);
+                if (sigp) want = min(want, w.credit[I]);
+                uint32_t take = want;
                 if constexpr (can_push) {
                     if (!last) {
-                        uint32_t space = C - (w.qt[I] - w.qh[I]);
-                        uint32_t fit = (s.fanout == 1u) ? space : space / s.fanout;
-                        take = min(take, fit);
+                        const uint32_t space = P.C - (w.qt[I] - w.qh[I]);
+                        take = min(take, fan == 1u ? space : space / fan);
                     }
                 }
                 if (take == 0) break;
-                // keep ensembles full unless a signal forces the cut or the unit drains
-                if (!drain && !sig_pending && take < RS_W) break;
+                if (take < want) break;                       // wait for downstream space
+                if (!drain && !sigp && take < W) break;       // wait for a full ensemble
                 if (last) {
-                    run_aggregate<I>(take);
+                    aggregate<I>(take);
                 } else {
-                    if constexpr (can_push) run_element_stage<I>(take);
+                    if constexpr (can_push) element_stage<I>(take);
                 }
+                if (stop) return;
                 __syncwarp();
                 w.qh[I - 1] += take;
-                if (sig_pending) w.credit[I] -= take;
+                if (sigp) w.credit[I] -= take;
                 w.c_ens[I]++;
                 w.c_items[I] += take;
                 progress = true;
-            }
-            // signal phase: while the counter is 0 (receiver rules 2b)
-            if (STRAT == RS_STRATEGY_SIGNAL) {
-                while (w.credit[I] == 0 && w.sh[I - 1] != w.st[I - 1]) {
-                    uint32_t idx = (I - 1) * SC + (w.sh[I - 1] & (SC - 1));
-                    uint32_t word = M.sq[2 * idx];
-                    uint32_t cr = M.sq[2 * idx + 1];
-                    if (cr > 0) {
-                        w.credit[I] = cr;          // move the head signal's credit to the counter
-                        __syncwarp();
-                        if (lane == 0) M.sq[2 * idx + 1] = 0;
-                        __syncwarp();
-                        progress = true;
-                        break;
-                    }
-                    if constexpr (can_push) {
-                        if (!last && w.st[I] - w.sh[I] >= SC) break;   // no room to forward
-                    }
-                    w.sh[I - 1]++;
-                    w.c_sig[I]++;
-                    uint32_t k = word & ~SIG_END;
-                    if (!(word & SIG_END)) {
-                        w.ctxk[I] = k;             // Begin: switch parent context
-                        if (last) {
-                            w.acc_c = 0;
-                            w.acc_s = 0;
-                            w.acc_m = 0xFFFFFFFFu; // begin()
-                        }
-                    } else if (last) {
-                        if (lane == 0) {           // end(): one result per parent
-                            M.rc[k] = w.acc_c;
-                            M.rs[k] = w.acc_s;
-                            M.rm[k] = w.acc_m;
-                        }
-                    }
-                    __syncwarp();
-                    if constexpr (can_push) {
-                        if (!last) push_signal(I, word);   // forward with fresh credit
-                    }
-                    __syncwarp();
-                    progress = true;
+                if constexpr (I == 1) {
+                    if (P.st[0].op == D_ENUM_LOAD) release_below(E0 + w.qh[0]);
                 }
             }
+            if (STRAT == RS_STRATEGY_SIGNAL) progress |= signal_phase<I>(last);
             if (!progress) break;
         }
     }
 
-    __device__ __forceinline__ bool queues_empty() const
+    __device__ __forceinline__ bool edge_empty(int e) const
     {
-        bool e = true;
-#pragma unroll
-        for (int i = 0; i < RS_MAX_EDGES; ++i)
-            if (i < P.n_stages - 1) e = e && (w.qh[i] == w.qt[i]) && (w.sh[i] == w.st[i]);
-        return e;
+        return (w.qh[e] == w.qt[e]) && (w.sh[e] == w.st[e]);
     }
 
-    // ---- run one unit to completion ----
+    // ---- run one unit to completion: the non-preemptive scheduler of Section 2.1 ----
+    // Each sweep offers every node a firing, upstream first.
     __device__ __forceinline__ void run_unit()
     {
-        uint32_t epos = 0, ek = 0;
-        bool begun = false;
 #pragma unroll
-        for (int i = 0; i < RS_MAX_EDGES; ++i) {
-            w.qh[i] = w.qt[i] = w.sh[i] = w.st[i] = w.em[i] = 0;
-        }
+        for (int i = 0; i < RS_MAX_EDGES; ++i) w.qh[i] = w.qt[i] = w.sh[i] = w.st[i] = w.em[i] = 0;
 #pragma unroll
         for (int i = 0; i < RS_MAX_STAGES; ++i) w.credit[i] = w.ctxk[i] = 0;
-        if (STRAT == RS_STRATEGY_TAG && total > 0) {
-            // first non-empty region
-            for (;;) {
-                uint32_t e2 = M.moff[min(ek + lane + 1, nk)];
-                uint32_t cnt = __popc(__ballot_sync(FULLMASK, e2 <= 0u));
-                ek += cnt;
-                if (cnt < 32) break;
-            }
-        }
         w.acc_c = 0;
         w.acc_s = 0;
         w.acc_m = 0xFFFFFFFFu;
+        ek = 0;
+        if (STRAT == RS_STRATEGY_TAG) {
+            // enumeration emits every position of the unit at once; node 1 derives tags
+            w.qt[0] = total;
+            w.c_ens[0]++;
+            w.c_items[0] += total;
+            ek1 = 0;
+            if (total > 0) advance_ek1(0, 0);
+        }
         for (unsigned long long sweep = 0;; ++sweep) {
-            bool drain;
-            if (STRAT == RS_STRATEGY_TAG) {
-                enum_tag(epos, ek);
-                drain = epos >= total;
-            } else {
-                enum_signal(epos, ek, begun);
-                drain = ek >= nk;
-            }
-            if (stop) return;
             w.c_fire[0]++;
-            fire<1>(drain);
-            fire<2>(drain);
-            fire<3>(drain);
-            fire<4>(drain);
-            fire<5>(drain);
-            if (drain && queues_empty()) break;
+            if (STRAT == RS_STRATEGY_SIGNAL) enum_signal();
+            bool d = (STRAT == RS_STRATEGY_TAG) || ek >= nk;
+            fire<1>(d);
+            d = d && edge_empty(0);
+            fire<2>(d);
+            d = d && (P.n_stages <= 2 || edge_empty(1));
+            fire<3>(d);
+            d = d && (P.n_stages <= 3 || edge_empty(2));
+            fire<4>(d);
+            d = d && (P.n_stages <= 4 || edge_empty(3));
+            fire<5>(d);
+            d = d && (P.n_stages <= 5 || edge_empty(4));
+            if (stop) return;
+            if (d) break;
             if (sweep >= P.budget) {
                 if (lane == 0) atomicOr(&P.hdr->status, ST_STALL);
                 stop = true;
@@ -648,8 +738,8 @@ struct Kern {
 
 // ---------------------------------------------------------------------------
 
-template <int STRAT>
-__global__ void __launch_bounds__(512) rs_pipeline_kernel(const __grid_constant__ KParams P)
+template <int STRAT, int V>
+__global__ void __launch_bounds__(256) rs_pipeline_kernel(const __grid_constant__ KParams P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -664,7 +754,7 @@ __global__ void __launch_bounds__(512) rs_pipeline_kernel(const __grid_constant_
     M.rs = (unsigned long long *)(wb + P.L.o_rs);
     M.rm = (uint32_t *)(wb + P.L.o_rm);
     M.qv = (uint32_t *)(wb + P.L.o_qv);
-    M.qtag = (uint32_t *)(wb + P.L.o_qt);
+    M.qtag = (uint16_t *)(wb + P.L.o_qt);
     M.sq = (uint32_t *)(wb + P.L.o_sq);
     M.scr = (uint32_t *)(wb + P.L.o_scr);
 
@@ -704,7 +794,7 @@ __global__ void __launch_bounds__(512) rs_pipeline_kernel(const __grid_constant_
         bool bad = false;
         uint32_t E0 = 0, total = 0;
 
-        // ---- parents of this unit: lengths -> local offsets (a1) ----
+        // ---- parents of this unit: lengths -> local offsets ----
         if (S.offsets) {
             uint32_t ob = S.offsets[r0];
             for (uint32_t k = lane; k <= nk; k += 32) M.moff[k] = S.offsets[r0 + k] - ob;
@@ -794,21 +884,20 @@ __global__ void __launch_bounds__(512) rs_pipeline_kernel(const __grid_constant_
         g.ntiles = g.tma ? (g.B - g.A + P.TE - 1) / P.TE : 0u;
         g.t_issued = g.t_ready = g.t_freed = 0;
 
-        Kern<STRAT> kern(P, M, w, g, lane);
-        kern.nk = nk;
-        kern.total = total;
-        kern.E0 = E0;
-        kern.r0 = r0;
-        if (g.tma) kern.issue_tiles();
-        kern.run_unit();
-        kern.finish_tiles();
-        if (kern.stop) {
+        Proc<STRAT, V> pr(P, M, w, g, lane);
+        pr.nk = nk;
+        pr.total = total;
+        pr.E0 = E0;
+        if (g.tma) pr.issue_tiles();
+        pr.run_unit();
+        pr.finish_tiles();
+        if (pr.stop) {
             stop = true;
             break;
         }
         __syncwarp();
 
-        // ---- per-region results, coalesced (a7) ----
+        // ---- per-parent results, coalesced ----
         for (uint32_t k = lane; k < nk; k += 32) {
             if (P.want_count) S.out_count[r0 + k] = M.rc[k];
             if (P.want_sum) S.out_sum[r0 + k] = M.rs[k];
@@ -817,7 +906,7 @@ __global__ void __launch_bounds__(512) rs_pipeline_kernel(const __grid_constant_
         __syncwarp();
     }
 
-    // ---- counters (a8) ----
+    // ---- counters ----
     if (lane == 0) {
         atomicAdd(&P.hdr->units, units);
 #pragma unroll
@@ -835,33 +924,37 @@ __global__ void __launch_bounds__(512) rs_pipeline_kernel(const __grid_constant_
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 
-static const void *kernel_ptr(int strategy)
+static const void *kernel_ptr(int strategy, int V)
 {
-    return strategy == RS_STRATEGY_SIGNAL ? (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL>
-                                          : (const void *)rs_pipeline_kernel<RS_STRATEGY_TAG>;
+    if (strategy == RS_STRATEGY_SIGNAL) {
+        if (V == 1) return (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, 1>;
+        if (V == 2) return (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, 2>;
+        return (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, 4>;
+    }
+    if (V == 1) return (const void *)rs_pipeline_kernel<RS_STRATEGY_TAG, 1>;
+    if (V == 2) return (const void *)rs_pipeline_kernel<RS_STRATEGY_TAG, 2>;
+    return (const void *)rs_pipeline_kernel<RS_STRATEGY_TAG, 4>;
 }
 
-int rs_kernel_occupancy(int strategy, int block, size_t smem, int *blocks_per_sm)
+int rs_kernel_occupancy(int strategy, int V, int block, size_t smem, int *blocks_per_sm)
 {
-    const void *f = kernel_ptr(strategy);
+    const void *f = kernel_ptr(strategy, V);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
     return (int)e;
 }
 
-int rs_kernel_max_smem_optin(size_t smem)
+int rs_kernel_max_smem_optin(int strategy, int V, size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(kernel_ptr(RS_STRATEGY_SIGNAL), cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(kernel_ptr(strategy, V), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(kernel_ptr(RS_STRATEGY_TAG), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return (int)e;
 }
 
 int rs_launch_kernel(const KParams &P, int grid, int block, size_t smem, void *stream)
 {
-    const void *f = kernel_ptr(P.strategy);
+    const void *f = kernel_ptr(P.strategy, (int)P.V);
     void *args[] = {(void *)&P};
     cudaError_t e = cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, (cudaStream_t)stream);
     return (int)e;

@@ -67,17 +67,19 @@ def test_invalid_pipelines_rejected(pipe):
 
 
 def test_queue_capacity_must_hold_worst_case_output():
-    # fan-out 4 needs >= 32 * 5 slots; 128 is too small, 256 is fine
-    st, _ = _create([("enum_hash",), ("expand", 4, 1), ("aggregate",)], queue_capacity=128)
+    # fan-out 4 at W = 128 needs >= 128 * 5 slots; 512 is too small, 1024 is fine
+    st, _ = _create([("enum_hash",), ("expand", 4, 1), ("aggregate",)], queue_capacity=512)
     assert st == rs.RS_ERR_INVALID
-    st, h = _create([("enum_hash",), ("expand", 4, 1), ("aggregate",)], queue_capacity=256)
+    st, h = _create([("enum_hash",), ("expand", 4, 1), ("aggregate",)], queue_capacity=1024)
     assert st == rs.RS_OK
     rs.lib().rs_pipeline_destroy(h)
     st, _ = _create(wl.pipeline_cascade(), queue_capacity=96)      # not a power of two
     assert st == rs.RS_ERR_INVALID
     st, _ = _create(wl.pipeline_cascade(), tiles_in_flight=3)
     assert st == rs.RS_ERR_INVALID
-    st, _ = _create(wl.pipeline_cascade(), ensemble_width=64)
+    st, _ = _create(wl.pipeline_cascade(), ensemble_width=48)
+    assert st == rs.RS_ERR_INVALID
+    st, _ = _create(wl.pipeline_cascade(), ensemble_width=128, tile_elements=64)   # tile < W
     assert st == rs.RS_ERR_INVALID
 
 
@@ -112,11 +114,13 @@ def test_stream_submit_validation_and_workspace_size():
 
 
 def test_opts_round_trip():
-    p = rs.Pipeline(wl.pipeline_cascade(), strategy="signal", queue_capacity=128, regions_per_unit=16)
+    p = rs.Pipeline(wl.pipeline_cascade(), strategy="signal", queue_capacity=512, regions_per_unit=16)
     o = p.opts
-    assert o["strategy"] == 0 and o["queue_capacity"] == 128 and o["regions_per_unit"] == 16
+    assert o["strategy"] == 0 and o["queue_capacity"] == 512 and o["regions_per_unit"] == 16
     p.set_opts(strategy="tag", warps_per_block=8)
     assert p.opts["strategy"] == 1 and p.opts["warps_per_block"] == 8
+    with pytest.raises(rs.RsError):
+        p.set_opts(warps_per_block=16)
     with pytest.raises(rs.RsError):
         p.set_opts(regions_per_unit=1000)
     p.close()
