@@ -212,9 +212,14 @@ def run_case(args, rs, torch):
     Used to give profilers a small, fixed launch sequence."""
     parts = args.case.split(":")
     mean, strat = float(parts[0]), parts[1]
-    n = 1 << int(parts[2]) if len(parts) > 2 else N_ELEM
+    n = 1 << int(parts[2]) if len(parts) > 2 and parts[2] else N_ELEM
+    opts = {}
+    if len(parts) > 3:
+        for kv in parts[3].split(","):
+            k, v = kv.split("=")
+            opts[k] = int(v)
     s = wl.cascade_stream(n_total=n, mean=mean, seed=SEED)
-    p = rs.Pipeline(wl.pipeline_cascade(), strategy=strat)
+    p = rs.Pipeline(wl.pipeline_cascade(), strategy=strat, **opts)
     out = p.submit(rs.to_device(s), outputs=("count", "sum"))
     p.timing_enable(args.steps + args.warmup)
     for _ in range(args.warmup):
@@ -230,7 +235,8 @@ def run_case(args, rs, torch):
     print(json.dumps({"case": args.case, "n": n, "regions": int(s["R"]), "kernel_ms": kms,
                       "items_per_s": n / (kms * 1e-3), "alg_gbs": ab / (kms * 1e-3) / 1e9,
                       "opts": p.opts, "active_lane_fraction": st["active_lane_fraction"],
-                      "ensembles": st["ensembles"], "firings": st["firings"]}), flush=True)
+                      "ensembles": st["ensembles"], "firings": st["firings"], "cycles": st["cycles"]}),
+          flush=True)
     del out
 
 
@@ -243,7 +249,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--case", default=None,
-                    help="MEAN:STRATEGY[:N_LOG2] -- run one stream with a fixed strategy (for profilers)")
+                    help="MEAN:STRATEGY[:N_LOG2[:OPT=V,...]] -- one stream, fixed strategy and options "
+                         "(a small fixed launch sequence for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

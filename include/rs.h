@@ -190,6 +190,12 @@ typedef struct {
     uint64_t items[RS_MAX_STAGES];     /* items consumed per node (active lanes)            */
     uint64_t signals[RS_MAX_STAGES];   /* signals consumed per node                         */
     uint64_t firings[RS_MAX_STAGES];   /* scheduler firings per node                        */
+    uint64_t cycles[16];               /* profiling build only (else 0): SM cycles summed over
+                                          processors in setup, look-back, tile waits, signal
+                                          emission, nodes 1..5 (slots 5..9, tile waits
+                                          included in node 1), result flush, lifetime, and
+                                          inside the nodes: node 1's gather, stage compute,
+                                          compaction, tile recycling                       */
 } rs_stats;
 
 /* Synchronise `stream`, read the workspace counters of the last rs_run and return

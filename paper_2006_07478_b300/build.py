@@ -9,6 +9,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "librs.so")
+PROF_LIB = os.path.join(HERE, "librs_prof.so")   # same code with the per-phase cycle counters
 SOURCES = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cu")))
 DEPS = SOURCES + sorted(glob.glob(os.path.join(HERE, "csrc", "*.h"))) + [os.path.join(ROOT, "include", "rs.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -17,30 +18,33 @@ FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std
 _lock = threading.Lock()
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in DEPS)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into librs.so if it is missing or older than its sources."""
+def build(force: bool = False, verbose: bool = False, profile: bool = False) -> str:
+    """Compile every .cu under csrc/ into librs.so (or, with profile=True, into
+    librs_prof.so with the cycle-breakdown counters) if missing or out of date."""
+    lib = PROF_LIB if profile else LIB
     with _lock:
-        if not force and not stale():
-            return LIB
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [NVCC, *FLAGS, "-I", os.path.join(ROOT, "include"), "-I", os.path.join(HERE, "csrc"),
+        if not force and not stale(lib):
+            return lib
+        tmp = lib + f".tmp{os.getpid()}"
+        extra = ["-DRS_PROFILE=1"] if profile else []
+        cmd = [NVCC, *FLAGS, *extra, "-I", os.path.join(ROOT, "include"), "-I", os.path.join(HERE, "csrc"),
                "-o", tmp, *SOURCES]
         out = subprocess.run(cmd, capture_output=True, text=True)
         if out.returncode != 0:
             raise RuntimeError("nvcc failed:\n" + out.stdout + out.stderr)
         if verbose:
             print(out.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force=True, verbose=True)
-    print(LIB)
+    print(build(force=True, verbose=True))
+    print(build(force=True, profile=True))

@@ -34,6 +34,7 @@ struct rs_pipeline {
     DevStream *table_host = nullptr;
     size_t table_cap = 0;
     bool table_dirty = true;
+    void *table_ws = nullptr;      // workspace the table's pointers refer to
     cudaEvent_t upload_done = nullptr;
     bool upload_pending = false;
     // graph
@@ -305,27 +306,71 @@ static uint32_t choose_K(const rs_pipeline *p, const rs_stream_desc &s)
     return K;
 }
 
-struct Plan {
-    uint64_t total_units;
-    uint32_t Kmax;
-    size_t hdr_bytes, lb_off, lb_bytes, table_off, table_bytes, total;
+struct StreamPlan {
+    uint32_t mode, K, n_units, plan_tiles, D;
+    size_t slots_off, ucount_off, planlb_off, rec_off;
 };
 
+struct Plan {
+    uint64_t total_units, plan_tiles;
+    uint32_t Kmax;
+    size_t hdr_bytes, zero_end, table_off, table_bytes, total;
+    std::vector<StreamPlan> sp;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Work decomposition and workspace layout for the submitted streams:
+// [header | per stream: slots, unit count, planner look-back words | per stream: unit
+//  records | stream table].  Everything before zero_end is cleared by every run.
 static Plan make_plan(const rs_pipeline *p)
 {
     Plan pl;
-    memset(&pl, 0, sizeof pl);
+    pl.total_units = pl.plan_tiles = 0;
     pl.Kmax = 1;
-    for (const auto &s : p->streams) {
-        uint32_t K = choose_K(p, s);
-        if (K > pl.Kmax) pl.Kmax = K;
-        pl.total_units += (s.n_regions + K - 1) / K;
+    pl.hdr_bytes = align256(sizeof(WsHeader));
+    const bool load = p->stages[0].kind == RS_ENUM_LOAD;
+    size_t off = pl.hdr_bytes;
+    pl.sp.resize(p->streams.size());
+    for (size_t i = 0; i < p->streams.size(); ++i) {
+        const rs_stream_desc &s = p->streams[i];
+        StreamPlan &q = pl.sp[i];
+        memset(&q, 0, sizeof q);
+        if (load) {
+            q.mode = UNIT_MERGE;
+            const uint32_t kp = p->opts.regions_per_unit ? p->opts.regions_per_unit : 128u;
+            q.D = RS_STEP_REGION * kp;           // a unit owns <= kp parents and holds <= D elements
+            q.K = kp + 1;                        // plus the parent continued from an earlier unit
+            uint64_t steps = (uint64_t)RS_STEP_REGION * s.n_regions + s.n_elements;
+            q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
+            q.plan_tiles = (uint32_t)((s.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE);
+        } else {
+            q.mode = UNIT_REGIONS;
+            q.K = choose_K(p, s);
+            q.n_units = (uint32_t)((s.n_regions + q.K - 1) / q.K);
+        }
+        if (q.K > pl.Kmax) pl.Kmax = q.K;
+        pl.total_units += q.n_units;
+        pl.plan_tiles += q.plan_tiles;
+        if (q.mode == UNIT_MERGE) {
+            q.slots_off = off;
+            off = align256(off + (size_t)q.n_units * sizeof(Slot));
+            q.ucount_off = off;
+            off = align256(off + 4);
+            q.planlb_off = off;
+            off = align256(off + (size_t)q.plan_tiles * 8);
+        }
     }
-    pl.hdr_bytes = (sizeof(WsHeader) + 255) & ~(size_t)255;
-    pl.lb_off = pl.hdr_bytes;
-    pl.lb_bytes = ((pl.total_units * 8) + 255) & ~(size_t)255;
-    pl.table_off = pl.lb_off + pl.lb_bytes;
-    pl.table_bytes = ((p->streams.size() * sizeof(DevStream)) + 255) & ~(size_t)255;
+    pl.zero_end = off;
+    for (size_t i = 0; i < p->streams.size(); ++i) {
+        StreamPlan &q = pl.sp[i];
+        if (q.mode == UNIT_MERGE) {
+            q.rec_off = off;
+            off = align256(off + ((size_t)q.n_units + 1) * sizeof(UnitRec));
+        }
+    }
+    pl.table_off = off;
+    pl.table_bytes = align256(p->streams.size() * sizeof(DevStream));
     pl.total = pl.table_off + pl.table_bytes;
     return pl;
 }
@@ -333,12 +378,20 @@ static Plan make_plan(const rs_pipeline *p)
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 
 static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax, bool any_load, bool need_ctx,
-                              bool need_par)
+                              bool need_par, bool want_min)
 {
     const rs_pipeline_opts &o = p->opts;
     SmemLayout L;
     memset(&L, 0, sizeof L);
     size_t off = 0;
+    L.o_prof = (uint32_t)off;
+    off += 8 * RS_PROF_SLOTS;
+    L.o_cnt = (uint32_t)off;
+    off += 8 * 4 * RS_MAX_STAGES;
+    L.o_pend = (uint32_t)off;
+    off += 128;   // the prefetched next unit's descriptor (a Pending record)
+    L.o_mmeta = (uint32_t)off;
+    off += 16;
     L.o_mbar = (uint32_t)off;
     off += any_load ? 8 * o.tiles_in_flight : 0;
     off = align_up(off, 16);
@@ -349,17 +402,20 @@ static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax,
     off += any_load ? (size_t)o.tiles_in_flight * o.tile_elements * 4 : 0;
     L.o_rs = (uint32_t)off;
     off += (size_t)Kmax * 8;
-    L.o_off = (uint32_t)off;
-    off += (size_t)(Kmax + 1) * 4;
-    off = align_up(off, 16);
-    L.o_ctx = (uint32_t)off;
-    off += need_ctx ? (size_t)Kmax * 4 : 0;
-    L.o_par = (uint32_t)off;
-    off += need_par ? (size_t)Kmax * 4 : 0;
+    for (int b = 0; b < 2; ++b) {
+        L.o_raw[b] = (uint32_t)off;
+        off += (size_t)(Kmax + 1) * 4;
+        L.o_moff[b] = (uint32_t)off;
+        off += (size_t)(Kmax + 1) * 4;
+        L.o_ctxb[b] = (uint32_t)off;
+        off += need_ctx ? (size_t)Kmax * 4 : 0;
+        L.o_parb[b] = (uint32_t)off;
+        off += need_par ? (size_t)Kmax * 4 : 0;
+    }
     L.o_rc = (uint32_t)off;
     off += (size_t)Kmax * 4;
     L.o_rm = (uint32_t)off;
-    off += (size_t)Kmax * 4;
+    off += want_min ? (size_t)Kmax * 4 : 0;
     off = align_up(off, 16);
     // rings for edges 1..n-2 (edge 0 carries element positions, staged in the tiles)
     const uint32_t nr = p->n_stages - 2;
@@ -429,7 +485,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
 
     // ---- stream table (pinned host copy, uploaded by every run) ----
     const size_t ns = p->streams.size();
-    if (p->table_dirty || !p->table_host) {
+    if (p->table_dirty || !p->table_host || p->table_ws != ws) {
         if (p->upload_pending) {
             if ((e = cudaEventSynchronize(p->upload_done)) != cudaSuccess) return cuda_fail(e);
             p->upload_pending = false;
@@ -443,12 +499,13 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
                 return cuda_fail(e);
             p->table_cap = cap;
         }
-        uint32_t base = 0;
+        uint32_t base = 0, pbase = 0;
+        unsigned char *wsd = (unsigned char *)ws;
         for (size_t i = 0; i < ns; ++i) {
             const rs_stream_desc &s = p->streams[i];
+            const StreamPlan &q = pl.sp[i];
             DevStream &d = p->table_host[i];
             memset(&d, 0, sizeof d);
-            uint32_t K = choose_K(p, s);
             d.parents = s.parents;
             d.len = s.region_len;
             d.offsets = s.region_offsets;
@@ -459,13 +516,25 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
             d.out_min = s.out_min;
             d.n_elements = s.n_elements;
             d.R = (uint32_t)s.n_regions;
-            d.K = K;
-            d.n_units = (uint32_t)((s.n_regions + K - 1) / K);
+            d.K = q.K;
+            d.n_units = q.n_units;
             d.unit_base = base;
             d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
+            d.mode = q.mode;
+            if (q.mode == UNIT_MERGE) {
+                d.rec = (UnitRec *)(wsd + q.rec_off);
+                d.slots = (Slot *)(wsd + q.slots_off);
+                d.u_count = (uint32_t *)(wsd + q.ucount_off);
+                d.plan_lb = (unsigned long long *)(wsd + q.planlb_off);
+                d.plan_tiles = q.plan_tiles;
+                d.plan_base = pbase;
+                d.D = q.D;
+                pbase += q.plan_tiles;
+            }
             base += d.n_units;
         }
         p->table_dirty = false;
+        p->table_ws = ws;
     }
 
     // ---- kernel parameters ----
@@ -481,9 +550,9 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.strategy = strategy;
     P.n_streams = (uint32_t)ns;
     P.total_units = (uint32_t)pl.total_units;
+    P.plan_tiles = (uint32_t)pl.plan_tiles;
     P.streams = (const DevStream *)(wsb + pl.table_off);
     P.hdr = (WsHeader *)wsb;
-    P.lookback = (unsigned long long *)(wsb + pl.lb_off);
     P.V = o.ensemble_width / RS_W;
     P.C = o.queue_capacity;
     P.SC = o.signal_capacity;
@@ -508,7 +577,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
     P.budget = o.device_budget;
     P.spin_limit = 2000000000ull;   // 2 s on the global timer
-    P.L = make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par);
+    P.L = make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
 
     Lc.block = (int)o.warps_per_block * 32;
     Lc.smem = (size_t)P.L.per_warp * o.warps_per_block;
@@ -516,7 +585,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     if (pl.total_units == 0) return RS_OK;
     if (Lc.grid == 0) {
         int bps = 0;
-        int ce = rs_kernel_occupancy(strategy, (int)P.V, Lc.block, Lc.smem, &bps);
+        int ce = rs_kernel_occupancy(P, Lc.block, Lc.smem, &bps);
         if (ce != 0) return cuda_fail((cudaError_t)ce);
         if (bps == 0) return RS_ERR_CAPACITY;
         Lc.grid = bps * p->n_sm;
@@ -526,7 +595,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
             if (Lc.grid < 1) Lc.grid = 1;
         }
     } else {
-        int ce = rs_kernel_max_smem_optin(strategy, (int)P.V, Lc.smem);
+        int ce = rs_kernel_max_smem_optin(P, Lc.smem);
         if (ce != 0) return cuda_fail((cudaError_t)ce);
     }
     return RS_OK;
@@ -538,7 +607,7 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
     if (Lc.pl.total_units == 0) return RS_OK;   // only empty streams: nothing to launch
     cudaError_t e;
     unsigned char *wsb = (unsigned char *)ws;
-    if ((e = cudaMemsetAsync(wsb, 0, Lc.pl.table_off, stream)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(wsb, 0, Lc.pl.zero_end, stream)) != cudaSuccess) return cuda_fail(e);
     if ((e = cudaMemcpyAsync(wsb + Lc.pl.table_off, p->table_host, p->streams.size() * sizeof(DevStream),
                              cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         return cuda_fail(e);
@@ -553,8 +622,22 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
     const bool timed = !capturing && p->t_cap > 0;
     const uint32_t slot = timed ? (p->t_count % p->t_cap) : 0;
     if (timed && (e = cudaEventRecord(p->tev[2 * slot], stream)) != cudaSuccess) return cuda_fail(e);
+    if (Lc.P.plan_tiles > 0) {
+        // planner: offsets and merge-path unit records for every UNIT_MERGE stream
+        int pg = (int)((Lc.P.plan_tiles + 7) / 8);
+        int cap = p->n_sm * 8;
+        if (pg > cap) pg = cap;
+        if (pg < 1) pg = 1;
+        int le = rs_launch_planner(Lc.P, pg, (void *)stream);
+        if (le != 0) return cuda_fail((cudaError_t)le);
+    }
     int le = rs_launch_kernel(Lc.P, Lc.grid, Lc.block, Lc.smem, (void *)stream);
     if (le != 0) return cuda_fail((cudaError_t)le);
+    if (Lc.P.plan_tiles > 0) {
+        int fg = p->n_sm * 4;
+        le = rs_launch_finalize(Lc.P, fg, (void *)stream);
+        if (le != 0) return cuda_fail((cudaError_t)le);
+    }
     if (timed) {
         if ((e = cudaEventRecord(p->tev[2 * slot + 1], stream)) != cudaSuccess) return cuda_fail(e);
         p->t_count++;
@@ -624,6 +707,7 @@ rs_status rs_get_stats(rs_pipeline *p, const void *workspace, rs_cuda_stream str
         out->signals[i] = h.counters[4 * i + 2];
         out->firings[i] = h.counters[4 * i + 3];
     }
+    for (int i = 0; i < RS_PROF_SLOTS && i < 16; ++i) out->cycles[i] = h.cyc[i];
     if (h.status & (ST_STALL | ST_LOOKBACK_TIMEOUT | ST_COPY_TIMEOUT | ST_OVERFLOW)) return RS_ERR_STALL;
     if (h.status & ST_BAD_INPUT) return RS_ERR_DEVICE_INPUT;
     return RS_OK;

@@ -32,6 +32,30 @@ struct DevStage {
     uint32_t pad[3];
 };
 
+// Work decomposition of a stream.
+enum : uint32_t {
+    UNIT_REGIONS = 0,   // a unit is K whole consecutive parents (hashed elements: no offsets needed)
+    UNIT_MERGE = 1,     // merge-path units: a parent costs RS_STEP_REGION steps, an element 1 step,
+                        // a unit is D steps (DevStream.D); parents straddling units are split
+};
+#define RS_STEP_REGION 16u   // merge-path steps per parent (a unit of D steps owns <= D/16 parents)
+#define RS_PLAN_TILE 1024u                                  // parents per planner tile
+
+// Start of merge-path unit u: i = parents whose header step lies before u*D, j = absolute
+// index of the unit's first element, head_off / first_off = absolute offsets of parents
+// i-1 and i.
+struct UnitRec {
+    uint32_t i, j, head_off, first_off;
+};
+
+// Partial aggregate of a parent processed in pieces (indexed by the unit owning it).
+struct Slot {
+    unsigned long long sum;
+    uint32_t count, min_inv;   // min_inv = max of ~value: 0 is the identity
+    uint32_t region;           // parent id + 1, set by the owning unit; 0 = slot unused
+    uint32_t pad;
+};
+
 // Stream table entry (lives in the workspace).
 struct DevStream {
     const uint32_t *parents;
@@ -44,11 +68,18 @@ struct DevStream {
     uint32_t *out_min;
     uint64_t n_elements;
     uint32_t R;
-    uint32_t K;          // parents per unit
-    uint32_t n_units;
+    uint32_t K;          // parents per unit (UNIT_REGIONS)
+    uint32_t n_units;    // units (UNIT_MERGE: an upper bound; the planner records the count)
     uint32_t unit_base;  // first global ticket of this stream
     uint32_t tma_ok;     // elements pointer 16-byte aligned: stage tiles with bulk copies
-    uint32_t pad;
+    uint32_t mode;       // UNIT_REGIONS or UNIT_MERGE
+    // UNIT_MERGE only (workspace arrays)
+    UnitRec *rec;        // n_units + 1 records
+    Slot *slots;         // n_units slots
+    uint32_t *u_count;   // units actually used, written by the planner
+    unsigned long long *plan_lb;   // planner look-back words, one per planner tile
+    uint32_t plan_tiles, plan_base;
+    uint32_t D;          // merge-path steps per unit
 };
 
 // Status bits written by the device.
@@ -59,20 +90,41 @@ enum : uint32_t {
     ST_BAD_INPUT = 8u,
     ST_OVERFLOW = 16u,
 };
+#define ST_ANY_STALL (ST_STALL | ST_LOOKBACK_TIMEOUT | ST_COPY_TIMEOUT | ST_OVERFLOW)
+
+// Cycle-breakdown slots (optional profiling counters).
+enum : int {
+    PF_SETUP = 0,      // claim + stream lookup + lengths/offsets + context loads
+    PF_LOOKBACK = 1,   // waiting on predecessors' prefix words
+    PF_TILEWAIT = 2,   // waiting for bulk copies to land
+    PF_ENUM = 3,       // enumeration (signal emission)
+    PF_NODE0 = 4,      // PF_NODE0 + i: firing node i (1..5), minus tile waits
+    PF_FLUSH = 10,     // writing per-parent results
+    PF_TOTAL = 11,     // whole warp lifetime
+    PF_GATHER1 = 12,   // node 1: parents and elements of an ensemble (inside node 1)
+    PF_COMPUTE = 13,   // element stages: the stage's op on the ensemble (inside nodes)
+    PF_COMPACT = 14,   // element stages: ballot compaction into the next ring (inside nodes)
+    PF_TILES = 15,     // node 1: recycling tiles and issuing bulk copies (inside node 1)
+    RS_PROF_SLOTS = 16
+};
 
 // Workspace header (reset by a memset before every run).
 struct WsHeader {
     unsigned int cursor;
     unsigned int status;
-    unsigned int pad[14];
+    unsigned int plan_cursor;
+    unsigned int pad[13];
     unsigned long long units;
     unsigned long long counters[4 * RS_MAX_STAGES];   // ensembles, items, signals, firings
+    // optional cycle breakdown (KParams.profile): SM clock cycles summed over warps
+    unsigned long long cyc[RS_PROF_SLOTS];
 };
 
 // Per-warp shared-memory layout (byte offsets from the warp's base).
 struct SmemLayout {
     uint32_t per_warp;
-    uint32_t o_mbar, o_tiles, o_off, o_ctx, o_par, o_rc, o_rs, o_rm, o_qv, o_qt, o_sq, o_scr;
+    uint32_t o_prof, o_cnt, o_pend, o_mbar, o_mmeta, o_tiles, o_rc, o_rs, o_rm, o_qv, o_qt, o_sq, o_scr;
+    uint32_t o_raw[2], o_moff[2], o_ctxb[2], o_parb[2];   // double-buffered unit metadata
 };
 
 struct KParams {
@@ -81,6 +133,7 @@ struct KParams {
     int strategy;                 // RS_STRATEGY_SIGNAL or RS_STRATEGY_TAG
     uint32_t n_streams;
     uint32_t total_units;
+    uint32_t plan_tiles;          // planner tickets over all UNIT_MERGE streams
     const DevStream *streams;
     WsHeader *hdr;
     unsigned long long *lookback; // one word per unit
@@ -90,10 +143,14 @@ struct KParams {
     uint32_t any_load;
     unsigned long long budget;
     unsigned long long spin_limit;
+    uint32_t profile;             // accumulate the cycle breakdown
     SmemLayout L;
 };
 
-// Launch helper implemented in rs_kernel.cu.
+// Launch helpers implemented in rs_kernel.cu.
 int rs_launch_kernel(const KParams &P, int grid, int block, size_t smem, void *stream);
-int rs_kernel_max_smem_optin(int strategy, int V, size_t smem);
-int rs_kernel_occupancy(int strategy, int V, int block, size_t smem, int *blocks_per_sm);
+int rs_launch_planner(const KParams &P, int grid, void *stream);
+int rs_launch_finalize(const KParams &P, int grid, void *stream);
+int rs_kernel_max_smem_optin(const KParams &P, size_t smem);
+int rs_kernel_occupancy(const KParams &P, int block, size_t smem, int *blocks_per_sm);
+int rs_kernel_is_specialised(const KParams &P);

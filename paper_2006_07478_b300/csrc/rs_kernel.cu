@@ -30,6 +30,22 @@
 #include "rs_internal.h"
 
 #define FULLMASK 0xFFFFFFFFu
+
+// Cycle breakdown, compiled in only for the profiling build (-DRS_PROFILE=1): lane 0
+// of each warp adds SM clock cycles per phase into a per-warp shared-memory array,
+// folded into the workspace header at exit.
+#ifdef RS_PROFILE
+#define PROF_NOW() clock64()
+#define PROF_ADD(slot, t0)                                   \
+    do {                                                     \
+        if (lane == 0) M.prof[slot] += clock64() - (t0);     \
+    } while (0)
+#else
+#define PROF_NOW() 0ll
+#define PROF_ADD(slot, t0) \
+    do {                   \
+    } while (0)
+#endif
 #define LB_AGG (1ull << 62)
 #define LB_INCL (2ull << 62)
 #define LB_VAL ((1ull << 62) - 1)
@@ -96,6 +112,31 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// 4-byte asynchronous copy global -> shared (no register staging)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// arrive on an mbarrier once all of this thread's earlier cp.async copies have landed
+__device__ __forceinline__ void cp_async_arrive(unsigned long long *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -146,6 +187,28 @@ __device__ __forceinline__ unsigned long long warp_sum_u32_wide(uint32_t v)
 }
 
 // ---------------------------------------------------------------------------
+// Shared memory: one dynamic array; every per-processor array is addressed by a
+// 32-bit element index into it, so all accesses are shared-memory loads and stores
+// with 32-bit address arithmetic.
+
+extern __shared__ __align__(128) unsigned char smem_raw[];
+
+template <typename T>
+struct SArr {
+    uint32_t base;   // index of element 0, in units of T, from the start of smem_raw
+    __device__ __forceinline__ T &operator[](uint32_t i) const { return reinterpret_cast<T *>(smem_raw)[base + i]; }
+    __device__ __forceinline__ T *ptr() const { return reinterpret_cast<T *>(smem_raw) + base; }
+};
+
+template <typename T>
+__device__ __forceinline__ SArr<T> sarr(uint32_t byte_off)
+{
+    SArr<T> a;
+    a.base = byte_off / (uint32_t)sizeof(T);
+    return a;
+}
+
+// ---------------------------------------------------------------------------
 // per-warp (per-processor) state, all warp-uniform, held in registers
 
 struct Warp {
@@ -160,16 +223,17 @@ struct Warp {
     // aggregate accumulator (signal strategy)
     uint32_t acc_c, acc_m;
     unsigned long long acc_s;
-    // counters
-    unsigned long long c_ens[RS_MAX_STAGES], c_items[RS_MAX_STAGES], c_sig[RS_MAX_STAGES],
-        c_fire[RS_MAX_STAGES];
 };
 
 struct Smem {
-    unsigned long long *mbar;
-    uint32_t *tiles, *moff, *mctx, *mpar, *rc, *rm, *qv, *sq, *scr;
-    uint16_t *qtag;
-    unsigned long long *rs;
+    SArr<unsigned long long> prof, mbar, mmeta, rs, cnt;   // cnt: per node {ensembles, items, signals, firings}
+    SArr<uint32_t> tiles, moff, mctx, mpar, rc, rm, qv, sq, scr;
+    SArr<uint16_t> qtag;
+    SArr<uint32_t> mraw0, mraw1, mmoff0, mmoff1, mctx0, mctx1, mpar0, mpar1;
+    __device__ __forceinline__ SArr<uint32_t> raw(uint32_t b) const { return b ? mraw1 : mraw0; }
+    __device__ __forceinline__ SArr<uint32_t> moffb(uint32_t b) const { return b ? mmoff1 : mmoff0; }
+    __device__ __forceinline__ SArr<uint32_t> ctxb(uint32_t b) const { return b ? mctx1 : mctx0; }
+    __device__ __forceinline__ SArr<uint32_t> parb(uint32_t b) const { return b ? mpar1 : mpar0; }
 };
 
 // element staging for one unit
@@ -177,6 +241,8 @@ struct Stage {
     const uint32_t *elements;
     uint32_t A, B;          // bulk-copied element range [A, B) (absolute, 16-byte aligned)
     uint32_t ntiles, t_issued, t_ready, t_freed;
+    uint32_t ready_lim;     // every element below this (absolute) is readable
+    uint32_t free_lim;      // node 1 reading at or past this frees the oldest tile
     uint32_t phase;         // bit s = parity of slot s's next completion
     bool tma;
     bool failed;
@@ -184,7 +250,371 @@ struct Stage {
 
 // ---------------------------------------------------------------------------
 
-template <int STRAT, int V>
+// A claimed work unit.  UNIT_REGIONS: K whole consecutive parents starting at r0.
+// UNIT_MERGE: the elements [j0, j1) of the stream and the parents whose header step
+// lies in the unit ([i0, i1)), preceded by the parent continued from an earlier unit
+// (the head) when some of its elements fall in [j0, j1).
+struct Unit {
+    uint32_t ticket, stream, lu, r0, nk;
+    uint32_t i0, i1, j0, j1, head_off, first_off, ebase;
+    bool valid, skip, has_head;
+};
+
+// The next unit, prefetched while the current one runs: its parents' lengths (or CSR
+// offsets), context words and ids land in metadata buffer `buf` by cp.async and are
+// turned into unit-local offsets once they have landed.
+struct Pending {
+    Unit u;
+    uint32_t buf, phase;     // metadata buffer; mbarrier parity of each buffer (bit b)
+    bool scanned, bad, split_tail;
+    uint32_t total, E0;      // elements in the unit and absolute index of its first one
+    uint32_t tail_off, tail_len;   // absolute offset and length of the last owned parent
+};
+
+static_assert(sizeof(Pending) <= 128, "the prefetched unit record must fit its shared-memory slot");
+
+__device__ __forceinline__ Unit describe_unit(const KParams &P, uint32_t ticket)
+{
+    Unit u;
+    u.ticket = ticket;
+    u.valid = ticket < P.total_units;
+    u.skip = false;
+    u.has_head = false;
+    u.stream = u.lu = u.r0 = u.nk = 0;
+    u.i0 = u.i1 = u.j0 = u.j1 = u.head_off = u.first_off = u.ebase = 0;
+    if (!u.valid) return u;
+    // stream owning this ticket: the last one whose unit_base <= ticket
+    uint32_t lo = 0, hi = P.n_streams - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (P.streams[mid].unit_base <= ticket) lo = mid; else hi = mid - 1;
+    }
+    const DevStream &S = P.streams[lo];
+    u.stream = lo;
+    u.lu = ticket - S.unit_base;
+    if (S.mode == UNIT_MERGE) {
+        if (u.lu >= *S.u_count) {   // beyond the units the planner laid out
+            u.skip = true;
+            return u;
+        }
+        const UnitRec a = S.rec[u.lu], b = S.rec[u.lu + 1];
+        u.i0 = a.i;
+        u.j0 = a.j;
+        u.head_off = a.head_off;
+        u.first_off = a.first_off;
+        u.i1 = b.i;
+        u.j1 = b.j;
+        u.ebase = S.rec[0].j;
+        u.has_head = u.j0 < u.first_off;
+        u.r0 = u.has_head ? u.i0 - 1 : u.i0;
+        u.nk = (u.has_head ? 1u : 0u) + (u.i1 - u.i0);
+        if (u.nk > S.D / RS_STEP_REGION + 1 || u.j1 < u.j0 || u.i1 < u.i0) u.skip = true;   // inconsistent records
+    } else {
+        u.r0 = u.lu * S.K;
+        u.nk = min(S.K, S.R - u.r0);
+    }
+    return u;
+}
+
+// issue the unit's metadata copies into buffer b; every lane arrives on mmeta[b]
+__device__ __forceinline__ void prefetch_meta(const KParams &P, Smem &M, const Unit &u, uint32_t b,
+                                              uint32_t lane)
+{
+    const DevStream &S = P.streams[u.stream];
+    if (!u.skip) {
+        if (S.mode == UNIT_MERGE) {
+            const uint32_t hh = u.has_head ? 1u : 0u, no = u.i1 - u.i0;
+            if (S.offsets) {
+                for (uint32_t q = lane; q <= no; q += 32) cp_async4(M.raw(b).ptr() + hh + q, S.offsets + u.i0 + q);
+            } else {
+                for (uint32_t q = lane; q < no; q += 32) cp_async4(M.raw(b).ptr() + hh + q, S.len + u.i0 + q);
+            }
+        } else if (S.offsets) {
+            for (uint32_t k = lane; k <= u.nk; k += 32) cp_async4(M.raw(b).ptr() + k, S.offsets + u.r0 + k);
+        } else {
+            for (uint32_t k = lane; k < u.nk; k += 32) cp_async4(M.raw(b).ptr() + k, S.len + u.r0 + k);
+        }
+        if (P.need_ctx && S.ctx)
+            for (uint32_t k = lane; k < u.nk; k += 32) cp_async4(M.ctxb(b).ptr() + k, S.ctx + u.r0 + k);
+        if (P.need_par && S.parents)
+            for (uint32_t k = lane; k < u.nk; k += 32) cp_async4(M.parb(b).ptr() + k, S.parents + u.r0 + k);
+    }
+    cp_async_arrive(&M.mmeta[b]);
+}
+
+// Metadata of `pu` has landed: build the unit-local offsets moff[0..nk] (positions of
+// each parent's first element relative to the unit's first element, clamped to the
+// unit) and note whether the last owned parent continues into later units.
+__device__ __forceinline__ void scan_meta(Pending &pu, const KParams &P, Smem &M, uint32_t lane)
+{
+    const DevStream &S = P.streams[pu.u.stream];
+    const SArr<uint32_t> raw = M.raw(pu.buf);
+    const SArr<uint32_t> mo = M.moffb(pu.buf);
+    const uint32_t nk = pu.u.nk;
+    pu.bad = false;
+    pu.split_tail = false;
+    pu.tail_off = pu.tail_len = 0;
+    if (pu.u.skip) {
+        pu.total = 0;
+        pu.E0 = 0;
+        pu.scanned = true;
+        return;
+    }
+    if (S.mode == UNIT_MERGE) {
+        const uint32_t hh = pu.u.has_head ? 1u : 0u, no = pu.u.i1 - pu.u.i0;
+        const uint32_t j0 = pu.u.j0, tot = pu.u.j1 - pu.u.j0;
+        uint32_t carry = pu.u.first_off;   // absolute offset of the first owned parent
+        bool dec = false;
+        for (uint32_t b = 0; b < no; b += 32) {
+            const uint32_t q = b + lane;
+            uint32_t start, L = 0;
+            if (S.offsets) {
+                start = q < no ? raw[hh + q] : 0u;
+                L = q < no ? raw[hh + q + 1] - start : 0u;
+                dec |= q < no && raw[hh + q + 1] < start;
+            } else {
+                L = q < no ? raw[hh + q] : 0u;
+                const uint32_t incl = warp_incl_scan_u32(L, lane);
+                start = carry + incl - L;
+                carry += __shfl_sync(FULLMASK, incl, 31);
+            }
+            if (q < no) {
+                const uint32_t rel = start > j0 ? start - j0 : 0u;
+                mo[hh + q] = min(rel, tot);
+                if (q == no - 1) {
+                    pu.tail_off = start;   // lane-local; broadcast below
+                    pu.tail_len = L;
+                }
+            }
+        }
+        // the last owned parent's offset and length, from the lane that saw it
+        if (no > 0) {
+            const uint32_t src = (no - 1) & 31u;
+            pu.tail_off = __shfl_sync(FULLMASK, pu.tail_off, src);
+            pu.tail_len = __shfl_sync(FULLMASK, pu.tail_len, src);
+            pu.split_tail = (unsigned long long)pu.tail_off + pu.tail_len > pu.u.j1;
+        }
+        if (lane == 0) {
+            if (hh) mo[0] = 0;
+            mo[nk] = tot;
+        }
+        pu.bad = __any_sync(FULLMASK, dec);
+        pu.total = tot;
+        pu.E0 = j0;
+    } else if (S.offsets) {
+        const uint32_t ob = raw[0];
+        bool dec = false;
+        for (uint32_t k = lane; k <= nk; k += 32) {
+            const uint32_t o = raw[k];
+            dec |= o < ob;
+            mo[k] = o - ob;
+        }
+        __syncwarp();
+        for (uint32_t k = lane; k < nk; k += 32) dec |= mo[k + 1] < mo[k];
+        pu.bad = __any_sync(FULLMASK, dec);
+        pu.total = mo[nk];
+        pu.E0 = ob;
+    } else {
+        uint32_t carry = 0;
+        for (uint32_t b = 0; b < nk; b += 32) {
+            const uint32_t k = b + lane;
+            const uint32_t L = (k < nk) ? raw[k] : 0u;
+            const uint32_t incl = warp_incl_scan_u32(L, lane);
+            if (k < nk) mo[k] = carry + incl - L;
+            carry += __shfl_sync(FULLMASK, incl, 31);
+        }
+        if (lane == 0) mo[nk] = carry;
+        pu.total = carry;
+        pu.E0 = 0;
+    }
+    __syncwarp();
+    pu.scanned = true;
+}
+
+// non-blocking: build the pending unit's offsets if its metadata has landed
+__device__ __forceinline__ void poll_next(Pending &pu, const KParams &P, Smem &M, uint32_t lane)
+{
+    if (!pu.u.valid || pu.scanned) return;
+    if (!__all_sync(FULLMASK, mbar_test_wait(&M.mmeta[pu.buf], (pu.phase >> pu.buf) & 1u))) return;
+    pu.phase ^= 1u << pu.buf;
+    scan_meta(pu, P, M, lane);
+}
+
+// A parent processed in pieces: fold this piece's partial aggregate into the slot of
+// the unit owning the parent (reductions, no returned value, no fence); the owner also
+// records the parent id, and the finalize kernel writes the merged result after this
+// kernel.  Integer count / sum / min are associative and commutative, so the result
+// does not depend on the order of the pieces.
+__device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint32_t off_abs, uint32_t ebase,
+                                            bool owner_piece, uint32_t cnt, unsigned long long sum, uint32_t mn)
+{
+    const unsigned long long D = S.D, c = RS_STEP_REGION;
+    const unsigned long long Pr = c * r + (off_abs - ebase);
+    Slot *sl = &S.slots[Pr / D];
+    if (cnt) {
+        atomicAdd(&sl->count, cnt);
+        atomicAdd(&sl->sum, sum);
+        atomicMax(&sl->min_inv, ~mn);
+    }
+    if (owner_piece) sl->region = r + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Planner: parent offsets (a single-pass decoupled look-back scan of the lengths, or
+// the CSR offsets as given) and the merge-path unit records of every UNIT_MERGE stream.
+// One warp per tile of RS_PLAN_TILE parents; lane l takes 32 consecutive parents.
+
+__global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KParams P)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned long long c = RS_STEP_REGION;
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&P.hdr->plan_cursor, 1u);
+        t = __shfl_sync(FULLMASK, t, 0);
+        if (t >= P.plan_tiles) break;
+        uint32_t lo = 0, hi = P.n_streams - 1;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) >> 1;
+            if (P.streams[mid].plan_base <= t) lo = mid; else hi = mid - 1;
+        }
+        const DevStream &S = P.streams[lo];
+        const unsigned long long D = S.D;
+        const uint32_t tile = t - S.plan_base;
+        const uint32_t r_lo = tile * RS_PLAN_TILE;
+        const uint32_t r_hi = min(r_lo + RS_PLAN_TILE, S.R);
+        const uint32_t rb = r_lo + 32u * lane;
+        const uint32_t nl = rb < r_hi ? min(32u, r_hi - rb) : 0u;
+        const uint32_t base_abs = S.offsets ? S.offsets[0] : 0u;
+        uint32_t lsum = 0;
+        if (S.offsets) {
+            if (nl) lsum = S.offsets[rb + nl] - S.offsets[rb];
+        } else {
+            for (uint32_t j = 0; j < nl; ++j) lsum += S.len[rb + j];
+        }
+        const uint32_t incl = warp_incl_scan_u32(lsum, lane);
+        const uint32_t tsum = __shfl_sync(FULLMASK, incl, 31);
+        uint32_t E = 0;   // offset of parent r_lo relative to the stream's first element
+        bool stop = false;
+        if (S.offsets) {
+            E = S.offsets[r_lo] - base_abs;
+        } else {
+            unsigned long long *lb = S.plan_lb;
+            if (tile == 0) {
+                if (lane == 0) st_release_u64(&lb[0], LB_INCL | (unsigned long long)tsum);
+            } else {
+                if (lane == 0) st_release_u64(&lb[tile], LB_AGG | (unsigned long long)tsum);
+                unsigned long long excl = 0;
+                int jt = (int)tile - 1;
+                unsigned long long t0 = global_ns();
+                uint32_t it = 0;
+                for (;;) {
+                    const int idx = jt - (int)lane;
+                    const unsigned long long wv = (idx >= 0) ? ld_acquire_u64(&lb[idx]) : LB_INCL;
+                    const uint32_t flag = (uint32_t)(wv >> 62);
+                    const uint32_t notready = __ballot_sync(FULLMASK, flag == 0u);
+                    const uint32_t inclm = __ballot_sync(FULLMASK, flag == 2u);
+                    const uint32_t stopm = notready | inclm;
+                    if (stopm == 0u) {
+                        excl += warp_sum_u64(wv & LB_VAL);
+                        jt -= 32;
+                        continue;
+                    }
+                    const uint32_t first = __ffs(stopm) - 1;
+                    if (notready & (1u << first)) {
+                        if ((++it & 15u) == 0 && global_ns() - t0 > P.spin_limit) {
+                            if (lane == 0) atomicOr(&P.hdr->status, ST_LOOKBACK_TIMEOUT);
+                            stop = true;
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    excl += warp_sum_u64(lane <= first ? (wv & LB_VAL) : 0ull);
+                    break;
+                }
+                E = (uint32_t)excl;
+                if (lane == 0) st_release_u64(&lb[tile], LB_INCL | (excl + tsum));
+            }
+        }
+        if (stop) break;
+        // unit records: unit u starts inside parent r's merge-path span (P_r, P_{r+1}]
+        bool bad = false;
+        uint32_t off = E + incl - lsum;
+        for (uint32_t j = 0; j < nl && !bad; ++j) {
+            const uint32_t r = rb + j;
+            const uint32_t Lr = S.offsets ? S.offsets[r + 1] - S.offsets[r] : S.len[r];
+            const unsigned long long Pr = c * r + off, Pn = Pr + c + Lr;
+            for (unsigned long long u = Pr / D + 1; u <= Pn / D; ++u) {
+                if (u > S.n_units) {
+                    bad = true;
+                    break;
+                }
+                const long long into = (long long)(u * D) - (long long)(Pr + c);
+                const uint32_t je = (uint32_t)(into <= 0 ? 0 : (into >= (long long)Lr ? Lr : into));
+                UnitRec rc;
+                rc.i = r + 1;
+                rc.j = base_abs + off + je;
+                rc.head_off = base_abs + off;
+                rc.first_off = base_abs + off + Lr;
+                S.rec[u] = rc;
+            }
+            off += Lr;
+        }
+        if (tile == 0 && lane == 0) {
+            UnitRec rc;
+            rc.i = 0;
+            rc.j = rc.head_off = rc.first_off = base_abs;
+            S.rec[0] = rc;
+        }
+        if (tile + 1 == S.plan_tiles && lane == 0) {
+            const uint32_t N = E + tsum;
+            const unsigned long long U = (c * S.R + N + D - 1) / D;
+            if (U > S.n_units) {
+                bad = true;
+            } else {
+                UnitRec rc;
+                rc.i = S.R;
+                rc.j = rc.first_off = base_abs + N;
+                rc.head_off = base_abs + N;
+                S.rec[U] = rc;
+                *S.u_count = (uint32_t)U;
+            }
+        }
+        if (__any_sync(FULLMASK, bad) && lane == 0) atomicOr(&P.hdr->status, ST_BAD_INPUT);
+    }
+}
+
+// Compile-time pipeline signature: the enumerate op and the element-stage ops
+// (0 = no such stage; the aggregate follows the last one).  OE == 0 marks the generic
+// kernel, which reads every op from the parameters at run time.  A specialised
+// kernel carries only the code its own nodes execute, which keeps its hot loop small
+// enough for the instruction cache.
+template <int OE_, int O1_, int O2_, int O3_, int O4_>
+struct Sig {
+    static constexpr bool generic = OE_ == 0;
+    static constexpr int n = generic ? 0 : 2 + (O1_ != 0) + (O2_ != 0) + (O3_ != 0) + (O4_ != 0);
+    template <int I>
+    __host__ __device__ static constexpr int op()
+    {
+        return I == 0 ? OE_ : (I == n - 1 ? (int)D_AGG : (I == 1 ? O1_ : I == 2 ? O2_ : I == 3 ? O3_ : O4_));
+    }
+    template <int I>
+    __host__ __device__ static constexpr bool present() { return generic ? (I < RS_MAX_STAGES) : (I < n); }
+    template <int I>
+    __host__ __device__ static constexpr bool maybe_last() { return generic ? true : (I == n - 1); }
+    template <int I>
+    __host__ __device__ static constexpr bool maybe_elem() { return generic ? (I + 1 < RS_MAX_STAGES) : (I < n - 1); }
+};
+using GenericSig = Sig<0, 0, 0, 0, 0>;
+
+// per-node counters live in the processor's shared memory (lane 0 updates them)
+#define CNT_ADD(node, field, v)                                       \
+    do {                                                              \
+        if (lane == 0) M.cnt[4 * (node) + (field)] += (unsigned long long)(v); \
+    } while (0)
+
+template <int STRAT, int V, class S>
 struct Proc {
     static constexpr uint32_t W = 32u * V;   // ensemble width (items per firing)
     const KParams &P;
@@ -192,6 +622,8 @@ struct Proc {
     Warp &w;
     Stage &g;
     const uint32_t lane;
+    Pending *nxt;    // the prefetched next unit, in this processor's shared memory
+    bool nxt_open;   // its metadata still has to be turned into offsets
     // current unit
     uint32_t nk, total, E0;
     uint32_t ek;     // enumerate: next parent to open (signal strategy)
@@ -199,9 +631,19 @@ struct Proc {
     bool stop;
 
     __device__ __forceinline__ Proc(const KParams &P_, Smem &M_, Warp &w_, Stage &g_, uint32_t lane_)
-        : P(P_), M(M_), w(w_), g(g_), lane(lane_), nk(0), total(0), E0(0), ek(0), ek1(0), stop(false) {}
+        : P(P_), M(M_), w(w_), g(g_), lane(lane_), nk(0), total(0), E0(0), ek(0), ek1(0), stop(false)
+    {
+        nxt = nullptr;
+        nxt_open = false;
+    }
 
-    __device__ __forceinline__ bool loading() const { return P.st[0].op == D_ENUM_LOAD; }
+    __device__ __forceinline__ int nst() const { return S::generic ? P.n_stages : S::n; }
+    template <int I>
+    __device__ __forceinline__ uint32_t op() const
+    {
+        if constexpr (S::generic) return P.st[I].op;
+        else return (uint32_t)S::template op<I>();
+    }
 
     // ---- tile staging (TMA bulk copies into a ring of NT*TE elements) ----
     __device__ __forceinline__ void issue_tiles()
@@ -215,7 +657,7 @@ struct Proc {
             if (lane == 0) {
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&M.mbar[slot], cnt * 4u);
-                bulk_g2s(M.tiles + slot * TE, g.elements + start, cnt * 4u, &M.mbar[slot]);
+                bulk_g2s(M.tiles.ptr() + slot * TE, g.elements + start, cnt * 4u, &M.mbar[slot]);
             }
             g.t_issued++;
         }
@@ -231,6 +673,7 @@ struct Proc {
             uint32_t slot = g.t_ready & (NT - 1);
             uint32_t par = (g.phase >> slot) & 1u;
             if (!mbar_try_wait(&M.mbar[slot], par)) {
+                const long long pt = PROF_NOW();
                 unsigned long long t0 = global_ns();
                 uint32_t it = 0;
                 while (!mbar_try_wait(&M.mbar[slot], par)) {
@@ -239,6 +682,8 @@ struct Proc {
                         break;
                     }
                 }
+                PROF_ADD(PF_TILEWAIT, pt);
+                (void)pt;
                 if (g.failed) {
                     if (lane == 0) atomicOr(&P.hdr->status, ST_COPY_TIMEOUT);
                     stop = true;
@@ -248,6 +693,7 @@ struct Proc {
             g.phase ^= 1u << slot;
             g.t_ready++;
         }
+        g.ready_lim = (g.t_ready >= g.ntiles) ? 0xFFFFFFFFu : g.A + g.t_ready * TE;
     }
 
     // node 1 has consumed every element below e_read (absolute): recycle tiles
@@ -260,6 +706,7 @@ struct Proc {
             g.t_freed++;
             freed = true;
         }
+        g.free_lim = g.A + (g.t_freed + 1) * TE;
         if (freed) {
             __syncwarp();
             issue_tiles();
@@ -315,8 +762,8 @@ struct Proc {
             w.qt[0] += Lsum;
             w.em[0] = 0;
             ek += m;
-            w.c_ens[0]++;
-            w.c_items[0] += Lsum;
+            CNT_ADD(0, 0, 1);
+            CNT_ADD(0, 1, Lsum);
         }
     }
 
@@ -361,70 +808,122 @@ struct Proc {
     }
 
     // ---- gather one ensemble of node I: x[s], k[s] for lane's items 32 s + lane ----
-    template <int I>
-    __device__ __forceinline__ void gather(uint32_t take, uint32_t (&x)[V], uint32_t (&k)[V])
+    // returns true when every item of the ensemble has the same parent (k[0])
+    // F: a full ensemble (take == W), compiled without per-item guards
+    template <int I, bool F>
+    __device__ __forceinline__ bool gather(uint32_t take, uint32_t (&x)[V], uint32_t (&k)[V])
     {
+        if (F) take = W;
+        bool uni = true;
         if constexpr (I == 1) {
             const uint32_t q0 = w.qh[0];
-            const bool hashed = P.st[0].op == D_ENUM_HASH;
-            if (!hashed) {
-                ensure_ready(E0 + q0 + take);
-            }
+            const bool hashed = op<0>() == D_ENUM_HASH;
+            // parent of every item
+            if (STRAT == RS_STRATEGY_TAG) {
+                const uint32_t end0 = M.moff[ek1 + 1];
+                if (end0 >= q0 + take) {
+                    // the whole ensemble lies in one parent
 #pragma unroll
-            for (int s = 0; s < V; ++s) {
-                const uint32_t sb = 32u * s;
-                k[s] = 0;
-                x[s] = 0;
-                if (sb < take) {
-                    const uint32_t n = min(32u, take - sb);
-                    const uint32_t pos = q0 + sb + lane;
-                    uint32_t kk;
-                    if (STRAT == RS_STRATEGY_TAG) {
-                        kk = assign_parents(q0 + sb, n);
-                        uint32_t klast = __shfl_sync(FULLMASK, kk, n - 1);
-                        if (q0 + sb + n < total && M.moff[klast + 1] <= q0 + sb + n)
-                            advance_ek1(klast, q0 + sb + n);
-                        else
-                            ek1 = klast;
-                    } else {
-                        kk = w.ctxk[1];
+                    for (int s = 0; s < V; ++s) k[s] = ek1;
+                    if (end0 == q0 + take && q0 + take < total) advance_ek1(ek1, q0 + take);
+                } else {
+                    uni = false;
+#pragma unroll
+                    for (int s = 0; s < V; ++s) {
+                        const uint32_t sb = 32u * s;
+                        k[s] = ek1;
+                        if (sb < take) {
+                            const uint32_t n = min(32u, take - sb);
+                            const uint32_t kk = assign_parents(q0 + sb, n);
+                            const uint32_t klast = __shfl_sync(FULLMASK, kk, n - 1);
+                            if (q0 + sb + n < total && M.moff[klast + 1] <= q0 + sb + n)
+                                advance_ek1(klast, q0 + sb + n);
+                            else
+                                ek1 = klast;
+                            k[s] = kk;
+                        }
                     }
-                    k[s] = kk;
-                    if (lane < n) {
-                        if (hashed)
-                            x[s] = fmix32(M.mpar[kk] ^ fmix32((pos - M.moff[kk]) ^ RS_GOLD));
-                        else
-                            x[s] = load_elem(E0 + pos);
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < V; ++s) k[s] = w.ctxk[1];
+            }
+            // the elements themselves (getItem(i) of Figure 4)
+            if (hashed) {
+#pragma unroll
+                for (int s = 0; s < V; ++s) {
+                    const uint32_t q = 32u * s + lane;
+                    x[s] = (F || q < take) ? fmix32(M.mpar[k[s]] ^ fmix32((q0 + q - M.moff[k[s]]) ^ RS_GOLD)) : 0u;
+                }
+            } else {
+                const uint32_t e_lo = E0 + q0;
+                if (e_lo + take > g.ready_lim) ensure_ready(e_lo + take);
+                if (g.tma && e_lo + take <= g.B) {
+                    const uint32_t base = e_lo - g.A, mask = P.NT * P.TE - 1;
+#pragma unroll
+                    for (int s = 0; s < V; ++s) {
+                        const uint32_t q = 32u * s + lane;
+                        x[s] = (F || q < take) ? M.tiles[(base + q) & mask] : 0u;
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < V; ++s) {
+                        const uint32_t q = 32u * s + lane;
+                        x[s] = q < take ? load_elem(e_lo + q) : 0u;
                     }
                 }
             }
         } else {
             const uint32_t C = P.C, cm = C - 1;
             const uint32_t rb = (I - 2) * C;   // input edge I-1 is ring I-2
+            const uint32_t h = w.qh[I - 1];
+            if (STRAT == RS_STRATEGY_TAG) {
+                // tags are non-decreasing along a queue: equal ends mean one parent
+                const uint32_t k0 = M.qtag[rb + (h & cm)];
+                uni = k0 == M.qtag[rb + ((h + take - 1) & cm)];
+#pragma unroll
+                for (int s = 0; s < V; ++s) k[s] = k0;
+            } else {
+#pragma unroll
+                for (int s = 0; s < V; ++s) k[s] = w.ctxk[I];
+            }
 #pragma unroll
             for (int s = 0; s < V; ++s) {
                 const uint32_t q = 32u * s + lane;
                 x[s] = 0;
-                k[s] = (STRAT == RS_STRATEGY_TAG) ? 0u : w.ctxk[I];
-                if (q < take) {
-                    const uint32_t slot = rb + ((w.qh[I - 1] + q) & cm);
+                if (F || q < take) {
+                    const uint32_t slot = rb + ((h + q) & cm);
                     x[s] = M.qv[slot];
-                    if (STRAT == RS_STRATEGY_TAG) k[s] = M.qtag[slot];
+                    if (STRAT == RS_STRATEGY_TAG && !uni) k[s] = M.qtag[slot];
                 }
             }
         }
+        return uni;
     }
 
     // ---- one ensemble through element stage I (filter / map / expand) ----
-    template <int I>
+    template <int I, bool F>
     __device__ __forceinline__ void element_stage(uint32_t take)
     {
+        if (F) take = W;
         const DevStage &sd = P.st[I];
+        const uint32_t opc = op<I>();
         const uint32_t C = P.C, cm = C - 1;
         const uint32_t orb = (I - 1) * C;   // output edge I is ring I-1
         uint32_t x[V], k[V];
-        gather<I>(take, x, k);
-        if (sd.op == D_EXPAND) {
+        const long long pg = PROF_NOW();
+        (void)pg;
+        const bool uni = gather<I, F>(take, x, k);
+        if constexpr (I == 1) {
+#ifdef RS_PROFILE
+            // make the gather's loads complete before reading the clock
+            uint32_t sink = 0;
+            for (int s2 = 0; s2 < V; ++s2) sink ^= x[s2];
+            if (sink == 0xFFFFFFFFu && lane == 99) M.scr[0] = sink;
+#endif
+            PROF_ADD(PF_GATHER1, pg);
+        }
+        if (opc == D_EXPAND) {
 #pragma unroll
             for (int s = 0; s < V; ++s) {
                 if (32u * s < take) {
@@ -445,47 +944,69 @@ struct Proc {
             }
             return;
         }
+        const long long pc = PROF_NOW();
+        (void)pc;
         bool keep[V];
         uint32_t y[V];
+        // the parent's context word (t_r) or hashed id, once per ensemble when uniform
+        uint32_t cu = 0;
+        if (opc == D_FILT_HASH_CTX && uni) cu = M.mctx[k[0]];
+        if (opc == D_FILT_WEIGHT && uni) cu = fmix32(M.mpar[k[0]] ^ sd.c0);
 #pragma unroll
         for (int s = 0; s < V; ++s) {
             const uint32_t xs = x[s];
             bool kp;
             uint32_t ys = xs;
-            switch (sd.op) {
+            switch (opc) {
             case D_FILT_MASK: kp = (xs & sd.p0) == sd.p1; break;
             case D_FILT_MOD: kp = (xs % sd.p0) == sd.p1; break;
-            case D_FILT_HASH_CTX: kp = (fmix32(xs ^ sd.c0) ^ M.mctx[k[s]]) < sd.p1; break;
-            case D_FILT_WEIGHT: kp = fmix32(xs ^ sd.c0) < fmix32(M.mpar[k[s]] ^ sd.c0); break;
+            case D_FILT_HASH_CTX: kp = (fmix32(xs ^ sd.c0) ^ (uni ? cu : M.mctx[k[s]])) < sd.p1; break;
+            case D_FILT_WEIGHT:
+                kp = fmix32(xs ^ sd.c0) < (uni ? cu : fmix32(M.mpar[k[s]] ^ sd.c0));
+                break;
             case D_MAP_MULADD: ys = xs * sd.p0 + sd.p1; kp = true; break;
             default: kp = false; break;
             }
-            keep[s] = kp && (32u * s + lane < take);
+            keep[s] = kp && (F || 32u * s + lane < take);
             y[s] = ys;
         }
+#ifdef RS_PROFILE
+        {
+            uint32_t sink = 0;
+            for (int s2 = 0; s2 < V; ++s2) sink ^= keep[s2] ? y[s2] : 0u;
+            if (sink == 0xFFFFFFFFu && lane == 99) M.scr[0] = sink;
+        }
+#endif
+        PROF_ADD(PF_COMPUTE, pc);
+        const long long pp = PROF_NOW();
+        (void)pp;
         const uint32_t lt = lanemask_lt();
+        // all ballots first, then every kept item's slot from one running base
+        uint32_t bal[V];
+#pragma unroll
+        for (int s = 0; s < V; ++s) bal[s] = (F || 32u * s < take) ? __ballot_sync(FULLMASK, keep[s]) : 0u;
+        uint32_t base = w.qt[I];
 #pragma unroll
         for (int s = 0; s < V; ++s) {
-            if (32u * s < take) {
-                uint32_t b = __ballot_sync(FULLMASK, keep[s]);
-                if (keep[s]) {
-                    uint32_t slot = orb + ((w.qt[I] + __popc(b & lt)) & cm);
-                    M.qv[slot] = y[s];
-                    if (STRAT == RS_STRATEGY_TAG) M.qtag[slot] = (uint16_t)k[s];
-                }
-                uint32_t np = __popc(b);
-                w.qt[I] += np;
-                w.em[I] += np;
+            if (keep[s]) {
+                const uint32_t slot = orb + ((base + __popc(bal[s] & lt)) & cm);
+                M.qv[slot] = y[s];
+                if (STRAT == RS_STRATEGY_TAG) M.qtag[slot] = (uint16_t)k[s];
             }
+            base += __popc(bal[s]);
         }
+        w.em[I] += base - w.qt[I];
+        w.qt[I] = base;
+        PROF_ADD(PF_COMPACT, pp);
     }
 
     // ---- one ensemble into the aggregate (node I = n-1) ----
-    template <int I>
+    template <int I, bool F>
     __device__ __forceinline__ void aggregate(uint32_t take)
     {
+        if (F) take = W;
         uint32_t x[V], k[V];
-        gather<I>(take, x, k);
+        (void)gather<I, F>(take, x, k);
         if (STRAT == RS_STRATEGY_SIGNAL) {
             // the whole ensemble belongs to the current parent (Section 3.3)
             unsigned long long part = 0;
@@ -521,7 +1042,7 @@ struct Proc {
                 if (lane == 0) {
                     M.rc[k0] += n;
                     M.rs[k0] += sm;
-                    M.rm[k0] = min(M.rm[k0], mn);
+                    if (P.want_min) M.rm[k0] = min(M.rm[k0], mn);
                 }
             } else {
                 uint32_t kprev = __shfl_up_sync(FULLMASK, kk, 1);
@@ -547,7 +1068,7 @@ struct Proc {
                 if (act && tail) {
                     M.rc[kk] += lane - hl + 1;
                     M.rs[kk] += ps - before;
-                    M.rm[kk] = min(M.rm[kk], m);
+                    if (P.want_min) M.rm[kk] = min(M.rm[kk], m);
                 }
             }
             __syncwarp();
@@ -579,7 +1100,7 @@ struct Proc {
                 break;
             }
             uint32_t room = 32u;
-            if constexpr (I + 1 < RS_MAX_STAGES) {
+            if constexpr (S::template maybe_elem<I>()) {
                 if (!last) room = SC - (w.st[I] - w.sh[I]);
             }
             const uint32_t mmax = min(min(32u, w.st[I - 1] - w.sh[I - 1]), room);
@@ -603,7 +1124,7 @@ struct Proc {
                     const bool fresh = (begins & lanemask_lt()) != 0u;
                     M.rc[kk] = fresh ? 0u : w.acc_c;
                     M.rs[kk] = fresh ? 0ull : w.acc_s;
-                    M.rm[kk] = fresh ? 0xFFFFFFFFu : w.acc_m;
+                    if (P.want_min) M.rm[kk] = fresh ? 0xFFFFFFFFu : w.acc_m;
                 }
                 if (begins) {
                     w.acc_c = 0;
@@ -611,7 +1132,7 @@ struct Proc {
                     w.acc_m = 0xFFFFFFFFu;
                 }
             } else {
-                if constexpr (I + 1 < RS_MAX_STAGES) {
+                if constexpr (S::template maybe_elem<I>()) {
                     const uint32_t c0 = (w.sh[I] == w.st[I]) ? (w.qt[I] - w.qh[I]) : w.em[I];
                     if (mine) {
                         const uint32_t o = sidx(I, w.st[I] + lane);
@@ -624,7 +1145,7 @@ struct Proc {
             }
             __syncwarp();
             w.sh[I - 1] += m;
-            w.c_sig[I] += m;
+            CNT_ADD(I, 2, m);
             progress = true;
         }
         return progress;
@@ -637,17 +1158,30 @@ struct Proc {
     template <int I>
     __device__ __forceinline__ void fire(bool drain)
     {
-        if (I >= P.n_stages || stop) return;
-        constexpr bool can_push = I + 1 < RS_MAX_STAGES;
-        const bool last = !can_push || (I == P.n_stages - 1);
-        const uint32_t fan = P.st[I].fanout;
+        if constexpr (S::template present<I>()) {
+            if (I >= nst() || stop) return;
+            const long long pt = PROF_NOW();
+            (void)pt;
+            fire_body<I>(drain);
+            PROF_ADD(PF_NODE0 + I, pt);
+        }
+    }
+
+    template <int I>
+    __device__ __forceinline__ void fire_body(bool drain)
+    {
+        constexpr bool can_push = S::template maybe_elem<I>();
+        const bool last = !can_push || (I == nst() - 1);
+        // a-priori maximum outputs per input (Section 3.2): 1 unless the stage expands
+        const uint32_t fan = (S::generic || S::template op<I>() == (int)D_EXPAND) ? P.st[I].fanout : 1u;
         bool fired = false;
+        uint32_t n_ens = 0, n_items = 0;   // folded into the shared counters once per firing
         for (;;) {
             const bool sigp = (STRAT == RS_STRATEGY_SIGNAL) && (w.sh[I - 1] != w.st[I - 1]);
             const uint32_t avail0 = w.qt[I - 1] - w.qh[I - 1];
             if (!(drain ? (avail0 > 0 || sigp) : (avail0 >= W || sigp))) break;
             if (!fired) {
-                w.c_fire[I]++;
+                CNT_ADD(I, 3, 1);
                 fired = true;
             }
             bool progress = false;
@@ -666,23 +1200,37 @@ struct Proc {
                 if (take < want) break;                       // wait for downstream space
                 if (!drain && !sigp && take < W) break;       // wait for a full ensemble
                 if (last) {
-                    aggregate<I>(take);
+                    if constexpr (S::template maybe_last<I>()) {
+                        if (take == W) aggregate<I, true>(take); else aggregate<I, false>(take);
+                    }
                 } else {
-                    if constexpr (can_push) element_stage<I>(take);
+                    if constexpr (can_push) {
+                        if (take == W) element_stage<I, true>(take); else element_stage<I, false>(take);
+                    }
                 }
-                if (stop) return;
+                if (stop) break;
                 __syncwarp();
                 w.qh[I - 1] += take;
                 if (sigp) w.credit[I] -= take;
-                w.c_ens[I]++;
-                w.c_items[I] += take;
+                n_ens++;
+                n_items += take;
                 progress = true;
                 if constexpr (I == 1) {
-                    if (P.st[0].op == D_ENUM_LOAD) release_below(E0 + w.qh[0]);
+                    if (op<0>() == D_ENUM_LOAD && E0 + w.qh[0] >= g.free_lim) {
+                        const long long pt2 = PROF_NOW();
+                        (void)pt2;
+                        release_below(E0 + w.qh[0]);
+                        PROF_ADD(PF_TILES, pt2);
+                    }
                 }
             }
+            if (stop) break;
             if (STRAT == RS_STRATEGY_SIGNAL) progress |= signal_phase<I>(last);
             if (!progress) break;
+        }
+        if (n_ens) {
+            CNT_ADD(I, 0, n_ens);
+            CNT_ADD(I, 1, n_items);
         }
     }
 
@@ -706,25 +1254,34 @@ struct Proc {
         if (STRAT == RS_STRATEGY_TAG) {
             // enumeration emits every position of the unit at once; node 1 derives tags
             w.qt[0] = total;
-            w.c_ens[0]++;
-            w.c_items[0] += total;
+            CNT_ADD(0, 0, 1);
+            CNT_ADD(0, 1, total);
             ek1 = 0;
             if (total > 0) advance_ek1(0, 0);
         }
         for (unsigned long long sweep = 0;; ++sweep) {
-            w.c_fire[0]++;
-            if (STRAT == RS_STRATEGY_SIGNAL) enum_signal();
+            CNT_ADD(0, 3, 1);
+            if (nxt_open) {
+                poll_next(*nxt, P, M, lane);
+                nxt_open = !nxt->scanned;
+            }
+            if (STRAT == RS_STRATEGY_SIGNAL) {
+                const long long pt = PROF_NOW();
+                (void)pt;
+                enum_signal();
+                PROF_ADD(PF_ENUM, pt);
+            }
             bool d = (STRAT == RS_STRATEGY_TAG) || ek >= nk;
             fire<1>(d);
             d = d && edge_empty(0);
             fire<2>(d);
-            d = d && (P.n_stages <= 2 || edge_empty(1));
+            d = d && (nst() <= 2 || edge_empty(1));
             fire<3>(d);
-            d = d && (P.n_stages <= 3 || edge_empty(2));
+            d = d && (nst() <= 3 || edge_empty(2));
             fire<4>(d);
-            d = d && (P.n_stages <= 4 || edge_empty(3));
+            d = d && (nst() <= 4 || edge_empty(3));
             fire<5>(d);
-            d = d && (P.n_stages <= 5 || edge_empty(4));
+            d = d && (nst() <= 5 || edge_empty(4));
             if (stop) return;
             if (d) break;
             if (sweep >= P.budget) {
@@ -738,139 +1295,142 @@ struct Proc {
 
 // ---------------------------------------------------------------------------
 
-template <int STRAT, int V>
-__global__ void __launch_bounds__(256) rs_pipeline_kernel(const __grid_constant__ KParams P)
+template <int STRAT, int V, class SG>
+__global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_constant__ KParams P)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    unsigned char *wb = smem_raw + (size_t)warp * P.L.per_warp;
+    const uint32_t wb = warp * P.L.per_warp;   // this processor's byte offset in shared memory
     Smem M;
-    M.mbar = (unsigned long long *)(wb + P.L.o_mbar);
-    M.tiles = (uint32_t *)(wb + P.L.o_tiles);
-    M.moff = (uint32_t *)(wb + P.L.o_off);
-    M.mctx = (uint32_t *)(wb + P.L.o_ctx);
-    M.mpar = (uint32_t *)(wb + P.L.o_par);
-    M.rc = (uint32_t *)(wb + P.L.o_rc);
-    M.rs = (unsigned long long *)(wb + P.L.o_rs);
-    M.rm = (uint32_t *)(wb + P.L.o_rm);
-    M.qv = (uint32_t *)(wb + P.L.o_qv);
-    M.qtag = (uint16_t *)(wb + P.L.o_qt);
-    M.sq = (uint32_t *)(wb + P.L.o_sq);
-    M.scr = (uint32_t *)(wb + P.L.o_scr);
+    M.prof = sarr<unsigned long long>(wb + P.L.o_prof);
+    M.cnt = sarr<unsigned long long>(wb + P.L.o_cnt);
+    Pending *const pend = reinterpret_cast<Pending *>(smem_raw + wb + P.L.o_pend);
+    M.mbar = sarr<unsigned long long>(wb + P.L.o_mbar);
+    M.mmeta = sarr<unsigned long long>(wb + P.L.o_mmeta);
+    M.tiles = sarr<uint32_t>(wb + P.L.o_tiles);
+    M.mraw0 = sarr<uint32_t>(wb + P.L.o_raw[0]);
+    M.mraw1 = sarr<uint32_t>(wb + P.L.o_raw[1]);
+    M.mmoff0 = sarr<uint32_t>(wb + P.L.o_moff[0]);
+    M.mmoff1 = sarr<uint32_t>(wb + P.L.o_moff[1]);
+    M.mctx0 = sarr<uint32_t>(wb + P.L.o_ctxb[0]);
+    M.mctx1 = sarr<uint32_t>(wb + P.L.o_ctxb[1]);
+    M.mpar0 = sarr<uint32_t>(wb + P.L.o_parb[0]);
+    M.mpar1 = sarr<uint32_t>(wb + P.L.o_parb[1]);
+    M.moff = M.mmoff0;
+    M.mctx = M.mctx0;
+    M.mpar = M.mpar0;
+    M.rc = sarr<uint32_t>(wb + P.L.o_rc);
+    M.rs = sarr<unsigned long long>(wb + P.L.o_rs);
+    M.rm = sarr<uint32_t>(wb + P.L.o_rm);
+    M.qv = sarr<uint32_t>(wb + P.L.o_qv);
+    M.qtag = sarr<uint16_t>(wb + P.L.o_qt);
+    M.sq = sarr<uint32_t>(wb + P.L.o_sq);
+    M.scr = sarr<uint32_t>(wb + P.L.o_scr);
 
-    if (P.any_load && lane == 0) {
-        for (uint32_t s = 0; s < P.NT; ++s) mbar_init(&M.mbar[s], 1);
+    if (lane == 0) {
+        if (P.any_load)
+            for (uint32_t s = 0; s < P.NT; ++s) mbar_init(&M.mbar[s], 1);
+        mbar_init(&M.mmeta[0], 32);   // one arrival per lane per metadata prefetch
+        mbar_init(&M.mmeta[1], 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+#ifdef RS_PROFILE
+    if (lane < RS_PROF_SLOTS) M.prof[lane] = 0;
+#endif
+    const long long t_start = PROF_NOW();
+    (void)t_start;
     __syncwarp();
 
     Warp w;
-#pragma unroll
-    for (int i = 0; i < RS_MAX_STAGES; ++i) w.c_ens[i] = w.c_items[i] = w.c_sig[i] = w.c_fire[i] = 0;
+    if (lane < 4 * RS_MAX_STAGES) M.cnt[lane] = 0;
     Stage g;
     g.phase = 0;
     g.failed = false;
     unsigned long long units = 0;
     bool stop = false;
+    const bool load = (SG::generic ? P.st[0].op : (uint32_t)SG::template op<0>()) == D_ENUM_LOAD;
 
-    while (!stop) {
-        uint32_t ticket = 0;
-        if (lane == 0) ticket = atomicAdd(&P.hdr->cursor, 1u);
-        ticket = __shfl_sync(FULLMASK, ticket, 0);
-        if (ticket >= P.total_units) break;
+    // first unit: claim and prefetch
+    Pending cur;
+    {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&P.hdr->cursor, 1u);
+        t = __shfl_sync(FULLMASK, t, 0);
+        cur.u = describe_unit(P, t);
+        cur.buf = 0;
+        cur.phase = 0;
+        cur.scanned = false;
+        cur.bad = false;
+        cur.split_tail = false;
+        cur.total = cur.E0 = cur.tail_off = cur.tail_len = 0;
+        if (cur.u.valid) prefetch_meta(P, M, cur.u, 0, lane);
+    }
+
+    while (cur.u.valid && !stop) {
+        long long pt_setup = PROF_NOW();
+        (void)pt_setup;
         units++;
-        // stream owning this ticket: the last one whose unit_base <= ticket
-        uint32_t lo = 0, hi = P.n_streams - 1;
-        while (lo < hi) {
-            uint32_t mid = (lo + hi + 1) >> 1;
-            if (P.streams[mid].unit_base <= ticket) lo = mid; else hi = mid - 1;
-        }
-        const DevStream &S = P.streams[lo];
-        const uint32_t lu = ticket - S.unit_base;
-        const uint32_t K = S.K;
-        const uint32_t r0 = lu * K;
-        const uint32_t nk = min(K, S.R - r0);
-        const bool load = P.st[0].op == D_ENUM_LOAD;
-        bool bad = false;
-        uint32_t E0 = 0, total = 0;
+        // claim the next unit now; its ticket is read after this unit's setup
+        uint32_t next_ticket = 0;
+        if (lane == 0) next_ticket = atomicAdd(&P.hdr->cursor, 1u);
 
-        // ---- parents of this unit: lengths -> local offsets ----
-        if (S.offsets) {
-            uint32_t ob = S.offsets[r0];
-            for (uint32_t k = lane; k <= nk; k += 32) M.moff[k] = S.offsets[r0 + k] - ob;
-            __syncwarp();
-            bool dec = false;
-            for (uint32_t k = lane; k < nk; k += 32) dec |= M.moff[k + 1] < M.moff[k];
-            bad = __any_sync(FULLMASK, dec);
-            E0 = ob;
-            total = M.moff[nk];
-        } else {
-            uint32_t carry = 0;
-            for (uint32_t b = 0; b < nk; b += 32) {
-                uint32_t k = b + lane;
-                uint32_t L = (k < nk) ? S.len[r0 + k] : 0u;
-                uint32_t incl = warp_incl_scan_u32(L, lane);
-                if (k < nk) M.moff[k] = carry + incl - L;
-                carry += __shfl_sync(FULLMASK, incl, 31);
-            }
-            if (lane == 0) M.moff[nk] = carry;
-            total = carry;
-            if (load) {
-                // decoupled look-back over this stream's units
-                unsigned long long *lb = P.lookback + S.unit_base;
-                if (lu == 0) {
-                    if (lane == 0) st_release_u64(&lb[0], LB_INCL | (unsigned long long)total);
-                } else {
-                    if (lane == 0) st_release_u64(&lb[lu], LB_AGG | (unsigned long long)total);
-                    unsigned long long excl = 0;
-                    int j = (int)lu - 1;
-                    unsigned long long t0 = global_ns();
-                    uint32_t it = 0;
-                    for (;;) {
-                        int idx = j - (int)lane;
-                        unsigned long long wv = (idx >= 0) ? ld_acquire_u64(&lb[idx]) : LB_INCL;
-                        uint32_t flag = (uint32_t)(wv >> 62);
-                        uint32_t notready = __ballot_sync(FULLMASK, flag == 0u);
-                        uint32_t incl = __ballot_sync(FULLMASK, flag == 2u);
-                        uint32_t stopm = notready | incl;
-                        if (stopm == 0u) {
-                            excl += warp_sum_u64(wv & LB_VAL);
-                            j -= 32;
-                            continue;
-                        }
-                        uint32_t first = __ffs(stopm) - 1;
-                        if (notready & (1u << first)) {
-                            if ((++it & 15u) == 0 && global_ns() - t0 > P.spin_limit) {
-                                if (lane == 0) atomicOr(&P.hdr->status, ST_LOOKBACK_TIMEOUT);
-                                stop = true;
-                                break;
-                            }
-                            __nanosleep(32);
-                            continue;
-                        }
-                        excl += warp_sum_u64(lane <= first ? (wv & LB_VAL) : 0ull);
+        const DevStream &S = P.streams[cur.u.stream];
+        const uint32_t r0 = cur.u.r0, nk = cur.u.nk;
+        const uint32_t b = cur.buf;
+        if (!cur.scanned) {
+            // wait (bounded) for this unit's metadata
+            const uint32_t par = (cur.phase >> b) & 1u;
+            if (!mbar_try_wait(&M.mmeta[b], par)) {
+                unsigned long long t0 = global_ns();
+                uint32_t it = 0;
+                while (!mbar_try_wait(&M.mmeta[b], par)) {
+                    if ((++it & 63u) == 0 && global_ns() - t0 > P.spin_limit) {
+                        if (lane == 0) atomicOr(&P.hdr->status, ST_COPY_TIMEOUT);
+                        stop = true;
                         break;
                     }
-                    E0 = (uint32_t)excl;
-                    if (lane == 0) st_release_u64(&lb[lu], LB_INCL | (excl + total));
-                    if (stop) break;
                 }
+                if (stop) break;
             }
+            cur.phase ^= 1u << b;
+            scan_meta(cur, P, M, lane);
         }
+        const uint32_t E0 = cur.E0;
+        const uint32_t total = cur.total;
+        bool bad = cur.bad;
         if (load && !bad && (unsigned long long)E0 + total > S.n_elements) bad = true;
-        if (bad) {
-            if (lane == 0) atomicOr(&P.hdr->status, ST_BAD_INPUT);
+
+        // the prefetched next unit (its copies overlap this unit's work)
+        Pending &nxt = *pend;
+        __syncwarp();
+        {
+            const uint32_t t = __shfl_sync(FULLMASK, next_ticket, 0);
+            nxt.u = describe_unit(P, t);
+            nxt.buf = b ^ 1u;
+            nxt.phase = cur.phase;
+            nxt.scanned = false;
+            nxt.bad = false;
+            nxt.split_tail = false;
+            nxt.total = nxt.E0 = nxt.tail_off = nxt.tail_len = 0;
+            if (nxt.u.valid) prefetch_meta(P, M, nxt.u, nxt.buf, lane);
+        }
+
+        if (bad || cur.u.skip) {
+            if (bad && lane == 0) atomicOr(&P.hdr->status, ST_BAD_INPUT);
+            cur = nxt;
             continue;
         }
-        if (P.need_ctx)
-            for (uint32_t k = lane; k < nk; k += 32) M.mctx[k] = S.ctx ? S.ctx[r0 + k] : 0u;
-        if (P.need_par)
-            for (uint32_t k = lane; k < nk; k += 32) M.mpar[k] = S.parents ? S.parents[r0 + k] : r0 + k;
+        M.moff = M.moffb(b);
+        M.mctx = M.ctxb(b);
+        M.mpar = M.parb(b);
+        if (P.need_ctx && !S.ctx)
+            for (uint32_t k = lane; k < nk; k += 32) M.mctx[k] = 0u;
+        if (P.need_par && !S.parents)
+            for (uint32_t k = lane; k < nk; k += 32) M.mpar[k] = r0 + k;
         if (STRAT == RS_STRATEGY_TAG) {
             for (uint32_t k = lane; k < nk; k += 32) {
                 M.rc[k] = 0;
                 M.rs[k] = 0;
-                M.rm[k] = 0xFFFFFFFFu;
+                if (P.want_min) M.rm[k] = 0xFFFFFFFFu;
             }
         }
         __syncwarp();
@@ -883,8 +1443,13 @@ __global__ void __launch_bounds__(256) rs_pipeline_kernel(const __grid_constant_
         if (g.B < g.A) g.B = g.A;
         g.ntiles = g.tma ? (g.B - g.A + P.TE - 1) / P.TE : 0u;
         g.t_issued = g.t_ready = g.t_freed = 0;
+        g.ready_lim = g.tma ? (g.ntiles ? g.A : 0xFFFFFFFFu) : 0xFFFFFFFFu;
+        g.free_lim = g.A + P.TE;
 
-        Proc<STRAT, V> pr(P, M, w, g, lane);
+        PROF_ADD(PF_SETUP, pt_setup);
+        Proc<STRAT, V, SG> pr(P, M, w, g, lane);
+        pr.nxt = pend;
+        pr.nxt_open = nxt.u.valid && !nxt.scanned;
         pr.nk = nk;
         pr.total = total;
         pr.E0 = E0;
@@ -898,63 +1463,159 @@ __global__ void __launch_bounds__(256) rs_pipeline_kernel(const __grid_constant_
         __syncwarp();
 
         // ---- per-parent results, coalesced ----
+        const long long pt_fl = PROF_NOW();
+        (void)pt_fl;
+        // parents processed in pieces (the continued head, a last parent running past
+        // the unit) merge through their owner's slot; the rest are written directly
+        const bool split_head = cur.u.has_head;
+        const bool split_tail = cur.split_tail;
         for (uint32_t k = lane; k < nk; k += 32) {
+            if ((k == 0 && split_head) || (k == nk - 1 && split_tail)) continue;
             if (P.want_count) S.out_count[r0 + k] = M.rc[k];
             if (P.want_sum) S.out_sum[r0 + k] = M.rs[k];
             if (P.want_min) S.out_min[r0 + k] = M.rm[k];
         }
+        if (lane == 0) {
+            if (split_head)
+                merge_piece(S, r0, cur.u.head_off, cur.u.ebase, false, M.rc[0], M.rs[0],
+                            P.want_min ? M.rm[0] : 0xFFFFFFFFu);
+            if (split_tail && !(split_head && nk == 1))
+                merge_piece(S, r0 + nk - 1, cur.tail_off, cur.u.ebase, true, M.rc[nk - 1], M.rs[nk - 1],
+                            P.want_min ? M.rm[nk - 1] : 0xFFFFFFFFu);
+        }
         __syncwarp();
+        PROF_ADD(PF_FLUSH, pt_fl);
+        cur = nxt;
+    }
+    // a prefetch may still be in flight when the loop ends (error exit): let it land
+    if (cur.u.valid && !cur.scanned) {
+        const uint32_t par = (cur.phase >> cur.buf) & 1u;
+        unsigned long long t0 = global_ns();
+        uint32_t it = 0;
+        while (!mbar_try_wait(&M.mmeta[cur.buf], par)) {
+            if ((++it & 63u) == 0 && global_ns() - t0 > P.spin_limit) break;
+        }
     }
 
     // ---- counters ----
+    PROF_ADD(PF_TOTAL, t_start);
+    __syncwarp();
+#ifdef RS_PROFILE
+    if (lane < RS_PROF_SLOTS) atomicAdd(&P.hdr->cyc[lane], M.prof[lane]);
+#endif
     if (lane == 0) {
         atomicAdd(&P.hdr->units, units);
-#pragma unroll
-        for (int i = 0; i < RS_MAX_STAGES; ++i) {
-            if (i < P.n_stages) {
-                atomicAdd(&P.hdr->counters[4 * i + 0], w.c_ens[i]);
-                atomicAdd(&P.hdr->counters[4 * i + 1], w.c_items[i]);
-                atomicAdd(&P.hdr->counters[4 * i + 2], w.c_sig[i]);
-                atomicAdd(&P.hdr->counters[4 * i + 3], w.c_fire[i]);
-            }
-        }
+        for (int i = 0; i < 4 * P.n_stages; ++i) atomicAdd(&P.hdr->counters[i], M.cnt[i]);
     }
 }
 
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 
-static const void *kernel_ptr(int strategy, int V)
+// Kernel table: specialised signatures for the pipelines the workloads use, plus the
+// generic kernel for any other stage list.
+struct KEntry {
+    int strategy, V, oe, o1, o2, o3, o4;
+    const void *fn;
+};
+
+#define RS_KSIG(ST, V, OE, O1, O2, O3, O4) \
+    {ST, V, OE, O1, O2, O3, O4, (const void *)rs_pipeline_kernel<ST, V, Sig<OE, O1, O2, O3, O4>>}
+#define RS_KALLV(ST, OE, O1, O2, O3, O4) \
+    RS_KSIG(ST, 1, OE, O1, O2, O3, O4), RS_KSIG(ST, 2, OE, O1, O2, O3, O4), RS_KSIG(ST, 4, OE, O1, O2, O3, O4)
+#define RS_KBOTH(OE, O1, O2, O3, O4) \
+    RS_KALLV(RS_STRATEGY_SIGNAL, OE, O1, O2, O3, O4), RS_KALLV(RS_STRATEGY_TAG, OE, O1, O2, O3, O4)
+
+static const KEntry g_kernels[] = {
+    // loaded elements -> three context hash filters -> aggregate
+    RS_KBOTH(D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),
+    // hashed elements -> power-of-two modulus filter -> multiply-add map -> aggregate
+    RS_KBOTH(D_ENUM_HASH, D_FILT_MASK, D_MAP_MULADD, 0, 0),
+    // loaded elements (edges) -> weight comparison -> aggregate
+    RS_KBOTH(D_ENUM_LOAD, D_FILT_WEIGHT, 0, 0, 0),
+    // any other stage list
+    RS_KBOTH(0, 0, 0, 0, 0),
+};
+
+static const void *kernel_ptr(const KParams &P)
 {
-    if (strategy == RS_STRATEGY_SIGNAL) {
-        if (V == 1) return (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, 1>;
-        if (V == 2) return (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, 2>;
-        return (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, 4>;
+    int ops[5] = {0, 0, 0, 0, 0};
+    ops[0] = (int)P.st[0].op;
+    for (int i = 1; i < P.n_stages - 1 && i < 5; ++i) ops[i] = (int)P.st[i].op;
+    const void *generic = nullptr;
+    for (const KEntry &e : g_kernels) {
+        if (e.strategy != P.strategy || e.V != (int)P.V) continue;
+        if (e.oe == 0) {
+            generic = e.fn;
+            continue;
+        }
+        if (e.oe == ops[0] && e.o1 == ops[1] && e.o2 == ops[2] && e.o3 == ops[3] && e.o4 == ops[4]) return e.fn;
     }
-    if (V == 1) return (const void *)rs_pipeline_kernel<RS_STRATEGY_TAG, 1>;
-    if (V == 2) return (const void *)rs_pipeline_kernel<RS_STRATEGY_TAG, 2>;
-    return (const void *)rs_pipeline_kernel<RS_STRATEGY_TAG, 4>;
+    return generic;
 }
 
-int rs_kernel_occupancy(int strategy, int V, int block, size_t smem, int *blocks_per_sm)
+int rs_kernel_occupancy(const KParams &P, int block, size_t smem, int *blocks_per_sm)
 {
-    const void *f = kernel_ptr(strategy, V);
+    const void *f = kernel_ptr(P);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, block, smem);
     return (int)e;
 }
 
-int rs_kernel_max_smem_optin(int strategy, int V, size_t smem)
+int rs_kernel_max_smem_optin(const KParams &P, size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(kernel_ptr(strategy, V), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel_ptr(P), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return (int)e;
+}
+
+int rs_kernel_is_specialised(const KParams &P)
+{
+    for (const KEntry &e : g_kernels)
+        if (e.fn == kernel_ptr(P)) return e.oe != 0;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Finalize: write the merged result of every parent that was processed in pieces.
+
+__global__ void __launch_bounds__(256) rs_finalize_kernel(const __grid_constant__ KParams P)
+{
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (uint32_t si = 0; si < P.n_streams; ++si) {
+        const DevStream &S = P.streams[si];
+        if (S.mode != UNIT_MERGE || S.R == 0) continue;
+        const uint32_t U = *S.u_count;
+        for (uint32_t u = tid; u < U; u += nth) {
+            const Slot sl = S.slots[u];
+            if (sl.region == 0) continue;
+            const uint32_t r = sl.region - 1;
+            if (P.want_count) S.out_count[r] = sl.count;
+            if (P.want_sum) S.out_sum[r] = sl.sum;
+            if (P.want_min) S.out_min[r] = ~sl.min_inv;
+        }
+    }
+}
+
+int rs_launch_finalize(const KParams &P, int grid, void *stream)
+{
+    void *args[] = {(void *)&P};
+    cudaError_t e = cudaLaunchKernel((const void *)rs_finalize_kernel, dim3(grid), dim3(256), args, 0,
+                                     (cudaStream_t)stream);
+    return (int)e;
+}
+
+int rs_launch_planner(const KParams &P, int grid, void *stream)
+{
+    void *args[] = {(void *)&P};
+    cudaError_t e = cudaLaunchKernel((const void *)rs_plan_kernel, dim3(grid), dim3(256), args, 0,
+                                     (cudaStream_t)stream);
     return (int)e;
 }
 
 int rs_launch_kernel(const KParams &P, int grid, int block, size_t smem, void *stream)
 {
-    const void *f = kernel_ptr(P.strategy, (int)P.V);
+    const void *f = kernel_ptr(P);
     void *args[] = {(void *)&P};
     cudaError_t e = cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, (cudaStream_t)stream);
     return (int)e;

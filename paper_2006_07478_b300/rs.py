@@ -71,9 +71,13 @@ class RegionResults(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("device_status", ctypes.c_uint32), ("n_nodes", ctypes.c_uint32), ("units", ctypes.c_uint64),
                 ("ensembles", ctypes.c_uint64 * RS_MAX_STAGES), ("items", ctypes.c_uint64 * RS_MAX_STAGES),
-                ("signals", ctypes.c_uint64 * RS_MAX_STAGES), ("firings", ctypes.c_uint64 * RS_MAX_STAGES)]
+                ("signals", ctypes.c_uint64 * RS_MAX_STAGES), ("firings", ctypes.c_uint64 * RS_MAX_STAGES),
+                ("cycles", ctypes.c_uint64 * 16)]
+    CYCLE_SLOTS = ("setup", "lookback", "tile_wait", "enumerate", "node1", "node2", "node3", "node4",
+                   "node5", "flush", "total")
 
-    def as_dict(self):
+    def as_dict(self, W: int = 32):
+        """Counters as lists per node; active-lane fraction = items / (W * ensembles)."""
         n = self.n_nodes
         ens = list(self.ensembles)[:n]
         items = list(self.items)[:n]
@@ -81,7 +85,13 @@ class Stats(ctypes.Structure):
             "device_status": self.device_status, "units": self.units,
             "ensembles": ens, "items": items,
             "signals": list(self.signals)[:n], "firings": list(self.firings)[:n],
-            "active_lane_fraction": [(it / (32.0 * e)) if e else 0.0 for it, e in zip(items, ens)],
+            "ensemble_width": W,
+            "cycles": {k: int(self.cycles[i]) for i, k in enumerate(self.CYCLE_SLOTS[:4])} |
+                      {self.CYCLE_SLOTS[4 + j]: int(self.cycles[4 + 1 + j]) for j in range(5)} |
+                      {"flush": int(self.cycles[10]), "total": int(self.cycles[11]),
+                       "n1_gather": int(self.cycles[12]), "compute": int(self.cycles[13]),
+                       "compact": int(self.cycles[14]), "tiles": int(self.cycles[15])},
+            "active_lane_fraction": [(it / (float(W) * e)) if e else 0.0 for it, e in zip(items, ens)],
         }
 
 
@@ -100,9 +110,12 @@ def lib(build_if_missing: bool = True):
     if _lib is None:
         if build_if_missing:
             _build.build()
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"librs.so not found at {_build.LIB}; the CUDA library is required")
-        L = ctypes.CDLL(_build.LIB)
+        path = _build.PROF_LIB if os.environ.get("RS_PROFILE_BUILD") == "1" else _build.LIB
+        if build_if_missing and path == _build.PROF_LIB:
+            _build.build(profile=True)
+        if not os.path.exists(path):
+            raise RuntimeError(f"{os.path.basename(path)} not found at {path}; the CUDA library is required")
+        L = ctypes.CDLL(path)
         P, U32, U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
         sig = {
             "rs_default_opts": ([ctypes.POINTER(Opts)], ctypes.c_int),
@@ -299,7 +312,7 @@ class Pipeline:
         st = lib().rs_get_stats(self._h, ctypes.c_void_p(ws.data_ptr()), _cur_stream(), ctypes.byref(s))
         if raise_on_error:
             check(st, "rs_get_stats")
-        d = s.as_dict()
+        d = s.as_dict(self.opts["ensemble_width"])
         d["status"] = st
         return d
 

@@ -47,8 +47,9 @@ def test_hashed_uniform_10k(rs, strategy):
         R = s["R"]
         for node in (1, 2, 3):
             assert st["signals"][node] == 2 * R                  # Begin and End reach every node
-        # no ensemble spans a region boundary: at least sum ceil(L/32) ensembles at node 1
-        assert st["ensembles"][1] >= int(np.sum((s["len"].astype(np.int64) + 31) // 32))
+        # no ensemble spans a region boundary: at least sum ceil(L/W) ensembles at node 1
+        W = st["ensemble_width"]
+        assert st["ensembles"][1] >= int(np.sum((s["len"].astype(np.int64) + W - 1) // W))
 
 
 @pytest.mark.parametrize("strategy", STRATEGIES)
