@@ -112,7 +112,7 @@ typedef struct {
     uint32_t tile_elements;     /* elements per bulk-copy tile for RS_ENUM_LOAD, a power of
                                    two in W..4096; 0 = 256                                    */
     uint32_t tiles_in_flight;   /* staging tiles per processor, 2 or 4; 0 = 4                 */
-    uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = 4                            */
+    uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = 8                            */
     uint32_t grid;              /* CTAs; 0 = a persistent grid (SMs x resident CTAs per SM)   */
     uint32_t reserved;
     uint64_t device_budget;     /* scheduler sweeps allowed per claimed unit before the device

@@ -85,7 +85,7 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
     if (o->signal_capacity == 0) o->signal_capacity = 32;
     if (o->tile_elements == 0) o->tile_elements = 256;
     if (o->tiles_in_flight == 0) o->tiles_in_flight = 4;
-    if (o->warps_per_block == 0) o->warps_per_block = 4;
+    if (o->warps_per_block == 0) o->warps_per_block = 8;
     if (o->device_budget == 0) o->device_budget = 1ull << 22;
     return RS_OK;
 }
@@ -828,20 +828,38 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
     }
     std::vector<rs_pipeline_opts> cand;
     const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
-    const uint32_t Ks[3] = {K0 > 1 ? K0 / 2 : 1, K0, K0 * 2 <= RS_MAX_K ? K0 * 2 : K0};
+    // unit size: loaded streams use merge-path units of 128 or 256 parents; hashed ones
+    // whole-parent units around the size the mean length suggests
+    const bool merge = p->stages[0].kind == RS_ENUM_LOAD;
+    uint32_t Ks[2];
+    if (merge) {
+        Ks[0] = 128;
+        Ks[1] = 256;
+    } else {
+        Ks[0] = K0;
+        Ks[1] = K0 * 2 <= RS_MAX_K ? K0 * 2 : (K0 > 1 ? K0 / 2 : K0);
+    }
+    const uint32_t widths[2] = {2 * RS_W, 4 * RS_W};
     const uint32_t wpbs[2] = {4, 8};
+    const uint32_t fan = max_fanout_of(p->stages, p->n_stages);
     try {
         for (uint32_t si = 0; si < 2; ++si)
-            for (uint32_t ki = 0; ki < 3; ++ki)
-                for (uint32_t wi = 0; wi < 2; ++wi) {
-                    if (ki > 0 && Ks[ki] == Ks[ki - 1]) continue;
-                    rs_pipeline_opts c = base;
-                    c.strategy = strategies[si];
-                    c.regions_per_unit = Ks[ki];
-                    c.warps_per_block = wpbs[wi];
-                    c.grid = 0;
-                    cand.push_back(c);
-                }
+            for (uint32_t ki = 0; ki < 2; ++ki)
+                for (uint32_t xi = 0; xi < 2; ++xi)
+                    for (uint32_t wi = 0; wi < 2; ++wi) {
+                        if (ki > 0 && Ks[ki] == Ks[0]) continue;
+                        rs_pipeline_opts c = base;
+                        c.strategy = strategies[si];
+                        c.regions_per_unit = Ks[ki];
+                        c.ensemble_width = widths[xi];
+                        c.queue_capacity = 0;
+                        c.warps_per_block = wpbs[wi];
+                        c.grid = 0;
+                        fill_defaults(&c, fan);
+                        if (c.tile_elements < c.ensemble_width) c.tile_elements = c.ensemble_width;
+                        if (check_opts(&c, fan) != RS_OK) continue;
+                        cand.push_back(c);
+                    }
     } catch (...) {
         p->opts = base;
         return RS_ERR_NOMEM;

@@ -1201,11 +1201,11 @@ struct Proc {
                 if (!drain && !sigp && take < W) break;       // wait for a full ensemble
                 if (last) {
                     if constexpr (S::template maybe_last<I>()) {
-                        if (take == W) aggregate<I, true>(take); else aggregate<I, false>(take);
+                        aggregate<I, false>(take);
                     }
                 } else {
                     if constexpr (can_push) {
-                        if (take == W) element_stage<I, true>(take); else element_stage<I, false>(take);
+                        element_stage<I, false>(take);
                     }
                 }
                 if (stop) break;
