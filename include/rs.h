@@ -112,7 +112,8 @@ typedef struct {
     uint32_t tile_elements;     /* elements per bulk-copy tile for RS_ENUM_LOAD, a power of
                                    two in W..4096; 0 = 256                                    */
     uint32_t tiles_in_flight;   /* staging tiles per processor, 2 or 4; 0 = 4                 */
-    uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = 8                            */
+    uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = 8; fewer when their shared
+                                   memory would not fit one CTA                              */
     uint32_t grid;              /* CTAs; 0 = a persistent grid (SMs x resident CTAs per SM)   */
     uint32_t reserved;
     uint64_t device_budget;     /* scheduler sweeps allowed per claimed unit before the device
@@ -230,6 +231,29 @@ rs_status rs_timing_enable(rs_pipeline *p, uint32_t capacity);
 /* Wait for the recorded events, write up to `max` kernel durations in milliseconds
  * (launch order) to ms[], their number to *n, and empty the ring. */
 rs_status rs_timing_read(rs_pipeline *p, float *ms, uint32_t max, uint32_t *n);
+
+/* ---- running without a caller workspace ------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it serves callers that cannot
+ * allocate device memory when they run the pipeline (a host application that owns the
+ * device-memory budget through its own allocator or a hard cap, or a latency-critical
+ * loop where an allocation could synchronise the device).
+ *
+ * Same work and results as rs_run, but the scratch memory (work cursor, planner words,
+ * unit records, merge slots, stream table) lives in a fixed 16 MiB array compiled into
+ * the library (every GPU that loads the library holds it until the process exits).
+ * The call allocates nothing: no cudaMalloc, cudaFree or cudaMallocHost, and no
+ * allocating library routine.
+ *   - The first call on a device (with that device current) looks up the array's
+ *     device address once; make that first call before any stream capture.
+ *   - RS_ERR_CAPACITY, with nothing enqueued, if the submitted streams need more than
+ *     16 MiB of scratch (rs_workspace_size reports the need) or more than 64 streams
+ *     are submitted.
+ *   - Every call shares the one array and clears what must start at zero; calls whose
+ *     work overlaps on the GPU (other CUDA streams, other host threads, other
+ *     pipelines) race on it and must be serialised by the caller.
+ *   - rs_get_stats reads a caller workspace and does not apply to these runs. */
+rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream);
 
 /* ---- misc ---------------------------------------------------------------------- */
 

@@ -9,12 +9,14 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "rs_internal.h"
 
 #define RS_VERSION 1u
+#define RS_NOALLOC_MAX_STREAMS 64
 
 static thread_local int g_last_cuda = 0;
 
@@ -23,6 +25,19 @@ static rs_status cuda_fail(cudaError_t e)
     g_last_cuda = (int)e;
     return RS_ERR_CUDA;
 }
+
+struct StreamPlan {
+    uint32_t mode, K, n_units, plan_tiles, D;
+    size_t slots_off, ucount_off, planlb_off, rec_off;
+};
+
+// The workspace layout of make_plan in fixed arrays, for rs_run_noalloc (no allocation).
+struct FixedPlan {
+    uint64_t total_units, plan_tiles;
+    uint32_t Kmax;
+    size_t zero_end, table_off, total;
+    StreamPlan sp[RS_NOALLOC_MAX_STREAMS];
+};
 
 struct rs_pipeline {
     rs_stage_desc stages[RS_MAX_STAGES];
@@ -41,9 +56,14 @@ struct rs_pipeline {
     cudaGraphExec_t graph = nullptr;
     // device facts
     int n_sm = 0;
+    size_t smem_max = 0;   // largest dynamic shared memory a CTA may opt in to
     // per-launch timing ring
     std::vector<cudaEvent_t> tev;   // 2 events per slot
     uint32_t t_cap = 0, t_count = 0;
+    // stream table and plan for rs_run_noalloc, part of the pipeline object so that call
+    // needs no allocation of its own
+    DevStream noalloc_table[RS_NOALLOC_MAX_STREAMS];
+    FixedPlan noalloc_plan;
 };
 
 static void timing_free(rs_pipeline *p)
@@ -306,10 +326,6 @@ static uint32_t choose_K(const rs_pipeline *p, const rs_stream_desc &s)
     return K;
 }
 
-struct StreamPlan {
-    uint32_t mode, K, n_units, plan_tiles, D;
-    size_t slots_off, ucount_off, planlb_off, rec_off;
-};
 
 struct Plan {
     uint64_t total_units, plan_tiles;
@@ -579,8 +595,19 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.spin_limit = 2000000000ull;   // 2 s on the global timer
     P.L = make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
 
-    Lc.block = (int)o.warps_per_block * 32;
-    Lc.smem = (size_t)P.L.per_warp * o.warps_per_block;
+    // processors per CTA: as asked, but no more than fit the per-block shared memory
+    uint32_t wpb = o.warps_per_block;
+    if (!p->smem_max) {
+        int dev = 0, v = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return cuda_fail(e);
+        p->smem_max = (size_t)v;
+    }
+    while (wpb > 1 && (size_t)P.L.per_warp * wpb > p->smem_max) --wpb;
+    if ((size_t)P.L.per_warp * wpb > p->smem_max) return RS_ERR_CAPACITY;
+    Lc.block = (int)wpb * 32;
+    Lc.smem = (size_t)P.L.per_warp * wpb;
     Lc.grid = (int)o.grid;
     if (pl.total_units == 0) return RS_OK;
     if (Lc.grid == 0) {
@@ -589,9 +616,9 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
         if (ce != 0) return cuda_fail((cudaError_t)ce);
         if (bps == 0) return RS_ERR_CAPACITY;
         Lc.grid = bps * p->n_sm;
-        uint64_t warps = (uint64_t)Lc.grid * o.warps_per_block;   // no more processors than units
+        uint64_t warps = (uint64_t)Lc.grid * wpb;   // no more processors than units
         if (warps > pl.total_units) {
-            Lc.grid = (int)((pl.total_units + o.warps_per_block - 1) / o.warps_per_block);
+            Lc.grid = (int)((pl.total_units + wpb - 1) / wpb);
             if (Lc.grid < 1) Lc.grid = 1;
         }
     } else {
@@ -907,3 +934,237 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// rs_run_noalloc: the same work as rs_run, with its scratch memory in a fixed array
+// compiled into this library instead of a workspace passed by the caller.
+//
+// Some callers cannot allocate device memory when they run the pipeline: a host
+// application that owns the whole device-memory budget through its own allocator or a
+// hard cap, or a latency-critical loop in which an allocation (which may synchronise
+// the device) is not acceptable.  This entry point lets them run without a workspace:
+// it allocates nothing (no cudaMalloc / cudaFree / cudaMallocHost, no library that
+// allocates), and uses the scratch array below.  The array is RS_NOALLOC_WS_BYTES on
+// every GPU that loads the library, held until the process exits.
+
+#define RS_NOALLOC_WS_BYTES (16u << 20)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RS_NOALLOC_WS_BYTES];
+
+// Device address of the scratch array, looked up once per device (with that device
+// current) on the first rs_run_noalloc call made while it is current.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];
+
+static rs_status noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= 256) return RS_ERR_CAPACITY;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e);
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = g_noalloc_addr[dev];
+    return RS_OK;
+}
+
+static void make_plan_fixed(const rs_pipeline *p, FixedPlan *pl)
+{
+    pl->total_units = pl->plan_tiles = 0;
+    pl->Kmax = 1;
+    const bool load = p->stages[0].kind == RS_ENUM_LOAD;
+    size_t off = align256(sizeof(WsHeader));
+    const size_t ns = p->streams.size();
+    for (size_t i = 0; i < ns; ++i) {
+        const rs_stream_desc &s = p->streams[i];
+        StreamPlan &q = pl->sp[i];
+        memset(&q, 0, sizeof q);
+        if (load) {
+            q.mode = UNIT_MERGE;
+            const uint32_t kp = p->opts.regions_per_unit ? p->opts.regions_per_unit : 128u;
+            q.D = RS_STEP_REGION * kp;
+            q.K = kp + 1;
+            uint64_t steps = (uint64_t)RS_STEP_REGION * s.n_regions + s.n_elements;
+            q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
+            q.plan_tiles = (uint32_t)((s.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE);
+        } else {
+            q.mode = UNIT_REGIONS;
+            q.K = choose_K(p, s);
+            q.n_units = (uint32_t)((s.n_regions + q.K - 1) / q.K);
+        }
+        if (q.K > pl->Kmax) pl->Kmax = q.K;
+        pl->total_units += q.n_units;
+        pl->plan_tiles += q.plan_tiles;
+        if (q.mode == UNIT_MERGE) {
+            q.slots_off = off;
+            off = align256(off + (size_t)q.n_units * sizeof(Slot));
+            q.ucount_off = off;
+            off = align256(off + 4);
+            q.planlb_off = off;
+            off = align256(off + (size_t)q.plan_tiles * 8);
+        }
+    }
+    pl->zero_end = off;
+    for (size_t i = 0; i < ns; ++i) {
+        StreamPlan &q = pl->sp[i];
+        if (q.mode == UNIT_MERGE) {
+            q.rec_off = off;
+            off = align256(off + ((size_t)q.n_units + 1) * sizeof(UnitRec));
+        }
+    }
+    pl->table_off = off;
+    pl->total = off + align256(ns * sizeof(DevStream));
+}
+
+extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
+{
+    if (!p) return RS_ERR_INVALID;
+    if (p->streams.empty()) return RS_ERR_NOT_READY;
+    if (p->streams.size() > RS_NOALLOC_MAX_STREAMS) return RS_ERR_CAPACITY;
+    FixedPlan &pl = p->noalloc_plan;
+    make_plan_fixed(p, &pl);
+    if (pl.total > RS_NOALLOC_WS_BYTES) return RS_ERR_CAPACITY;   // beyond the fixed scratch
+    if (pl.total_units >= (1ull << 31)) return RS_ERR_CAPACITY;
+    void *ws = nullptr;
+    rs_status st = noalloc_scratch(&ws);
+    if (st != RS_OK) return st;
+    cudaError_t e;
+    if (!p->n_sm) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e);
+    }
+    const int strategy = resolve_strategy(p);
+    const rs_pipeline_opts &o = p->opts;
+    unsigned char *wsb = (unsigned char *)ws;
+    const size_t ns = p->streams.size();
+
+    // stream table in the pipeline's own host memory (pointers into the scratch array)
+    uint32_t base = 0, pbase = 0;
+    for (size_t i = 0; i < ns; ++i) {
+        const rs_stream_desc &s = p->streams[i];
+        const StreamPlan &q = pl.sp[i];
+        DevStream &d = p->noalloc_table[i];
+        memset(&d, 0, sizeof d);
+        d.parents = s.parents;
+        d.len = s.region_len;
+        d.offsets = s.region_offsets;
+        d.elements = s.elements;
+        d.ctx = s.ctx;
+        d.out_count = s.out_count;
+        d.out_sum = (unsigned long long *)s.out_sum;
+        d.out_min = s.out_min;
+        d.n_elements = s.n_elements;
+        d.R = (uint32_t)s.n_regions;
+        d.K = q.K;
+        d.n_units = q.n_units;
+        d.unit_base = base;
+        d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
+        d.mode = q.mode;
+        if (q.mode == UNIT_MERGE) {
+            d.rec = (UnitRec *)(wsb + q.rec_off);
+            d.slots = (Slot *)(wsb + q.slots_off);
+            d.u_count = (uint32_t *)(wsb + q.ucount_off);
+            d.plan_lb = (unsigned long long *)(wsb + q.planlb_off);
+            d.plan_tiles = q.plan_tiles;
+            d.plan_base = pbase;
+            d.D = q.D;
+            pbase += q.plan_tiles;
+        }
+        base += d.n_units;
+    }
+    if (pl.total_units == 0) return RS_OK;
+
+    KParams P;
+    memset(&P, 0, sizeof P);
+    bool need_ctx = false, need_par = p->stages[0].kind == RS_ENUM_HASH;
+    for (uint32_t i = 0; i < p->n_stages; ++i) {
+        P.st[i] = to_dev(p->stages[i]);
+        if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_HASH_CTX_LT) need_ctx = true;
+        if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_WEIGHT_LT) need_par = true;
+    }
+    P.n_stages = (int)p->n_stages;
+    P.strategy = strategy;
+    P.n_streams = (uint32_t)ns;
+    P.total_units = (uint32_t)pl.total_units;
+    P.plan_tiles = (uint32_t)pl.plan_tiles;
+    P.streams = (const DevStream *)(wsb + pl.table_off);
+    P.hdr = (WsHeader *)wsb;
+    P.V = o.ensemble_width / RS_W;
+    P.C = o.queue_capacity;
+    P.SC = o.signal_capacity;
+    P.TE = o.tile_elements;
+    P.NT = o.tiles_in_flight;
+    P.need_ctx = need_ctx;
+    P.need_par = need_par;
+    bool wc = false, wsum = false, wm = false;
+    for (const auto &s : p->streams) {
+        wc |= s.out_count != nullptr;
+        wsum |= s.out_sum != nullptr;
+        wm |= s.out_min != nullptr;
+    }
+    for (const auto &s : p->streams) {
+        if (s.n_regions == 0) continue;
+        if ((wc && !s.out_count) || (wsum && !s.out_sum) || (wm && !s.out_min)) return RS_ERR_INVALID;
+    }
+    P.want_count = wc;
+    P.want_sum = wsum;
+    P.want_min = wm;
+    P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
+    P.budget = o.device_budget;
+    P.spin_limit = 2000000000ull;
+    P.L = make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
+    if (!p->smem_max) {
+        int dev = 0, v = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+        if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return cuda_fail(e);
+        p->smem_max = (size_t)v;
+    }
+    uint32_t wpb = o.warps_per_block;
+    while (wpb > 1 && (size_t)P.L.per_warp * wpb > p->smem_max) --wpb;
+    if ((size_t)P.L.per_warp * wpb > p->smem_max) return RS_ERR_CAPACITY;
+    const int block = (int)wpb * 32;
+    const size_t smem = (size_t)P.L.per_warp * wpb;
+    int grid = (int)o.grid;
+    if (grid == 0) {
+        int bps = 0;
+        int ce = rs_kernel_occupancy(P, block, smem, &bps);
+        if (ce != 0) return cuda_fail((cudaError_t)ce);
+        if (bps == 0) return RS_ERR_CAPACITY;
+        grid = bps * p->n_sm;
+        uint64_t warps = (uint64_t)grid * wpb;
+        if (warps > pl.total_units) grid = (int)((pl.total_units + wpb - 1) / wpb);
+        if (grid < 1) grid = 1;
+    } else {
+        int ce = rs_kernel_max_smem_optin(P, smem);
+        if (ce != 0) return cuda_fail((cudaError_t)ce);
+    }
+
+    // the scratch keeps the previous call's contents: clear the part that must start at 0
+    cudaStream_t cs = (cudaStream_t)stream;
+    if ((e = cudaMemsetAsync(wsb, 0, pl.zero_end, cs)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(wsb + pl.table_off, p->noalloc_table, ns * sizeof(DevStream), cudaMemcpyHostToDevice,
+                             cs)) != cudaSuccess)
+        return cuda_fail(e);
+    if (P.plan_tiles > 0) {
+        int pg = (int)((P.plan_tiles + 7) / 8);
+        if (pg > p->n_sm * 8) pg = p->n_sm * 8;
+        if (pg < 1) pg = 1;
+        int le = rs_launch_planner(P, pg, (void *)cs);
+        if (le != 0) return cuda_fail((cudaError_t)le);
+    }
+    int le = rs_launch_kernel(P, grid, block, smem, (void *)cs);
+    if (le != 0) return cuda_fail((cudaError_t)le);
+    if (P.plan_tiles > 0) {
+        le = rs_launch_finalize(P, p->n_sm * 4, (void *)cs);
+        if (le != 0) return cuda_fail((cudaError_t)le);
+    }
+    return RS_OK;
+}

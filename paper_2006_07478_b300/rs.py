@@ -34,8 +34,8 @@ EXPORTS = [
     "rs_default_opts", "rs_pipeline_create", "rs_pipeline_destroy", "rs_pipeline_set_opts",
     "rs_pipeline_get_opts", "rs_stream_submit", "rs_clear_streams", "rs_workspace_size", "rs_run",
     "rs_fetch_region_results", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
-    "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_status_string",
-    "rs_last_cuda_error", "rs_version",
+    "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_run_noalloc",
+    "rs_status_string", "rs_last_cuda_error", "rs_version",
 ]
 
 
@@ -137,6 +137,7 @@ def lib(build_if_missing: bool = True):
                             ctypes.c_int),
             "rs_timing_enable": ([P, U32], ctypes.c_int),
             "rs_timing_read": ([P, ctypes.POINTER(ctypes.c_float), U32, ctypes.POINTER(U32)], ctypes.c_int),
+            "rs_run_noalloc": ([P, P], ctypes.c_int),
             "rs_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "rs_last_cuda_error": ([], ctypes.c_int),
             "rs_version": ([], U32),
@@ -305,6 +306,10 @@ class Pipeline:
     def run(self):
         ws = self.workspace()
         check(lib().rs_run(self._h, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _cur_stream()), "rs_run")
+
+    def run_noalloc(self):
+        """rs_run without a workspace: scratch in the library's fixed device array."""
+        check(lib().rs_run_noalloc(self._h, _cur_stream()), "rs_run_noalloc")
 
     def stats(self, raise_on_error=True) -> dict:
         ws = self.workspace()
