@@ -207,6 +207,159 @@ def read_traffic():
         return None
 
 
+def bench_graph(rs, torch, peak):
+    """Graph-edge stream: 2^22 vertices, 2^26 edges (Zipf hubs); items = edges."""
+    g = wl.graph_stream()
+    E, V = wl.n_elements(g), g["R"]
+    p = rs.Pipeline(wl.pipeline_graph_edges(), strategy="tag")
+    out = p.submit(rs.to_device(g), outputs=("count", "min"))
+    best, _ = p.autotune(trials=2)
+    p.timing_enable(16)
+    for _ in range(3):
+        p.run()
+    torch.cuda.synchronize()
+    p.timing_read()
+    for _ in range(7):
+        p.run()
+    kms = statistics.median(p.timing_read())
+    st = p.stats()
+    rng = np.random.default_rng(2)
+    from oracle import oracle
+    idx = np.unique(np.concatenate([rng.integers(0, V, 1000), np.argsort(np.diff(g["offsets"]))[-8:]]))
+    want = oracle.run_sampled(wl.pipeline_graph_edges(), g, idx)
+    got = rs.results_to_numpy(out)
+    exact = bool(np.array_equal(got["count"][idx], want["count"]) and np.array_equal(got["min"][idx], want["min"]))
+    ab = 4 * E + 4 * (V + 1) + 8 * V
+    p.close()
+    return {"workload": "graph: 2^22 vertices, 2^26 edges, Zipf(2.1) out-degree capped at 2^16; keep w(dst)<w(src); "
+                        "count and min dst per vertex",
+            "kernel_ms": kms, "items_per_s": E / (kms * 1e-3), "alg_gbs": ab / (kms * 1e-3) / 1e9,
+            "frac_of_measured_hbm": ab / (kms * 1e-3) / 1e9 / peak, "max_degree": int(np.diff(g["offsets"]).max()),
+            "chosen": {"strategy": "signal" if best["strategy"] == 0 else "tag",
+                       "regions_per_unit": best["regions_per_unit"], "ensemble_width": best["ensemble_width"]},
+            "active_lane_fraction": [round(x, 4) for x in st["active_lane_fraction"]],
+            "sampled_exact": exact}
+
+
+def bench_batched(rs, torch):
+    """4,096 independent hashed streams (lognormal sizes): one persistent launch for all
+    of them replayed from a CUDA graph, against one launch per stream."""
+    streams = wl.batched_streams()
+    pipe = wl.pipeline_hash_filter_map()
+    items = sum(wl.n_elements(s) for s in streams)
+    devs = [rs.to_device(s) for s in streams]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        p = rs.Pipeline(pipe, strategy="tag")
+        outs = [p.submit(d) for d in devs]
+        best, _ = p.autotune(trials=1)
+        p.graph_capture()
+        for _ in range(3):
+            p.graph_launch()
+        side.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(side)
+        for _ in range(reps):
+            p.graph_launch()
+        e1.record(side)
+        side.synchronize()
+        one_ms = e0.elapsed_time(e1) / reps
+        # one launch per stream: the same work, a pipeline (and workspace) per stream
+        singles = []
+        for d in devs:
+            q = rs.Pipeline(pipe, strategy=("signal" if best["strategy"] == 0 else "tag"),
+                            regions_per_unit=best["regions_per_unit"], ensemble_width=best["ensemble_width"])
+            q.submit(d)
+            q.workspace()
+            singles.append(q)
+        for q in singles[:64]:
+            q.run()
+        side.synchronize()
+        t0 = time.perf_counter()
+        e0.record(side)
+        for q in singles:
+            q.run()
+        e1.record(side)
+        side.synchronize()
+        per_ms = e0.elapsed_time(e1)
+        per_wall = (time.perf_counter() - t0) * 1e3
+    # exactness of a few streams against the oracle
+    from oracle import oracle
+    exact = True
+    for i in (0, 1, 2047, 4095):
+        want = oracle.run(pipe, streams[i])
+        got = rs.results_to_numpy(outs[i])
+        exact &= all(np.array_equal(got[k], want[k]) for k in got)
+    for q in singles:
+        q.close()
+    p.graph_release()
+    p.close()
+    return {"workload": "4096 hashed streams, sizes lognormal(median 2^14, sigma 1.5, cap 2^22), regions U{1..512}",
+            "items": items, "batched_graph_ms": one_ms, "batched_items_per_s": items / (one_ms * 1e-3),
+            "per_stream_launch_ms": per_ms, "per_stream_items_per_s": items / (per_ms * 1e-3),
+            "per_stream_host_wall_ms": per_wall, "speedup": per_ms / one_ms, "sampled_exact": bool(exact),
+            "chosen": {"strategy": "signal" if best["strategy"] == 0 else "tag",
+                       "regions_per_unit": best["regions_per_unit"], "ensemble_width": best["ensemble_width"]}}
+
+
+def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: float = 4.0):
+    """Open-loop Poisson arrivals of batched-size hashed streams into the
+    continuous-batching server; latency = scheduled arrival -> completion seen."""
+    pool = wl.batched_streams()
+    pipe = wl.pipeline_hash_filter_map()
+    reqs = [rs.host_request(s) for s in pool]
+    sizes = [wl.n_elements(s) for s in pool]
+    busy = [False] * len(pool)
+    arrivals = wl.poisson_arrivals(rate, seconds, seed=4)
+    srv = rs.Server(pipe, arena_bytes=int(arena_gb * (1 << 30)), strategy="tag")
+    stamps, owner, lat, done_items = {}, {}, [], 0
+    t0 = time.perf_counter()
+    a = 0
+    pending = []
+    while True:
+        now = time.perf_counter() - t0
+        while a < len(arrivals) and arrivals[a] <= now:
+            pending.append(a)
+            a += 1
+        keep = []
+        for j in pending:
+            slot = j % len(pool)
+            if busy[slot]:
+                keep.append(j)
+                continue
+            busy[slot] = True
+            rid = srv.submit(reqs[slot])
+            stamps[rid] = arrivals[j]
+            owner[rid] = slot
+        pending = keep
+        srv.progress()
+        for rid in srv.poll():
+            tdone = time.perf_counter() - t0
+            lat.append((stamps[rid], tdone - stamps[rid]))
+            slot = owner.pop(rid)
+            busy[slot] = False
+            done_items += sizes[slot]
+        if a >= len(arrivals) and not pending and not owner:
+            break
+        if now > seconds + 30:
+            break
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    L = np.array([x[1] for x in lat]) * 1e3
+    Lw = np.array([x[1] for x in lat if x[0] >= 1.0]) * 1e3
+    return {"workload": f"Poisson {rate:.0f} streams/s for {seconds:.0f} s, batched-size hashed streams, "
+                        f"arena {arena_gb:.0f} GiB",
+            "requests": int(len(lat)), "items_per_s": done_items / wall,
+            "p50_ms": float(np.percentile(L, 50)) if len(L) else None,
+            "p99_ms": float(np.percentile(L, 99)) if len(L) else None,
+            "p50_ms_after_1s": float(np.percentile(Lw, 50)) if len(Lw) else None,
+            "p99_ms_after_1s": float(np.percentile(Lw, 99)) if len(Lw) else None,
+            "batches": st["batches"], "largest_batch": st["largest_batch"],
+            "arena_peak_bytes": st["arena_peak"], "wall_s": wall}
+
+
 def run_case(args, rs, torch):
     """One stream, one fixed strategy: warm-up launches then `steps` timed launches.
     Used to give profilers a small, fixed launch sequence."""
@@ -248,6 +401,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the graph, batched and serving sections")
     ap.add_argument("--case", default=None,
                     help="MEAN:STRATEGY[:N_LOG2[:OPT=V,...]] -- one stream, fixed strategy and options "
                          "(a small fixed launch sequence for profilers)")
@@ -427,6 +582,16 @@ def main():
         cpu = {"value": items / secs, "unit": "items/s", "cores": threads, "kind": "oracle",
                "sample": f"{done} of the 5 streams, whole ({items} elements), {threads} threads"}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        for name, fn in (("graph_edges", lambda: bench_graph(rs, torch, peak)),
+                         ("batched", lambda: bench_batched(rs, torch)),
+                         ("serving", lambda: bench_serving(rs, torch, args.serve_seconds))):
+            try:
+                extras[name] = fn()
+            except Exception as exc:   # report, do not lose the main line
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "items/s", "n_gpus": world, "steps": args.steps,
@@ -444,7 +609,8 @@ def main():
             "clocks": sampler.summary(t_start, t_end),
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "gpu_launches": sum(len(k) for k in kernel_ms),
+            "gpu_launches": 3 * sum(len(k) for k in kernel_ms),   # planner, pipeline, finalize per run
+            **extras,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -232,6 +232,54 @@ rs_status rs_timing_enable(rs_pipeline *p, uint32_t capacity);
  * (launch order) to ms[], their number to *n, and empty the ring. */
 rs_status rs_timing_read(rs_pipeline *p, float *ms, uint32_t max, uint32_t *n);
 
+/* ---- serving: continuous batching of arriving streams --------------------------- */
+
+typedef struct rs_server rs_server;
+
+/* One request: a whole stream in HOST memory (page-locked for asynchronous copies).
+ * The input arrays must stay valid, and the output arrays must not be read, until the
+ * request id comes back from rs_server_poll. */
+typedef struct {
+    uint64_t n_regions;
+    const uint32_t *parents;     /* host, R ids, or NULL (p_r = r)                  */
+    const uint32_t *region_len;  /* host, R lengths                                 */
+    const uint32_t *elements;    /* host, for RS_ENUM_LOAD, else NULL               */
+    uint64_t n_elements;
+    const uint32_t *ctx;         /* host, R context words, or NULL                  */
+    uint32_t *out_count;         /* host outputs, R entries each, or NULL           */
+    uint64_t *out_sum;
+    uint32_t *out_min;
+    uint64_t total_elements_hint;
+} rs_request;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, batches, largest_batch;
+    uint64_t in_flight, queued;          /* batches on the GPU, requests waiting for memory */
+    uint64_t arena_live, arena_peak;     /* bytes of the arena in use now / at most          */
+} rs_server_stats;
+
+/* A server over one stage list.  `arena` (device, caller-owned, 256-byte aligned) is
+ * the device memory budget: a request is admitted only when its inputs and outputs fit
+ * in the arena's free part (a ring), and every batch's workspace comes from it too.
+ * Up to max_batch requests (0 = 4096) form one batch = one rs_run; up to max_inflight
+ * (0 = 2) batches are queued on `stream` at once, so arrivals during a batch join the
+ * next one.  No CUDA call is made here. */
+rs_status rs_server_create(const rs_stage_desc *stages, uint32_t n_stages, const rs_pipeline_opts *opts,
+                           void *arena, uint64_t arena_bytes, uint32_t max_batch, uint32_t max_inflight,
+                           rs_cuda_stream stream, rs_server **out);
+/* Queue a request (host-side only; admitted by a later rs_server_progress).
+ * RS_ERR_CAPACITY if it needs more than half the arena. */
+rs_status rs_server_submit(rs_server *s, const rs_request *r, uint64_t *req_id);
+/* Non-blocking step: retire finished batches (their results are in the host outputs),
+ * admit queued requests while the arena has room (copies on `stream`), and launch the
+ * forming batch if fewer than max_inflight batches are running. */
+rs_status rs_server_progress(rs_server *s);
+/* Ids of requests completed since the last poll (up to max; *n = how many). */
+rs_status rs_server_poll(rs_server *s, uint64_t *ids, uint32_t max, uint32_t *n);
+rs_status rs_server_get_stats(const rs_server *s, rs_server_stats *out);
+/* Synchronise the server's stream and free the server. */
+rs_status rs_server_destroy(rs_server *s);
+
 /* ---- running without a caller workspace ------------------------------------------ */
 
 /* The paper has no counterpart to this entry point; it serves callers that cannot

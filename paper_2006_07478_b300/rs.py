@@ -35,7 +35,8 @@ EXPORTS = [
     "rs_pipeline_get_opts", "rs_stream_submit", "rs_clear_streams", "rs_workspace_size", "rs_run",
     "rs_fetch_region_results", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
     "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_run_noalloc",
-    "rs_status_string", "rs_last_cuda_error", "rs_version",
+    "rs_server_create", "rs_server_submit", "rs_server_progress", "rs_server_poll", "rs_server_get_stats",
+    "rs_server_destroy", "rs_status_string", "rs_last_cuda_error", "rs_version",
 ]
 
 
@@ -95,6 +96,21 @@ class Stats(ctypes.Structure):
         }
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("n_regions", ctypes.c_uint64), ("parents", ctypes.c_void_p), ("region_len", ctypes.c_void_p),
+                ("elements", ctypes.c_void_p), ("n_elements", ctypes.c_uint64), ("ctx", ctypes.c_void_p),
+                ("out_count", ctypes.c_void_p), ("out_sum", ctypes.c_void_p), ("out_min", ctypes.c_void_p),
+                ("total_elements_hint", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "batches", "largest_batch",
+                                               "in_flight", "queued", "arena_live", "arena_peak")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class RsError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -138,6 +154,13 @@ def lib(build_if_missing: bool = True):
             "rs_timing_enable": ([P, U32], ctypes.c_int),
             "rs_timing_read": ([P, ctypes.POINTER(ctypes.c_float), U32, ctypes.POINTER(U32)], ctypes.c_int),
             "rs_run_noalloc": ([P, P], ctypes.c_int),
+            "rs_server_create": ([ctypes.POINTER(StageDesc), U32, ctypes.POINTER(Opts), P, U64, U32, U32, P,
+                                  ctypes.POINTER(P)], ctypes.c_int),
+            "rs_server_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(U64)], ctypes.c_int),
+            "rs_server_progress": ([P], ctypes.c_int),
+            "rs_server_poll": ([P, ctypes.POINTER(U64), U32, ctypes.POINTER(U32)], ctypes.c_int),
+            "rs_server_get_stats": ([P, ctypes.POINTER(ServerStats)], ctypes.c_int),
+            "rs_server_destroy": ([P], ctypes.c_int),
             "rs_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "rs_last_cuda_error": ([], ctypes.c_int),
             "rs_version": ([], U32),
@@ -353,6 +376,95 @@ class Pipeline:
         check(lib().rs_autotune(self._h, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _cur_stream(), trials,
                                 ctypes.byref(best), ctypes.byref(ms)), "rs_autotune")
         return best.as_dict(), float(ms.value)
+
+
+class Server:
+    """Continuous-batching server (rs_server_*) over one stage list.
+
+    The arena (device memory budget) is a torch uint8 tensor owned by this object.
+    Requests are host streams: dicts of pinned int32/int64 CPU tensors (see
+    `host_request`); their outputs are filled in place when poll() reports the id."""
+
+    def __init__(self, stages, arena_bytes, strategy="tag", max_batch=0, max_inflight=0, stream=None, **opts):
+        import torch
+        self.stages = list(stages)
+        arr = (StageDesc * len(self.stages))(*[stage_desc(s) for s in self.stages])
+        o = make_opts(strategy, **opts)
+        self.arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device="cuda")
+        off = (-self.arena.data_ptr()) % 256
+        self._arena_view = self.arena[off:]
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        check(lib().rs_server_create(arr, len(self.stages), ctypes.byref(o),
+                                     ctypes.c_void_p(self._arena_view.data_ptr()), int(arena_bytes),
+                                     int(max_batch), int(max_inflight), ctypes.c_void_p(self.stream.cuda_stream),
+                                     ctypes.byref(h)), "rs_server_create")
+        self._h = h
+        self._live = {}
+        self._ids = (ctypes.c_uint64 * 4096)()
+
+    def submit(self, req: dict) -> int:
+        r = Request()
+        r.n_regions = int(req["R"])
+        r.parents = _ptr(req.get("parents"))
+        r.region_len = _ptr(req.get("len"))
+        el = req.get("elements")
+        r.elements = _ptr(el)
+        r.n_elements = 0 if el is None else int(el.numel())
+        r.ctx = _ptr(req.get("ctx"))
+        r.out_count = _ptr(req.get("count"))
+        r.out_sum = _ptr(req.get("sum"))
+        r.out_min = _ptr(req.get("min"))
+        r.total_elements_hint = int(req.get("total_elements", 0))
+        rid = ctypes.c_uint64()
+        check(lib().rs_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), "rs_server_submit")
+        self._live[int(rid.value)] = req      # keep the host buffers alive until done
+        return int(rid.value)
+
+    def progress(self):
+        check(lib().rs_server_progress(self._h), "rs_server_progress")
+
+    def poll(self) -> list:
+        n = ctypes.c_uint32()
+        check(lib().rs_server_poll(self._h, self._ids, 4096, ctypes.byref(n)), "rs_server_poll")
+        done = [int(self._ids[i]) for i in range(n.value)]
+        for i in done:
+            self._live.pop(i, None)
+        return done
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(lib().rs_server_get_stats(self._h, ctypes.byref(st)), "rs_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rs_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def host_request(stream: dict, outputs=("count", "sum", "min")) -> dict:
+    """Pinned host tensors for a server request: inputs from a host stream (numpy uint32)
+    and empty output buffers."""
+    import numpy as np
+    import torch
+    req = {"R": int(stream["R"])}
+    for k in ("parents", "len", "elements", "ctx"):
+        a = stream.get(k)
+        req[k] = None if a is None else torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+    R = req["R"]
+    req["count"] = torch.empty(R, dtype=torch.int32).pin_memory() if "count" in outputs else None
+    req["sum"] = torch.empty(R, dtype=torch.int64).pin_memory() if "sum" in outputs else None
+    req["min"] = torch.empty(R, dtype=torch.int32).pin_memory() if "min" in outputs else None
+    if stream.get("len") is not None:
+        req["total_elements"] = int(np.asarray(stream["len"], dtype=np.uint64).sum())
+    return req
 
 
 def to_device(stream: dict) -> dict:

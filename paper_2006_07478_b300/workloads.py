@@ -251,27 +251,25 @@ def lognormal_stream_sizes(n_streams: int, median: float, sigma: float, cap: int
     return np.clip(n, 1, cap).astype(np.int64)
 
 
-def uniform_region_lengths_lockstep(sizes: np.ndarray, lo: int, hi: int, seed: int) -> list:
-    """Per stream, region lengths U{lo..hi} from that stream's own xorshift64
-    substream until its size is reached (last region truncated)."""
-    S = sizes.shape[0]
-    states = np.array([substream_seed(seed, 0x5000 + i) for i in range(S)], dtype=U64)
-    remaining = sizes.astype(np.int64).copy()
-    cols = []
-    while True:
-        active = remaining > 0
-        if not active.any():
-            break
-        xorshift64_lockstep(states)
-        L = uniform_int(states, lo, hi)
-        L = np.where(active, np.minimum(L, remaining), 0)
-        cols.append(L)
-        remaining -= L
-    M = np.stack(cols, axis=1) if cols else np.zeros((S, 0), dtype=np.int64)
+def uniform_region_lengths(sizes: np.ndarray, lo: int, hi: int, seed: int) -> list:
+    """Per stream, region lengths U{lo..hi} drawn from that stream's own splitmix64
+    substream (counter-based, so each stream vectorises) until its size is reached;
+    the last region is truncated."""
     out = []
-    for i in range(S):
-        row = M[i]
-        out.append(row[row > 0].astype(np.uint32))
+    mean = 0.5 * (lo + hi)
+    for i, n in enumerate(sizes.astype(np.int64)):
+        sub = substream_seed(seed, 0x5000 + i)
+        m = int(n / mean * 1.25) + 32
+        while True:
+            L = uniform_int(splitmix64_counter(sub, 0, m), lo, hi)
+            cs = np.cumsum(L)
+            if cs[-1] >= n:
+                break
+            m *= 2
+        last = int(np.searchsorted(cs, n))
+        L = L[: last + 1].copy()
+        L[-1] -= int(cs[last]) - int(n)
+        out.append(L.astype(np.uint32))
     return out
 
 
@@ -280,7 +278,7 @@ def batched_streams(n_streams: int = 4096, median: float = 2 ** 14, sigma: float
     """Many independent hashed-element streams with lognormal sizes; parent ids are
     the global region ordinal across the batch so streams do not repeat."""
     sizes = lognormal_stream_sizes(n_streams, median, sigma, cap, seed)
-    lens = uniform_region_lengths_lockstep(sizes, lo, hi, seed)
+    lens = uniform_region_lengths(sizes, lo, hi, seed)
     streams = []
     base = 0
     for i, L in enumerate(lens):

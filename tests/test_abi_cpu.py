@@ -124,3 +124,31 @@ def test_opts_round_trip():
     with pytest.raises(rs.RsError):
         p.set_opts(regions_per_unit=1000)
     p.close()
+
+
+def test_server_argument_checks_without_gpu():
+    L = rs.lib()
+    pipe = wl.pipeline_hash_filter_map()
+    arr = (rs.StageDesc * len(pipe))(*[rs.stage_desc(s) for s in pipe])
+    o = rs.make_opts()
+    h = ctypes.c_void_p()
+    # no arena / unaligned arena / too small arena
+    assert L.rs_server_create(arr, len(pipe), ctypes.byref(o), None, 1 << 20, 0, 0, None, ctypes.byref(h)) == \
+        rs.RS_ERR_INVALID
+    assert L.rs_server_create(arr, len(pipe), ctypes.byref(o), ctypes.c_void_p(0x1001), 1 << 20, 0, 0, None,
+                              ctypes.byref(h)) == rs.RS_ERR_INVALID
+    assert L.rs_server_create(arr, len(pipe), ctypes.byref(o), ctypes.c_void_p(0x1000), 1024, 0, 0, None,
+                              ctypes.byref(h)) == rs.RS_ERR_INVALID
+    # a valid server (the arena address is never touched without work)
+    assert L.rs_server_create(arr, len(pipe), ctypes.byref(o), ctypes.c_void_p(0x100000), 1 << 20, 0, 0, None,
+                              ctypes.byref(h)) == rs.RS_OK
+    r = rs.Request()
+    r.n_regions = 1 << 20          # needs more than half the arena
+    r.region_len = ctypes.c_void_p(0x2000)
+    r.out_count = ctypes.c_void_p(0x3000)
+    rid = ctypes.c_uint64()
+    assert L.rs_server_submit(h, ctypes.byref(r), ctypes.byref(rid)) == rs.RS_ERR_CAPACITY
+    r.n_regions = 16
+    assert L.rs_server_submit(h, ctypes.byref(r), ctypes.byref(rid)) == rs.RS_OK
+    st = rs.ServerStats()
+    assert L.rs_server_get_stats(h, ctypes.byref(st)) == rs.RS_OK and st.submitted == 1

@@ -1,0 +1,99 @@
+"""Serving form (continuous batching) on the GPU: every request's result equals the
+oracle's, whether it ran in a mix with many others or alone, including when a small
+arena forces requests to wait for memory.  Bit-exact (integer results)."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2006_07478_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2006_07478_b300 import rs as _rs
+    _rs.lib()
+    return _rs
+
+
+def _drain(srv, n, budget_s=60.0):
+    import time
+    done = []
+    t0 = time.time()
+    while len(done) < n:
+        srv.progress()
+        done += srv.poll()
+        assert time.time() - t0 < budget_s, srv.stats()
+    return done
+
+
+def _check(rs, req, stream, pipe):
+    want = oracle.run(pipe, stream)
+    got = rs.results_to_numpy({k: req[k] for k in ("count", "sum", "min")})
+    for k in got:
+        assert np.array_equal(got[k], want[k]), k
+
+
+@pytest.mark.parametrize("strategy", ["tag", "signal"])
+def test_mix_equals_alone(rs, strategy):
+    pipe = wl.pipeline_hash_filter_map()
+    streams = wl.batched_streams(n_streams=40, median=2 ** 10, sigma=1.5, cap=1 << 14, seed=21)
+    srv = rs.Server(pipe, arena_bytes=64 << 20, strategy=strategy)
+    reqs = [rs.host_request(s) for s in streams]
+    ids = [srv.submit(r) for r in reqs]
+    done = _drain(srv, len(ids))
+    assert sorted(done) == sorted(ids)
+    st = srv.stats()
+    assert st["completed"] == len(ids) and st["arena_live"] == 0
+    for r, s in zip(reqs, streams):
+        _check(rs, r, s, pipe)
+    # the same stream alone in its own batch gives the same result
+    alone = rs.host_request(streams[7])
+    srv.submit(alone)
+    _drain(srv, 1)
+    for k in ("count", "sum", "min"):
+        assert np.array_equal(alone[k].numpy(), reqs[7][k].numpy()), k
+    srv.close()
+
+
+def test_small_arena_admission_waits_for_memory(rs):
+    """An arena that holds only a few requests at a time: later requests wait until
+    earlier batches release their space, and all finish correctly."""
+    pipe = wl.pipeline_cascade()
+    streams = [wl.cascade_stream(n_total=1 << 15, mean=16, seed=30 + i) for i in range(24)]
+    srv = rs.Server(pipe, arena_bytes=1 << 20, strategy="tag")
+    reqs = [rs.host_request(s, outputs=("count", "sum")) for s in streams]
+    ids = [srv.submit(r) for r in reqs]
+    _drain(srv, len(ids))
+    st = srv.stats()
+    assert st["arena_peak"] <= 1 << 20 and st["batches"] > 1
+    for r, s in zip(reqs, streams):
+        want = oracle.run(pipe, s)
+        got = rs.results_to_numpy({"count": r["count"], "sum": r["sum"]})
+        for k in got:
+            assert np.array_equal(got[k], want[k]), k
+    srv.close()
+
+
+def test_requests_arriving_during_a_batch_join_the_next(rs):
+    import time
+    pipe = wl.pipeline_hash_filter_map()
+    streams = wl.batched_streams(n_streams=64, median=2 ** 12, sigma=1.0, cap=1 << 16, seed=5)
+    srv = rs.Server(pipe, arena_bytes=256 << 20, strategy="tag", max_inflight=2)
+    reqs = [rs.host_request(s) for s in streams]
+    done = []
+    for i, r in enumerate(reqs):
+        srv.submit(r)
+        if i % 8 == 7:
+            srv.progress()
+            done += srv.poll()
+    done += _drain(srv, len(reqs) - len(done))
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["batches"] >= 2
+    for r, s in zip(reqs, streams):
+        _check(rs, r, s, pipe)
+    srv.close()
