@@ -32,6 +32,7 @@ struct Req {
 struct Batch {
     rs_pipeline *p = nullptr;
     std::vector<uint64_t> ids;
+    uint64_t ws_bound = 0;       // workspace this batch will need, bounded from above
     uint64_t head_after = 0;     // ring head after this batch's last allocation
     uint64_t live_bytes = 0;     // bytes this batch holds in the ring
     cudaEvent_t ev = nullptr;
@@ -87,6 +88,22 @@ static bool ring_alloc(rs_server *s, uint64_t b, uint64_t *off, uint64_t *charge
     if (s->live > s->peak) s->peak = s->live;
     *charged = b + skip;
     return true;
+}
+
+// Upper bound of the workspace bytes one more stream adds to a batch (the layout of
+// rs_workspace_size: merge slots, unit count, planner words and unit records for loaded
+// streams, one stream-table entry for every stream, each piece 256-byte aligned).
+static uint64_t stream_ws_bound(const rs_server *s, const rs_request &r)
+{
+    uint64_t b = a256(sizeof(DevStream)) + 256;
+    if (s->st[0].kind == RS_ENUM_LOAD && r.n_regions) {
+        const uint64_t kp = s->opts.regions_per_unit ? s->opts.regions_per_unit : 128;
+        const uint64_t D = RS_STEP_REGION * kp;
+        const uint64_t units = (RS_STEP_REGION * r.n_regions + r.n_elements + D - 1) / D;
+        const uint64_t tiles = (r.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE;
+        b += a256(units * sizeof(Slot)) + 256 + a256(tiles * 8) + a256((units + 1) * sizeof(UnitRec));
+    }
+    return b;
 }
 
 static uint64_t request_bytes(const rs_server *s, const rs_request &r)
@@ -257,10 +274,22 @@ rs_status rs_server_progress(rs_server *s)
     // 2. admit queued requests while the arena has room
     while (!s->queued.empty() && s->forming.ids.size() < s->max_batch) {
         Req &q = s->queued.front();
-        uint64_t off = 0, charged = 0;
-        if (!ring_alloc(s, q.bytes, &off, &charged)) break;   // admission by free device memory
+        // admission by free device memory: the request and the batch's grown workspace
+        // must both fit (the workspace is taken from the ring when the batch launches)
+        const uint64_t ws_next = s->forming.ws_bound + stream_ws_bound(s, q.r) + 512;
+        const uint64_t h0 = s->head, t0 = s->tail, l0 = s->live, p0 = s->peak;
+        uint64_t off = 0, charged = 0, woff = 0, wch = 0;
+        if (!ring_alloc(s, q.bytes, &off, &charged)) break;
+        const uint64_t h1 = s->head, t1 = s->tail, l1 = s->live, p1 = s->peak;
+        const bool ws_fits = ring_alloc(s, a256(ws_next), &woff, &wch);
+        if (!ws_fits) {
+            s->head = h0; s->tail = t0; s->live = l0; s->peak = p0;   // undo the request's allocation
+            break;
+        }
+        s->head = h1; s->tail = t1; s->live = l1; s->peak = p1;       // keep only the request's
         q.off = off;
         s->forming.live_bytes += charged;
+        s->forming.ws_bound = ws_next - 512;
         rs_status st = admit(s, q);
         if (st != RS_OK) return st;
         s->forming_members.push_back(q);
