@@ -749,6 +749,8 @@ struct Proc {
             bool mine = lane < m;
             uint32_t L = mine ? (M.moff[k + 1] - M.moff[k]) : 0u;
             uint32_t Lsum = __reduce_add_sync(FULLMASK, L);
+            // enumeration ensembles: each parent's positions are cut into W-wide pieces
+            const uint32_t ens = __reduce_add_sync(FULLMASK, (L + W - 1) / W);
             uint32_t first = (w.sh[0] == w.st[0]) ? (w.qt[0] - w.qh[0]) : w.em[0];
             if (mine) {
                 uint32_t b = sidx(0, w.st[0] + 2 * lane), e = sidx(0, w.st[0] + 2 * lane + 1);
@@ -762,7 +764,7 @@ struct Proc {
             w.qt[0] += Lsum;
             w.em[0] = 0;
             ek += m;
-            CNT_ADD(0, 0, 1);
+            CNT_ADD(0, 0, ens);
             CNT_ADD(0, 1, Lsum);
         }
     }
@@ -1254,7 +1256,7 @@ struct Proc {
         if (STRAT == RS_STRATEGY_TAG) {
             // enumeration emits every position of the unit at once; node 1 derives tags
             w.qt[0] = total;
-            CNT_ADD(0, 0, 1);
+            CNT_ADD(0, 0, (total + W - 1) / W);
             CNT_ADD(0, 1, total);
             ek1 = 0;
             if (total > 0) advance_ek1(0, 0);
