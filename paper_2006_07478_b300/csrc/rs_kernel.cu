@@ -462,12 +462,27 @@ __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint
 // ---------------------------------------------------------------------------
 // Planner: parent offsets (a single-pass decoupled look-back scan of the lengths, or
 // the CSR offsets as given) and the merge-path unit records of every UNIT_MERGE stream.
-// One warp per tile of RS_PLAN_TILE parents; lane l takes 32 consecutive parents.
+// One warp per tile of RS_PLAN_TILE parents, read in rounds of 128: in round k lane l
+// holds the four parents r_lo + 128 k + 4 l .. + 3, so each load instruction of the warp
+// covers one contiguous 512-byte row, and every round's loads are issued before the
+// first is used.  Unit u starts inside the merge-path span (P_r, P_r + c + L_r] of the
+// parent r that contains u D (P_r = c r + offset of r, c = RS_STEP_REGION); positions
+// are taken relative to the tile, so locating the units costs one 32-bit division per
+// lane and round instead of two 64-bit divisions per parent.
+
+constexpr int PLAN_ROUNDS = RS_PLAN_TILE / 128;
+
+// x / d for x < 2^32 in the common case (d <= 16 * RS_MAX_K)
+__device__ __forceinline__ unsigned long long plan_div(unsigned long long x, uint32_t d)
+{
+    if ((x >> 32) == 0) return (uint32_t)x / d;
+    return x / d;
+}
 
 __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KParams P)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    const unsigned long long c = RS_STEP_REGION;
+    const uint32_t c = RS_STEP_REGION;
     for (;;) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(&P.hdr->plan_cursor, 1u);
@@ -479,21 +494,51 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
             if (P.streams[mid].plan_base <= t) lo = mid; else hi = mid - 1;
         }
         const DevStream &S = P.streams[lo];
-        const unsigned long long D = S.D;
+        const uint32_t D = S.D;
         const uint32_t tile = t - S.plan_base;
         const uint32_t r_lo = tile * RS_PLAN_TILE;
         const uint32_t r_hi = min(r_lo + RS_PLAN_TILE, S.R);
-        const uint32_t rb = r_lo + 32u * lane;
-        const uint32_t nl = rb < r_hi ? min(32u, r_hi - rb) : 0u;
         const uint32_t base_abs = S.offsets ? S.offsets[0] : 0u;
-        uint32_t lsum = 0;
+
+        // lengths of the lane's four parents in every round (0 past the tile's end)
+        uint32_t L[PLAN_ROUNDS][4];
         if (S.offsets) {
-            if (nl) lsum = S.offsets[rb + nl] - S.offsets[rb];
+#pragma unroll
+            for (int k = 0; k < PLAN_ROUNDS; ++k) {
+                const uint32_t r = r_lo + 128u * k + 4u * lane;
+                uint32_t a[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) a[j] = S.offsets[min(r + j, r_hi)];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) L[k][j] = a[j + 1] - a[j];
+            }
         } else {
-            for (uint32_t j = 0; j < nl; ++j) lsum += S.len[rb + j];
+            const bool vec = ((uintptr_t)S.len & 15u) == 0;
+#pragma unroll
+            for (int k = 0; k < PLAN_ROUNDS; ++k) {
+                const uint32_t r = r_lo + 128u * k + 4u * lane;
+                if (vec && r + 4u <= r_hi) {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(S.len + r));
+                    L[k][0] = v.x;
+                    L[k][1] = v.y;
+                    L[k][2] = v.z;
+                    L[k][3] = v.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) L[k][j] = (r + j < r_hi) ? __ldg(S.len + r + j) : 0u;
+                }
+            }
         }
-        const uint32_t incl = warp_incl_scan_u32(lsum, lane);
-        const uint32_t tsum = __shfl_sync(FULLMASK, incl, 31);
+        // per round: the lane's element count, its inclusive scan, the round total
+        uint32_t ls[PLAN_ROUNDS], incl[PLAN_ROUNDS];
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int k = 0; k < PLAN_ROUNDS; ++k) {
+            ls[k] = L[k][0] + L[k][1] + L[k][2] + L[k][3];
+            incl[k] = warp_incl_scan_u32(ls[k], lane);
+            tsum += __shfl_sync(FULLMASK, incl[k], 31);
+        }
+
         uint32_t E = 0;   // offset of parent r_lo relative to the stream's first element
         bool stop = false;
         if (S.offsets) {
@@ -538,28 +583,54 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
             }
         }
         if (stop) break;
-        // unit records: unit u starts inside parent r's merge-path span (P_r, P_{r+1}]
+
+        // unit records.  Frame: X = P - qt D, where qt = floor(P_{r_lo} / D), so the
+        // tile starts at X = rem < D and unit qt + m starts at X = m D.
         bool bad = false;
-        uint32_t off = E + incl - lsum;
-        for (uint32_t j = 0; j < nl && !bad; ++j) {
-            const uint32_t r = rb + j;
-            const uint32_t Lr = S.offsets ? S.offsets[r + 1] - S.offsets[r] : S.len[r];
-            const unsigned long long Pr = c * r + off, Pn = Pr + c + Lr;
-            for (unsigned long long u = Pr / D + 1; u <= Pn / D; ++u) {
-                if (u > S.n_units) {
-                    bad = true;
-                    break;
+        const unsigned long long Pt = (unsigned long long)c * r_lo + E;
+        const unsigned long long qt = Pt / D;
+        const uint32_t rem = (uint32_t)(Pt - qt * D);
+        uint32_t pre = 0;   // elements of the tile before this round
+#pragma unroll
+        for (int k = 0; k < PLAN_ROUNDS; ++k) {
+            const uint32_t rloc = 128u * k + 4u * lane;        // first parent, tile-relative
+            const uint32_t r = r_lo + rloc;
+            const uint32_t nl = r < r_hi ? min(4u, r_hi - r) : 0u;
+            const uint32_t offl = pre + incl[k] - ls[k];        // its element offset in the tile
+            const unsigned long long xa = rem + (unsigned long long)c * rloc + offl;
+            const unsigned long long xb = xa + (unsigned long long)c * nl + ls[k];
+            unsigned long long m = plan_div(xa, D);
+            if (nl && plan_div(xb, D) > m) {
+                unsigned long long x = xa;
+                uint32_t off = offl;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if ((uint32_t)j < nl) {
+                        const uint32_t Lr = L[k][j];
+                        const unsigned long long xn = x + c + Lr;
+                        while ((m + 1) * D <= xn) {
+                            ++m;
+                            const unsigned long long u = qt + m;
+                            if (u > S.n_units) {
+                                bad = true;
+                                break;
+                            }
+                            const long long into = (long long)(m * D) - (long long)(x + c);
+                            const uint32_t je = (uint32_t)(into <= 0 ? 0 : (into >= (long long)Lr ? Lr : into));
+                            const uint32_t oa = base_abs + E + off;
+                            UnitRec rc;
+                            rc.i = r + j + 1;
+                            rc.j = oa + je;
+                            rc.head_off = oa;
+                            rc.first_off = oa + Lr;
+                            S.rec[u] = rc;
+                        }
+                        x = xn;
+                        off += Lr;
+                    }
                 }
-                const long long into = (long long)(u * D) - (long long)(Pr + c);
-                const uint32_t je = (uint32_t)(into <= 0 ? 0 : (into >= (long long)Lr ? Lr : into));
-                UnitRec rc;
-                rc.i = r + 1;
-                rc.j = base_abs + off + je;
-                rc.head_off = base_abs + off;
-                rc.first_off = base_abs + off + Lr;
-                S.rec[u] = rc;
             }
-            off += Lr;
+            pre += __shfl_sync(FULLMASK, incl[k], 31);
         }
         if (tile == 0 && lane == 0) {
             UnitRec rc;
@@ -569,7 +640,7 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
         }
         if (tile + 1 == S.plan_tiles && lane == 0) {
             const uint32_t N = E + tsum;
-            const unsigned long long U = (c * S.R + N + D - 1) / D;
+            const unsigned long long U = ((unsigned long long)c * S.R + N + D - 1) / D;
             if (U > S.n_units) {
                 bad = true;
             } else {
