@@ -110,12 +110,16 @@ typedef struct {
     uint32_t regions_per_unit;  /* parents claimed per atomic step, <= 256; 0 = from the mean
                                    region length (about 2048 elements per claim)              */
     uint32_t tile_elements;     /* elements per bulk-copy tile for RS_ENUM_LOAD, a power of
-                                   two in W..4096; 0 = 256                                    */
+                                   two in W..4096; 0 = W                                      */
     uint32_t tiles_in_flight;   /* staging tiles per processor, 2 or 4; 0 = 4                 */
     uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = 8; fewer when their shared
                                    memory would not fit one CTA                              */
     uint32_t grid;              /* CTAs; 0 = a persistent grid (SMs x resident CTAs per SM)   */
-    uint32_t reserved;
+    uint32_t region_cost;       /* RS_ENUM_LOAD streams are cut into merge-path work units in
+                                   which a parent costs region_cost steps and an element one;
+                                   a unit holds <= regions_per_unit parents and <=
+                                   region_cost * regions_per_unit elements.  Power of two in
+                                   1..256; 0 = 16                                            */
     uint64_t device_budget;     /* scheduler sweeps allowed per claimed unit before the device
                                    reports RS_ERR_STALL; 0 = 2^22                            */
 } rs_pipeline_opts;
@@ -197,6 +201,11 @@ typedef struct {
                                           included in node 1), result flush, lifetime, and
                                           inside the nodes: node 1's gather, stage compute,
                                           compaction, tile recycling                       */
+    /* launch shape of the last enqueued pipeline kernel (host-side facts) */
+    uint32_t grid;                     /* CTAs                                              */
+    uint32_t block;                    /* threads per CTA (32 per processor)                */
+    uint32_t smem_per_block;           /* dynamic shared memory per CTA, bytes              */
+    uint32_t blocks_per_sm;            /* resident CTAs per SM (occupancy calculator)       */
 } rs_stats;
 
 /* Synchronise `stream`, read the workspace counters of the last rs_run and return
@@ -214,10 +223,14 @@ rs_status rs_graph_release(rs_pipeline *p);
 
 /* ---- autotuning (Section 5: choose per workload, from measurements) ------------ */
 
-/* Time candidate configurations (strategy x regions_per_unit x queue capacity x
- * warps_per_block) on the submitted streams with CUDA events, `trials` timed runs
- * each after one warm-up, keep the fastest in the pipeline and return it in *best
- * (and its mean milliseconds in *best_ms).  Overwrites the streams' outputs. */
+/* Choose options by timed trials on the submitted streams (the profile-guided choice
+ * of Section 5): for each strategy, a coordinate search from the defaults over the
+ * unit shape (regions_per_unit x region_cost, or whole-parent unit sizes for hashed
+ * streams), then ensemble width, processors per CTA and tile size, each change kept
+ * when faster; a strategy starting above three times the best so far is dropped.
+ * Each trial is one warm-up and `trials` timed runs (CUDA events).  The fastest is
+ * kept in the pipeline and returned in *best (mean milliseconds in *best_ms).
+ * Overwrites the streams' outputs. */
 rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream,
                       uint32_t trials, rs_pipeline_opts *best, float *best_ms);
 

@@ -27,7 +27,7 @@ static rs_status cuda_fail(cudaError_t e)
 }
 
 struct StreamPlan {
-    uint32_t mode, K, n_units, plan_tiles, D;
+    uint32_t mode, K, n_units, plan_tiles, D, c;
     size_t slots_off, ucount_off, planlb_off, rec_off;
 };
 
@@ -64,6 +64,8 @@ struct rs_pipeline {
     // needs no allocation of its own
     DevStream noalloc_table[RS_NOALLOC_MAX_STREAMS];
     FixedPlan noalloc_plan;
+    // launch shape of the last prepared launch (reported by rs_get_stats)
+    uint32_t last_grid = 0, last_block = 0, last_smem = 0, last_bps = 0;
 };
 
 static void timing_free(rs_pipeline *p)
@@ -103,9 +105,10 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
         o->queue_capacity = c;
     }
     if (o->signal_capacity == 0) o->signal_capacity = 32;
-    if (o->tile_elements == 0) o->tile_elements = 256;
+    if (o->tile_elements == 0) o->tile_elements = o->ensemble_width;
     if (o->tiles_in_flight == 0) o->tiles_in_flight = 4;
     if (o->warps_per_block == 0) o->warps_per_block = 8;
+    if (o->region_cost == 0) o->region_cost = RS_STEP_REGION;
     if (o->device_budget == 0) o->device_budget = 1ull << 22;
     return RS_OK;
 }
@@ -123,6 +126,7 @@ static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
     if (!is_pow2(o->tile_elements) || o->tile_elements < W || o->tile_elements > 4096) return RS_ERR_INVALID;
     if (o->tiles_in_flight != 2 && o->tiles_in_flight != 4) return RS_ERR_INVALID;
     if (o->warps_per_block < 1 || o->warps_per_block > 8) return RS_ERR_INVALID;
+    if (!is_pow2(o->region_cost) || o->region_cost > 256) return RS_ERR_INVALID;
     return RS_OK;
 }
 
@@ -355,9 +359,10 @@ static Plan make_plan(const rs_pipeline *p)
         if (load) {
             q.mode = UNIT_MERGE;
             const uint32_t kp = p->opts.regions_per_unit ? p->opts.regions_per_unit : 128u;
-            q.D = RS_STEP_REGION * kp;           // a unit owns <= kp parents and holds <= D elements
+            q.c = p->opts.region_cost ? p->opts.region_cost : RS_STEP_REGION;
+            q.D = q.c * kp;                      // a unit owns <= kp parents and holds <= D elements
             q.K = kp + 1;                        // plus the parent continued from an earlier unit
-            uint64_t steps = (uint64_t)RS_STEP_REGION * s.n_regions + s.n_elements;
+            uint64_t steps = (uint64_t)q.c * s.n_regions + s.n_elements;
             q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
             q.plan_tiles = (uint32_t)((s.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE);
         } else {
@@ -401,7 +406,9 @@ static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax,
     memset(&L, 0, sizeof L);
     size_t off = 0;
     L.o_prof = (uint32_t)off;
+#ifdef RS_PROFILE
     off += 8 * RS_PROF_SLOTS;
+#endif
     L.o_cnt = (uint32_t)off;
     off += 8 * 4 * RS_MAX_STAGES;
     L.o_pend = (uint32_t)off;
@@ -412,12 +419,16 @@ static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax,
     off += any_load ? 8 * o.tiles_in_flight : 0;
     off = align_up(off, 16);
     L.o_scr = (uint32_t)off;
-    off += 32 * 4;
+    off += (size_t)4 * (o.ensemble_width > 32 ? o.ensemble_width : 32);   // window marks (tag strategy)
     off = align_up(off, 128);
     L.o_tiles = (uint32_t)off;
     off += any_load ? (size_t)o.tiles_in_flight * o.tile_elements * 4 : 0;
+    // per-parent accumulators: every parent for the signal strategy; the tag strategy
+    // updates the outputs directly and keeps only the two pieces a unit may share with
+    // its neighbours (the continued first parent and a last parent running past it)
+    const size_t nacc = strategy == RS_STRATEGY_TAG ? 2 : (size_t)Kmax;
     L.o_rs = (uint32_t)off;
-    off += (size_t)Kmax * 8;
+    off += nacc * 8;
     for (int b = 0; b < 2; ++b) {
         L.o_raw[b] = (uint32_t)off;
         off += (size_t)(Kmax + 1) * 4;
@@ -429,16 +440,16 @@ static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax,
         off += need_par ? (size_t)Kmax * 4 : 0;
     }
     L.o_rc = (uint32_t)off;
-    off += (size_t)Kmax * 4;
+    off += nacc * 4;
     L.o_rm = (uint32_t)off;
-    off += want_min ? (size_t)Kmax * 4 : 0;
+    off += want_min ? nacc * 4 : 0;
     off = align_up(off, 16);
     // rings for edges 1..n-2 (edge 0 carries element positions, staged in the tiles)
     const uint32_t nr = p->n_stages - 2;
+    // tag strategy: one 64-bit slot {value, tag} per item; signal strategy: 32-bit values
     L.o_qv = (uint32_t)off;
-    off += (size_t)nr * o.queue_capacity * 4;
+    off += (size_t)nr * o.queue_capacity * (strategy == RS_STRATEGY_TAG ? 8 : 4);
     L.o_qt = (uint32_t)off;
-    off += strategy == RS_STRATEGY_TAG ? (size_t)nr * o.queue_capacity * 2 : 0;
     off = align_up(off, 16);
     // signal rings for edges 0..n-2
     L.o_sq = (uint32_t)off;
@@ -545,6 +556,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
                 d.plan_tiles = q.plan_tiles;
                 d.plan_base = pbase;
                 d.D = q.D;
+                d.c = q.c;
                 pbase += q.plan_tiles;
             }
             base += d.n_units;
@@ -615,6 +627,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
         int ce = rs_kernel_occupancy(P, Lc.block, Lc.smem, &bps);
         if (ce != 0) return cuda_fail((cudaError_t)ce);
         if (bps == 0) return RS_ERR_CAPACITY;
+        p->last_bps = (uint32_t)bps;
         Lc.grid = bps * p->n_sm;
         uint64_t warps = (uint64_t)Lc.grid * wpb;   // no more processors than units
         if (warps > pl.total_units) {
@@ -624,7 +637,14 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     } else {
         int ce = rs_kernel_max_smem_optin(P, Lc.smem);
         if (ce != 0) return cuda_fail((cudaError_t)ce);
+        int bps = 0;
+        ce = rs_kernel_occupancy(P, Lc.block, Lc.smem, &bps);
+        if (ce != 0) return cuda_fail((cudaError_t)ce);
+        p->last_bps = (uint32_t)bps;
     }
+    p->last_grid = (uint32_t)Lc.grid;
+    p->last_block = (uint32_t)Lc.block;
+    p->last_smem = (uint32_t)Lc.smem;
     return RS_OK;
 }
 
@@ -735,6 +755,10 @@ rs_status rs_get_stats(rs_pipeline *p, const void *workspace, rs_cuda_stream str
         out->firings[i] = h.counters[4 * i + 3];
     }
     for (int i = 0; i < RS_PROF_SLOTS && i < 16; ++i) out->cycles[i] = h.cyc[i];
+    out->grid = p->last_grid;
+    out->block = p->last_block;
+    out->smem_per_block = p->last_smem;
+    out->blocks_per_sm = p->last_bps;
     if (h.status & (ST_STALL | ST_LOOKBACK_TIMEOUT | ST_COPY_TIMEOUT | ST_OVERFLOW)) return RS_ERR_STALL;
     if (h.status & ST_BAD_INPUT) return RS_ERR_DEVICE_INPUT;
     return RS_OK;
@@ -844,7 +868,9 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
     if (p->streams.empty()) return RS_ERR_NOT_READY;
     if (trials == 0) trials = 3;
     const rs_pipeline_opts base = p->opts;
-    // units sized from the mean (K0) and half / double of it
+    const uint32_t fan = max_fanout_of(p->stages, p->n_stages);
+    const bool merge = p->stages[0].kind == RS_ENUM_LOAD;
+    // whole-parent units (hashed streams) sized from the mean region length
     rs_pipeline_opts probe = base;
     probe.regions_per_unit = 0;
     p->opts = probe;
@@ -853,74 +879,104 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
         uint32_t k = choose_K(p, s);
         if (k > K0) K0 = k;
     }
-    std::vector<rs_pipeline_opts> cand;
-    const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
-    // unit size: loaded streams use merge-path units of 128 or 256 parents; hashed ones
-    // whole-parent units around the size the mean length suggests
-    const bool merge = p->stages[0].kind == RS_ENUM_LOAD;
-    uint32_t Ks[2];
-    if (merge) {
-        Ks[0] = 128;
-        Ks[1] = 256;
-    } else {
-        Ks[0] = K0;
-        Ks[1] = K0 * 2 <= RS_MAX_K ? K0 * 2 : (K0 > 1 ? K0 / 2 : K0);
-    }
-    const uint32_t widths[2] = {2 * RS_W, 4 * RS_W};
-    const uint32_t wpbs[2] = {4, 8};
-    const uint32_t fan = max_fanout_of(p->stages, p->n_stages);
-    try {
-        for (uint32_t si = 0; si < 2; ++si)
-            for (uint32_t ki = 0; ki < 2; ++ki)
-                for (uint32_t xi = 0; xi < 2; ++xi)
-                    for (uint32_t wi = 0; wi < 2; ++wi) {
-                        if (ki > 0 && Ks[ki] == Ks[0]) continue;
-                        rs_pipeline_opts c = base;
-                        c.strategy = strategies[si];
-                        c.regions_per_unit = Ks[ki];
-                        c.ensemble_width = widths[xi];
-                        c.queue_capacity = 0;
-                        c.warps_per_block = wpbs[wi];
-                        c.grid = 0;
-                        fill_defaults(&c, fan);
-                        if (c.tile_elements < c.ensemble_width) c.tile_elements = c.ensemble_width;
-                        if (check_opts(&c, fan) != RS_OK) continue;
-                        cand.push_back(c);
-                    }
-    } catch (...) {
-        p->opts = base;
-        return RS_ERR_NOMEM;
-    }
+
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaError_t e;
     if ((e = cudaEventCreate(&ev0)) != cudaSuccess) { p->opts = base; return cuda_fail(e); }
     if ((e = cudaEventCreate(&ev1)) != cudaSuccess) { cudaEventDestroy(ev0); p->opts = base; return cuda_fail(e); }
-    float best_t = 1e30f;
-    rs_pipeline_opts best_o = base;
     rs_status result = RS_OK;
-    for (const auto &c : cand) {
+    // mean time of `trials` runs of configuration c; +inf when it does not fit or stalls
+    auto time_of = [&](rs_pipeline_opts c) -> float {
+        c.queue_capacity = 0;
+        c.grid = 0;
+        fill_defaults(&c, fan);
+        if (c.tile_elements < c.ensemble_width) c.tile_elements = c.ensemble_width;
+        if (check_opts(&c, fan) != RS_OK) return 1e30f;
         p->opts = c;
         p->table_dirty = true;
-        uint64_t need = make_plan(p).total;
-        if (need > workspace_bytes) continue;
+        if (make_plan(p).total > workspace_bytes) return 1e30f;
         rs_status st = run_impl(p, workspace, workspace_bytes, (cudaStream_t)stream);
-        if (st == RS_ERR_CAPACITY) continue;
-        if (st != RS_OK) { result = st; break; }
+        if (st == RS_ERR_CAPACITY) return 1e30f;
+        if (st != RS_OK) { result = st; return 1e30f; }
         cudaEventRecord(ev0, (cudaStream_t)stream);
         for (uint32_t t = 0; t < trials && st == RS_OK; ++t)
             st = run_impl(p, workspace, workspace_bytes, (cudaStream_t)stream);
         cudaEventRecord(ev1, (cudaStream_t)stream);
-        if (st != RS_OK) { result = st; break; }
-        if ((e = cudaEventSynchronize(ev1)) != cudaSuccess) { result = cuda_fail(e); break; }
+        if (st != RS_OK) { result = st; return 1e30f; }
+        if ((e = cudaEventSynchronize(ev1)) != cudaSuccess) { result = cuda_fail(e); return 1e30f; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
-        ms /= (float)trials;
         rs_stats stt;
-        rs_status ss = rs_get_stats(p, workspace, stream, &stt);
-        if (ss != RS_OK) continue;   // a configuration that stalls is never chosen
-        if (ms < best_t) {
-            best_t = ms;
-            best_o = c;
+        if (rs_get_stats(p, workspace, stream, &stt) != RS_OK) return 1e30f;   // never choose a stall
+        return ms / (float)trials;
+    };
+
+    // Per strategy, a coordinate search from the defaults: unit shape, then ensemble
+    // width, processors per CTA and tile size, each kept when it is faster.  A strategy
+    // whose starting point is over three times the best found so far is dropped.
+    float best_t = 1e30f;
+    rs_pipeline_opts best_o = base;
+    const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
+    // (regions per unit, steps per parent): merge-path units of 2048 or 4096 steps with
+    // 32..256 parents; whole-parent units of K0, 2 K0 or K0 / 2 parents
+    uint32_t shapes[5][2];
+    int n_shapes = 0;
+    if (merge) {
+        const uint32_t sh[5][2] = {{128, 16}, {256, 16}, {128, 32}, {64, 64}, {32, 128}};
+        for (int i = 0; i < 5; ++i) { shapes[i][0] = sh[i][0]; shapes[i][1] = sh[i][1]; }
+        n_shapes = 5;
+    } else {
+        shapes[0][0] = K0;
+        shapes[0][1] = RS_STEP_REGION;
+        n_shapes = 1;
+        if (K0 * 2 <= RS_MAX_K) { shapes[n_shapes][0] = K0 * 2; shapes[n_shapes++][1] = RS_STEP_REGION; }
+        if (K0 > 1) { shapes[n_shapes][0] = K0 / 2; shapes[n_shapes++][1] = RS_STEP_REGION; }
+    }
+    for (uint32_t si = 0; si < 2 && result == RS_OK; ++si) {
+        rs_pipeline_opts cur = base;
+        cur.strategy = strategies[si];
+        cur.ensemble_width = 4 * RS_W;
+        cur.warps_per_block = 8;
+        cur.tile_elements = 0;
+        cur.tiles_in_flight = 0;
+        cur.regions_per_unit = shapes[0][0];
+        cur.region_cost = shapes[0][1];
+        float cur_t = time_of(cur);
+        if (cur_t > 3.f * best_t) continue;
+        for (int i = 1; i < n_shapes && result == RS_OK; ++i) {
+            rs_pipeline_opts c = cur;
+            c.regions_per_unit = shapes[i][0];
+            c.region_cost = shapes[i][1];
+            const float t = time_of(c);
+            if (t < cur_t) { cur_t = t; cur = c; }
+        }
+        {
+            rs_pipeline_opts c = cur;
+            c.ensemble_width = 2 * RS_W;
+            c.tile_elements = 0;
+            const float t = time_of(c);
+            if (t < cur_t) { cur_t = t; cur = c; }
+        }
+        {
+            rs_pipeline_opts c = cur;
+            c.warps_per_block = 4;
+            const float t = time_of(c);
+            if (t < cur_t) { cur_t = t; cur = c; }
+        }
+        if (merge) {
+            // tiles of W elements (the default) against 2 W
+            rs_pipeline_opts c = cur;
+            c.tile_elements = 2 * cur.ensemble_width;
+            const float t = time_of(c);
+            if (t < cur_t) { cur_t = t; cur = c; }
+        }
+        if (cur_t < best_t) {
+            best_t = cur_t;
+            best_o = cur;
+            best_o.queue_capacity = 0;
+            best_o.grid = 0;
+            fill_defaults(&best_o, fan);
+            if (best_o.tile_elements < best_o.ensemble_width) best_o.tile_elements = best_o.ensemble_width;
         }
     }
     cudaEventDestroy(ev0);
@@ -987,9 +1043,10 @@ static void make_plan_fixed(const rs_pipeline *p, FixedPlan *pl)
         if (load) {
             q.mode = UNIT_MERGE;
             const uint32_t kp = p->opts.regions_per_unit ? p->opts.regions_per_unit : 128u;
-            q.D = RS_STEP_REGION * kp;
+            q.c = p->opts.region_cost ? p->opts.region_cost : RS_STEP_REGION;
+            q.D = q.c * kp;
             q.K = kp + 1;
-            uint64_t steps = (uint64_t)RS_STEP_REGION * s.n_regions + s.n_elements;
+            uint64_t steps = (uint64_t)q.c * s.n_regions + s.n_elements;
             q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
             q.plan_tiles = (uint32_t)((s.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE);
         } else {
@@ -1075,6 +1132,7 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
             d.plan_tiles = q.plan_tiles;
             d.plan_base = pbase;
             d.D = q.D;
+            d.c = q.c;
             pbase += q.plan_tiles;
         }
         base += d.n_units;

@@ -35,10 +35,10 @@ struct DevStage {
 // Work decomposition of a stream.
 enum : uint32_t {
     UNIT_REGIONS = 0,   // a unit is K whole consecutive parents (hashed elements: no offsets needed)
-    UNIT_MERGE = 1,     // merge-path units: a parent costs RS_STEP_REGION steps, an element 1 step,
+    UNIT_MERGE = 1,     // merge-path units: a parent costs DevStream::c steps, an element 1 step,
                         // a unit is D steps (DevStream.D); parents straddling units are split
 };
-#define RS_STEP_REGION 16u   // merge-path steps per parent (a unit of D steps owns <= D/16 parents)
+#define RS_STEP_REGION 16u   // default merge-path steps per parent (rs_pipeline_opts.region_cost)
 #define RS_PLAN_TILE 1024u                                  // parents per planner tile
 
 // Start of merge-path unit u: i = parents whose header step lies before u*D, j = absolute
@@ -80,6 +80,7 @@ struct DevStream {
     unsigned long long *plan_lb;   // planner look-back words, one per planner tile
     uint32_t plan_tiles, plan_base;
     uint32_t D;          // merge-path steps per unit
+    uint32_t c;          // merge-path steps per parent (an element costs one)
 };
 
 // Status bits written by the device.

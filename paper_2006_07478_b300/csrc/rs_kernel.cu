@@ -229,6 +229,7 @@ struct Smem {
     SArr<unsigned long long> prof, mbar, mmeta, rs, cnt;   // cnt: per node {ensembles, items, signals, firings}
     SArr<uint32_t> tiles, moff, mctx, mpar, rc, rm, qv, sq, scr;
     SArr<uint16_t> qtag;
+    SArr<unsigned long long> q64;   // tag strategy: ring slots packing {value, tag}
     SArr<uint32_t> mraw0, mraw1, mmoff0, mmoff1, mctx0, mctx1, mpar0, mpar1;
     __device__ __forceinline__ SArr<uint32_t> raw(uint32_t b) const { return b ? mraw1 : mraw0; }
     __device__ __forceinline__ SArr<uint32_t> moffb(uint32_t b) const { return b ? mmoff1 : mmoff0; }
@@ -308,7 +309,7 @@ __device__ __forceinline__ Unit describe_unit(const KParams &P, uint32_t ticket)
         u.has_head = u.j0 < u.first_off;
         u.r0 = u.has_head ? u.i0 - 1 : u.i0;
         u.nk = (u.has_head ? 1u : 0u) + (u.i1 - u.i0);
-        if (u.nk > S.D / RS_STEP_REGION + 1 || u.j1 < u.j0 || u.i1 < u.i0) u.skip = true;   // inconsistent records
+        if (u.nk > S.D / S.c + 1 || u.j1 < u.j0 || u.i1 < u.i0) u.skip = true;   // inconsistent records
     } else {
         u.r0 = u.lu * S.K;
         u.nk = min(S.K, S.R - u.r0);
@@ -448,7 +449,7 @@ __device__ __forceinline__ void poll_next(Pending &pu, const KParams &P, Smem &M
 __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint32_t off_abs, uint32_t ebase,
                                             bool owner_piece, uint32_t cnt, unsigned long long sum, uint32_t mn)
 {
-    const unsigned long long D = S.D, c = RS_STEP_REGION;
+    const unsigned long long D = S.D, c = S.c;
     const unsigned long long Pr = c * r + (off_abs - ebase);
     Slot *sl = &S.slots[Pr / D];
     if (cnt) {
@@ -466,13 +467,13 @@ __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint
 // holds the four parents r_lo + 128 k + 4 l .. + 3, so each load instruction of the warp
 // covers one contiguous 512-byte row, and every round's loads are issued before the
 // first is used.  Unit u starts inside the merge-path span (P_r, P_r + c + L_r] of the
-// parent r that contains u D (P_r = c r + offset of r, c = RS_STEP_REGION); positions
+// parent r that contains u D (P_r = c r + offset of r, c = the stream's parent cost); positions
 // are taken relative to the tile, so locating the units costs one 32-bit division per
 // lane and round instead of two 64-bit divisions per parent.
 
 constexpr int PLAN_ROUNDS = RS_PLAN_TILE / 128;
 
-// x / d for x < 2^32 in the common case (d <= 16 * RS_MAX_K)
+// x / d, with a 32-bit division when x < 2^32 (d = c K <= 2^16)
 __device__ __forceinline__ unsigned long long plan_div(unsigned long long x, uint32_t d)
 {
     if ((x >> 32) == 0) return (uint32_t)x / d;
@@ -482,7 +483,6 @@ __device__ __forceinline__ unsigned long long plan_div(unsigned long long x, uin
 __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KParams P)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t c = RS_STEP_REGION;
     for (;;) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(&P.hdr->plan_cursor, 1u);
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
             if (P.streams[mid].plan_base <= t) lo = mid; else hi = mid - 1;
         }
         const DevStream &S = P.streams[lo];
-        const uint32_t D = S.D;
+        const uint32_t D = S.D, c = S.c;
         const uint32_t tile = t - S.plan_base;
         const uint32_t r_lo = tile * RS_PLAN_TILE;
         const uint32_t r_hi = min(r_lo + RS_PLAN_TILE, S.R);
@@ -656,6 +656,94 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
     }
 }
 
+// ---------------------------------------------------------------------------
+// Element staging: bulk copies (TMA) of the unit's elements into a ring of NT tiles of
+// TE elements in the processor's shared memory, each tile's arrival counted on its own
+// mbarrier.
+
+__device__ __forceinline__ void tiles_issue(const KParams &P, Smem &M, Stage &g, uint32_t lane)
+{
+    const uint32_t TE = P.TE, NT = P.NT;
+    while (g.t_issued < g.ntiles && g.t_issued < g.t_freed + NT) {
+        uint32_t t = g.t_issued;
+        uint32_t start = g.A + t * TE;
+        uint32_t cnt = min(TE, g.B - start);
+        uint32_t slot = t & (NT - 1);
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&M.mbar[slot], cnt * 4u);
+            bulk_g2s(M.tiles.ptr() + slot * TE, g.elements + start, cnt * 4u, &M.mbar[slot]);
+        }
+        g.t_issued++;
+    }
+}
+
+// make the staged elements below e_hi (absolute) readable; false (with the status bit
+// set) when a copy has not landed within the spin limit
+__device__ __forceinline__ bool tiles_ready(const KParams &P, Smem &M, Stage &g, uint32_t lane, uint32_t e_hi)
+{
+    if (!g.tma) return true;
+    const uint32_t TE = P.TE, NT = P.NT;
+    uint32_t lim = min(e_hi, g.B);
+    while (g.t_ready < g.t_issued && g.A + g.t_ready * TE < lim) {
+        uint32_t slot = g.t_ready & (NT - 1);
+        uint32_t par = (g.phase >> slot) & 1u;
+        if (!mbar_try_wait(&M.mbar[slot], par)) {
+            const long long pt = PROF_NOW();
+            unsigned long long t0 = global_ns();
+            uint32_t it = 0;
+            while (!mbar_try_wait(&M.mbar[slot], par)) {
+                if ((++it & 63u) == 0 && global_ns() - t0 > P.spin_limit) {
+                    g.failed = true;
+                    break;
+                }
+            }
+            PROF_ADD(PF_TILEWAIT, pt);
+            (void)pt;
+            if (g.failed) {
+                if (lane == 0) atomicOr(&P.hdr->status, ST_COPY_TIMEOUT);
+                return false;
+            }
+        }
+        g.phase ^= 1u << slot;
+        g.t_ready++;
+    }
+    g.ready_lim = (g.t_ready >= g.ntiles) ? 0xFFFFFFFFu : g.A + g.t_ready * TE;
+    return true;
+}
+
+// every element below e_read (absolute) has been consumed: recycle tiles, refill them
+__device__ __forceinline__ void tiles_release(const KParams &P, Smem &M, Stage &g, uint32_t lane, uint32_t e_read)
+{
+    if (!g.tma) return;
+    const uint32_t TE = P.TE;
+    bool freed = false;
+    while (g.t_freed < g.t_ready && g.A + (g.t_freed + 1) * TE <= e_read) {
+        g.t_freed++;
+        freed = true;
+    }
+    g.free_lim = g.A + (g.t_freed + 1) * TE;
+    if (freed) {
+        __syncwarp();
+        tiles_issue(P, M, g, lane);
+    }
+}
+
+// the parent containing unit-local position pos (< moff[nk]), searching from `from`
+// (which starts at or before pos); empty parents are skipped
+__device__ __forceinline__ uint32_t parent_at(const Smem &M, uint32_t from, uint32_t pos, uint32_t nk,
+                                              uint32_t lane)
+{
+    uint32_t k = from;
+    for (;;) {
+        const uint32_t e2 = M.moff[min(k + lane + 1, nk)];
+        const uint32_t cnt = __popc(__ballot_sync(FULLMASK, e2 <= pos));
+        k += cnt;
+        if (cnt < 32) break;
+    }
+    return k;
+}
+
 // Compile-time pipeline signature: the enumerate op and the element-stage ops
 // (0 = no such stage; the aggregate follows the last one).  OE == 0 marks the generic
 // kernel, which reads every op from the parameters at run time.  A specialised
@@ -716,73 +804,13 @@ struct Proc {
         else return (uint32_t)S::template op<I>();
     }
 
-    // ---- tile staging (TMA bulk copies into a ring of NT*TE elements) ----
-    __device__ __forceinline__ void issue_tiles()
-    {
-        const uint32_t TE = P.TE, NT = P.NT;
-        while (g.t_issued < g.ntiles && g.t_issued < g.t_freed + NT) {
-            uint32_t t = g.t_issued;
-            uint32_t start = g.A + t * TE;
-            uint32_t cnt = min(TE, g.B - start);
-            uint32_t slot = t & (NT - 1);
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&M.mbar[slot], cnt * 4u);
-                bulk_g2s(M.tiles.ptr() + slot * TE, g.elements + start, cnt * 4u, &M.mbar[slot]);
-            }
-            g.t_issued++;
-        }
-    }
-
-    // make elements below e_hi (absolute) readable from the ring
+    // ---- tile staging ----
+    __device__ __forceinline__ void issue_tiles() { tiles_issue(P, M, g, lane); }
     __device__ __forceinline__ void ensure_ready(uint32_t e_hi)
     {
-        if (!g.tma) return;
-        const uint32_t TE = P.TE, NT = P.NT;
-        uint32_t lim = min(e_hi, g.B);
-        while (g.t_ready < g.t_issued && g.A + g.t_ready * TE < lim) {
-            uint32_t slot = g.t_ready & (NT - 1);
-            uint32_t par = (g.phase >> slot) & 1u;
-            if (!mbar_try_wait(&M.mbar[slot], par)) {
-                const long long pt = PROF_NOW();
-                unsigned long long t0 = global_ns();
-                uint32_t it = 0;
-                while (!mbar_try_wait(&M.mbar[slot], par)) {
-                    if ((++it & 63u) == 0 && global_ns() - t0 > P.spin_limit) {
-                        g.failed = true;
-                        break;
-                    }
-                }
-                PROF_ADD(PF_TILEWAIT, pt);
-                (void)pt;
-                if (g.failed) {
-                    if (lane == 0) atomicOr(&P.hdr->status, ST_COPY_TIMEOUT);
-                    stop = true;
-                    return;
-                }
-            }
-            g.phase ^= 1u << slot;
-            g.t_ready++;
-        }
-        g.ready_lim = (g.t_ready >= g.ntiles) ? 0xFFFFFFFFu : g.A + g.t_ready * TE;
+        if (!tiles_ready(P, M, g, lane, e_hi)) stop = true;
     }
-
-    // node 1 has consumed every element below e_read (absolute): recycle tiles
-    __device__ __forceinline__ void release_below(uint32_t e_read)
-    {
-        if (!g.tma) return;
-        const uint32_t TE = P.TE;
-        bool freed = false;
-        while (g.t_freed < g.t_ready && g.A + (g.t_freed + 1) * TE <= e_read) {
-            g.t_freed++;
-            freed = true;
-        }
-        g.free_lim = g.A + (g.t_freed + 1) * TE;
-        if (freed) {
-            __syncwarp();
-            issue_tiles();
-        }
-    }
+    __device__ __forceinline__ void release_below(uint32_t e_read) { tiles_release(P, M, g, lane, e_read); }
 
     __device__ __forceinline__ uint32_t load_elem(uint32_t e) const
     {
@@ -869,16 +897,7 @@ struct Proc {
     }
 
     // advance ek1 from parent `from` to the parent containing position pos (< total)
-    __device__ __forceinline__ void advance_ek1(uint32_t from, uint32_t pos)
-    {
-        ek1 = from;
-        for (;;) {
-            uint32_t e2 = M.moff[min(ek1 + lane + 1, nk)];
-            uint32_t cnt = __popc(__ballot_sync(FULLMASK, e2 <= pos));
-            ek1 += cnt;
-            if (cnt < 32) break;
-        }
-    }
+    __device__ __forceinline__ void advance_ek1(uint32_t from, uint32_t pos) { ek1 = parent_at(M, from, pos, nk, lane); }
 
     // ---- gather one ensemble of node I: x[s], k[s] for lane's items 32 s + lane ----
     // returns true when every item of the ensemble has the same parent (k[0])
@@ -1080,7 +1099,7 @@ struct Proc {
         if (F) take = W;
         uint32_t x[V], k[V];
         (void)gather<I, F>(take, x, k);
-        if (STRAT == RS_STRATEGY_SIGNAL) {
+        if constexpr (STRAT == RS_STRATEGY_SIGNAL) {
             // the whole ensemble belongs to the current parent (Section 3.3)
             unsigned long long part = 0;
             uint32_t mn = 0xFFFFFFFFu;
@@ -1097,7 +1116,7 @@ struct Proc {
             w.acc_s += ((unsigned long long)hi << 16) + lo;
             w.acc_m = min(w.acc_m, __reduce_min_sync(FULLMASK, mn));
             return;
-        }
+        } else {
 #pragma unroll
         for (int s = 0; s < V; ++s) {
             const uint32_t sb = 32u * s;
@@ -1145,6 +1164,7 @@ struct Proc {
                 }
             }
             __syncwarp();
+        }
         }
     }
 
@@ -1368,6 +1388,443 @@ struct Proc {
 
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// Tag strategy (Section 3.3, the alternative to signals): every item carries the local
+// index of its parent, so ensembles are never cut at parent boundaries and there are
+// no signal queues.  Items of an ensemble are placed lane-major -- item q is item
+// q % V of lane q / V -- so each lane's V items are adjacent in a ring and move with
+// 16-byte shared-memory accesses.  A ring slot packs {value, tag} into 64 bits.
+// Node 1 reads the staged elements in windows of W aligned to the tile ring; the
+// unit's first and last windows are partial and masked at their ends.  Compaction
+// (Section 4.1's 0..k outputs per item) is a warp scan of each lane's output count.
+
+__device__ __forceinline__ unsigned long long tag_pack(uint32_t v, uint32_t k)
+{
+    return ((unsigned long long)k << 32) | v;
+}
+
+template <int V, class S>
+struct TagProc {
+    static constexpr uint32_t W = 32u * V;
+    const KParams &P;
+    Smem &M;
+    Stage &g;
+    const uint32_t lane;
+    Pending *nxt;    // the prefetched next unit, in this processor's shared memory
+    bool nxt_open;   // its metadata still has to be turned into offsets
+    uint32_t nk, total, E0;
+    uint32_t s0;     // ring-relative index of the unit's first element
+    uint32_t ek1;    // parent containing node 1's next position
+    // edge 0: node 1's next window start and the end, ring-relative; edges e >= 1:
+    // free-running cursors of the shared-memory rings (slot = cursor & (C - 1))
+    uint32_t qh[RS_MAX_EDGES], qt[RS_MAX_EDGES];
+    bool stop;
+    // results: parents 1..nk-2 (and 0, nk-1 unless split) go straight to the outputs;
+    // a split first parent accumulates in slot 0, a split last parent in slot 1
+    const DevStream *S_;
+    uint32_t r0;
+    bool hsplit, tsplit;
+
+    __device__ __forceinline__ TagProc(const KParams &P_, Smem &M_, Stage &g_, uint32_t lane_)
+        : P(P_), M(M_), g(g_), lane(lane_), nxt(nullptr), nxt_open(false), nk(0), total(0), E0(0), s0(0),
+          ek1(0), stop(false), S_(nullptr), r0(0), hsplit(false), tsplit(false)
+    {
+    }
+
+    // accumulator slot of parent k if it is a split piece, else -1
+    __device__ __forceinline__ int split_slot(uint32_t k) const
+    {
+        if (k == 0 && hsplit) return 0;
+        if (k == nk - 1 && tsplit) return 1;
+        return -1;
+    }
+
+    // fold a partial result for parent k: into its slot (split piece) or the outputs
+    __device__ __forceinline__ void fold(uint32_t k, uint32_t cnt, unsigned long long sum, uint32_t mn) const
+    {
+        const int sl = split_slot(k);
+        if (sl >= 0) {
+            atomicAdd(&M.rc[sl], cnt);
+            atomicAdd(&M.rs[sl], sum);
+            if (P.want_min) atomicMin(&M.rm[sl], mn);
+        } else {
+            if (P.want_count) atomicAdd(S_->out_count + r0 + k, cnt);
+            if (P.want_sum) atomicAdd(S_->out_sum + r0 + k, sum);
+            if (P.want_min) atomicMin(S_->out_min + r0 + k, mn);
+        }
+    }
+
+    __device__ __forceinline__ int nst() const { return S::generic ? P.n_stages : S::n; }
+    template <int I>
+    __device__ __forceinline__ uint32_t op() const
+    {
+        if constexpr (S::generic) return P.st[I].op;
+        else return (uint32_t)S::template op<I>();
+    }
+
+    // ---- the stage op of node I on the lane's items (filter / map), Section 4.1 ----
+    template <int I>
+    __device__ __forceinline__ void apply(const uint32_t (&x)[V], const uint32_t (&k)[V], uint32_t vmask, bool uni,
+                                          bool (&keep)[V], uint32_t (&y)[V]) const
+    {
+        const DevStage &sd = P.st[I];
+        const uint32_t opc = op<I>();
+        uint32_t cu = 0;
+        if (opc == D_FILT_HASH_CTX && uni) cu = M.mctx[k[0]];
+        if (opc == D_FILT_WEIGHT && uni) cu = fmix32(M.mpar[k[0]] ^ sd.c0);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const uint32_t xs = x[j];
+            bool kp;
+            uint32_t ys = xs;
+            switch (opc) {
+            case D_FILT_MASK: kp = (xs & sd.p0) == sd.p1; break;
+            case D_FILT_MOD: kp = (xs % sd.p0) == sd.p1; break;
+            case D_FILT_HASH_CTX: kp = (fmix32(xs ^ sd.c0) ^ (uni ? cu : M.mctx[k[j]])) < sd.p1; break;
+            case D_FILT_WEIGHT: kp = fmix32(xs ^ sd.c0) < (uni ? cu : fmix32(M.mpar[k[j]] ^ sd.c0)); break;
+            case D_MAP_MULADD: ys = xs * sd.p0 + sd.p1; kp = true; break;
+            default: kp = false; break;
+            }
+            keep[j] = kp && ((vmask >> j) & 1u);
+            y[j] = ys;
+        }
+    }
+
+    // append the lane's kept items, in lane-major order, to the ring of edge I
+    template <int I>
+    __device__ __forceinline__ void push(const bool (&keep)[V], const uint32_t (&y)[V], const uint32_t (&k)[V])
+    {
+        const uint32_t cm = P.C - 1, rb = (I - 1) * P.C;
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j) c += keep[j] ? 1u : 0u;
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        uint32_t pos = qt[I] + incl - c;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            if (keep[j]) {
+                M.q64[rb + (pos & cm)] = tag_pack(y[j], k[j]);
+                ++pos;
+            }
+        }
+        qt[I] += __shfl_sync(FULLMASK, incl, 31);
+    }
+
+    // expansion stage (0..fanout outputs per item): item x emits n = hash32(x, p0) mod
+    // (fanout + 1) values hash32(x, p0 + 1 + i), i < n, in order
+    template <int I>
+    __device__ __forceinline__ void expand(const uint32_t (&x)[V], const uint32_t (&k)[V], uint32_t vmask)
+    {
+        const DevStage &sd = P.st[I];
+        const uint32_t cm = P.C - 1, rb = (I - 1) * P.C;
+        uint32_t nout[V], c = 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            nout[j] = ((vmask >> j) & 1u) ? fmix32(x[j] ^ sd.c0) % (sd.fanout + 1u) : 0u;
+            c += nout[j];
+        }
+        const uint32_t incl = warp_incl_scan_u32(c, lane);
+        uint32_t pos = qt[I] + incl - c;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            for (uint32_t o = 0; o < nout[j]; ++o) {
+                const uint32_t yv = fmix32(x[j] ^ fmix32((sd.p0 + 1u + o) ^ RS_GOLD));
+                M.q64[rb + (pos & cm)] = tag_pack(yv, k[j]);
+                ++pos;
+            }
+        }
+        qt[I] += __shfl_sync(FULLMASK, incl, 31);
+    }
+
+    // the aggregate (Section 4.2): count, sum and min of each parent's surviving items.
+    // One parent in the ensemble: a warp reduction and one update; several: one update
+    // per item.  The updates are reductions (associative, commutative), so their order
+    // does not matter.
+    __device__ __forceinline__ void aggregate(const uint32_t (&x)[V], const uint32_t (&k)[V], uint32_t vmask, bool uni,
+                                              uint32_t take)
+    {
+        if (uni) {
+            uint32_t lo = 0, hi = 0, mn = 0xFFFFFFFFu;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                if ((vmask >> j) & 1u) {
+                    lo += x[j] & 0xFFFFu;
+                    hi += x[j] >> 16;
+                    mn = min(mn, x[j]);
+                }
+            }
+            lo = __reduce_add_sync(FULLMASK, lo);
+            hi = __reduce_add_sync(FULLMASK, hi);
+            if (P.want_min) mn = __reduce_min_sync(FULLMASK, mn);
+            if (lane == 0) fold(k[0], take, ((unsigned long long)hi << 16) + lo, mn);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                if ((vmask >> j) & 1u) fold(k[j], 1u, (unsigned long long)x[j], x[j]);
+        }
+        __syncwarp();
+    }
+
+    // ---- node 1: one window of W ring-relative positions [qh[0], qh[0] + W) ----
+    // Fills x, k and the lane's valid bits; returns the number of valid items.
+    __device__ __forceinline__ uint32_t gather1(uint32_t (&x)[V], uint32_t (&k)[V], uint32_t &vmask, bool &uni)
+    {
+        const uint32_t r0 = qh[0];
+        const uint32_t lo = r0 > s0 ? r0 - s0 : 0u;           // first position of the window
+        const uint32_t hi = min(r0 + W - s0, total);          // end position (exclusive)
+        const uint32_t rl = r0 + V * lane;                    // the lane's first ring-relative index
+        vmask = 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const uint32_t r = rl + j;
+            if (r >= s0 && r - s0 < total) vmask |= 1u << j;
+        }
+        // parents: one for the whole window, or marks of the parents starting in it
+        const uint32_t end_k = M.moff[ek1 + 1];
+        uni = end_k >= hi;
+        if (uni) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) k[j] = ek1;
+            if (end_k == hi && hi < total) ek1 = parent_at(M, ek1, hi, nk, lane);
+        } else {
+            // scr[r - r0] = the non-empty parent whose first element is at ring index r
+#pragma unroll
+            for (int j = 0; j < V; ++j) M.scr[V * lane + j] = 0u;
+            __syncwarp();
+            for (uint32_t base = ek1 + 1;; base += 32) {
+                const uint32_t kk = base + lane;
+                const bool in = kk < nk;
+                const uint32_t st = in ? M.moff[kk] : total;
+                const uint32_t en = in ? M.moff[kk + 1] : total;
+                if (in && en > st && st < hi) M.scr[st + s0 - r0] = kk;
+                const uint32_t st31 = __shfl_sync(FULLMASK, st, 31);
+                if (!(base + 32 < nk && st31 < hi)) break;
+            }
+            __syncwarp();
+            uint32_t m[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) m[j] = M.scr[V * lane + j];
+            uint32_t lm = 0;
+#pragma unroll
+            for (int j = 0; j < V; ++j) lm = max(lm, m[j]);
+            // parent indices grow with position: a running maximum over the window
+            uint32_t incl = lm;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULLMASK, incl, d);
+                if (lane >= (uint32_t)d) incl = max(incl, t);
+            }
+            const uint32_t before = __shfl_up_sync(FULLMASK, incl, 1);
+            uint32_t cur = max(ek1, lane ? before : 0u);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                cur = max(cur, m[j]);
+                k[j] = cur;
+            }
+            const uint32_t last = max(ek1, __shfl_sync(FULLMASK, incl, 31));
+            ek1 = (hi < total && M.moff[last + 1] <= hi) ? parent_at(M, last, hi, nk, lane) : last;
+            __syncwarp();
+        }
+        // the elements (getItem of Figure 4)
+        if (op<0>() == D_ENUM_HASH) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const uint32_t p = rl + j - s0;
+                x[j] = ((vmask >> j) & 1u) ? fmix32(M.mpar[k[j]] ^ fmix32((p - M.moff[k[j]]) ^ RS_GOLD)) : 0u;
+            }
+        } else if (g.tma) {
+            if (!tiles_ready(P, M, g, lane, E0 + hi)) {
+                stop = true;
+                return 0;
+            }
+            const uint32_t mask = P.NT * P.TE - 1;
+            if (E0 + hi <= g.B) {
+                const uint32_t *tp = M.tiles.ptr() + (rl & mask);
+                if constexpr (V == 4) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(tp);
+                    x[0] = v.x;
+                    x[1 % V] = v.y;
+                    x[2 % V] = v.z;
+                    x[3 % V] = v.w;
+                } else if constexpr (V == 2) {
+                    const uint2 v = *reinterpret_cast<const uint2 *>(tp);
+                    x[0] = v.x;
+                    x[1 % V] = v.y;
+                } else {
+                    x[0] = tp[0];
+                }
+            } else {
+                // the unit's last few elements (past the last 16-byte boundary) are not staged
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const uint32_t e = E0 + (rl + j - s0);
+                    x[j] = 0u;
+                    if ((vmask >> j) & 1u) x[j] = e < g.B ? M.tiles[(rl + j) & mask] : __ldg(g.elements + e);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) x[j] = ((vmask >> j) & 1u) ? __ldg(g.elements + E0 + (rl + j - s0)) : 0u;
+        }
+        return hi - lo;
+    }
+
+    // ---- nodes I >= 2: an ensemble of `take` items from the ring of edge I - 1 ----
+    template <int I>
+    __device__ __forceinline__ void gather_ring(uint32_t take, uint32_t (&x)[V], uint32_t (&k)[V], uint32_t &vmask,
+                                                bool &uni) const
+    {
+        const uint32_t cm = P.C - 1, rb = (I - 2) * P.C;
+        const uint32_t h = qh[I - 1];
+        const unsigned long long *sp = M.q64.ptr() + rb + ((h + V * lane) & cm);
+        unsigned long long v[V];
+        if (V == 1 || (h & (V - 1)) != 0) {
+            // a head off the V-slot grid (not produced by the scheduler; kept for safety)
+#pragma unroll
+            for (int j = 0; j < V; ++j) v[j] = M.q64[rb + ((h + V * lane + j) & cm)];
+        } else {
+#pragma unroll
+            for (int t = 0; t < V / 2; ++t) {
+                const ulonglong2 w2 = reinterpret_cast<const ulonglong2 *>(sp)[t];
+                v[2 * t] = w2.x;
+                v[2 * t + 1] = w2.y;
+            }
+        }
+        vmask = 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            x[j] = (uint32_t)v[j];
+            k[j] = (uint32_t)(v[j] >> 32);
+            if (V * lane + j < take) vmask |= 1u << j;
+        }
+        // tags never decrease along a ring: equal ends mean one parent
+        const uint32_t k0 = __shfl_sync(FULLMASK, k[0], 0);
+        const uint32_t kl = (uint32_t)(M.q64[rb + ((h + take - 1) & cm)] >> 32);
+        uni = k0 == kl;
+        // slots past `take` hold stale words: give them the first item's parent
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+            if (uni || !((vmask >> j) & 1u)) k[j] = k0;
+    }
+
+    // ---- fire node I (Section 2.1's non-preemptive scheduler offers it the processor) ----
+    template <int I>
+    __device__ __forceinline__ void fire(bool drain)
+    {
+        if constexpr (S::template present<I>()) {
+            if (I >= nst() || stop) return;
+            const long long pt = PROF_NOW();
+            (void)pt;
+            fire_body<I>(drain);
+            PROF_ADD(PF_NODE0 + I, pt);
+        }
+    }
+
+    template <int I>
+    __device__ __forceinline__ void fire_body(bool drain)
+    {
+        constexpr bool can_push = S::template maybe_elem<I>();
+        const bool last = !can_push || (I == nst() - 1);
+        const uint32_t fan = (S::generic || S::template op<I>() == (int)D_EXPAND) ? P.st[I].fanout : 1u;
+        uint32_t n_ens = 0, n_items = 0;
+        for (;;) {
+            uint32_t x[V], k[V], vmask, take;
+            bool uni;
+            if constexpr (I == 1) {
+                if (qh[0] >= qt[0]) break;
+            } else {
+                const uint32_t avail = qt[I - 1] - qh[I - 1];
+                if (avail == 0 || (!drain && avail < W)) break;
+            }
+            if constexpr (can_push) {
+                if (!last && P.C - (qt[I] - qh[I]) < W * fan) break;   // wait for downstream space
+            }
+            if constexpr (I == 1) {
+                take = gather1(x, k, vmask, uni);
+                if (stop) break;
+            } else {
+                take = min(W, qt[I - 1] - qh[I - 1]);
+                gather_ring<I>(take, x, k, vmask, uni);
+            }
+            if (last) {
+                if constexpr (S::template maybe_last<I>()) aggregate(x, k, vmask, uni, take);
+            } else {
+                if constexpr (can_push) {
+                    if (op<I>() == D_EXPAND) {
+                        expand<I>(x, k, vmask);
+                    } else {
+                        bool keep[V];
+                        uint32_t y[V];
+                        apply<I>(x, k, vmask, uni, keep, y);
+                        push<I>(keep, y, k);
+                    }
+                }
+            }
+            if constexpr (I == 1) {
+                qh[0] += W;
+                if (op<0>() == D_ENUM_LOAD) tiles_release(P, M, g, lane, E0 + min(qh[0] - s0, total));
+            } else {
+                qh[I - 1] += take;
+            }
+            n_ens++;
+            n_items += take;
+        }
+        if (n_ens) {
+            CNT_ADD(I, 0, n_ens);
+            CNT_ADD(I, 1, n_items);
+            CNT_ADD(I, 3, 1);
+        }
+    }
+
+    __device__ __forceinline__ bool edge_empty(int e) const { return qh[e] >= qt[e]; }
+
+    // ---- run one unit to completion: sweeps offering every node a firing, upstream first ----
+    __device__ __forceinline__ void run_unit()
+    {
+#pragma unroll
+        for (int i = 0; i < RS_MAX_EDGES; ++i) qh[i] = qt[i] = 0;
+        s0 = (g.tma && op<0>() == D_ENUM_LOAD) ? (E0 - g.A) : 0u;
+        qt[0] = total ? s0 + total : 0u;
+        CNT_ADD(0, 0, (total + W - 1) / W);
+        CNT_ADD(0, 1, total);
+        ek1 = 0;
+        if (total > 0) ek1 = parent_at(M, 0, 0, nk, lane);
+        for (unsigned long long sweep = 0;; ++sweep) {
+            CNT_ADD(0, 3, 1);
+            if (nxt_open) {
+                poll_next(*nxt, P, M, lane);
+                nxt_open = !nxt->scanned;
+            }
+            fire<1>(true);
+            bool d = edge_empty(0);
+            fire<2>(d);
+            d = d && (nst() <= 2 || edge_empty(1));
+            fire<3>(d);
+            d = d && (nst() <= 3 || edge_empty(2));
+            fire<4>(d);
+            d = d && (nst() <= 4 || edge_empty(3));
+            fire<5>(d);
+            d = d && (nst() <= 5 || edge_empty(4));
+            if (stop) return;
+            if (d) break;
+            if (sweep >= P.budget) {
+                if (lane == 0) atomicOr(&P.hdr->status, ST_STALL);
+                stop = true;
+                return;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void finish_tiles()
+    {
+        if (!g.tma) return;
+        if (!tiles_ready(P, M, g, lane, 0xFFFFFFFFu)) stop = true;
+        g.t_freed = g.t_ready;
+    }
+};
+
+// ---------------------------------------------------------------------------
+
 template <int STRAT, int V, class SG>
 __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_constant__ KParams P)
 {
@@ -1396,6 +1853,7 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
     M.rm = sarr<uint32_t>(wb + P.L.o_rm);
     M.qv = sarr<uint32_t>(wb + P.L.o_qv);
     M.qtag = sarr<uint16_t>(wb + P.L.o_qt);
+    M.q64 = sarr<unsigned long long>(wb + P.L.o_qv);
     M.sq = sarr<uint32_t>(wb + P.L.o_sq);
     M.scr = sarr<uint32_t>(wb + P.L.o_scr);
 
@@ -1499,11 +1957,21 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
             for (uint32_t k = lane; k < nk; k += 32) M.mctx[k] = 0u;
         if (P.need_par && !S.parents)
             for (uint32_t k = lane; k < nk; k += 32) M.mpar[k] = r0 + k;
-        if (STRAT == RS_STRATEGY_TAG) {
+        const bool split_head = cur.u.has_head;
+        const bool split_tail = cur.split_tail;
+        if constexpr (STRAT == RS_STRATEGY_TAG) {
+            // every whole parent's results start at the identity in the outputs (empty
+            // parents included); the two split pieces start in their slots
             for (uint32_t k = lane; k < nk; k += 32) {
-                M.rc[k] = 0;
-                M.rs[k] = 0;
-                if (P.want_min) M.rm[k] = 0xFFFFFFFFu;
+                if ((k == 0 && split_head) || (k == nk - 1 && split_tail)) continue;
+                if (P.want_count) S.out_count[r0 + k] = 0u;
+                if (P.want_sum) S.out_sum[r0 + k] = 0ull;
+                if (P.want_min) S.out_min[r0 + k] = 0xFFFFFFFFu;
+            }
+            if (lane < 2) {
+                M.rc[lane] = 0;
+                M.rs[lane] = 0;
+                if (P.want_min) M.rm[lane] = 0xFFFFFFFFu;
             }
         }
         __syncwarp();
@@ -1520,16 +1988,35 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
         g.free_lim = g.A + P.TE;
 
         PROF_ADD(PF_SETUP, pt_setup);
-        Proc<STRAT, V, SG> pr(P, M, w, g, lane);
-        pr.nxt = pend;
-        pr.nxt_open = nxt.u.valid && !nxt.scanned;
-        pr.nk = nk;
-        pr.total = total;
-        pr.E0 = E0;
-        if (g.tma) pr.issue_tiles();
-        pr.run_unit();
-        pr.finish_tiles();
-        if (pr.stop) {
+        bool pstop;
+        if constexpr (STRAT == RS_STRATEGY_TAG) {
+            TagProc<V, SG> pr(P, M, g, lane);
+            pr.S_ = &S;
+            pr.r0 = r0;
+            pr.hsplit = split_head;
+            pr.tsplit = split_tail;
+            pr.nxt = pend;
+            pr.nxt_open = nxt.u.valid && !nxt.scanned;
+            pr.nk = nk;
+            pr.total = total;
+            pr.E0 = E0;
+            if (g.tma) tiles_issue(P, M, g, lane);
+            pr.run_unit();
+            pr.finish_tiles();
+            pstop = pr.stop;
+        } else {
+            Proc<STRAT, V, SG> pr(P, M, w, g, lane);
+            pr.nxt = pend;
+            pr.nxt_open = nxt.u.valid && !nxt.scanned;
+            pr.nk = nk;
+            pr.total = total;
+            pr.E0 = E0;
+            if (g.tma) pr.issue_tiles();
+            pr.run_unit();
+            pr.finish_tiles();
+            pstop = pr.stop;
+        }
+        if (pstop) {
             stop = true;
             break;
         }
@@ -1539,22 +2026,26 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
         const long long pt_fl = PROF_NOW();
         (void)pt_fl;
         // parents processed in pieces (the continued head, a last parent running past
-        // the unit) merge through their owner's slot; the rest are written directly
-        const bool split_head = cur.u.has_head;
-        const bool split_tail = cur.split_tail;
-        for (uint32_t k = lane; k < nk; k += 32) {
-            if ((k == 0 && split_head) || (k == nk - 1 && split_tail)) continue;
-            if (P.want_count) S.out_count[r0 + k] = M.rc[k];
-            if (P.want_sum) S.out_sum[r0 + k] = M.rs[k];
-            if (P.want_min) S.out_min[r0 + k] = M.rm[k];
+        // the unit) merge through their owner's slot; the rest are written directly (tag
+        // strategy: already updated in place)
+        if constexpr (STRAT != RS_STRATEGY_TAG) {
+            for (uint32_t k = lane; k < nk; k += 32) {
+                if ((k == 0 && split_head) || (k == nk - 1 && split_tail)) continue;
+                if (P.want_count) S.out_count[r0 + k] = M.rc[k];
+                if (P.want_sum) S.out_sum[r0 + k] = M.rs[k];
+                if (P.want_min) S.out_min[r0 + k] = M.rm[k];
+            }
         }
+        // accumulator of the first and the last parent: index 0 and nk - 1 (signal
+        // strategy), slots 0 and 1 (tag strategy; one slot when they are the same parent)
+        const uint32_t ah = 0, at = (STRAT == RS_STRATEGY_TAG) ? ((split_head && nk == 1) ? 0u : 1u) : nk - 1;
         if (lane == 0) {
             if (split_head)
-                merge_piece(S, r0, cur.u.head_off, cur.u.ebase, false, M.rc[0], M.rs[0],
-                            P.want_min ? M.rm[0] : 0xFFFFFFFFu);
+                merge_piece(S, r0, cur.u.head_off, cur.u.ebase, false, M.rc[ah], M.rs[ah],
+                            P.want_min ? M.rm[ah] : 0xFFFFFFFFu);
             if (split_tail && !(split_head && nk == 1))
-                merge_piece(S, r0 + nk - 1, cur.tail_off, cur.u.ebase, true, M.rc[nk - 1], M.rs[nk - 1],
-                            P.want_min ? M.rm[nk - 1] : 0xFFFFFFFFu);
+                merge_piece(S, r0 + nk - 1, cur.tail_off, cur.u.ebase, true, M.rc[at], M.rs[at],
+                            P.want_min ? M.rm[at] : 0xFFFFFFFFu);
         }
         __syncwarp();
         PROF_ADD(PF_FLUSH, pt_fl);

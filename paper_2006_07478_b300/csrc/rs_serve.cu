@@ -98,8 +98,9 @@ static uint64_t stream_ws_bound(const rs_server *s, const rs_request &r)
     uint64_t b = a256(sizeof(DevStream)) + 256;
     if (s->st[0].kind == RS_ENUM_LOAD && r.n_regions) {
         const uint64_t kp = s->opts.regions_per_unit ? s->opts.regions_per_unit : 128;
-        const uint64_t D = RS_STEP_REGION * kp;
-        const uint64_t units = (RS_STEP_REGION * r.n_regions + r.n_elements + D - 1) / D;
+        const uint64_t c = s->opts.region_cost ? s->opts.region_cost : RS_STEP_REGION;
+        const uint64_t D = c * kp;
+        const uint64_t units = (c * r.n_regions + r.n_elements + D - 1) / D;
         const uint64_t tiles = (r.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE;
         b += a256(units * sizeof(Slot)) + 256 + a256(tiles * 8) + a256((units + 1) * sizeof(UnitRec));
     }

@@ -50,11 +50,11 @@ class Opts(ctypes.Structure):
                 ("signal_capacity", ctypes.c_uint32), ("strategy", ctypes.c_uint32),
                 ("regions_per_unit", ctypes.c_uint32), ("tile_elements", ctypes.c_uint32),
                 ("tiles_in_flight", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
-                ("grid", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("grid", ctypes.c_uint32), ("region_cost", ctypes.c_uint32),
                 ("device_budget", ctypes.c_uint64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class StreamDesc(ctypes.Structure):
@@ -73,7 +73,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("device_status", ctypes.c_uint32), ("n_nodes", ctypes.c_uint32), ("units", ctypes.c_uint64),
                 ("ensembles", ctypes.c_uint64 * RS_MAX_STAGES), ("items", ctypes.c_uint64 * RS_MAX_STAGES),
                 ("signals", ctypes.c_uint64 * RS_MAX_STAGES), ("firings", ctypes.c_uint64 * RS_MAX_STAGES),
-                ("cycles", ctypes.c_uint64 * 16)]
+                ("cycles", ctypes.c_uint64 * 16), ("grid", ctypes.c_uint32), ("block", ctypes.c_uint32),
+                ("smem_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
     CYCLE_SLOTS = ("setup", "lookback", "tile_wait", "enumerate", "node1", "node2", "node3", "node4",
                    "node5", "flush", "total")
 
@@ -93,6 +94,8 @@ class Stats(ctypes.Structure):
                        "n1_gather": int(self.cycles[12]), "compute": int(self.cycles[13]),
                        "compact": int(self.cycles[14]), "tiles": int(self.cycles[15])},
             "active_lane_fraction": [(it / (float(W) * e)) if e else 0.0 for it, e in zip(items, ens)],
+            "launch": {"grid": self.grid, "block": self.block, "smem_per_block": self.smem_per_block,
+                       "blocks_per_sm": self.blocks_per_sm},
         }
 
 

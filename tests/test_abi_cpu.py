@@ -81,6 +81,13 @@ def test_queue_capacity_must_hold_worst_case_output():
     assert st == rs.RS_ERR_INVALID
     st, _ = _create(wl.pipeline_cascade(), ensemble_width=128, tile_elements=64)   # tile < W
     assert st == rs.RS_ERR_INVALID
+    st, _ = _create(wl.pipeline_cascade(), region_cost=24)                          # not a power of two
+    assert st == rs.RS_ERR_INVALID
+    st, _ = _create(wl.pipeline_cascade(), region_cost=512)                         # above 256
+    assert st == rs.RS_ERR_INVALID
+    st, h = _create(wl.pipeline_cascade(), region_cost=1, regions_per_unit=256)
+    assert st == rs.RS_OK
+    rs.lib().rs_pipeline_destroy(h)
 
 
 def test_stream_submit_validation_and_workspace_size():
