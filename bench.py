@@ -450,7 +450,8 @@ def main():
         tuned.append(best)
         row = {"mean": m, "regions": int(s["R"]), "alg_bytes": alg_bytes(s),
                "chosen": {"strategy": "signal" if best["strategy"] == 0 else "tag",
-                          "regions_per_unit": best["regions_per_unit"], "warps_per_block": best["warps_per_block"]}}
+                          **{k: best[k] for k in ("ensemble_width", "regions_per_unit", "region_cost",
+                                                  "tile_elements", "warps_per_block")}}}
         # both strategies at the tuned unit size, kernel-only event timing
         for strat in ("tag", "signal"):
             p.set_opts(strategy=strat)
@@ -466,7 +467,8 @@ def main():
             kms = statistics.median(ms)
             gbs = alg_bytes(s) / (kms * 1e-3) / 1e9
             row[strat] = {"kernel_ms": kms, "items_per_s": N_ELEM / (kms * 1e-3), "alg_gbs": gbs,
-                          "active_lane_fraction": [round(x, 4) for x in st["active_lane_fraction"]]}
+                          "active_lane_fraction": [round(x, 4) for x in st["active_lane_fraction"]],
+                          "launch": st["launch"]}
         p.set_opts(**{k: v for k, v in best.items() if k != "strategy"}, strategy=best["strategy"])
         per_mean.append(row)
 

@@ -107,13 +107,14 @@ typedef struct {
                                    legal power of two >= 64                                  */
     uint32_t signal_capacity;   /* signal-queue slots per edge; power of two >= 4; 0 = 32     */
     uint32_t strategy;          /* rs_strategy                                                 */
-    uint32_t regions_per_unit;  /* parents claimed per atomic step, <= 256; 0 = from the mean
+    uint32_t regions_per_unit;  /* parents claimed per atomic step, <= 512; 0 = from the mean
                                    region length (about 2048 elements per claim)              */
     uint32_t tile_elements;     /* elements per bulk-copy tile for RS_ENUM_LOAD, a power of
                                    two in W..4096; 0 = W                                      */
     uint32_t tiles_in_flight;   /* staging tiles per processor, 2 or 4; 0 = 4                 */
-    uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = 8; fewer when their shared
-                                   memory would not fit one CTA                              */
+    uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = the count (8, 4, 2 or 1)
+                                   giving the most resident processors per SM; fewer when
+                                   their shared memory would not fit one CTA                */
     uint32_t grid;              /* CTAs; 0 = a persistent grid (SMs x resident CTAs per SM)   */
     uint32_t region_cost;       /* RS_ENUM_LOAD streams are cut into merge-path work units in
                                    which a parent costs region_cost steps and an element one;

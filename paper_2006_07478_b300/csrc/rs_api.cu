@@ -66,6 +66,10 @@ struct rs_pipeline {
     FixedPlan noalloc_plan;
     // launch shape of the last prepared launch (reported by rs_get_stats)
     uint32_t last_grid = 0, last_block = 0, last_smem = 0, last_bps = 0;
+    // the automatic processors-per-CTA choice, for the kernel and per-processor bytes
+    // it was made for
+    const void *auto_key_fn = nullptr;
+    uint32_t auto_key_bytes = 0, auto_wpb = 0;
 };
 
 static void timing_free(rs_pipeline *p)
@@ -107,7 +111,6 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
     if (o->signal_capacity == 0) o->signal_capacity = 32;
     if (o->tile_elements == 0) o->tile_elements = o->ensemble_width;
     if (o->tiles_in_flight == 0) o->tiles_in_flight = 4;
-    if (o->warps_per_block == 0) o->warps_per_block = 8;
     if (o->region_cost == 0) o->region_cost = RS_STEP_REGION;
     if (o->device_budget == 0) o->device_budget = 1ull << 22;
     return RS_OK;
@@ -125,7 +128,7 @@ static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
     if (o->regions_per_unit > RS_MAX_K) return RS_ERR_INVALID;
     if (!is_pow2(o->tile_elements) || o->tile_elements < W || o->tile_elements > 4096) return RS_ERR_INVALID;
     if (o->tiles_in_flight != 2 && o->tiles_in_flight != 4) return RS_ERR_INVALID;
-    if (o->warps_per_block < 1 || o->warps_per_block > 8) return RS_ERR_INVALID;
+    if (o->warps_per_block > 8) return RS_ERR_INVALID;   // 0: chosen per launch
     if (!is_pow2(o->region_cost) || o->region_cost > 256) return RS_ERR_INVALID;
     return RS_OK;
 }
@@ -430,8 +433,8 @@ static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax,
     L.o_rs = (uint32_t)off;
     off += nacc * 8;
     for (int b = 0; b < 2; ++b) {
+        // the unit-local offsets are built in place over the loaded lengths / offsets
         L.o_raw[b] = (uint32_t)off;
-        off += (size_t)(Kmax + 1) * 4;
         L.o_moff[b] = (uint32_t)off;
         off += (size_t)(Kmax + 1) * 4;
         L.o_ctxb[b] = (uint32_t)off;
@@ -477,6 +480,35 @@ extern "C" rs_status rs_workspace_size(const rs_pipeline *p, uint64_t *bytes)
 {
     if (!p || !bytes) return RS_ERR_INVALID;
     *bytes = make_plan(p).total;
+    return RS_OK;
+}
+
+// warps_per_block = 0: the processors per CTA (8, 4, 2 or 1) giving the most resident
+// processors per SM for this kernel and per-processor shared memory (host-side
+// occupancy queries only; remembered for the same kernel and size)
+static rs_status auto_wpb(rs_pipeline *p, const KParams &P, uint32_t *out)
+{
+    const void *kf = rs_kernel_entry(P);
+    if (p->auto_key_fn == kf && p->auto_key_bytes == P.L.per_warp) {
+        *out = p->auto_wpb;
+        return RS_OK;
+    }
+    uint32_t best_w = 0, best_res = 0;
+    for (uint32_t cand = 8; cand >= 1; cand >>= 1) {
+        if ((size_t)P.L.per_warp * cand > p->smem_max) continue;
+        int bps = 0;
+        int ce = rs_kernel_occupancy(P, (int)cand * 32, (size_t)P.L.per_warp * cand, &bps);
+        if (ce != 0) return cuda_fail((cudaError_t)ce);
+        if ((uint32_t)bps * cand > best_res) {
+            best_res = (uint32_t)bps * cand;
+            best_w = cand;
+        }
+    }
+    if (best_w == 0) return RS_ERR_CAPACITY;
+    p->auto_key_fn = kf;
+    p->auto_key_bytes = P.L.per_warp;
+    p->auto_wpb = best_w;
+    *out = best_w;
     return RS_OK;
 }
 
@@ -607,7 +639,8 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.spin_limit = 2000000000ull;   // 2 s on the global timer
     P.L = make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
 
-    // processors per CTA: as asked, but no more than fit the per-block shared memory
+    // processors per CTA: as asked, but no more than fit the per-block shared memory;
+    // 0 = the count (8, 4, 2 or 1) giving the most resident processors per SM
     uint32_t wpb = o.warps_per_block;
     if (!p->smem_max) {
         int dev = 0, v = 0;
@@ -615,6 +648,10 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
         if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
             return cuda_fail(e);
         p->smem_max = (size_t)v;
+    }
+    if (wpb == 0) {
+        rs_status ws = auto_wpb(p, P, &wpb);
+        if (ws != RS_OK) return ws;
     }
     while (wpb > 1 && (size_t)P.L.per_warp * wpb > p->smem_max) --wpb;
     if ((size_t)P.L.per_warp * wpb > p->smem_max) return RS_ERR_CAPACITY;
@@ -919,12 +956,12 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
     const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
     // (regions per unit, steps per parent): merge-path units of 2048 or 4096 steps with
     // 32..256 parents; whole-parent units of K0, 2 K0 or K0 / 2 parents
-    uint32_t shapes[5][2];
+    uint32_t shapes[6][2];
     int n_shapes = 0;
     if (merge) {
-        const uint32_t sh[5][2] = {{128, 16}, {256, 16}, {128, 32}, {64, 64}, {32, 128}};
-        for (int i = 0; i < 5; ++i) { shapes[i][0] = sh[i][0]; shapes[i][1] = sh[i][1]; }
-        n_shapes = 5;
+        const uint32_t sh[6][2] = {{128, 16}, {256, 16}, {512, 16}, {128, 32}, {64, 64}, {32, 128}};
+        for (int i = 0; i < 6; ++i) { shapes[i][0] = sh[i][0]; shapes[i][1] = sh[i][1]; }
+        n_shapes = 6;
     } else {
         shapes[0][0] = K0;
         shapes[0][1] = RS_STEP_REGION;
@@ -936,7 +973,7 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
         rs_pipeline_opts cur = base;
         cur.strategy = strategies[si];
         cur.ensemble_width = 4 * RS_W;
-        cur.warps_per_block = 8;
+        cur.warps_per_block = 0;
         cur.tile_elements = 0;
         cur.tiles_in_flight = 0;
         cur.regions_per_unit = shapes[0][0];
@@ -957,9 +994,9 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
             const float t = time_of(c);
             if (t < cur_t) { cur_t = t; cur = c; }
         }
-        {
+        for (uint32_t wb : {4u, 8u}) {
             rs_pipeline_opts c = cur;
-            c.warps_per_block = 4;
+            c.warps_per_block = wb;
             const float t = time_of(c);
             if (t < cur_t) { cur_t = t; cur = c; }
         }
@@ -1186,6 +1223,10 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
         p->smem_max = (size_t)v;
     }
     uint32_t wpb = o.warps_per_block;
+    if (wpb == 0) {
+        rs_status ws = auto_wpb(p, P, &wpb);
+        if (ws != RS_OK) return ws;
+    }
     while (wpb > 1 && (size_t)P.L.per_warp * wpb > p->smem_max) --wpb;
     if ((size_t)P.L.per_warp * wpb > p->smem_max) return RS_ERR_CAPACITY;
     const int block = (int)wpb * 32;

@@ -7,7 +7,7 @@
 
 #define RS_W 32                       // lanes of one SIMD processor (a warp)
 #define RS_MAX_EDGES (RS_MAX_STAGES - 1)
-#define RS_MAX_K 256                  // parents per work unit
+#define RS_MAX_K 512                  // parents per work unit
 #define RS_GOLD 0x9E3779B9u
 
 // Device operation codes: the public (kind, op) pair flattened, with variants the
@@ -154,4 +154,5 @@ int rs_launch_planner(const KParams &P, int grid, void *stream);
 int rs_launch_finalize(const KParams &P, int grid, void *stream);
 int rs_kernel_max_smem_optin(const KParams &P, size_t smem);
 int rs_kernel_occupancy(const KParams &P, int block, size_t smem, int *blocks_per_sm);
+const void *rs_kernel_entry(const KParams &P);   // the kernel a launch with P would use
 int rs_kernel_is_specialised(const KParams &P);

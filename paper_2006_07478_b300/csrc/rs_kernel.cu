@@ -370,9 +370,12 @@ __device__ __forceinline__ void scan_meta(Pending &pu, const KParams &P, Smem &M
             const uint32_t q = b + lane;
             uint32_t start, L = 0;
             if (S.offsets) {
+                // raw and mo share storage: every lane reads its pair before any writes
                 start = q < no ? raw[hh + q] : 0u;
-                L = q < no ? raw[hh + q + 1] - start : 0u;
-                dec |= q < no && raw[hh + q + 1] < start;
+                const uint32_t nx = q < no ? raw[hh + q + 1] : 0u;
+                L = nx - start;
+                dec |= q < no && nx < start;
+                __syncwarp();
             } else {
                 L = q < no ? raw[hh + q] : 0u;
                 const uint32_t incl = warp_incl_scan_u32(L, lane);
@@ -404,6 +407,7 @@ __device__ __forceinline__ void scan_meta(Pending &pu, const KParams &P, Smem &M
         pu.E0 = j0;
     } else if (S.offsets) {
         const uint32_t ob = raw[0];
+        __syncwarp();   // raw and mo share storage
         bool dec = false;
         for (uint32_t k = lane; k <= nk; k += 32) {
             const uint32_t o = raw[k];
@@ -2117,6 +2121,8 @@ static const void *kernel_ptr(const KParams &P)
     }
     return generic;
 }
+
+const void *rs_kernel_entry(const KParams &P) { return kernel_ptr(P); }
 
 int rs_kernel_occupancy(const KParams &P, int block, size_t smem, int *blocks_per_sm)
 {
