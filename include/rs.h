@@ -111,7 +111,10 @@ typedef struct {
                                    region length (about 2048 elements per claim)              */
     uint32_t tile_elements;     /* elements per bulk-copy tile for RS_ENUM_LOAD, a power of
                                    two in W..4096; 0 = W                                      */
-    uint32_t tiles_in_flight;   /* staging tiles per processor, 2 or 4; 0 = 4                 */
+    uint32_t tiles_in_flight;   /* staging tiles per processor, 2 or 4; or 0: no staging --
+                                   each lane reads its elements with 16-byte loads issued
+                                   two ensembles ahead.  0 is the tag strategy's default;
+                                   for the signal strategy 0 means 4                        */
     uint32_t warps_per_block;   /* processors per CTA, 1..8; 0 = the count (8, 4, 2 or 1)
                                    giving the most resident processors per SM; fewer when
                                    their shared memory would not fit one CTA                */

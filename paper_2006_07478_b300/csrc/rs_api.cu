@@ -110,7 +110,9 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
     }
     if (o->signal_capacity == 0) o->signal_capacity = 32;
     if (o->tile_elements == 0) o->tile_elements = o->ensemble_width;
-    if (o->tiles_in_flight == 0) o->tiles_in_flight = 4;
+    // tiles_in_flight 0: the tag strategy reads elements directly (no staging tiles);
+    // the signal strategy stages 4 tiles
+    if (o->tiles_in_flight == 0 && o->strategy != RS_STRATEGY_TAG) o->tiles_in_flight = 4;
     if (o->region_cost == 0) o->region_cost = RS_STEP_REGION;
     if (o->device_budget == 0) o->device_budget = 1ull << 22;
     return RS_OK;
@@ -127,7 +129,7 @@ static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
     if (o->strategy > RS_STRATEGY_AUTO) return RS_ERR_INVALID;
     if (o->regions_per_unit > RS_MAX_K) return RS_ERR_INVALID;
     if (!is_pow2(o->tile_elements) || o->tile_elements < W || o->tile_elements > 4096) return RS_ERR_INVALID;
-    if (o->tiles_in_flight != 2 && o->tiles_in_flight != 4) return RS_ERR_INVALID;
+    if (o->tiles_in_flight != 0 && o->tiles_in_flight != 2 && o->tiles_in_flight != 4) return RS_ERR_INVALID;
     if (o->warps_per_block > 8) return RS_ERR_INVALID;   // 0: chosen per launch
     if (!is_pow2(o->region_cost) || o->region_cost > 256) return RS_ERR_INVALID;
     return RS_OK;
@@ -1001,11 +1003,18 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
             if (t < cur_t) { cur_t = t; cur = c; }
         }
         if (merge) {
-            // tiles of W elements (the default) against 2 W
-            rs_pipeline_opts c = cur;
-            c.tile_elements = 2 * cur.ensemble_width;
-            const float t = time_of(c);
-            if (t < cur_t) { cur_t = t; cur = c; }
+            // element staging: the tag strategy's direct loads (its default) against
+            // 4 tiles of W and of 2 W elements; the signal strategy's tiles of W against 2 W
+            const bool tag = cur.strategy == RS_STRATEGY_TAG;
+            const uint32_t base_nt = cur.tiles_in_flight;
+            for (uint32_t m : {1u, 2u}) {
+                if (!tag && m == 1) continue;
+                rs_pipeline_opts c = cur;
+                c.tiles_in_flight = tag ? 4 : base_nt;
+                c.tile_elements = m * cur.ensemble_width;
+                const float t = time_of(c);
+                if (t < cur_t) { cur_t = t; cur = c; }
+            }
         }
         if (cur_t < best_t) {
             best_t = cur_t;

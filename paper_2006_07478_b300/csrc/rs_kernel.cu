@@ -112,6 +112,23 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// streaming loads (read once: no L1 allocation) of 4 / 2 consecutive words
+__device__ __forceinline__ uint4 ld_stream_v4(const uint32_t *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_stream_v2(const uint32_t *p)
+{
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
 // 4-byte asynchronous copy global -> shared (no register staging)
 __device__ __forceinline__ void cp_async4(void *dst, const void *src)
 {
@@ -1428,11 +1445,44 @@ struct TagProc {
     const DevStream *S_;
     uint32_t r0;
     bool hsplit, tsplit;
+    // direct element loads (no staging tiles; 16-byte-aligned elements): each lane
+    // reads its V elements of a window with one vector load, issued two windows ahead
+    bool direct;
+    uint32_t A;              // absolute index of ring-relative position 0 (E0 rounded down to 4)
+    uint32_t lim;            // elements in the stream (loads stay below it)
+    uint32_t pf_r;           // ring-relative start of the next window to load
+    uint32_t pf0[V], pf1[V]; // the loaded next two windows
 
     __device__ __forceinline__ TagProc(const KParams &P_, Smem &M_, Stage &g_, uint32_t lane_)
         : P(P_), M(M_), g(g_), lane(lane_), nxt(nullptr), nxt_open(false), nk(0), total(0), E0(0), s0(0),
-          ek1(0), stop(false), S_(nullptr), r0(0), hsplit(false), tsplit(false)
+          ek1(0), stop(false), S_(nullptr), r0(0), hsplit(false), tsplit(false), direct(false), A(0), lim(0),
+          pf_r(0)
     {
+    }
+
+    // the lane's V elements of the window starting at ring-relative index r
+    __device__ __forceinline__ void load_window(uint32_t r, uint32_t (&x)[V]) const
+    {
+        const uint32_t e = A + r + V * lane;
+        const uint32_t *src = g.elements + e;
+        if (e + V <= lim) {
+            if constexpr (V == 4) {
+                const uint4 v = ld_stream_v4(src);
+                x[0] = v.x;
+                x[1 % V] = v.y;
+                x[2 % V] = v.z;
+                x[3 % V] = v.w;
+            } else if constexpr (V == 2) {
+                const uint2 v = ld_stream_v2(src);
+                x[0] = v.x;
+                x[1 % V] = v.y;
+            } else {
+                x[0] = __ldg(src);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) x[j] = (e + j < lim) ? __ldg(src + j) : 0u;
+        }
     }
 
     // accumulator slot of parent k if it is a split piece, else -1
@@ -1636,8 +1686,16 @@ struct TagProc {
                 const uint32_t p = rl + j - s0;
                 x[j] = ((vmask >> j) & 1u) ? fmix32(M.mpar[k[j]] ^ fmix32((p - M.moff[k[j]]) ^ RS_GOLD)) : 0u;
             }
+        } else if (direct) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                x[j] = pf0[j];
+                pf0[j] = pf1[j];
+            }
+            if (pf_r < qt[0]) load_window(pf_r, pf1);
+            pf_r += W;
         } else if (g.tma) {
-            if (!tiles_ready(P, M, g, lane, E0 + hi)) {
+            if (E0 + hi > g.ready_lim && !tiles_ready(P, M, g, lane, E0 + hi)) {
                 stop = true;
                 return 0;
             }
@@ -1766,7 +1824,10 @@ struct TagProc {
             }
             if constexpr (I == 1) {
                 qh[0] += W;
-                if (op<0>() == D_ENUM_LOAD) tiles_release(P, M, g, lane, E0 + min(qh[0] - s0, total));
+                if (op<0>() == D_ENUM_LOAD && g.tma) {
+                    const uint32_t e_read = E0 + min(qh[0] - s0, total);
+                    if (e_read >= g.free_lim) tiles_release(P, M, g, lane, e_read);
+                }
             } else {
                 qh[I - 1] += take;
             }
@@ -1787,8 +1848,16 @@ struct TagProc {
     {
 #pragma unroll
         for (int i = 0; i < RS_MAX_EDGES; ++i) qh[i] = qt[i] = 0;
-        s0 = (g.tma && op<0>() == D_ENUM_LOAD) ? (E0 - g.A) : 0u;
+        direct = op<0>() == D_ENUM_LOAD && !g.tma && P.NT == 0 && S_->tma_ok;
+        s0 = (g.tma && op<0>() == D_ENUM_LOAD) ? (E0 - g.A) : (direct ? (E0 & 3u) : 0u);
         qt[0] = total ? s0 + total : 0u;
+        if (direct) {
+            A = E0 - s0;
+            lim = S_->n_elements < 0xFFFFFFFFull ? (uint32_t)S_->n_elements : 0xFFFFFFFFu;
+            if (qt[0] > 0) load_window(0, pf0);
+            if (qt[0] > W) load_window(W, pf1);
+            pf_r = 2 * W;
+        }
         CNT_ADD(0, 0, (total + W - 1) / W);
         CNT_ADD(0, 1, total);
         ek1 = 0;
@@ -1982,7 +2051,7 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
 
         // ---- element staging: bulk copies of [A, B) in tiles ----
         g.elements = S.elements;
-        g.tma = load && S.tma_ok;
+        g.tma = load && S.tma_ok && P.NT > 0;
         g.A = E0 & ~3u;
         g.B = (E0 + total) & ~3u;
         if (g.B < g.A) g.B = g.A;
