@@ -152,7 +152,7 @@ typedef struct {
     const uint32_t *region_offsets; /* device, R+1 non-decreasing CSR offsets (element index
                                        of each parent's first element); NULL = from lengths */
     const uint32_t *elements;       /* device, element array for RS_ENUM_LOAD, else NULL     */
-    uint64_t n_elements;            /* entries in `elements` (bounds check), < 2^32          */
+    uint64_t n_elements;            /* entries in `elements` (bounds check), < 2^32 - 4096   */
     const uint32_t *ctx;            /* device, R context words t_r, or NULL (t_r = 0)        */
     uint32_t *out_count;            /* device, R; count of survivors per region (or NULL)    */
     uint64_t *out_sum;              /* device, R; sum of survivors per region (or NULL)      */

@@ -17,6 +17,10 @@
 
 #define RS_VERSION 1u
 #define RS_NOALLOC_MAX_STREAMS 64
+#define RS_TAG_MAX_K 65536u         // parents per unit (tag strategy; the signal strategy's
+                                    // per-parent shared memory limits it to RS_MAX_K)
+#define RS_TAG_UNIT_STEPS 4096u     // tag strategy: default merge-path steps per unit
+#define RS_TAG_UNIT_ELEMS 8192.0    // tag strategy: hashed units of about this many elements
 
 static thread_local int g_last_cuda = 0;
 
@@ -109,11 +113,11 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
         o->queue_capacity = c;
     }
     if (o->signal_capacity == 0) o->signal_capacity = 32;
-    if (o->tile_elements == 0) o->tile_elements = o->ensemble_width;
+    if (o->tile_elements == 0) o->tile_elements = o->ensemble_width < 128 ? o->ensemble_width : 128;
     // tiles_in_flight 0: the tag strategy reads elements directly (no staging tiles);
     // the signal strategy stages 4 tiles
     if (o->tiles_in_flight == 0 && o->strategy != RS_STRATEGY_TAG) o->tiles_in_flight = 4;
-    if (o->region_cost == 0) o->region_cost = RS_STEP_REGION;
+    // region_cost 0 stays 0: resolved per strategy when units are planned
     if (o->device_budget == 0) o->device_budget = 1ull << 22;
     return RS_OK;
 }
@@ -121,17 +125,18 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
 static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
 {
     const uint32_t W = o->ensemble_width;
-    if (W != RS_W && W != 2 * RS_W && W != 4 * RS_W) return RS_ERR_INVALID;
+    if (W != RS_W && W != 2 * RS_W && W != 4 * RS_W && W != 8 * RS_W) return RS_ERR_INVALID;
     if (!is_pow2(o->queue_capacity) || o->queue_capacity < W * (fan + 1) || o->queue_capacity > 4096)
         return RS_ERR_INVALID;
     if (!is_pow2(o->signal_capacity) || o->signal_capacity < 4 || o->signal_capacity > 1024)
         return RS_ERR_INVALID;
     if (o->strategy > RS_STRATEGY_AUTO) return RS_ERR_INVALID;
-    if (o->regions_per_unit > RS_MAX_K) return RS_ERR_INVALID;
-    if (!is_pow2(o->tile_elements) || o->tile_elements < W || o->tile_elements > 4096) return RS_ERR_INVALID;
+    if (o->regions_per_unit > RS_TAG_MAX_K) return RS_ERR_INVALID;
+    const uint32_t Wt = W < 128 ? W : 128;   // signal-strategy tiles hold at least one ensemble
+    if (!is_pow2(o->tile_elements) || o->tile_elements < Wt || o->tile_elements > 4096) return RS_ERR_INVALID;
     if (o->tiles_in_flight != 0 && o->tiles_in_flight != 2 && o->tiles_in_flight != 4) return RS_ERR_INVALID;
     if (o->warps_per_block > 8) return RS_ERR_INVALID;   // 0: chosen per launch
-    if (!is_pow2(o->region_cost) || o->region_cost > 256) return RS_ERR_INVALID;
+    if (o->region_cost != 0 && (!is_pow2(o->region_cost) || o->region_cost > 256)) return RS_ERR_INVALID;
     return RS_OK;
 }
 
@@ -172,6 +177,7 @@ static DevStage to_dev(const rs_stage_desc &s)
     d.p0 = s.params[0];
     d.p1 = s.params[1];
     d.c0 = host_fmix32(s.params[0] ^ RS_GOLD);
+    d.c0s = d.c0 ^ (d.c0 >> 16);
     switch (s.kind) {
     case RS_ENUM_HASH: d.op = D_ENUM_HASH; break;
     case RS_ENUM_LOAD: d.op = D_ENUM_LOAD; break;
@@ -293,7 +299,7 @@ rs_status rs_stream_submit(rs_pipeline *p, const rs_stream_desc *s, uint64_t *st
     if (s->n_regions > 0) {
         if (!s->region_len && !s->region_offsets) return RS_ERR_INVALID;
         if (p->stages[0].kind == RS_ENUM_LOAD && (!s->elements || s->n_elements == 0)) return RS_ERR_INVALID;
-        if (s->n_elements >= (1ull << 32)) return RS_ERR_CAPACITY;
+        if (s->n_elements >= (1ull << 32) - 4096) return RS_ERR_CAPACITY;   // positions stay 32-bit
         for (uint32_t i = 1; i + 1 < p->n_stages; ++i)
             if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_HASH_CTX_LT) {
                 // ctx may be NULL (t_r = 0)
@@ -322,19 +328,71 @@ rs_status rs_clear_streams(rs_pipeline *p)
 
 // ---------------------------------------------------------------------------
 
-static uint32_t choose_K(const rs_pipeline *p, const rs_stream_desc &s)
+// whole-parent units (hashed enumeration): about 2048 elements per unit for the signal
+// strategy (its per-parent shared memory caps K at RS_MAX_K), about 8192 for the tag
+// strategy
+static uint32_t choose_K(const rs_pipeline *p, const rs_pipeline_opts &o, const rs_stream_desc &s, int strategy)
 {
-    if (p->opts.regions_per_unit) return p->opts.regions_per_unit;
+    if (o.regions_per_unit) return o.regions_per_unit;
     if (s.n_regions == 0) return 1;
     uint64_t tot = s.total_elements_hint;
     if (!tot && p->stages[0].kind == RS_ENUM_LOAD) tot = s.n_elements;
     double mean = tot ? (double)tot / (double)s.n_regions : 32.0;
-    double want = 2048.0 / (mean > 1e-9 ? mean : 1e-9);
+    const bool tag = strategy == RS_STRATEGY_TAG;
+    double want = (tag ? RS_TAG_UNIT_ELEMS : 2048.0) / (mean > 1e-9 ? mean : 1e-9);
+    const uint32_t kmax = tag ? RS_TAG_MAX_K : RS_MAX_K;
     uint32_t K = 1;
-    while (K * 2 <= want && K * 2 <= RS_MAX_K) K *= 2;
+    while (K * 2 <= want && K * 2 <= kmax) K *= 2;
     return K;
 }
 
+// merge-path unit shape: c steps per parent, D steps per unit
+static void merge_shape(const rs_pipeline_opts &o, int strategy, uint32_t *c, uint32_t *D, uint32_t *K)
+{
+    if (strategy == RS_STRATEGY_TAG) {
+        // a parent costs region_cost steps (default 1); a unit is region_cost x
+        // regions_per_unit steps (default 4096)
+        const uint32_t cc = o.region_cost ? o.region_cost : 1u;
+        uint32_t k = o.regions_per_unit;
+        if (!k) k = RS_TAG_UNIT_STEPS / cc ? RS_TAG_UNIT_STEPS / cc : 1u;
+        *c = cc;
+        *D = cc * k;
+        *K = k;
+    } else {
+        const uint32_t kp = o.regions_per_unit ? o.regions_per_unit : 128u;
+        *c = o.region_cost ? o.region_cost : RS_STEP_REGION;
+        *D = *c * kp;      // a unit owns <= kp parents and holds <= D elements
+        *K = kp + 1;       // plus the parent continued from an earlier unit
+    }
+}
+
+// the work decomposition of one stream
+static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int strategy, const rs_stream_desc &s,
+                        StreamPlan &q)
+{
+    memset(&q, 0, sizeof q);
+    if (p->stages[0].kind == RS_ENUM_LOAD) {
+        q.mode = UNIT_MERGE;
+        merge_shape(o, strategy, &q.c, &q.D, &q.K);
+        uint64_t steps = (uint64_t)q.c * s.n_regions + s.n_elements;
+        q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
+        q.plan_tiles = (uint32_t)((s.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE);
+    } else {
+        q.mode = UNIT_REGIONS;
+        q.K = choose_K(p, o, s, strategy);
+        q.n_units = (uint32_t)((s.n_regions + q.K - 1) / q.K);
+    }
+}
+
+// bytes of a stream's per-run scratch: merge slots (signal strategy only), unit count,
+// planner look-back words; then its unit records
+static size_t stream_zeroed_bytes(const StreamPlan &q, int strategy)
+{
+    if (q.mode != UNIT_MERGE) return 0;
+    size_t b = 0;
+    if (strategy != RS_STRATEGY_TAG) b += (size_t)q.n_units * sizeof(Slot);
+    return b;
+}
 
 struct Plan {
     uint64_t total_units, plan_tiles;
@@ -344,64 +402,96 @@ struct Plan {
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 
-// Work decomposition and workspace layout for the submitted streams:
+// Lay out the workspace for a list of stream plans:
 // [header | per stream: slots, unit count, planner look-back words | per stream: unit
 //  records | stream table].  Everything before zero_end is cleared by every run.
-static Plan make_plan(const rs_pipeline *p)
+template <class SP>
+static void layout_plan(SP *sp, size_t ns, int strategy, uint64_t *total_units, uint64_t *plan_tiles,
+                        uint32_t *Kmax, size_t *zero_end, size_t *table_off, size_t *total)
 {
-    Plan pl;
-    pl.total_units = pl.plan_tiles = 0;
-    pl.Kmax = 1;
-    pl.hdr_bytes = align256(sizeof(WsHeader));
-    const bool load = p->stages[0].kind == RS_ENUM_LOAD;
-    size_t off = pl.hdr_bytes;
-    pl.sp.resize(p->streams.size());
-    for (size_t i = 0; i < p->streams.size(); ++i) {
-        const rs_stream_desc &s = p->streams[i];
-        StreamPlan &q = pl.sp[i];
-        memset(&q, 0, sizeof q);
-        if (load) {
-            q.mode = UNIT_MERGE;
-            const uint32_t kp = p->opts.regions_per_unit ? p->opts.regions_per_unit : 128u;
-            q.c = p->opts.region_cost ? p->opts.region_cost : RS_STEP_REGION;
-            q.D = q.c * kp;                      // a unit owns <= kp parents and holds <= D elements
-            q.K = kp + 1;                        // plus the parent continued from an earlier unit
-            uint64_t steps = (uint64_t)q.c * s.n_regions + s.n_elements;
-            q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
-            q.plan_tiles = (uint32_t)((s.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE);
-        } else {
-            q.mode = UNIT_REGIONS;
-            q.K = choose_K(p, s);
-            q.n_units = (uint32_t)((s.n_regions + q.K - 1) / q.K);
-        }
-        if (q.K > pl.Kmax) pl.Kmax = q.K;
-        pl.total_units += q.n_units;
-        pl.plan_tiles += q.plan_tiles;
+    *total_units = *plan_tiles = 0;
+    *Kmax = 1;
+    size_t off = align256(sizeof(WsHeader));
+    for (size_t i = 0; i < ns; ++i) {
+        StreamPlan &q = sp[i];
+        if (q.K > *Kmax) *Kmax = q.K;
+        *total_units += q.n_units;
+        *plan_tiles += q.plan_tiles;
         if (q.mode == UNIT_MERGE) {
             q.slots_off = off;
-            off = align256(off + (size_t)q.n_units * sizeof(Slot));
+            off = align256(off + stream_zeroed_bytes(q, strategy));
             q.ucount_off = off;
             off = align256(off + 4);
             q.planlb_off = off;
             off = align256(off + (size_t)q.plan_tiles * 8);
         }
     }
-    pl.zero_end = off;
-    for (size_t i = 0; i < p->streams.size(); ++i) {
-        StreamPlan &q = pl.sp[i];
+    *zero_end = off;
+    for (size_t i = 0; i < ns; ++i) {
+        StreamPlan &q = sp[i];
         if (q.mode == UNIT_MERGE) {
             q.rec_off = off;
             off = align256(off + ((size_t)q.n_units + 1) * sizeof(UnitRec));
         }
     }
-    pl.table_off = off;
-    pl.table_bytes = align256(p->streams.size() * sizeof(DevStream));
-    pl.total = pl.table_off + pl.table_bytes;
+    *table_off = off;
+    *total = off + align256(ns * sizeof(DevStream));
+}
+
+static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts &o)
+{
+    Plan pl;
+    pl.hdr_bytes = align256(sizeof(WsHeader));
+    pl.sp.resize(p->streams.size());
+    for (size_t i = 0; i < p->streams.size(); ++i) plan_stream(p, o, strategy, p->streams[i], pl.sp[i]);
+    layout_plan(pl.sp.data(), pl.sp.size(), strategy, &pl.total_units, &pl.plan_tiles, &pl.Kmax, &pl.zero_end,
+                &pl.table_off, &pl.total);
+    pl.table_bytes = pl.total - pl.table_off;
     return pl;
 }
 
-static size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
+// Per-processor shared memory of the tag kernel: counters, window marks (W words),
+// node 1's staging ring of element windows (loaded enumeration only),
+// the rings of edges 1..n-2 (values and region tags, two arrays), and the parent records
+// (2 PR entries each: region id and operand, start offset, parent id).  PR >= W + 64
+// covers every record node 1 can still need (the parents of one window plus one chunk).
+static SmemLayout make_tag_layout(const rs_pipeline *p)
+{
+    const rs_pipeline_opts &o = p->opts;
+    const uint32_t W = o.ensemble_width;
+    SmemLayout L;
+    memset(&L, 0, sizeof L);
+    size_t off = 0;
+    L.o_prof = (uint32_t)off;
+#ifdef RS_PROFILE
+    off += 8 * RS_PROF_SLOTS;
+#endif
+    L.o_cnt = (uint32_t)off;
+    off += 8 * 4 * RS_MAX_STAGES;
+    off = align_up(off, 16);
+    L.o_scr = (uint32_t)off;
+    off += (size_t)4 * W;
+    off = align_up(off, 16);
+    L.o_tiles = (uint32_t)off;    // node 1's staged element windows (4 x W)
+    off += p->stages[0].kind == RS_ENUM_LOAD ? (size_t)4 * W * 4 : 0;
+    L.o_qv = (uint32_t)off;       // ring values
+    off += (size_t)(p->n_stages - 2) * o.queue_capacity * 4;
+    L.o_qt = (uint32_t)off;       // ring tags (region ids)
+    off += (size_t)(p->n_stages - 2) * o.queue_capacity * 4;
+    uint32_t pr = 128;
+    while (pr < W + 64) pr <<= 1;
+    L.pr = pr;
+    L.o_nra = (uint32_t)off;      // {region, operand}, mirrored (2 PR entries)
+    off += (size_t)2 * pr * 8;
+    L.o_nst = (uint32_t)off;      // start offsets (PR entries)
+    off += (size_t)pr * 4;
+    L.o_npar = (uint32_t)off;     // parent ids, hashed enumeration only (PR entries)
+    off += p->stages[0].kind == RS_ENUM_HASH ? (size_t)pr * 4 : 0;
+    L.per_warp = (uint32_t)align_up(off, 128);
+    return L;
+}
 
 static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax, bool any_load, bool need_ctx,
                               bool need_par, bool want_min)
@@ -478,10 +568,39 @@ static int resolve_strategy(const rs_pipeline *p)
     return mean >= 1024.0 ? RS_STRATEGY_SIGNAL : RS_STRATEGY_TAG;
 }
 
+// Unit shapes (regions_per_unit, region_cost) rs_autotune tries for the tag strategy on
+// merge-path streams.
+static const uint32_t k_tag_shapes[][2] = {{4096, 1}, {8192, 1}, {16384, 1}, {2048, 1}, {1024, 4}, {256, 16}};
+
+// Workspace for either strategy with the current options and for every configuration
+// rs_autotune may try, so one workspace serves them all.
+static size_t workspace_need(const rs_pipeline *p)
+{
+    size_t need = 0;
+    for (int strategy : {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL}) {
+        const size_t t = make_plan(p, strategy, p->opts).total;
+        if (t > need) need = t;
+    }
+    rs_pipeline_opts o = p->opts;
+    for (const auto &sh : k_tag_shapes) {
+        o.regions_per_unit = sh[0];
+        o.region_cost = sh[1];
+        const size_t t = make_plan(p, RS_STRATEGY_TAG, o).total;
+        if (t > need) need = t;
+    }
+    o = p->opts;
+    o.regions_per_unit = 0;
+    for (int strategy : {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL}) {
+        const size_t t = make_plan(p, strategy, o).total;
+        if (t > need) need = t;
+    }
+    return need;
+}
+
 extern "C" rs_status rs_workspace_size(const rs_pipeline *p, uint64_t *bytes)
 {
     if (!p || !bytes) return RS_ERR_INVALID;
-    *bytes = make_plan(p).total;
+    *bytes = workspace_need(p);
     return RS_OK;
 }
 
@@ -528,7 +647,9 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     if (!p || !ws) return RS_ERR_INVALID;
     if (p->streams.empty()) return RS_ERR_NOT_READY;
     Launch &Lc = *out;
-    Lc.pl = make_plan(p);
+    const int strategy = resolve_strategy(p);
+    if (strategy != RS_STRATEGY_TAG && p->opts.ensemble_width > 4 * RS_W) return RS_ERR_INVALID;
+    Lc.pl = make_plan(p, strategy, p->opts);
     const Plan &pl = Lc.pl;
     if (ws_bytes < pl.total) return RS_ERR_CAPACITY;
     if (((uintptr_t)ws & 255) != 0) return RS_ERR_INVALID;
@@ -540,7 +661,6 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
         if ((e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return cuda_fail(e);
     }
-    const int strategy = resolve_strategy(p);
     const rs_pipeline_opts &o = p->opts;
     unsigned char *wsb = (unsigned char *)ws;
 
@@ -639,7 +759,9 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
     P.budget = o.device_budget;
     P.spin_limit = 2000000000ull;   // 2 s on the global timer
-    P.L = make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
+    P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p)
+                                      : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
+    P.plan_fill = strategy == RS_STRATEGY_TAG;
 
     // processors per CTA: as asked, but no more than fit the per-block shared memory;
     // 0 = the count (8, 4, 2 or 1) giving the most resident processors per SM
@@ -719,7 +841,8 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
     }
     int le = rs_launch_kernel(Lc.P, Lc.grid, Lc.block, Lc.smem, (void *)stream);
     if (le != 0) return cuda_fail((cudaError_t)le);
-    if (Lc.P.plan_tiles > 0) {
+    if (Lc.P.plan_tiles > 0 && !Lc.P.plan_fill) {
+        // signal strategy: parents processed in pieces get their merged results
         int fg = p->n_sm * 4;
         le = rs_launch_finalize(Lc.P, fg, (void *)stream);
         if (le != 0) return cuda_fail((cudaError_t)le);
@@ -909,31 +1032,32 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
     const rs_pipeline_opts base = p->opts;
     const uint32_t fan = max_fanout_of(p->stages, p->n_stages);
     const bool merge = p->stages[0].kind == RS_ENUM_LOAD;
-    // whole-parent units (hashed streams) sized from the mean region length
+    // whole-parent units (hashed streams) sized from the mean region length, per strategy
     rs_pipeline_opts probe = base;
     probe.regions_per_unit = 0;
-    p->opts = probe;
-    uint32_t K0 = 1;
+    uint32_t K0[2] = {1, 1};
     for (const auto &s : p->streams) {
-        uint32_t k = choose_K(p, s);
-        if (k > K0) K0 = k;
+        for (int si = 0; si < 2; ++si) {
+            const uint32_t k = choose_K(p, probe, s, si == 0 ? RS_STRATEGY_TAG : RS_STRATEGY_SIGNAL);
+            if (k > K0[si]) K0[si] = k;
+        }
     }
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaError_t e;
-    if ((e = cudaEventCreate(&ev0)) != cudaSuccess) { p->opts = base; return cuda_fail(e); }
-    if ((e = cudaEventCreate(&ev1)) != cudaSuccess) { cudaEventDestroy(ev0); p->opts = base; return cuda_fail(e); }
+    if ((e = cudaEventCreate(&ev0)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaEventCreate(&ev1)) != cudaSuccess) { cudaEventDestroy(ev0); return cuda_fail(e); }
     rs_status result = RS_OK;
     // mean time of `trials` runs of configuration c; +inf when it does not fit or stalls
     auto time_of = [&](rs_pipeline_opts c) -> float {
         c.queue_capacity = 0;
         c.grid = 0;
         fill_defaults(&c, fan);
-        if (c.tile_elements < c.ensemble_width) c.tile_elements = c.ensemble_width;
         if (check_opts(&c, fan) != RS_OK) return 1e30f;
         p->opts = c;
         p->table_dirty = true;
-        if (make_plan(p).total > workspace_bytes) return 1e30f;
+        const int strategy = resolve_strategy(p);
+        if (make_plan(p, strategy, c).total > workspace_bytes) return 1e30f;
         rs_status st = run_impl(p, workspace, workspace_bytes, (cudaStream_t)stream);
         if (st == RS_ERR_CAPACITY) return 1e30f;
         if (st != RS_OK) { result = st; return 1e30f; }
@@ -950,31 +1074,37 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
         return ms / (float)trials;
     };
 
-    // Per strategy, a coordinate search from the defaults: unit shape, then ensemble
-    // width, processors per CTA and tile size, each kept when it is faster.  A strategy
-    // whose starting point is over three times the best found so far is dropped.
+    // Per strategy, a coordinate search from a starting point: unit shape, then ensemble
+    // width, processors per CTA and (signal strategy) tile size, each change kept when it
+    // is faster.  A strategy whose starting point is over three times the best found so
+    // far is dropped.
     float best_t = 1e30f;
     rs_pipeline_opts best_o = base;
     const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
-    // (regions per unit, steps per parent): merge-path units of 2048 or 4096 steps with
-    // 32..256 parents; whole-parent units of K0, 2 K0 or K0 / 2 parents
-    uint32_t shapes[6][2];
-    int n_shapes = 0;
-    if (merge) {
-        const uint32_t sh[6][2] = {{128, 16}, {256, 16}, {512, 16}, {128, 32}, {64, 64}, {32, 128}};
-        for (int i = 0; i < 6; ++i) { shapes[i][0] = sh[i][0]; shapes[i][1] = sh[i][1]; }
-        n_shapes = 6;
-    } else {
-        shapes[0][0] = K0;
-        shapes[0][1] = RS_STEP_REGION;
-        n_shapes = 1;
-        if (K0 * 2 <= RS_MAX_K) { shapes[n_shapes][0] = K0 * 2; shapes[n_shapes++][1] = RS_STEP_REGION; }
-        if (K0 > 1) { shapes[n_shapes][0] = K0 / 2; shapes[n_shapes++][1] = RS_STEP_REGION; }
-    }
     for (uint32_t si = 0; si < 2 && result == RS_OK; ++si) {
+        const bool tag = strategies[si] == RS_STRATEGY_TAG;
+        // (regions per unit, steps per parent)
+        uint32_t shapes[8][2];
+        int n_shapes = 0;
+        if (merge && tag) {
+            for (const auto &sh : k_tag_shapes) {
+                shapes[n_shapes][0] = sh[0];
+                shapes[n_shapes++][1] = sh[1];
+            }
+        } else if (merge) {
+            const uint32_t sh[6][2] = {{128, 16}, {256, 16}, {512, 16}, {128, 32}, {64, 64}, {32, 128}};
+            for (int i = 0; i < 6; ++i) { shapes[i][0] = sh[i][0]; shapes[i][1] = sh[i][1]; }
+            n_shapes = 6;
+        } else {
+            const uint32_t k0 = K0[si], kmax = tag ? RS_TAG_MAX_K : RS_MAX_K;
+            shapes[n_shapes][0] = k0;
+            shapes[n_shapes++][1] = 0;
+            if (k0 * 2 <= kmax) { shapes[n_shapes][0] = k0 * 2; shapes[n_shapes++][1] = 0; }
+            if (k0 > 1) { shapes[n_shapes][0] = k0 / 2; shapes[n_shapes++][1] = 0; }
+        }
         rs_pipeline_opts cur = base;
         cur.strategy = strategies[si];
-        cur.ensemble_width = 4 * RS_W;
+        cur.ensemble_width = (tag ? 8 : 4) * RS_W;
         cur.warps_per_block = 0;
         cur.tile_elements = 0;
         cur.tiles_in_flight = 0;
@@ -989,9 +1119,10 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
             const float t = time_of(c);
             if (t < cur_t) { cur_t = t; cur = c; }
         }
-        {
+        for (uint32_t w : {4u, 2u}) {
+            if (!tag && w == 4) continue;
             rs_pipeline_opts c = cur;
-            c.ensemble_width = 2 * RS_W;
+            c.ensemble_width = w * RS_W;
             c.tile_elements = 0;
             const float t = time_of(c);
             if (t < cur_t) { cur_t = t; cur = c; }
@@ -1002,15 +1133,10 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
             const float t = time_of(c);
             if (t < cur_t) { cur_t = t; cur = c; }
         }
-        if (merge) {
-            // element staging: the tag strategy's direct loads (its default) against
-            // 4 tiles of W and of 2 W elements; the signal strategy's tiles of W against 2 W
-            const bool tag = cur.strategy == RS_STRATEGY_TAG;
-            const uint32_t base_nt = cur.tiles_in_flight;
-            for (uint32_t m : {1u, 2u}) {
-                if (!tag && m == 1) continue;
+        if (merge && !tag) {
+            // element staging: tiles of W against 2 W elements
+            for (uint32_t m : {2u}) {
                 rs_pipeline_opts c = cur;
-                c.tiles_in_flight = tag ? 4 : base_nt;
                 c.tile_elements = m * cur.ensemble_width;
                 const float t = time_of(c);
                 if (t < cur_t) { cur_t = t; cur = c; }
@@ -1022,7 +1148,6 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
             best_o.queue_capacity = 0;
             best_o.grid = 0;
             fill_defaults(&best_o, fan);
-            if (best_o.tile_elements < best_o.ensemble_width) best_o.tile_elements = best_o.ensemble_width;
         }
     }
     cudaEventDestroy(ev0);
@@ -1075,53 +1200,12 @@ static rs_status noalloc_scratch(void **out)
     return RS_OK;
 }
 
-static void make_plan_fixed(const rs_pipeline *p, FixedPlan *pl)
+static void make_plan_fixed(const rs_pipeline *p, int strategy, FixedPlan *pl)
 {
-    pl->total_units = pl->plan_tiles = 0;
-    pl->Kmax = 1;
-    const bool load = p->stages[0].kind == RS_ENUM_LOAD;
-    size_t off = align256(sizeof(WsHeader));
     const size_t ns = p->streams.size();
-    for (size_t i = 0; i < ns; ++i) {
-        const rs_stream_desc &s = p->streams[i];
-        StreamPlan &q = pl->sp[i];
-        memset(&q, 0, sizeof q);
-        if (load) {
-            q.mode = UNIT_MERGE;
-            const uint32_t kp = p->opts.regions_per_unit ? p->opts.regions_per_unit : 128u;
-            q.c = p->opts.region_cost ? p->opts.region_cost : RS_STEP_REGION;
-            q.D = q.c * kp;
-            q.K = kp + 1;
-            uint64_t steps = (uint64_t)q.c * s.n_regions + s.n_elements;
-            q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
-            q.plan_tiles = (uint32_t)((s.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE);
-        } else {
-            q.mode = UNIT_REGIONS;
-            q.K = choose_K(p, s);
-            q.n_units = (uint32_t)((s.n_regions + q.K - 1) / q.K);
-        }
-        if (q.K > pl->Kmax) pl->Kmax = q.K;
-        pl->total_units += q.n_units;
-        pl->plan_tiles += q.plan_tiles;
-        if (q.mode == UNIT_MERGE) {
-            q.slots_off = off;
-            off = align256(off + (size_t)q.n_units * sizeof(Slot));
-            q.ucount_off = off;
-            off = align256(off + 4);
-            q.planlb_off = off;
-            off = align256(off + (size_t)q.plan_tiles * 8);
-        }
-    }
-    pl->zero_end = off;
-    for (size_t i = 0; i < ns; ++i) {
-        StreamPlan &q = pl->sp[i];
-        if (q.mode == UNIT_MERGE) {
-            q.rec_off = off;
-            off = align256(off + ((size_t)q.n_units + 1) * sizeof(UnitRec));
-        }
-    }
-    pl->table_off = off;
-    pl->total = off + align256(ns * sizeof(DevStream));
+    for (size_t i = 0; i < ns; ++i) plan_stream(p, p->opts, strategy, p->streams[i], pl->sp[i]);
+    layout_plan(pl->sp, ns, strategy, &pl->total_units, &pl->plan_tiles, &pl->Kmax, &pl->zero_end, &pl->table_off,
+                &pl->total);
 }
 
 extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
@@ -1129,8 +1213,10 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     if (!p) return RS_ERR_INVALID;
     if (p->streams.empty()) return RS_ERR_NOT_READY;
     if (p->streams.size() > RS_NOALLOC_MAX_STREAMS) return RS_ERR_CAPACITY;
+    const int strategy = resolve_strategy(p);
+    if (strategy != RS_STRATEGY_TAG && p->opts.ensemble_width > 4 * RS_W) return RS_ERR_INVALID;
     FixedPlan &pl = p->noalloc_plan;
-    make_plan_fixed(p, &pl);
+    make_plan_fixed(p, strategy, &pl);
     if (pl.total > RS_NOALLOC_WS_BYTES) return RS_ERR_CAPACITY;   // beyond the fixed scratch
     if (pl.total_units >= (1ull << 31)) return RS_ERR_CAPACITY;
     void *ws = nullptr;
@@ -1143,7 +1229,6 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
         if ((e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return cuda_fail(e);
     }
-    const int strategy = resolve_strategy(p);
     const rs_pipeline_opts &o = p->opts;
     unsigned char *wsb = (unsigned char *)ws;
     const size_t ns = p->streams.size();
@@ -1223,7 +1308,9 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
     P.budget = o.device_budget;
     P.spin_limit = 2000000000ull;
-    P.L = make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
+    P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p)
+                                      : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
+    P.plan_fill = strategy == RS_STRATEGY_TAG;
     if (!p->smem_max) {
         int dev = 0, v = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
@@ -1270,7 +1357,7 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     }
     int le = rs_launch_kernel(P, grid, block, smem, (void *)cs);
     if (le != 0) return cuda_fail((cudaError_t)le);
-    if (P.plan_tiles > 0) {
+    if (P.plan_tiles > 0 && !P.plan_fill) {
         le = rs_launch_finalize(P, p->n_sm * 4, (void *)cs);
         if (le != 0) return cuda_fail((cudaError_t)le);
     }

@@ -29,7 +29,8 @@ struct DevStage {
     uint32_t fanout;
     uint32_t p0, p1;
     uint32_t c0;         // fmix32(p0 ^ RS_GOLD): the per-stage half of hash32, precomputed
-    uint32_t pad[3];
+    uint32_t c0s;        // c0 ^ (c0 >> 16): fmix32(x ^ c0) starts from x ^ (x >> 16) ^ c0s
+    uint32_t pad[2];
 };
 
 // Work decomposition of a stream.
@@ -126,6 +127,9 @@ struct SmemLayout {
     uint32_t per_warp;
     uint32_t o_prof, o_cnt, o_pend, o_mbar, o_mmeta, o_tiles, o_rc, o_rs, o_rm, o_qv, o_qt, o_sq, o_scr;
     uint32_t o_raw[2], o_moff[2], o_ctxb[2], o_parb[2];   // double-buffered unit metadata
+    // tag kernel: rings of records of the non-empty parents node 1 is reading (PR
+    // entries; the {region, operand} ring is mirrored to 2 PR)
+    uint32_t o_nra, o_nst, o_npar, pr;
 };
 
 struct KParams {
@@ -145,6 +149,7 @@ struct KParams {
     unsigned long long budget;
     unsigned long long spin_limit;
     uint32_t profile;             // accumulate the cycle breakdown
+    uint32_t plan_fill;           // planner writes every region's identity result (tag strategy)
     SmemLayout L;
 };
 
@@ -156,3 +161,6 @@ int rs_kernel_max_smem_optin(const KParams &P, size_t smem);
 int rs_kernel_occupancy(const KParams &P, int block, size_t smem, int *blocks_per_sm);
 const void *rs_kernel_entry(const KParams &P);   // the kernel a launch with P would use
 int rs_kernel_is_specialised(const KParams &P);
+// the tag strategy's kernel (rs_tag.cu)
+const void *rs_tag_kernel_entry(const KParams &P);
+int rs_tag_kernel_is_specialised(const KParams &P);

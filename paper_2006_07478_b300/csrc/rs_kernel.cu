@@ -29,7 +29,7 @@
 
 #include "rs_internal.h"
 
-#define FULLMASK 0xFFFFFFFFu
+#include "rs_device.cuh"
 
 // Cycle breakdown, compiled in only for the profiling build (-DRS_PROFILE=1): lane 0
 // of each warp adds SM clock cycles per phase into a per-warp shared-memory array,
@@ -51,179 +51,6 @@
 #define LB_VAL ((1ull << 62) - 1)
 #define SIG_END 0x80000000u
 
-// ---------------------------------------------------------------------------
-// small device helpers
-
-__device__ __forceinline__ uint32_t fmix32(uint32_t h)
-{
-    // MurmurHash3 32-bit finalizer
-    h ^= h >> 16;
-    h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
-    h *= 0xC2B2AE35u;
-    h ^= h >> 16;
-    return h;
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// 1-D bulk copy global -> shared, completion counted on an mbarrier (bytes % 16 == 0,
-// both addresses 16-byte aligned).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// streaming loads (read once: no L1 allocation) of 4 / 2 consecutive words
-__device__ __forceinline__ uint4 ld_stream_v4(const uint32_t *p)
-{
-    uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ uint2 ld_stream_v2(const uint32_t *p)
-{
-    uint2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
-    return v;
-}
-
-// 4-byte asynchronous copy global -> shared (no register staging)
-__device__ __forceinline__ void cp_async4(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
-// arrive on an mbarrier once all of this thread's earlier cp.async copies have landed
-__device__ __forceinline__ void cp_async_arrive(unsigned long long *bar)
-{
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ uint32_t lanemask_lt()
-{
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
-{
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULLMASK, v, d);
-    return v;
-}
-
-__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v, uint32_t lane)
-{
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t y = __shfl_up_sync(FULLMASK, v, d);
-        if (lane >= (uint32_t)d) v += y;
-    }
-    return v;
-}
-
-// sum of 32-bit values over the warp as a 64-bit total (inactive lanes pass 0)
-__device__ __forceinline__ unsigned long long warp_sum_u32_wide(uint32_t v)
-{
-    uint32_t lo = __reduce_add_sync(FULLMASK, v & 0xFFFFu);
-    uint32_t hi = __reduce_add_sync(FULLMASK, v >> 16);
-    return ((unsigned long long)hi << 16) + lo;
-}
-
-// ---------------------------------------------------------------------------
-// Shared memory: one dynamic array; every per-processor array is addressed by a
-// 32-bit element index into it, so all accesses are shared-memory loads and stores
-// with 32-bit address arithmetic.
-
-extern __shared__ __align__(128) unsigned char smem_raw[];
-
-template <typename T>
-struct SArr {
-    uint32_t base;   // index of element 0, in units of T, from the start of smem_raw
-    __device__ __forceinline__ T &operator[](uint32_t i) const { return reinterpret_cast<T *>(smem_raw)[base + i]; }
-    __device__ __forceinline__ T *ptr() const { return reinterpret_cast<T *>(smem_raw) + base; }
-};
-
-template <typename T>
-__device__ __forceinline__ SArr<T> sarr(uint32_t byte_off)
-{
-    SArr<T> a;
-    a.base = byte_off / (uint32_t)sizeof(T);
-    return a;
-}
 
 // ---------------------------------------------------------------------------
 // per-warp (per-processor) state, all warp-uniform, held in registers
@@ -550,6 +377,15 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
                 }
             }
         }
+        // tag strategy: every region starts at the identity result (count 0, sum 0, min
+        // 0xFFFFFFFF), written here, before the pipeline kernel folds survivors into it
+        if (P.plan_fill) {
+            for (uint32_t r = r_lo + lane; r < r_hi; r += 32) {
+                if (P.want_count) S.out_count[r] = 0u;
+                if (P.want_sum) S.out_sum[r] = 0ull;
+                if (P.want_min) S.out_min[r] = 0xFFFFFFFFu;
+            }
+        }
         // per round: the lane's element count, its inclusive scan, the round total
         uint32_t ls[PLAN_ROUNDS], incl[PLAN_ROUNDS];
         uint32_t tsum = 0;
@@ -765,28 +601,6 @@ __device__ __forceinline__ uint32_t parent_at(const Smem &M, uint32_t from, uint
     return k;
 }
 
-// Compile-time pipeline signature: the enumerate op and the element-stage ops
-// (0 = no such stage; the aggregate follows the last one).  OE == 0 marks the generic
-// kernel, which reads every op from the parameters at run time.  A specialised
-// kernel carries only the code its own nodes execute, which keeps its hot loop small
-// enough for the instruction cache.
-template <int OE_, int O1_, int O2_, int O3_, int O4_>
-struct Sig {
-    static constexpr bool generic = OE_ == 0;
-    static constexpr int n = generic ? 0 : 2 + (O1_ != 0) + (O2_ != 0) + (O3_ != 0) + (O4_ != 0);
-    template <int I>
-    __host__ __device__ static constexpr int op()
-    {
-        return I == 0 ? OE_ : (I == n - 1 ? (int)D_AGG : (I == 1 ? O1_ : I == 2 ? O2_ : I == 3 ? O3_ : O4_));
-    }
-    template <int I>
-    __host__ __device__ static constexpr bool present() { return generic ? (I < RS_MAX_STAGES) : (I < n); }
-    template <int I>
-    __host__ __device__ static constexpr bool maybe_last() { return generic ? true : (I == n - 1); }
-    template <int I>
-    __host__ __device__ static constexpr bool maybe_elem() { return generic ? (I + 1 < RS_MAX_STAGES) : (I < n - 1); }
-};
-using GenericSig = Sig<0, 0, 0, 0, 0>;
 
 // per-node counters live in the processor's shared memory (lane 0 updates them)
 #define CNT_ADD(node, field, v)                                       \
@@ -1410,493 +1224,6 @@ struct Proc {
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
-// Tag strategy (Section 3.3, the alternative to signals): every item carries the local
-// index of its parent, so ensembles are never cut at parent boundaries and there are
-// no signal queues.  Items of an ensemble are placed lane-major -- item q is item
-// q % V of lane q / V -- so each lane's V items are adjacent in a ring and move with
-// 16-byte shared-memory accesses.  A ring slot packs {value, tag} into 64 bits.
-// Node 1 reads the staged elements in windows of W aligned to the tile ring; the
-// unit's first and last windows are partial and masked at their ends.  Compaction
-// (Section 4.1's 0..k outputs per item) is a warp scan of each lane's output count.
-
-__device__ __forceinline__ unsigned long long tag_pack(uint32_t v, uint32_t k)
-{
-    return ((unsigned long long)k << 32) | v;
-}
-
-template <int V, class S>
-struct TagProc {
-    static constexpr uint32_t W = 32u * V;
-    const KParams &P;
-    Smem &M;
-    Stage &g;
-    const uint32_t lane;
-    Pending *nxt;    // the prefetched next unit, in this processor's shared memory
-    bool nxt_open;   // its metadata still has to be turned into offsets
-    uint32_t nk, total, E0;
-    uint32_t s0;     // ring-relative index of the unit's first element
-    uint32_t ek1;    // parent containing node 1's next position
-    // edge 0: node 1's next window start and the end, ring-relative; edges e >= 1:
-    // free-running cursors of the shared-memory rings (slot = cursor & (C - 1))
-    uint32_t qh[RS_MAX_EDGES], qt[RS_MAX_EDGES];
-    bool stop;
-    // results: parents 1..nk-2 (and 0, nk-1 unless split) go straight to the outputs;
-    // a split first parent accumulates in slot 0, a split last parent in slot 1
-    const DevStream *S_;
-    uint32_t r0;
-    bool hsplit, tsplit;
-    // direct element loads (no staging tiles; 16-byte-aligned elements): each lane
-    // reads its V elements of a window with one vector load, issued two windows ahead
-    bool direct;
-    uint32_t A;              // absolute index of ring-relative position 0 (E0 rounded down to 4)
-    uint32_t lim;            // elements in the stream (loads stay below it)
-    uint32_t pf_r;           // ring-relative start of the next window to load
-    uint32_t pf0[V], pf1[V]; // the loaded next two windows
-
-    __device__ __forceinline__ TagProc(const KParams &P_, Smem &M_, Stage &g_, uint32_t lane_)
-        : P(P_), M(M_), g(g_), lane(lane_), nxt(nullptr), nxt_open(false), nk(0), total(0), E0(0), s0(0),
-          ek1(0), stop(false), S_(nullptr), r0(0), hsplit(false), tsplit(false), direct(false), A(0), lim(0),
-          pf_r(0)
-    {
-    }
-
-    // the lane's V elements of the window starting at ring-relative index r
-    __device__ __forceinline__ void load_window(uint32_t r, uint32_t (&x)[V]) const
-    {
-        const uint32_t e = A + r + V * lane;
-        const uint32_t *src = g.elements + e;
-        if (e + V <= lim) {
-            if constexpr (V == 4) {
-                const uint4 v = ld_stream_v4(src);
-                x[0] = v.x;
-                x[1 % V] = v.y;
-                x[2 % V] = v.z;
-                x[3 % V] = v.w;
-            } else if constexpr (V == 2) {
-                const uint2 v = ld_stream_v2(src);
-                x[0] = v.x;
-                x[1 % V] = v.y;
-            } else {
-                x[0] = __ldg(src);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < V; ++j) x[j] = (e + j < lim) ? __ldg(src + j) : 0u;
-        }
-    }
-
-    // accumulator slot of parent k if it is a split piece, else -1
-    __device__ __forceinline__ int split_slot(uint32_t k) const
-    {
-        if (k == 0 && hsplit) return 0;
-        if (k == nk - 1 && tsplit) return 1;
-        return -1;
-    }
-
-    // fold a partial result for parent k: into its slot (split piece) or the outputs
-    __device__ __forceinline__ void fold(uint32_t k, uint32_t cnt, unsigned long long sum, uint32_t mn) const
-    {
-        const int sl = split_slot(k);
-        if (sl >= 0) {
-            atomicAdd(&M.rc[sl], cnt);
-            atomicAdd(&M.rs[sl], sum);
-            if (P.want_min) atomicMin(&M.rm[sl], mn);
-        } else {
-            if (P.want_count) atomicAdd(S_->out_count + r0 + k, cnt);
-            if (P.want_sum) atomicAdd(S_->out_sum + r0 + k, sum);
-            if (P.want_min) atomicMin(S_->out_min + r0 + k, mn);
-        }
-    }
-
-    __device__ __forceinline__ int nst() const { return S::generic ? P.n_stages : S::n; }
-    template <int I>
-    __device__ __forceinline__ uint32_t op() const
-    {
-        if constexpr (S::generic) return P.st[I].op;
-        else return (uint32_t)S::template op<I>();
-    }
-
-    // ---- the stage op of node I on the lane's items (filter / map), Section 4.1 ----
-    template <int I>
-    __device__ __forceinline__ void apply(const uint32_t (&x)[V], const uint32_t (&k)[V], uint32_t vmask, bool uni,
-                                          bool (&keep)[V], uint32_t (&y)[V]) const
-    {
-        const DevStage &sd = P.st[I];
-        const uint32_t opc = op<I>();
-        uint32_t cu = 0;
-        if (opc == D_FILT_HASH_CTX && uni) cu = M.mctx[k[0]];
-        if (opc == D_FILT_WEIGHT && uni) cu = fmix32(M.mpar[k[0]] ^ sd.c0);
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const uint32_t xs = x[j];
-            bool kp;
-            uint32_t ys = xs;
-            switch (opc) {
-            case D_FILT_MASK: kp = (xs & sd.p0) == sd.p1; break;
-            case D_FILT_MOD: kp = (xs % sd.p0) == sd.p1; break;
-            case D_FILT_HASH_CTX: kp = (fmix32(xs ^ sd.c0) ^ (uni ? cu : M.mctx[k[j]])) < sd.p1; break;
-            case D_FILT_WEIGHT: kp = fmix32(xs ^ sd.c0) < (uni ? cu : fmix32(M.mpar[k[j]] ^ sd.c0)); break;
-            case D_MAP_MULADD: ys = xs * sd.p0 + sd.p1; kp = true; break;
-            default: kp = false; break;
-            }
-            keep[j] = kp && ((vmask >> j) & 1u);
-            y[j] = ys;
-        }
-    }
-
-    // append the lane's kept items, in lane-major order, to the ring of edge I
-    template <int I>
-    __device__ __forceinline__ void push(const bool (&keep)[V], const uint32_t (&y)[V], const uint32_t (&k)[V])
-    {
-        const uint32_t cm = P.C - 1, rb = (I - 1) * P.C;
-        uint32_t c = 0;
-#pragma unroll
-        for (int j = 0; j < V; ++j) c += keep[j] ? 1u : 0u;
-        const uint32_t incl = warp_incl_scan_u32(c, lane);
-        uint32_t pos = qt[I] + incl - c;
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            if (keep[j]) {
-                M.q64[rb + (pos & cm)] = tag_pack(y[j], k[j]);
-                ++pos;
-            }
-        }
-        qt[I] += __shfl_sync(FULLMASK, incl, 31);
-    }
-
-    // expansion stage (0..fanout outputs per item): item x emits n = hash32(x, p0) mod
-    // (fanout + 1) values hash32(x, p0 + 1 + i), i < n, in order
-    template <int I>
-    __device__ __forceinline__ void expand(const uint32_t (&x)[V], const uint32_t (&k)[V], uint32_t vmask)
-    {
-        const DevStage &sd = P.st[I];
-        const uint32_t cm = P.C - 1, rb = (I - 1) * P.C;
-        uint32_t nout[V], c = 0;
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            nout[j] = ((vmask >> j) & 1u) ? fmix32(x[j] ^ sd.c0) % (sd.fanout + 1u) : 0u;
-            c += nout[j];
-        }
-        const uint32_t incl = warp_incl_scan_u32(c, lane);
-        uint32_t pos = qt[I] + incl - c;
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            for (uint32_t o = 0; o < nout[j]; ++o) {
-                const uint32_t yv = fmix32(x[j] ^ fmix32((sd.p0 + 1u + o) ^ RS_GOLD));
-                M.q64[rb + (pos & cm)] = tag_pack(yv, k[j]);
-                ++pos;
-            }
-        }
-        qt[I] += __shfl_sync(FULLMASK, incl, 31);
-    }
-
-    // the aggregate (Section 4.2): count, sum and min of each parent's surviving items.
-    // One parent in the ensemble: a warp reduction and one update; several: one update
-    // per item.  The updates are reductions (associative, commutative), so their order
-    // does not matter.
-    __device__ __forceinline__ void aggregate(const uint32_t (&x)[V], const uint32_t (&k)[V], uint32_t vmask, bool uni,
-                                              uint32_t take)
-    {
-        if (uni) {
-            uint32_t lo = 0, hi = 0, mn = 0xFFFFFFFFu;
-#pragma unroll
-            for (int j = 0; j < V; ++j) {
-                if ((vmask >> j) & 1u) {
-                    lo += x[j] & 0xFFFFu;
-                    hi += x[j] >> 16;
-                    mn = min(mn, x[j]);
-                }
-            }
-            lo = __reduce_add_sync(FULLMASK, lo);
-            hi = __reduce_add_sync(FULLMASK, hi);
-            if (P.want_min) mn = __reduce_min_sync(FULLMASK, mn);
-            if (lane == 0) fold(k[0], take, ((unsigned long long)hi << 16) + lo, mn);
-        } else {
-#pragma unroll
-            for (int j = 0; j < V; ++j)
-                if ((vmask >> j) & 1u) fold(k[j], 1u, (unsigned long long)x[j], x[j]);
-        }
-        __syncwarp();
-    }
-
-    // ---- node 1: one window of W ring-relative positions [qh[0], qh[0] + W) ----
-    // Fills x, k and the lane's valid bits; returns the number of valid items.
-    __device__ __forceinline__ uint32_t gather1(uint32_t (&x)[V], uint32_t (&k)[V], uint32_t &vmask, bool &uni)
-    {
-        const uint32_t r0 = qh[0];
-        const uint32_t lo = r0 > s0 ? r0 - s0 : 0u;           // first position of the window
-        const uint32_t hi = min(r0 + W - s0, total);          // end position (exclusive)
-        const uint32_t rl = r0 + V * lane;                    // the lane's first ring-relative index
-        vmask = 0;
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const uint32_t r = rl + j;
-            if (r >= s0 && r - s0 < total) vmask |= 1u << j;
-        }
-        // parents: one for the whole window, or marks of the parents starting in it
-        const uint32_t end_k = M.moff[ek1 + 1];
-        uni = end_k >= hi;
-        if (uni) {
-#pragma unroll
-            for (int j = 0; j < V; ++j) k[j] = ek1;
-            if (end_k == hi && hi < total) ek1 = parent_at(M, ek1, hi, nk, lane);
-        } else {
-            // scr[r - r0] = the non-empty parent whose first element is at ring index r
-#pragma unroll
-            for (int j = 0; j < V; ++j) M.scr[V * lane + j] = 0u;
-            __syncwarp();
-            for (uint32_t base = ek1 + 1;; base += 32) {
-                const uint32_t kk = base + lane;
-                const bool in = kk < nk;
-                const uint32_t st = in ? M.moff[kk] : total;
-                const uint32_t en = in ? M.moff[kk + 1] : total;
-                if (in && en > st && st < hi) M.scr[st + s0 - r0] = kk;
-                const uint32_t st31 = __shfl_sync(FULLMASK, st, 31);
-                if (!(base + 32 < nk && st31 < hi)) break;
-            }
-            __syncwarp();
-            uint32_t m[V];
-#pragma unroll
-            for (int j = 0; j < V; ++j) m[j] = M.scr[V * lane + j];
-            uint32_t lm = 0;
-#pragma unroll
-            for (int j = 0; j < V; ++j) lm = max(lm, m[j]);
-            // parent indices grow with position: a running maximum over the window
-            uint32_t incl = lm;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t t = __shfl_up_sync(FULLMASK, incl, d);
-                if (lane >= (uint32_t)d) incl = max(incl, t);
-            }
-            const uint32_t before = __shfl_up_sync(FULLMASK, incl, 1);
-            uint32_t cur = max(ek1, lane ? before : 0u);
-#pragma unroll
-            for (int j = 0; j < V; ++j) {
-                cur = max(cur, m[j]);
-                k[j] = cur;
-            }
-            const uint32_t last = max(ek1, __shfl_sync(FULLMASK, incl, 31));
-            ek1 = (hi < total && M.moff[last + 1] <= hi) ? parent_at(M, last, hi, nk, lane) : last;
-            __syncwarp();
-        }
-        // the elements (getItem of Figure 4)
-        if (op<0>() == D_ENUM_HASH) {
-#pragma unroll
-            for (int j = 0; j < V; ++j) {
-                const uint32_t p = rl + j - s0;
-                x[j] = ((vmask >> j) & 1u) ? fmix32(M.mpar[k[j]] ^ fmix32((p - M.moff[k[j]]) ^ RS_GOLD)) : 0u;
-            }
-        } else if (direct) {
-#pragma unroll
-            for (int j = 0; j < V; ++j) {
-                x[j] = pf0[j];
-                pf0[j] = pf1[j];
-            }
-            if (pf_r < qt[0]) load_window(pf_r, pf1);
-            pf_r += W;
-        } else if (g.tma) {
-            if (E0 + hi > g.ready_lim && !tiles_ready(P, M, g, lane, E0 + hi)) {
-                stop = true;
-                return 0;
-            }
-            const uint32_t mask = P.NT * P.TE - 1;
-            if (E0 + hi <= g.B) {
-                const uint32_t *tp = M.tiles.ptr() + (rl & mask);
-                if constexpr (V == 4) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(tp);
-                    x[0] = v.x;
-                    x[1 % V] = v.y;
-                    x[2 % V] = v.z;
-                    x[3 % V] = v.w;
-                } else if constexpr (V == 2) {
-                    const uint2 v = *reinterpret_cast<const uint2 *>(tp);
-                    x[0] = v.x;
-                    x[1 % V] = v.y;
-                } else {
-                    x[0] = tp[0];
-                }
-            } else {
-                // the unit's last few elements (past the last 16-byte boundary) are not staged
-#pragma unroll
-                for (int j = 0; j < V; ++j) {
-                    const uint32_t e = E0 + (rl + j - s0);
-                    x[j] = 0u;
-                    if ((vmask >> j) & 1u) x[j] = e < g.B ? M.tiles[(rl + j) & mask] : __ldg(g.elements + e);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < V; ++j) x[j] = ((vmask >> j) & 1u) ? __ldg(g.elements + E0 + (rl + j - s0)) : 0u;
-        }
-        return hi - lo;
-    }
-
-    // ---- nodes I >= 2: an ensemble of `take` items from the ring of edge I - 1 ----
-    template <int I>
-    __device__ __forceinline__ void gather_ring(uint32_t take, uint32_t (&x)[V], uint32_t (&k)[V], uint32_t &vmask,
-                                                bool &uni) const
-    {
-        const uint32_t cm = P.C - 1, rb = (I - 2) * P.C;
-        const uint32_t h = qh[I - 1];
-        const unsigned long long *sp = M.q64.ptr() + rb + ((h + V * lane) & cm);
-        unsigned long long v[V];
-        if (V == 1 || (h & (V - 1)) != 0) {
-            // a head off the V-slot grid (not produced by the scheduler; kept for safety)
-#pragma unroll
-            for (int j = 0; j < V; ++j) v[j] = M.q64[rb + ((h + V * lane + j) & cm)];
-        } else {
-#pragma unroll
-            for (int t = 0; t < V / 2; ++t) {
-                const ulonglong2 w2 = reinterpret_cast<const ulonglong2 *>(sp)[t];
-                v[2 * t] = w2.x;
-                v[2 * t + 1] = w2.y;
-            }
-        }
-        vmask = 0;
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            x[j] = (uint32_t)v[j];
-            k[j] = (uint32_t)(v[j] >> 32);
-            if (V * lane + j < take) vmask |= 1u << j;
-        }
-        // tags never decrease along a ring: equal ends mean one parent
-        const uint32_t k0 = __shfl_sync(FULLMASK, k[0], 0);
-        const uint32_t kl = (uint32_t)(M.q64[rb + ((h + take - 1) & cm)] >> 32);
-        uni = k0 == kl;
-        // slots past `take` hold stale words: give them the first item's parent
-#pragma unroll
-        for (int j = 0; j < V; ++j)
-            if (uni || !((vmask >> j) & 1u)) k[j] = k0;
-    }
-
-    // ---- fire node I (Section 2.1's non-preemptive scheduler offers it the processor) ----
-    template <int I>
-    __device__ __forceinline__ void fire(bool drain)
-    {
-        if constexpr (S::template present<I>()) {
-            if (I >= nst() || stop) return;
-            const long long pt = PROF_NOW();
-            (void)pt;
-            fire_body<I>(drain);
-            PROF_ADD(PF_NODE0 + I, pt);
-        }
-    }
-
-    template <int I>
-    __device__ __forceinline__ void fire_body(bool drain)
-    {
-        constexpr bool can_push = S::template maybe_elem<I>();
-        const bool last = !can_push || (I == nst() - 1);
-        const uint32_t fan = (S::generic || S::template op<I>() == (int)D_EXPAND) ? P.st[I].fanout : 1u;
-        uint32_t n_ens = 0, n_items = 0;
-        for (;;) {
-            uint32_t x[V], k[V], vmask, take;
-            bool uni;
-            if constexpr (I == 1) {
-                if (qh[0] >= qt[0]) break;
-            } else {
-                const uint32_t avail = qt[I - 1] - qh[I - 1];
-                if (avail == 0 || (!drain && avail < W)) break;
-            }
-            if constexpr (can_push) {
-                if (!last && P.C - (qt[I] - qh[I]) < W * fan) break;   // wait for downstream space
-            }
-            if constexpr (I == 1) {
-                take = gather1(x, k, vmask, uni);
-                if (stop) break;
-            } else {
-                take = min(W, qt[I - 1] - qh[I - 1]);
-                gather_ring<I>(take, x, k, vmask, uni);
-            }
-            if (last) {
-                if constexpr (S::template maybe_last<I>()) aggregate(x, k, vmask, uni, take);
-            } else {
-                if constexpr (can_push) {
-                    if (op<I>() == D_EXPAND) {
-                        expand<I>(x, k, vmask);
-                    } else {
-                        bool keep[V];
-                        uint32_t y[V];
-                        apply<I>(x, k, vmask, uni, keep, y);
-                        push<I>(keep, y, k);
-                    }
-                }
-            }
-            if constexpr (I == 1) {
-                qh[0] += W;
-                if (op<0>() == D_ENUM_LOAD && g.tma) {
-                    const uint32_t e_read = E0 + min(qh[0] - s0, total);
-                    if (e_read >= g.free_lim) tiles_release(P, M, g, lane, e_read);
-                }
-            } else {
-                qh[I - 1] += take;
-            }
-            n_ens++;
-            n_items += take;
-        }
-        if (n_ens) {
-            CNT_ADD(I, 0, n_ens);
-            CNT_ADD(I, 1, n_items);
-            CNT_ADD(I, 3, 1);
-        }
-    }
-
-    __device__ __forceinline__ bool edge_empty(int e) const { return qh[e] >= qt[e]; }
-
-    // ---- run one unit to completion: sweeps offering every node a firing, upstream first ----
-    __device__ __forceinline__ void run_unit()
-    {
-#pragma unroll
-        for (int i = 0; i < RS_MAX_EDGES; ++i) qh[i] = qt[i] = 0;
-        direct = op<0>() == D_ENUM_LOAD && !g.tma && P.NT == 0 && S_->tma_ok;
-        s0 = (g.tma && op<0>() == D_ENUM_LOAD) ? (E0 - g.A) : (direct ? (E0 & 3u) : 0u);
-        qt[0] = total ? s0 + total : 0u;
-        if (direct) {
-            A = E0 - s0;
-            lim = S_->n_elements < 0xFFFFFFFFull ? (uint32_t)S_->n_elements : 0xFFFFFFFFu;
-            if (qt[0] > 0) load_window(0, pf0);
-            if (qt[0] > W) load_window(W, pf1);
-            pf_r = 2 * W;
-        }
-        CNT_ADD(0, 0, (total + W - 1) / W);
-        CNT_ADD(0, 1, total);
-        ek1 = 0;
-        if (total > 0) ek1 = parent_at(M, 0, 0, nk, lane);
-        for (unsigned long long sweep = 0;; ++sweep) {
-            CNT_ADD(0, 3, 1);
-            if (nxt_open) {
-                poll_next(*nxt, P, M, lane);
-                nxt_open = !nxt->scanned;
-            }
-            fire<1>(true);
-            bool d = edge_empty(0);
-            fire<2>(d);
-            d = d && (nst() <= 2 || edge_empty(1));
-            fire<3>(d);
-            d = d && (nst() <= 3 || edge_empty(2));
-            fire<4>(d);
-            d = d && (nst() <= 4 || edge_empty(3));
-            fire<5>(d);
-            d = d && (nst() <= 5 || edge_empty(4));
-            if (stop) return;
-            if (d) break;
-            if (sweep >= P.budget) {
-                if (lane == 0) atomicOr(&P.hdr->status, ST_STALL);
-                stop = true;
-                return;
-            }
-        }
-    }
-
-    __device__ __forceinline__ void finish_tiles()
-    {
-        if (!g.tma) return;
-        if (!tiles_ready(P, M, g, lane, 0xFFFFFFFFu)) stop = true;
-        g.t_freed = g.t_ready;
-    }
-};
-
-// ---------------------------------------------------------------------------
 
 template <int STRAT, int V, class SG>
 __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_constant__ KParams P)
@@ -2032,21 +1359,6 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
             for (uint32_t k = lane; k < nk; k += 32) M.mpar[k] = r0 + k;
         const bool split_head = cur.u.has_head;
         const bool split_tail = cur.split_tail;
-        if constexpr (STRAT == RS_STRATEGY_TAG) {
-            // every whole parent's results start at the identity in the outputs (empty
-            // parents included); the two split pieces start in their slots
-            for (uint32_t k = lane; k < nk; k += 32) {
-                if ((k == 0 && split_head) || (k == nk - 1 && split_tail)) continue;
-                if (P.want_count) S.out_count[r0 + k] = 0u;
-                if (P.want_sum) S.out_sum[r0 + k] = 0ull;
-                if (P.want_min) S.out_min[r0 + k] = 0xFFFFFFFFu;
-            }
-            if (lane < 2) {
-                M.rc[lane] = 0;
-                M.rs[lane] = 0;
-                if (P.want_min) M.rm[lane] = 0xFFFFFFFFu;
-            }
-        }
         __syncwarp();
 
         // ---- element staging: bulk copies of [A, B) in tiles ----
@@ -2062,22 +1374,7 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
 
         PROF_ADD(PF_SETUP, pt_setup);
         bool pstop;
-        if constexpr (STRAT == RS_STRATEGY_TAG) {
-            TagProc<V, SG> pr(P, M, g, lane);
-            pr.S_ = &S;
-            pr.r0 = r0;
-            pr.hsplit = split_head;
-            pr.tsplit = split_tail;
-            pr.nxt = pend;
-            pr.nxt_open = nxt.u.valid && !nxt.scanned;
-            pr.nk = nk;
-            pr.total = total;
-            pr.E0 = E0;
-            if (g.tma) tiles_issue(P, M, g, lane);
-            pr.run_unit();
-            pr.finish_tiles();
-            pstop = pr.stop;
-        } else {
+        {
             Proc<STRAT, V, SG> pr(P, M, w, g, lane);
             pr.nxt = pend;
             pr.nxt_open = nxt.u.valid && !nxt.scanned;
@@ -2101,7 +1398,7 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
         // parents processed in pieces (the continued head, a last parent running past
         // the unit) merge through their owner's slot; the rest are written directly (tag
         // strategy: already updated in place)
-        if constexpr (STRAT != RS_STRATEGY_TAG) {
+        {
             for (uint32_t k = lane; k < nk; k += 32) {
                 if ((k == 0 && split_head) || (k == nk - 1 && split_tail)) continue;
                 if (P.want_count) S.out_count[r0 + k] = M.rc[k];
@@ -2111,7 +1408,7 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
         }
         // accumulator of the first and the last parent: index 0 and nk - 1 (signal
         // strategy), slots 0 and 1 (tag strategy; one slot when they are the same parent)
-        const uint32_t ah = 0, at = (STRAT == RS_STRATEGY_TAG) ? ((split_head && nk == 1) ? 0u : 1u) : nk - 1;
+        const uint32_t ah = 0, at = nk - 1;
         if (lane == 0) {
             if (split_head)
                 merge_piece(S, r0, cur.u.head_off, cur.u.ebase, false, M.rc[ah], M.rs[ah],
@@ -2160,8 +1457,7 @@ struct KEntry {
     {ST, V, OE, O1, O2, O3, O4, (const void *)rs_pipeline_kernel<ST, V, Sig<OE, O1, O2, O3, O4>>}
 #define RS_KALLV(ST, OE, O1, O2, O3, O4) \
     RS_KSIG(ST, 1, OE, O1, O2, O3, O4), RS_KSIG(ST, 2, OE, O1, O2, O3, O4), RS_KSIG(ST, 4, OE, O1, O2, O3, O4)
-#define RS_KBOTH(OE, O1, O2, O3, O4) \
-    RS_KALLV(RS_STRATEGY_SIGNAL, OE, O1, O2, O3, O4), RS_KALLV(RS_STRATEGY_TAG, OE, O1, O2, O3, O4)
+#define RS_KBOTH(OE, O1, O2, O3, O4) RS_KALLV(RS_STRATEGY_SIGNAL, OE, O1, O2, O3, O4)
 
 static const KEntry g_kernels[] = {
     // loaded elements -> three context hash filters -> aggregate
@@ -2176,6 +1472,7 @@ static const KEntry g_kernels[] = {
 
 static const void *kernel_ptr(const KParams &P)
 {
+    if (P.strategy == RS_STRATEGY_TAG) return rs_tag_kernel_entry(P);
     int ops[5] = {0, 0, 0, 0, 0};
     ops[0] = (int)P.st[0].op;
     for (int i = 1; i < P.n_stages - 1 && i < 5; ++i) ops[i] = (int)P.st[i].op;
@@ -2210,6 +1507,7 @@ int rs_kernel_max_smem_optin(const KParams &P, size_t smem)
 
 int rs_kernel_is_specialised(const KParams &P)
 {
+    if (P.strategy == RS_STRATEGY_TAG) return rs_tag_kernel_is_specialised(P);
     for (const KEntry &e : g_kernels)
         if (e.fn == kernel_ptr(P)) return e.oe != 0;
     return 0;

@@ -129,7 +129,7 @@ def test_opts_round_trip():
     with pytest.raises(rs.RsError):
         p.set_opts(warps_per_block=16)
     with pytest.raises(rs.RsError):
-        p.set_opts(regions_per_unit=1000)
+        p.set_opts(regions_per_unit=70000)
     p.close()
 
 

@@ -59,12 +59,13 @@ def test_noalloc_equals_run_on_two_calls(rs, ci):
 
 
 def test_noalloc_rejects_scratch_beyond_its_fixed_size(rs):
-    """A loaded stream of 2^27 parents needs more than the fixed 16 MiB of scratch:
-    the call returns RS_ERR_CAPACITY before enqueuing anything (the descriptor's
-    pointers are never dereferenced)."""
+    """A loaded stream of 2^31 parents needs more than the fixed 16 MiB of scratch
+    under any unit shape (its planner alone keeps one 8-byte look-back word per 1024
+    parents: 16 MiB): the call returns RS_ERR_CAPACITY before enqueuing anything, so the
+    descriptor's placeholder pointers are never dereferenced."""
     p = rs.Pipeline(wl.pipeline_cascade(), strategy="tag")
     d = rs.StreamDesc()
-    d.n_regions = 1 << 27
+    d.n_regions = 1 << 31
     d.region_len = ctypes.c_void_p(0x1000)
     d.elements = ctypes.c_void_p(0x2000)
     d.n_elements = 1 << 27
