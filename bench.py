@@ -179,7 +179,7 @@ def run_reference(args, rank: int, world: int):
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("rs_kernel.cu", "rs_internal.h"):
+    for fn in ("rs_tag.cu", "rs_kernel.cu", "rs_device.cuh", "rs_internal.h"):
         with open(os.path.join(ROOT, "paper_2006_07478_b300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -452,9 +452,15 @@ def main():
                "chosen": {"strategy": "signal" if best["strategy"] == 0 else "tag",
                           **{k: best[k] for k in ("ensemble_width", "regions_per_unit", "region_cost",
                                                   "tile_elements", "warps_per_block")}}}
-        # both strategies at the tuned unit size, kernel-only event timing
+        # both strategies, kernel-only event timing: the chosen one with the tuned options,
+        # the other with its own default unit shape (the strategies' units differ in kind)
+        chosen = "signal" if best["strategy"] == 0 else "tag"
         for strat in ("tag", "signal"):
-            p.set_opts(strategy=strat)
+            if strat == chosen:
+                p.set_opts(**{k: v for k, v in best.items() if k != "strategy"}, strategy=best["strategy"])
+            else:
+                p.set_opts(strategy=strat, regions_per_unit=0, region_cost=0, ensemble_width=128,
+                           tile_elements=0, tiles_in_flight=0, warps_per_block=0, queue_capacity=0)
             p.timing_enable(8)
             for _ in range(2):
                 p.run()
@@ -467,6 +473,7 @@ def main():
             kms = statistics.median(ms)
             gbs = alg_bytes(s) / (kms * 1e-3) / 1e9
             row[strat] = {"kernel_ms": kms, "items_per_s": N_ELEM / (kms * 1e-3), "alg_gbs": gbs,
+                          "options": "tuned" if strat == chosen else "strategy defaults",
                           "active_lane_fraction": [round(x, 4) for x in st["active_lane_fraction"]],
                           "launch": st["launch"]}
         p.set_opts(**{k: v for k, v in best.items() if k != "strategy"}, strategy=best["strategy"])
@@ -606,12 +613,14 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                          "frac_of_8tbs_spec": achieved / SPEC_HBM_GBS,
-                         "kernel": "rs_pipeline_kernel (all launches of the timed region)"},
+                         "kernel": "planner + pipeline kernel (rs_tag_kernel for the tag strategy) of "
+                                   "every run in the timed region"},
             "per_mean": per_mean,
             "clocks": sampler.summary(t_start, t_end),
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "gpu_launches": 3 * sum(len(k) for k in kernel_ms),   # planner, pipeline, finalize per run
+            # per run: planner + pipeline kernel, plus the finalize kernel for the signal strategy
+            "gpu_launches": sum(len(k) * (2 if t["strategy"] == 1 else 3) for k, t in zip(kernel_ms, tuned)),
             **extras,
         }
         print(json.dumps(line), flush=True)

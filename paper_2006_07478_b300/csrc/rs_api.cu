@@ -453,7 +453,7 @@ static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts
 }
 
 // Per-processor shared memory of the tag kernel: counters, window marks (W words),
-// node 1's staging ring of element windows (loaded enumeration only),
+// node 1's staging ring of four element windows (loaded enumeration only),
 // the rings of edges 1..n-2 (values and region tags, two arrays), and the parent records
 // (2 PR entries each: region id and operand, start offset, parent id).  PR >= W + 64
 // covers every record node 1 can still need (the parents of one window plus one chunk).
@@ -483,8 +483,8 @@ static SmemLayout make_tag_layout(const rs_pipeline *p)
     uint32_t pr = 128;
     while (pr < W + 64) pr <<= 1;
     L.pr = pr;
-    L.o_nra = (uint32_t)off;      // {region, operand}, mirrored (2 PR entries)
-    off += (size_t)2 * pr * 8;
+    L.o_nra = (uint32_t)off;      // {region, operand} (PR entries)
+    off += (size_t)pr * 8;
     L.o_nst = (uint32_t)off;      // start offsets (PR entries)
     off += (size_t)pr * 4;
     L.o_npar = (uint32_t)off;     // parent ids, hashed enumeration only (PR entries)
@@ -762,6 +762,8 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p)
                                       : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
     P.plan_fill = strategy == RS_STRATEGY_TAG;
+    P.m16 = 1u << 16;
+    P.m19 = 1u << 19;
 
     // processors per CTA: as asked, but no more than fit the per-block shared memory;
     // 0 = the count (8, 4, 2 or 1) giving the most resident processors per SM
@@ -1311,6 +1313,8 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p)
                                       : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
     P.plan_fill = strategy == RS_STRATEGY_TAG;
+    P.m16 = 1u << 16;
+    P.m19 = 1u << 19;
     if (!p->smem_max) {
         int dev = 0, v = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);

@@ -150,6 +150,8 @@ struct KParams {
     unsigned long long spin_limit;
     uint32_t profile;             // accumulate the cycle breakdown
     uint32_t plan_fill;           // planner writes every region's identity result (tag strategy)
+    uint32_t m16, m19;            // 2^16 and 2^19: x >> 16 = umulhi(x, m16), x >> 13 = umulhi(x, m19)
+                                  // (run-time values, so the shifts stay multiplies)
     SmemLayout L;
 };
 

@@ -8,8 +8,9 @@
 //   * Node 1 reads the unit's elements in windows of W = 32 V consecutive positions.
 //     Enumeration is zero-copy: the enumerate node's output queue is the element array
 //     itself (getItem(i) of Section 4 is node 1's load).  A window is split into slices
-//     of 32 VS positions; in each slice lane l takes VS consecutive positions, loaded
-//     with one 16-byte streaming load issued two windows ahead, so every load
+//     of 32 VS positions; in each slice lane l takes VS consecutive positions.  They are
+//     copied into a shared-memory ring of four windows by one 16-byte asynchronous copy
+//     per lane and slice (cp.async), three windows ahead of node 1, so every copy
 //     instruction of the warp reads one contiguous 512-byte row.
 //   * The unit's parents are streamed in chunks of 32, one per lane (its length or CSR
 //     offsets, context word and id).  A warp scan gives their offsets, and the non-empty
@@ -49,12 +50,26 @@ __device__ __forceinline__ unsigned long long pack2(uint32_t lo, uint32_t hi)
 }
 
 // fmix32(x ^ c0) where c0s = c0 ^ (c0 >> 16): the first xor-shift distributes over the
-// xor with the stage constant, which saves one instruction per hashed item
-__device__ __forceinline__ uint32_t fmix32_x(uint32_t x, uint32_t c0s)
+// xor with the stage constant.  Two of the three right shifts are taken as the high
+// word of a multiply by a power of two (m16 = 2^16, m19 = 2^19, so umulhi(h, m16) =
+// h >> 16 and umulhi(h, m19) = h >> 13): they run on the multiply pipe, which the
+// hash otherwise leaves idle, instead of the integer pipe that carries the rest.
+__device__ __forceinline__ uint32_t fmix32_x(uint32_t x, uint32_t c0s, uint32_t m16, uint32_t m19)
 {
-    uint32_t h = x ^ (x >> 16) ^ c0s;
+    uint32_t h = x ^ __umulhi(x, m16) ^ c0s;
     h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
+    h ^= __umulhi(h, m19);
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// fmix32 (MurmurHash3's 32-bit finalizer) with the same split of its shifts
+__device__ __forceinline__ uint32_t fmix32_m(uint32_t h, uint32_t m16, uint32_t m19)
+{
+    h ^= __umulhi(h, m16);
+    h *= 0x85EBCA6Bu;
+    h ^= __umulhi(h, m19);
     h *= 0xC2B2AE35u;
     h ^= h >> 16;
     return h;
@@ -73,6 +88,23 @@ __device__ __forceinline__ uint32_t scan_add(uint32_t v)
             : "r"(d));
     }
     return v;
+}
+
+// exclusive warp prefix sum and warp total of a small per-lane count c < 2^NB: each bit
+// of c is one ballot, and the prefix is the weighted popcount of the lower lanes' bits.
+// The NB chains are independent, so the latency is that of one ballot and one popcount
+// instead of five dependent shuffles.
+template <int NB>
+__device__ __forceinline__ void prefix_small(uint32_t c, uint32_t lt, uint32_t &ex, uint32_t &tot)
+{
+    ex = 0;
+    tot = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const uint32_t m = __ballot_sync(FULLMASK, (c >> b) & 1u);
+        ex += (uint32_t)__popc(m & lt) << b;
+        tot += (uint32_t)__popc(m) << b;
+    }
 }
 
 // inclusive warp scan (max); a lane with no source lane gets its own value back,
@@ -155,18 +187,6 @@ __device__ __forceinline__ TicketUnit describe(const KParams &P, uint32_t t, uin
     return u;
 }
 
-// L2 prefetch (a bulk asynchronous prefetch, no registers or shared memory held) of
-// the words [lo, hi) of an array of n words, in whole 16-byte granules inside it; only
-// for 16-byte-aligned arrays, as the prefetch wants aligned addresses
-__device__ __forceinline__ void l2_prefetch_u32(const uint32_t *base, uint32_t lo, uint32_t hi, uint32_t n)
-{
-    if (base == nullptr || ((uintptr_t)base & 15u) != 0) return;
-    hi = min(hi, n) & ~3u;
-    lo &= ~3u;
-    if (hi > lo)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + lo), "r"((hi - lo) * 4u) : "memory");
-}
-
 // asynchronous 16-byte copy global -> shared of src_bytes (0..16) bytes, the rest of
 // the 16 zero-filled (the source is 16-byte aligned); and its 4-byte form
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
@@ -184,12 +204,16 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// node 1's element windows in flight per processor (a shared-memory ring of NB windows)
-constexpr uint32_t NB = 4;
+// st.shared of v at byte address a when k != 0, as one predicated store (no branch)
+__device__ __forceinline__ void st_shared_if(uint32_t a, uint32_t v, uint32_t k)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.shared.u32 [%0], %1;\n\t}" ::"r"(a), "r"(v),
+                 "r"(k)
+                 : "memory");
+}
 
-// prefetch distances: elements ahead of node 1, parents ahead of the chunk loads
-constexpr uint32_t EPD = 4096, ECH = 1024;
-constexpr uint32_t MPD = 1024, MCH = 256;
+// node 1's element windows in flight per processor (a shared-memory ring of NB windows)
+constexpr uint32_t NB = 4;   // a power of two (slot = window count & (NB - 1))
 
 template <int V, class SG>
 struct TagEngine {
@@ -220,12 +244,10 @@ struct TagEngine {
     // windows [a, a + W) with a >= j0 and a + W <= flim are full, inside the current
     // parent and need no parent loads (flim = min(s_nx, j1, load_start))
     uint32_t flim, nfast;
-    // L2 prefetch cursors: next element (absolute) and next parent to prefetch
-    uint32_t epf, mpf;
     // node 1's staging ring: start of the next window to copy, windows copied and used
     uint32_t ia, wi, wc;
-    // the next unit: its claimed ticket (lane 0) and, once described early enough for
-    // its data to be prefetched while this unit runs, its description
+    // the next unit: its claimed ticket (lane 0) and, once described (during this unit's
+    // last windows), its description
     uint32_t nt;
     bool nxt_done;
     TicketUnit nxt;
@@ -256,7 +278,6 @@ struct TagEngine {
         load_start = s_nx = NONE;
         flim = 0;
         nfast = 0;
-        epf = mpf = 0;
         ia = wi = wc = 0;
         nt = 0;
         nxt_done = false;
@@ -384,10 +405,8 @@ struct TagEngine {
             uint32_t aux = 0, par = 0;
             if (o1 == D_FILT_WEIGHT || hashed()) par = S.parents ? pp : r;
             if (o1 == D_FILT_HASH_CTX) aux = S.ctx ? pc : 0u;
-            if (o1 == D_FILT_WEIGHT) aux = fmix32_x(par, P.st[1].c0s);
-            const unsigned long long e = pack2(r, aux);
-            nra[o] = e;
-            nra[o + PR] = e;
+            if (o1 == D_FILT_WEIGHT) aux = fmix32_x(par, P.st[1].c0s, P.m16, P.m19);
+            nra[o] = pack2(r, aux);
             nst[o] = st;
             if (hashed()) npar[o] = par;
         }
@@ -404,59 +423,17 @@ struct TagEngine {
         } else {
             load_start = end_last >= j1 ? NONE : end_last;
         }
-        if (load_start != NONE) {
-            prefetch_parents();
-            issue_chunk();
-        }
+        if (load_start != NONE) issue_chunk();
         if (s_nx == NONE && ord_cur + 1 != ord_loaded) s_nx = nst[(ord_cur + 1) & PRM];
         flim = min(min(s_nx, j1), load_start);
     }
 
-    // L2 prefetch of the parent arrays a chunk load will read: [p0, p1) of stream D
-    __device__ __forceinline__ void prefetch_parent_range(const DevStream &D, uint32_t p0, uint32_t p1) const
-    {
-        if (lane != 0) return;
-        if (D.offsets) l2_prefetch_u32(D.offsets, p0, p1 + 1, D.R + 1);
-        else l2_prefetch_u32(D.len, p0, p1, D.R);
-        const uint32_t o1 = op<1>();
-        if (o1 == D_FILT_HASH_CTX) l2_prefetch_u32(D.ctx, p0, p1, D.R);
-        if (o1 == D_FILT_WEIGHT || hashed()) l2_prefetch_u32(D.parents, p0, p1, D.R);
-    }
-
-    // keep the unit's parents prefetched up to MPD ahead of the chunk loads
-    __device__ __forceinline__ void prefetch_parents()
-    {
-        const uint32_t lim = min(cb + MPD, re);
-        while (mpf < lim) {
-            prefetch_parent_range(P.streams[sidx], mpf, min(mpf + MCH, re));
-            mpf += MCH;
-        }
-    }
-
-    // keep the unit's elements prefetched up to EPD ahead of node 1
-    __device__ __forceinline__ void prefetch_elements()
-    {
-        if (hashed()) return;
-        const uint32_t lim = min(a + EPD, j1);
-        while (epf < lim) {
-            if (lane == 0) l2_prefetch_u32(S.elements, epf, min(epf + ECH, j1), S.n_el);
-            epf += ECH;
-        }
-    }
-
-    // describe the next unit and prefetch its first elements and parents, so that its
-    // start does not wait on memory
+    // describe the next unit while this one still has work, so that the descriptor's
+    // loads overlap this unit's last windows
     __device__ __forceinline__ void resolve_next()
     {
         nxt = describe(P, __shfl_sync(FULLMASK, nt, 0), lane);
         nxt_done = true;
-        if (!nxt.work) return;
-        const DevStream &D = P.streams[nxt.stream];
-        if (lane == 0 && !hashed() && nxt.j1 != NONE) {
-            const uint32_t n = D.n_elements < 0xFFFFFFFFull ? (uint32_t)D.n_elements : 0xFFFFFFFFu;
-            l2_prefetch_u32(D.elements, nxt.j0, min(nxt.j0 + EPD, nxt.j1), n);
-        }
-        prefetch_parent_range(D, nxt.rs, min(nxt.rs + MCH, nxt.rend));
     }
 
     // make record o the current one
@@ -467,8 +444,10 @@ struct TagEngine {
         const unsigned long long e = nra[i];
         r_cur = (uint32_t)e;
         aux_cur = (uint32_t)(e >> 32);
-        st_cur = nst[i];
-        if (hashed()) par_cur = npar[i];
+        if (hashed()) {
+            st_cur = nst[i];
+            par_cur = npar[i];
+        }
         s_nx = (o + 1 != ord_loaded) ? nst[(o + 1) & PRM] : NONE;
         flim = min(min(s_nx, j1), load_start);
     }
@@ -543,8 +522,8 @@ struct TagEngine {
             switch (opc) {
             case D_FILT_MASK: kp = (x[j] & sd.p0) == sd.p1; break;
             case D_FILT_MOD: kp = (x[j] % sd.p0) == sd.p1; break;
-            case D_FILT_HASH_CTX: kp = (fmix32_x(x[j], sd.c0s) ^ aux[j]) < sd.p1; break;
-            case D_FILT_WEIGHT: kp = fmix32_x(x[j], sd.c0s) < aux[j]; break;
+            case D_FILT_HASH_CTX: kp = (fmix32_x(x[j], sd.c0s, P.m16, P.m19) ^ aux[j]) < sd.p1; break;
+            case D_FILT_WEIGHT: kp = fmix32_x(x[j], sd.c0s, P.m16, P.m19) < aux[j]; break;
             case D_MAP_MULADD: ys = x[j] * sd.p0 + sd.p1; kp = true; break;
             default: kp = false; break;
             }
@@ -570,26 +549,33 @@ struct TagEngine {
             for (int i = 0; i < GV; ++i) m |= (keep[g * GV + i] ? 1u : 0u) << i;
             c += (uint32_t)__popc(m) << (16 * g);
         }
-        const uint32_t incl = scan_add(c);
-        const uint32_t tot = __shfl_sync(FULLMASK, incl, 31);
-        const uint32_t ex = incl - c;
+        uint32_t ex, tot;
+        if constexpr (NG == 1 && GV <= 7) {
+            // a count of at most 7: three bit-sliced ballots
+            prefix_small<GV <= 1 ? 1 : (GV <= 3 ? 2 : 3)>(c, lanemask_lt(), ex, tot);
+        } else {
+            const uint32_t incl = scan_add(c);
+            tot = __shfl_sync(FULLMASK, incl, 31);
+            ex = incl - c;
+        }
         const uint32_t s0 = qt[I] & CM;
         uint32_t n = 0;
 #pragma unroll
         for (int g = 0; g < NG; ++g) n += (tot >> (16 * g)) & 0xFFFFu;
         if (s0 + n <= C) {
+            // byte addresses of the slots; kept items take consecutive ones
+            const uint32_t vb = smem_addr(rv.ptr()), tb = smem_addr(rt.ptr());
             uint32_t gb = rb + s0;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                uint32_t idx = gb + ((ex >> (16 * g)) & 0xFFFFu);
+                uint32_t off = 4u * (gb + ((ex >> (16 * g)) & 0xFFFFu));
 #pragma unroll
                 for (int i = 0; i < GV; ++i) {
                     const int j = g * GV + i;
-                    if (keep[j]) {
-                        rv[idx] = y[j];
-                        rt[idx] = r[j];
-                        ++idx;
-                    }
+                    const uint32_t k = keep[j] ? 1u : 0u;
+                    st_shared_if(vb + off, y[j], k);
+                    st_shared_if(tb + off, r[j], k);
+                    off += 4u * k;
                 }
                 gb += (tot >> (16 * g)) & 0xFFFFu;
             }
@@ -623,7 +609,7 @@ struct TagEngine {
         uint32_t nout[V], c = 0;
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            nout[j] = valid[j] ? fmix32_x(x[j], sd.c0s) % (sd.fanout + 1u) : 0u;
+            nout[j] = valid[j] ? fmix32_x(x[j], sd.c0s, P.m16, P.m19) % (sd.fanout + 1u) : 0u;
             c += nout[j] << (16 * (j / GV));
         }
         const uint32_t incl = scan_add(c);
@@ -720,13 +706,13 @@ struct TagEngine {
         } else if (opc == D_FILT_WEIGHT) {
             const uint32_t c0s = P.st[I].c0s;
             if (uni) {
-                const uint32_t w = fmix32_x(S.parents ? __ldg(S.parents + r0) : r0, c0s);
+                const uint32_t w = fmix32_x(S.parents ? __ldg(S.parents + r0) : r0, c0s, P.m16, P.m19);
 #pragma unroll
                 for (int j = 0; j < V; ++j) aux[j] = w;
             } else {
 #pragma unroll
                 for (int j = 0; j < V; ++j)
-                    if (valid[j]) aux[j] = fmix32_x(S.parents ? __ldg(S.parents + r[j]) : r[j], c0s);
+                    if (valid[j]) aux[j] = fmix32_x(S.parents ? __ldg(S.parents + r[j]) : r[j], c0s, P.m16, P.m19);
             }
         }
     }
@@ -751,7 +737,7 @@ struct TagEngine {
 #pragma unroll
                 for (int i = 0; i < VS; ++i) {
                     const uint32_t p = a + t * SW + VS * lane + i;
-                    x[t * VS + i] = fmix32(par_cur ^ fmix32((p - st_cur) ^ RS_GOLD));
+                    x[t * VS + i] = fmix32_m(par_cur ^ fmix32_m((p - st_cur) ^ RS_GOLD, P.m16, P.m19), P.m16, P.m19);
                 }
         } else {
             staged_window(x);
@@ -855,15 +841,14 @@ struct TagEngine {
                 }
                 carry = max(carry, __shfl_sync(FULLMASK, incl, 31));
             }
-            const uint32_t ob = ord_cur & PRM;   // records are mirrored: ob + rel < 2 PR
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                const unsigned long long e = nra[ob + rel[j]];
+                const unsigned long long e = nra[(ord_cur + rel[j]) & PRM];
                 r[j] = (uint32_t)e;
                 aux[j] = (uint32_t)(e >> 32);
                 if (hashed()) {
-                    st[j] = nst[(ob + rel[j]) & PRM];
-                    par[j] = npar[(ob + rel[j]) & PRM];
+                    st[j] = nst[(ord_cur + rel[j]) & PRM];
+                    par[j] = npar[(ord_cur + rel[j]) & PRM];
                 } else {
                     st[j] = par[j] = 0;
                 }
@@ -893,7 +878,7 @@ struct TagEngine {
                 for (int i = 0; i < VS; ++i) {
                     const int j = t * VS + i;
                     const uint32_t p = a + t * SW + VS * lane + i;
-                    x[j] = valid[j] ? fmix32(par[j] ^ fmix32((p - st[j]) ^ RS_GOLD)) : 0u;
+                    x[j] = valid[j] ? fmix32_m(par[j] ^ fmix32_m((p - st[j]) ^ RS_GOLD, P.m16, P.m19), P.m16, P.m19) : 0u;
                 }
         } else {
             staged_window(x);
@@ -1102,8 +1087,7 @@ struct TagEngine {
         }
         if (a >= j0 && a + W <= flim) fast_window();
         else node1();
-        prefetch_elements();
-        if (!nxt_done && a + 2 * EPD >= j1) resolve_next();
+        if (!nxt_done && a + 8 * W >= j1) resolve_next();
         pump();
         return true;
     }
@@ -1125,10 +1109,6 @@ struct TagEngine {
         unit_bad = false;
         load_start = (rs < rend && base < j1) ? base : NONE;
         a = j0 & ~3u;
-        epf = a;
-        mpf = rs;
-        prefetch_elements();
-        prefetch_parents();
         if (load_start != NONE) issue_chunk();
         ia = a;
         wi = wc = 0;
