@@ -470,6 +470,8 @@ static SmemLayout make_tag_layout(const rs_pipeline *p)
 #endif
     L.o_cnt = (uint32_t)off;
     off += 8 * 4 * RS_MAX_STAGES;
+    L.o_pend = (uint32_t)off;     // the next unit's description (7 words)
+    off += 32;
     off = align_up(off, 16);
     L.o_scr = (uint32_t)off;
     off += (size_t)4 * W;

@@ -116,14 +116,14 @@ __device__ __forceinline__ uint32_t scan_max(uint32_t v)
     return v;
 }
 
-// pointers of the stream being processed, held in registers
+// the stream being processed: what node 1 and the per-ensemble operands read, held in
+// registers (the rest is read from the stream table when needed)
 struct StreamRegs {
-    const uint32_t *elements, *len, *offsets, *ctx, *parents;
-    uint32_t *out_count, *out_min;
-    unsigned long long *out_sum;
-    uint32_t n_el;      // element count, clamped to 32 bits
-    uint32_t R;
-    bool vec;           // elements 16-byte aligned: vector loads
+    const uint32_t *elements, *ctx;
+    const uint32_t *meta;   // CSR offsets, or lengths
+    uint32_t n_el;          // element count, clamped to 32 bits
+    bool csr;               // meta holds offsets
+    bool vec;               // elements 16-byte aligned: vector copies
 };
 
 // A claimed ticket: its stream and merge-path unit.
@@ -224,10 +224,23 @@ struct TagEngine {
 
     const KParams &P;
     const uint32_t lane;
-    SArr<unsigned long long> cnt, nra;
-    SArr<uint32_t> rv, rt, nst, npar, marks;   // rings: values, tags
-    SArr<uint32_t> stg;                         // node 1's staged windows (NB x W elements)
-    const uint32_t PR, PRM, C, CM;
+    const uint32_t wb;   // this processor's byte offset in dynamic shared memory
+    // shared-memory arrays: byte offsets from the kernel parameters, so only wb lives in
+    // a register
+    __device__ __forceinline__ SArr<unsigned long long> cnt() const { return sarr<unsigned long long>(wb + P.L.o_cnt); }
+    __device__ __forceinline__ SArr<unsigned long long> nra() const { return sarr<unsigned long long>(wb + P.L.o_nra); }
+    __device__ __forceinline__ SArr<uint32_t> rv() const { return sarr<uint32_t>(wb + P.L.o_qv); }   // ring values
+    __device__ __forceinline__ SArr<uint32_t> rt() const { return sarr<uint32_t>(wb + P.L.o_qt); }   // ring tags
+    __device__ __forceinline__ SArr<uint32_t> nst() const { return sarr<uint32_t>(wb + P.L.o_nst); }
+    __device__ __forceinline__ SArr<uint32_t> npar() const { return sarr<uint32_t>(wb + P.L.o_npar); }
+    __device__ __forceinline__ SArr<uint32_t> marks() const { return sarr<uint32_t>(wb + P.L.o_scr); }
+    __device__ __forceinline__ SArr<uint32_t> stg() const { return sarr<uint32_t>(wb + P.L.o_tiles); }
+    __device__ __forceinline__ SArr<uint32_t> nxs() const { return sarr<uint32_t>(wb + P.L.o_pend); }
+    // ring capacity and record-ring size (powers of two), from the kernel parameters
+    __device__ __forceinline__ uint32_t C() const { return P.C; }
+    __device__ __forceinline__ uint32_t CM() const { return P.C - 1; }
+    __device__ __forceinline__ uint32_t PR() const { return P.L.pr; }
+    __device__ __forceinline__ uint32_t PRM() const { return P.L.pr - 1; }
 
     // free-running cursors of the rings; edge e (node e -> node e + 1, e >= 1) is ring e - 1
     uint32_t qh[RS_MAX_STAGES], qt[RS_MAX_STAGES];
@@ -250,7 +263,6 @@ struct TagEngine {
     // last windows), its description
     uint32_t nt;
     bool nxt_done;
-    TicketUnit nxt;
     uint32_t r_cur, aux_cur, st_cur, par_cur;
     // the next chunk, loaded ahead: this lane's parent cb + lane
     uint32_t pl0, pl1, pc, pp;
@@ -259,17 +271,9 @@ struct TagEngine {
     uint32_t ctr;
     bool stop, unit_bad, fill;
 
-    __device__ __forceinline__ TagEngine(const KParams &P_, uint32_t lane_, uint32_t wb)
-        : P(P_), lane(lane_), PR(P_.L.pr), PRM(P_.L.pr - 1), C(P_.C), CM(P_.C - 1)
+    __device__ __forceinline__ TagEngine(const KParams &P_, uint32_t lane_, uint32_t wb_)
+        : P(P_), lane(lane_), wb(wb_)
     {
-        cnt = sarr<unsigned long long>(wb + P.L.o_cnt);
-        rv = sarr<uint32_t>(wb + P.L.o_qv);
-        rt = sarr<uint32_t>(wb + P.L.o_qt);
-        nra = sarr<unsigned long long>(wb + P.L.o_nra);
-        nst = sarr<uint32_t>(wb + P.L.o_nst);
-        npar = sarr<uint32_t>(wb + P.L.o_npar);
-        marks = sarr<uint32_t>(wb + P.L.o_scr);
-        stg = sarr<uint32_t>(wb + P.L.o_tiles);
 #pragma unroll
         for (int e = 0; e < RS_MAX_STAGES; ++e) qh[e] = qt[e] = 0;
         sidx = NONE;
@@ -281,18 +285,14 @@ struct TagEngine {
         ia = wi = wc = 0;
         nt = 0;
         nxt_done = false;
-        nxt.valid = nxt.work = nxt.fill = false;
-        nxt.stream = nxt.rs = nxt.base = nxt.rend = nxt.j0 = nxt.j1 = 0;
         ord_loaded = ord_cur = 0;
         r_cur = aux_cur = st_cur = par_cur = 0;
         pl0 = pl1 = pc = pp = 0;
         ctr = 0;
         stop = unit_bad = fill = false;
-        S.elements = S.len = S.offsets = S.ctx = S.parents = nullptr;
-        S.out_count = S.out_min = nullptr;
-        S.out_sum = nullptr;
-        S.n_el = S.R = 0;
-        S.vec = false;
+        S.elements = S.ctx = S.meta = nullptr;
+        S.n_el = 0;
+        S.csr = S.vec = false;
     }
 
     __device__ __forceinline__ int n_st() const { return SG::generic ? P.n_stages : SG::n; }
@@ -319,23 +319,20 @@ struct TagEngine {
 
     __device__ __forceinline__ void flush_counters()
     {
-        if (lane < 4 * RS_MAX_STAGES) cnt[lane] += ctr;
+        if (lane < 4 * RS_MAX_STAGES) cnt()[lane] += ctr;
         ctr = 0;
     }
+
+    __device__ __forceinline__ const DevStream &D() const { return P.streams[sidx]; }
 
     __device__ __forceinline__ void set_stream(uint32_t si)
     {
         const DevStream &D = P.streams[si];
         S.elements = D.elements;
-        S.len = D.len;
-        S.offsets = D.offsets;
         S.ctx = D.ctx;
-        S.parents = D.parents;
-        S.out_count = D.out_count;
-        S.out_sum = D.out_sum;
-        S.out_min = D.out_min;
+        S.csr = D.offsets != nullptr;
+        S.meta = S.csr ? D.offsets : D.len;
         S.n_el = D.n_elements < 0xFFFFFFFFull ? (uint32_t)D.n_elements : 0xFFFFFFFFu;
-        S.R = D.R;
         S.vec = D.tma_ok != 0;
         sidx = si;
     }
@@ -348,15 +345,14 @@ struct TagEngine {
     {
         const uint32_t r = cb + lane;
         const bool in = r < re;
-        if (S.offsets) {
-            pl0 = in ? __ldg(S.offsets + r) : 0u;
-            pl1 = in ? __ldg(S.offsets + r + 1) : 0u;
-        } else {
-            pl0 = in ? __ldg(S.len + r) : 0u;
-        }
+        pl0 = in ? __ldg(S.meta + r) : 0u;
+        if (S.csr) pl1 = in ? __ldg(S.meta + r + 1) : 0u;
         const uint32_t o1 = op<1>();
         if (o1 == D_FILT_HASH_CTX && S.ctx) pc = in ? __ldg(S.ctx + r) : 0u;
-        if ((o1 == D_FILT_WEIGHT || hashed()) && S.parents) pp = in ? __ldg(S.parents + r) : 0u;
+        if (o1 == D_FILT_WEIGHT || hashed()) {
+            const uint32_t *pa = D().parents;
+            if (pa) pp = in ? __ldg(pa + r) : 0u;
+        }
     }
 
     __device__ __forceinline__ void bad_unit()
@@ -372,7 +368,7 @@ struct TagEngine {
     {
         // consistent input never holds more records than one window's parents plus a
         // chunk (fewer than PR - 32 before this load): anything else is inconsistent
-        if (ord_loaded - ord_cur > PR - 32) {
+        if (ord_loaded - ord_cur > PR() - 32) {
             bad_unit();
             return;
         }
@@ -380,7 +376,7 @@ struct TagEngine {
         const bool in = r < re;
         uint32_t st, L;
         bool bad = false;
-        if (S.offsets) {
+        if (S.csr) {
             st = pl0;
             L = pl1 - pl0;
             bad = in && pl1 < pl0;
@@ -391,24 +387,25 @@ struct TagEngine {
             cstart += __shfl_sync(FULLMASK, incl, 31);
         }
         if (fill && in) {
-            if (P.want_count) S.out_count[r] = 0u;
-            if (P.want_sum) S.out_sum[r] = 0ull;
-            if (P.want_min) S.out_min[r] = NONE;
+            const DevStream &d = D();
+            if (P.want_count) d.out_count[r] = 0u;
+            if (P.want_sum) d.out_sum[r] = 0ull;
+            if (P.want_min) d.out_min[r] = NONE;
         }
         const uint32_t nin = min(32u, re - cb);
         const uint32_t end_last = __shfl_sync(FULLMASK, st + L, nin - 1);   // start of parent cb + nin
         const bool nz = in && !bad && L > 0 && st + L > j0 && st < j1;
         const uint32_t b = __ballot_sync(FULLMASK, nz);
         if (nz) {
-            const uint32_t o = (ord_loaded + __popc(b & lanemask_lt())) & PRM;
+            const uint32_t o = (ord_loaded + __popc(b & lanemask_lt())) & PRM();
             const uint32_t o1 = op<1>();
             uint32_t aux = 0, par = 0;
-            if (o1 == D_FILT_WEIGHT || hashed()) par = S.parents ? pp : r;
+            if (o1 == D_FILT_WEIGHT || hashed()) par = D().parents ? pp : r;
             if (o1 == D_FILT_HASH_CTX) aux = S.ctx ? pc : 0u;
             if (o1 == D_FILT_WEIGHT) aux = fmix32_x(par, P.st[1].c0s, P.m16, P.m19);
-            nra[o] = pack2(r, aux);
-            nst[o] = st;
-            if (hashed()) npar[o] = par;
+            nra()[o] = pack2(r, aux);
+            nst()[o] = st;
+            if (hashed()) npar()[o] = par;
         }
         ord_loaded += __popc(b);
         __syncwarp();   // records (and identity results) precede their readers
@@ -424,31 +421,61 @@ struct TagEngine {
             load_start = end_last >= j1 ? NONE : end_last;
         }
         if (load_start != NONE) issue_chunk();
-        if (s_nx == NONE && ord_cur + 1 != ord_loaded) s_nx = nst[(ord_cur + 1) & PRM];
+        if (s_nx == NONE && ord_cur + 1 != ord_loaded) s_nx = nst()[(ord_cur + 1) & PRM()];
         flim = min(min(s_nx, j1), load_start);
     }
 
     // describe the next unit while this one still has work, so that the descriptor's
-    // loads overlap this unit's last windows
+    // loads overlap this unit's last windows; the description waits in shared memory
     __device__ __forceinline__ void resolve_next()
     {
-        nxt = describe(P, __shfl_sync(FULLMASK, nt, 0), lane);
+        const TicketUnit u = describe(P, __shfl_sync(FULLMASK, nt, 0), lane);
+        if (lane == 0) {
+            SArr<uint32_t> x = nxs();
+            x[0] = u.stream;
+            x[1] = u.rs;
+            x[2] = u.base;
+            x[3] = u.rend;
+            x[4] = u.j0;
+            x[5] = u.j1;
+            x[6] = (u.valid ? 1u : 0u) | (u.work ? 2u : 0u) | (u.fill ? 4u : 0u);
+        }
+        __syncwarp();
         nxt_done = true;
+    }
+
+    __device__ __forceinline__ TicketUnit next_unit()
+    {
+        if (!nxt_done) resolve_next();
+        const SArr<uint32_t> x = nxs();
+        TicketUnit u;
+        u.stream = x[0];
+        u.rs = x[1];
+        u.base = x[2];
+        u.rend = x[3];
+        u.j0 = x[4];
+        u.j1 = x[5];
+        const uint32_t f = x[6];
+        u.valid = f & 1u;
+        u.work = f & 2u;
+        u.fill = f & 4u;
+        __syncwarp();
+        return u;
     }
 
     // make record o the current one
     __device__ __forceinline__ void take_record(uint32_t o)
     {
         ord_cur = o;
-        const uint32_t i = o & PRM;
-        const unsigned long long e = nra[i];
+        const uint32_t i = o & PRM();
+        const unsigned long long e = nra()[i];
         r_cur = (uint32_t)e;
         aux_cur = (uint32_t)(e >> 32);
         if (hashed()) {
-            st_cur = nst[i];
-            par_cur = npar[i];
+            st_cur = nst()[i];
+            par_cur = npar()[i];
         }
-        s_nx = (o + 1 != ord_loaded) ? nst[(o + 1) & PRM] : NONE;
+        s_nx = (o + 1 != ord_loaded) ? nst()[(o + 1) & PRM()] : NONE;
         flim = min(min(s_nx, j1), load_start);
     }
 
@@ -463,7 +490,7 @@ struct TagEngine {
         const uint32_t wa = ia;
         if (wa < j1) {
             const uint32_t lim = min(j1, S.n_el);
-            const uint32_t sb = smem_addr(stg.ptr() + (wi & (NB - 1)) * W);
+            const uint32_t sb = smem_addr(stg().ptr() + (wi & (NB - 1)) * W);
 #pragma unroll
             for (int t = 0; t < NS; ++t) {
                 const uint32_t e = wa + t * SW + VS * lane;
@@ -489,7 +516,7 @@ struct TagEngine {
     {
         issue_window();
         cp_async_wait<NB - 1>();
-        const uint32_t *sp = stg.ptr() + (wc & (NB - 1)) * W;
+        const uint32_t *sp = stg().ptr() + (wc & (NB - 1)) * W;
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
             if constexpr (VS == 4) {
@@ -540,7 +567,7 @@ struct TagEngine {
     template <int I, int NG, int GV>
     __device__ __forceinline__ void push(const bool (&keep)[V], const uint32_t (&y)[V], const uint32_t (&r)[V])
     {
-        const uint32_t rb = (I - 1) * C;
+        const uint32_t rb = (I - 1) * C();
         uint32_t c = 0;
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
@@ -558,13 +585,13 @@ struct TagEngine {
             tot = __shfl_sync(FULLMASK, incl, 31);
             ex = incl - c;
         }
-        const uint32_t s0 = qt[I] & CM;
+        const uint32_t s0 = qt[I] & CM();
         uint32_t n = 0;
 #pragma unroll
         for (int g = 0; g < NG; ++g) n += (tot >> (16 * g)) & 0xFFFFu;
-        if (s0 + n <= C) {
+        if (s0 + n <= C()) {
             // byte addresses of the slots; kept items take consecutive ones
-            const uint32_t vb = smem_addr(rv.ptr()), tb = smem_addr(rt.ptr());
+            const uint32_t vb = smem_addr(rv().ptr()), tb = smem_addr(rt().ptr());
             uint32_t gb = rb + s0;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
@@ -588,8 +615,8 @@ struct TagEngine {
                 for (int i = 0; i < GV; ++i) {
                     const int j = g * GV + i;
                     if (keep[j]) {
-                        rv[rb + (pos & CM)] = y[j];
-                        rt[rb + (pos & CM)] = r[j];
+                        rv()[rb + (pos & CM())] = y[j];
+                        rt()[rb + (pos & CM())] = r[j];
                         ++pos;
                     }
                 }
@@ -605,7 +632,7 @@ struct TagEngine {
     __device__ __forceinline__ void expand(const uint32_t (&x)[V], const uint32_t (&r)[V], const bool (&valid)[V])
     {
         const DevStage &sd = P.st[I];
-        const uint32_t rb = (I - 1) * C;
+        const uint32_t rb = (I - 1) * C();
         uint32_t nout[V], c = 0;
 #pragma unroll
         for (int j = 0; j < V; ++j) {
@@ -624,8 +651,8 @@ struct TagEngine {
                 const int j = g * GV + i;
                 for (uint32_t o = 0; o < nout[j]; ++o) {
                     const uint32_t yv = fmix32(x[j] ^ fmix32((sd.p0 + 1u + o) ^ RS_GOLD));
-                    rv[rb + (pos & CM)] = yv;
-                    rt[rb + (pos & CM)] = r[j];
+                    rv()[rb + (pos & CM())] = yv;
+                    rt()[rb + (pos & CM())] = r[j];
                     ++pos;
                 }
             }
@@ -636,9 +663,10 @@ struct TagEngine {
 
     __device__ __forceinline__ void fold(uint32_t rr, uint32_t n, unsigned long long s, uint32_t mn) const
     {
-        if (P.want_count) atomicAdd(S.out_count + rr, n);
-        if (P.want_sum) atomicAdd(S.out_sum + rr, s);
-        if (P.want_min) atomicMin(S.out_min + rr, mn);
+        const DevStream &d = D();
+        if (P.want_count) atomicAdd(d.out_count + rr, n);
+        if (P.want_sum) atomicAdd(d.out_sum + rr, s);
+        if (P.want_min) atomicMin(d.out_min + rr, mn);
     }
 
     // the aggregate (Section 4.2): count, sum and min of each region's surviving items
@@ -706,13 +734,15 @@ struct TagEngine {
         } else if (opc == D_FILT_WEIGHT) {
             const uint32_t c0s = P.st[I].c0s;
             if (uni) {
-                const uint32_t w = fmix32_x(S.parents ? __ldg(S.parents + r0) : r0, c0s, P.m16, P.m19);
+                const uint32_t *pa = D().parents;
+                const uint32_t w = fmix32_x(pa ? __ldg(pa + r0) : r0, c0s, P.m16, P.m19);
 #pragma unroll
                 for (int j = 0; j < V; ++j) aux[j] = w;
             } else {
+                const uint32_t *pa = D().parents;
 #pragma unroll
                 for (int j = 0; j < V; ++j)
-                    if (valid[j]) aux[j] = fmix32_x(S.parents ? __ldg(S.parents + r[j]) : r[j], c0s, P.m16, P.m19);
+                    if (valid[j]) aux[j] = fmix32_x(pa ? __ldg(pa + r[j]) : r[j], c0s, P.m16, P.m19);
             }
         }
     }
@@ -792,7 +822,7 @@ struct TagEngine {
             // mark each parent start in the window with its record index (relative to
             // the current record), then a running maximum gives each position's parent
             __syncwarp();
-            uint4 *mk = reinterpret_cast<uint4 *>(marks.ptr());
+            uint4 *mk = reinterpret_cast<uint4 *>(marks().ptr());
 #pragma unroll
             for (uint32_t k = 0; k < W / 128; ++k) mk[k * 32 + lane] = make_uint4(0u, 0u, 0u, 0u);
             if constexpr (W < 128) {
@@ -803,9 +833,9 @@ struct TagEngine {
             for (uint32_t base = nx;; base += 32) {
                 const uint32_t o = base + lane;
                 const bool in = (o - nx) < (ord_loaded - nx);
-                const uint32_t s = in ? nst[o & PRM] : NONE;
+                const uint32_t s = in ? nst()[o & PRM()] : NONE;
                 const bool w = s < hi;
-                if (w && s >= a) marks[s - a] = o - ord_cur;
+                if (w && s >= a) marks()[s - a] = o - ord_cur;
                 if (!__shfl_sync(FULLMASK, w, 31)) break;
             }
             __syncwarp();
@@ -816,17 +846,17 @@ struct TagEngine {
                 uint32_t m[VS];
                 const uint32_t mo = t * SW + VS * lane;
                 if constexpr (VS == 4) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(marks.ptr() + mo);
+                    const uint4 v = *reinterpret_cast<const uint4 *>(marks().ptr() + mo);
                     m[0] = v.x;
                     m[1 % VS] = v.y;
                     m[2 % VS] = v.z;
                     m[3 % VS] = v.w;
                 } else if constexpr (VS == 2) {
-                    const uint2 v = *reinterpret_cast<const uint2 *>(marks.ptr() + mo);
+                    const uint2 v = *reinterpret_cast<const uint2 *>(marks().ptr() + mo);
                     m[0] = v.x;
                     m[1 % VS] = v.y;
                 } else {
-                    m[0] = marks[mo];
+                    m[0] = marks()[mo];
                 }
                 uint32_t lm = m[0];
 #pragma unroll
@@ -843,12 +873,12 @@ struct TagEngine {
             }
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                const unsigned long long e = nra[(ord_cur + rel[j]) & PRM];
+                const unsigned long long e = nra()[(ord_cur + rel[j]) & PRM()];
                 r[j] = (uint32_t)e;
                 aux[j] = (uint32_t)(e >> 32);
                 if (hashed()) {
-                    st[j] = nst[(ord_cur + rel[j]) & PRM];
-                    par[j] = npar[(ord_cur + rel[j]) & PRM];
+                    st[j] = nst()[(ord_cur + rel[j]) & PRM()];
+                    par[j] = npar()[(ord_cur + rel[j]) & PRM()];
                 } else {
                     st[j] = par[j] = 0;
                 }
@@ -913,16 +943,16 @@ struct TagEngine {
     __device__ __forceinline__ void gather(uint32_t take, uint32_t (&x)[V], uint32_t (&r)[V], bool (&valid)[V],
                                            bool &uni, uint32_t &r0) const
     {
-        const uint32_t rb = (I - 2) * C;
+        const uint32_t rb = (I - 2) * C();
         const uint32_t h = qh[I - 1];
         if (FULL || (h & (V - 1)) == 0) {
             // the lane's V slots are contiguous (C is a multiple of V)
-            const uint32_t s = rb + ((h + V * lane) & CM);
+            const uint32_t s = rb + ((h + V * lane) & CM());
             if constexpr (VS == 4) {
 #pragma unroll
                 for (int t = 0; t < NS; ++t) {
-                    const uint4 xv = *reinterpret_cast<const uint4 *>(rv.ptr() + s + 4 * t);
-                    const uint4 tv = *reinterpret_cast<const uint4 *>(rt.ptr() + s + 4 * t);
+                    const uint4 xv = *reinterpret_cast<const uint4 *>(rv().ptr() + s + 4 * t);
+                    const uint4 tv = *reinterpret_cast<const uint4 *>(rt().ptr() + s + 4 * t);
                     x[4 * t + 0] = xv.x;
                     x[4 * t + 1 % V] = xv.y;
                     x[4 * t + 2 % V] = xv.z;
@@ -933,28 +963,28 @@ struct TagEngine {
                     r[4 * t + 3 % V] = tv.w;
                 }
             } else if constexpr (VS == 2) {
-                const uint2 xv = *reinterpret_cast<const uint2 *>(rv.ptr() + s);
-                const uint2 tv = *reinterpret_cast<const uint2 *>(rt.ptr() + s);
+                const uint2 xv = *reinterpret_cast<const uint2 *>(rv().ptr() + s);
+                const uint2 tv = *reinterpret_cast<const uint2 *>(rt().ptr() + s);
                 x[0] = xv.x;
                 x[1 % V] = xv.y;
                 r[0] = tv.x;
                 r[1 % V] = tv.y;
             } else {
-                x[0] = rv[s];
-                r[0] = rt[s];
+                x[0] = rv()[s];
+                r[0] = rt()[s];
             }
         } else {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                x[j] = rv[rb + ((h + V * lane + j) & CM)];
-                r[j] = rt[rb + ((h + V * lane + j) & CM)];
+                x[j] = rv()[rb + ((h + V * lane + j) & CM())];
+                r[j] = rt()[rb + ((h + V * lane + j) & CM())];
             }
         }
 #pragma unroll
         for (int j = 0; j < V; ++j) valid[j] = FULL || V * lane + j < take;
         // tags never decrease along a ring: equal first and last tags mean one region
         r0 = __shfl_sync(FULLMASK, r[0], 0);
-        const uint32_t rl = rt[rb + ((h + take - 1) & CM)];
+        const uint32_t rl = rt()[rb + ((h + take - 1) & CM())];
         uni = r0 == rl;
     }
 
@@ -990,7 +1020,7 @@ struct TagEngine {
             const bool last = I == n_st() - 1;
             const uint32_t need = W * fanout<I>();
             uint32_t n_ens = 0;
-            while (qt[I - 1] - qh[I - 1] >= W && (last || C - (qt[I] - qh[I]) >= need)) {
+            while (qt[I - 1] - qh[I - 1] >= W && (last || C() - (qt[I] - qh[I]) >= need)) {
                 ensemble<I, true>(W);
                 qh[I - 1] += W;
                 ++n_ens;
@@ -1011,7 +1041,7 @@ struct TagEngine {
             uint32_t n_ens = 0, n_items = 0;
             for (;;) {
                 const uint32_t avail = qt[I - 1] - qh[I - 1];
-                if (avail == 0 || (!last && C - (qt[I] - qh[I]) < need)) break;
+                if (avail == 0 || (!last && C() - (qt[I] - qh[I]) < need)) break;
                 const uint32_t take = min(avail, W);
                 ensemble<I, false>(take);
                 qh[I - 1] += take;
@@ -1076,7 +1106,7 @@ struct TagEngine {
         if (n_st() > 2) {
             const uint32_t need = W * fanout<1>();
             uint64_t guard = 0;
-            while (C - (qt[1] - qh[1]) < need) {
+            while (C() - (qt[1] - qh[1]) < need) {
                 pump();
                 if (++guard > P.budget) {
                     if (lane == 0) atomicOr(&P.hdr->status, ST_STALL);
@@ -1145,7 +1175,7 @@ __global__ void __launch_bounds__(256, 2) rs_tag_kernel(const __grid_constant__ 
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t wb = warp * P.L.per_warp;
     TagEngine<V, SG> E(P, lane, wb);
-    if (lane < 4 * RS_MAX_STAGES) E.cnt[lane] = 0;
+    if (lane < 4 * RS_MAX_STAGES) E.cnt()[lane] = 0;
     __syncwarp();
 
     uint32_t t = 0;
@@ -1164,8 +1194,7 @@ __global__ void __launch_bounds__(256, 2) rs_tag_kernel(const __grid_constant__ 
             }
             E.run_unit(u.rs, u.base, u.rend, u.j0, u.j1, u.fill);
         }
-        if (!E.nxt_done) E.resolve_next();
-        u = E.nxt;
+        u = E.next_unit();
     }
     if (!E.stop) E.drain_all();
     E.flush_counters();
@@ -1173,7 +1202,7 @@ __global__ void __launch_bounds__(256, 2) rs_tag_kernel(const __grid_constant__ 
     __syncwarp();
     if (lane == 0) {
         atomicAdd(&P.hdr->units, units);
-        for (int i = 0; i < 4 * P.n_stages; ++i) atomicAdd(&P.hdr->counters[i], E.cnt[i]);
+        for (int i = 0; i < 4 * P.n_stages; ++i) atomicAdd(&P.hdr->counters[i], E.cnt()[i]);
     }
 }
 
