@@ -90,20 +90,18 @@ __device__ __forceinline__ uint32_t scan_add(uint32_t v)
     return v;
 }
 
-// exclusive warp prefix sum and warp total of a small per-lane count c < 2^NB: each bit
-// of c is one ballot, and the prefix is the weighted popcount of the lower lanes' bits.
+// exclusive warp prefix sum of a small per-lane count c < 2^NB: each bit of c is one
+// ballot, and the prefix is the weighted popcount of the lower lanes' bits.
 // The NB chains are independent, so the latency is that of one ballot and one popcount
 // instead of five dependent shuffles.
 template <int NB>
-__device__ __forceinline__ void prefix_small(uint32_t c, uint32_t lt, uint32_t &ex, uint32_t &tot)
+__device__ __forceinline__ void prefix_small(uint32_t c, uint32_t lt, uint32_t &ex)
 {
     ex = 0;
-    tot = 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const uint32_t m = __ballot_sync(FULLMASK, (c >> b) & 1u);
         ex += (uint32_t)__popc(m & lt) << b;
-        tot += (uint32_t)__popc(m) << b;
     }
 }
 
@@ -259,6 +257,7 @@ struct TagEngine {
     uint32_t flim, nfast;
     // node 1's staging ring: start of the next window to copy, windows copied and used
     uint32_t ia, wi, wc;
+    uint32_t clim;   // elements below min(j1, element count): windows ending there copy whole
     // the next unit: its claimed ticket (lane 0) and, once described (during this unit's
     // last windows), its description
     uint32_t nt;
@@ -283,6 +282,7 @@ struct TagEngine {
         flim = 0;
         nfast = 0;
         ia = wi = wc = 0;
+        clim = 0;
         nt = 0;
         nxt_done = false;
         ord_loaded = ord_cur = 0;
@@ -488,9 +488,14 @@ struct TagEngine {
     __device__ __forceinline__ void issue_window()
     {
         const uint32_t wa = ia;
-        if (wa < j1) {
+        const uint32_t sb = smem_addr(stg().ptr() + (wi & (NB - 1)) * W);
+        if (VS == 4 && S.vec && wa + W <= clim) {
+            // the whole window lies inside the unit and the array: plain 16-byte copies
+#pragma unroll
+            for (int t = 0; t < NS; ++t)
+                cp_async16(sb + 4u * (t * SW + VS * lane), S.elements + wa + t * SW + VS * lane, 16u);
+        } else if (wa < j1) {
             const uint32_t lim = min(j1, S.n_el);
-            const uint32_t sb = smem_addr(stg().ptr() + (wi & (NB - 1)) * W);
 #pragma unroll
             for (int t = 0; t < NS; ++t) {
                 const uint32_t e = wa + t * SW + VS * lane;
@@ -578,8 +583,9 @@ struct TagEngine {
         }
         uint32_t ex, tot;
         if constexpr (NG == 1 && GV <= 7) {
-            // a count of at most 7: three bit-sliced ballots
-            prefix_small<GV <= 1 ? 1 : (GV <= 3 ? 2 : 3)>(c, lanemask_lt(), ex, tot);
+            // a count of at most 7: bit-sliced ballots give the prefix, one shuffle the total
+            prefix_small<GV <= 1 ? 1 : (GV <= 3 ? 2 : 3)>(c, lanemask_lt(), ex);
+            tot = __shfl_sync(FULLMASK, ex + c, 31);
         } else {
             const uint32_t incl = scan_add(c);
             tot = __shfl_sync(FULLMASK, incl, 31);
@@ -590,8 +596,10 @@ struct TagEngine {
 #pragma unroll
         for (int g = 0; g < NG; ++g) n += (tot >> (16 * g)) & 0xFFFFu;
         if (s0 + n <= C()) {
-            // byte addresses of the slots; kept items take consecutive ones
+            // kept items take consecutive slots; the others are written to a scratch word
+            // of the processor (never read), so the stores need no branch or predicate
             const uint32_t vb = smem_addr(rv().ptr()), tb = smem_addr(rt().ptr());
+            const uint32_t trash = smem_addr(nxs().ptr() + 7);
             uint32_t gb = rb + s0;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
@@ -599,10 +607,11 @@ struct TagEngine {
 #pragma unroll
                 for (int i = 0; i < GV; ++i) {
                     const int j = g * GV + i;
-                    const uint32_t k = keep[j] ? 1u : 0u;
-                    st_shared_if(vb + off, y[j], k);
-                    st_shared_if(tb + off, r[j], k);
-                    off += 4u * k;
+                    const uint32_t va = keep[j] ? vb + off : trash;
+                    const uint32_t ta = keep[j] ? tb + off : trash;
+                    asm volatile("st.shared.u32 [%0], %1;" ::"r"(va), "r"(y[j]) : "memory");
+                    asm volatile("st.shared.u32 [%0], %1;" ::"r"(ta), "r"(r[j]) : "memory");
+                    off += keep[j] ? 4u : 0u;
                 }
                 gb += (tot >> (16 * g)) & 0xFFFFu;
             }
@@ -984,7 +993,9 @@ struct TagEngine {
         for (int j = 0; j < V; ++j) valid[j] = FULL || V * lane + j < take;
         // tags never decrease along a ring: equal first and last tags mean one region
         r0 = __shfl_sync(FULLMASK, r[0], 0);
-        const uint32_t rl = rt()[rb + ((h + take - 1) & CM())];
+        uint32_t rl;
+        if (FULL) rl = __shfl_sync(FULLMASK, r[V - 1], 31);
+        else rl = rt()[rb + ((h + take - 1) & CM())];
         uni = r0 == rl;
     }
 
@@ -1142,6 +1153,7 @@ struct TagEngine {
         if (load_start != NONE) issue_chunk();
         ia = a;
         wi = wc = 0;
+        clim = min(j1, S.n_el);
         if (!hashed())
             for (uint32_t k = 0; k + 1 < NB; ++k) issue_window();
         // the first non-empty parent (the one holding position j0)
