@@ -252,6 +252,7 @@ struct TagEngine {
     // parent-record counters (free-running), the record node 1 is in, and the start of
     // the record after it (NONE while not loaded)
     uint32_t cb, re, cstart, load_start, ord_loaded, ord_cur, s_nx;
+    uint32_t rlo;   // the unit's first parent (chunks start on multiples of 32 parents)
     // windows [a, a + W) with a >= j0 and a + W <= flim are full, inside the current
     // parent and need no parent loads (flim = min(s_nx, j1, load_start))
     uint32_t flim, nfast;
@@ -277,7 +278,7 @@ struct TagEngine {
         for (int e = 0; e < RS_MAX_STAGES; ++e) qh[e] = qt[e] = 0;
         sidx = NONE;
         j0 = j1 = a = 0;
-        cb = re = cstart = 0;
+        cb = re = cstart = rlo = 0;
         load_start = s_nx = NONE;
         flim = 0;
         nfast = 0;
@@ -340,11 +341,12 @@ struct TagEngine {
     // ---------------------------------------------------------------------------
     // parent stream (Section 4: findCount and getParent of each parent)
 
-    // load this lane's parent of the chunk at cb (consumed by the next load_chunk)
+    // load this lane's parent of the chunk at cb (consumed by the next load_chunk); chunks
+    // are aligned to 32 parents, so each load instruction reads whole 128-byte lines
     __device__ __forceinline__ void issue_chunk()
     {
         const uint32_t r = cb + lane;
-        const bool in = r < re;
+        const bool in = r >= rlo && r < re;
         pl0 = in ? __ldg(S.meta + r) : 0u;
         if (S.csr) pl1 = in ? __ldg(S.meta + r + 1) : 0u;
         const uint32_t o1 = op<1>();
@@ -373,7 +375,7 @@ struct TagEngine {
             return;
         }
         const uint32_t r = cb + lane;
-        const bool in = r < re;
+        const bool in = r >= rlo && r < re;
         uint32_t st, L;
         bool bad = false;
         if (S.csr) {
@@ -1143,7 +1145,8 @@ struct TagEngine {
     {
         j0 = rj0;
         j1 = rj1;
-        cb = rs;
+        cb = rs & ~31u;
+        rlo = rs;
         re = rend;
         cstart = base;
         fill = wfill;
