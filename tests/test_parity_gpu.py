@@ -206,3 +206,76 @@ def test_bench_size_sampled(rs, mean):
         frac = got["count"].astype(np.int64).sum() / (1 << 26)
         assert abs(frac - p) < 6 * np.sqrt(p * (1 - p) / (1 << 26))
         assert st["items"][1] == 1 << 26
+
+
+def _rand_u32(rng, n):
+    return rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_two_stage_pipelines_node1_aggregates(rs, strategy):
+    """enumerate -> aggregate: node 1 is the aggregate (one-region windows and windows
+    crossing parent starts, empty parents every seventh)."""
+    rng = np.random.default_rng(21)
+    L = rng.integers(0, 300, 2000).astype(np.uint32)
+    L[::7] = 0
+    s = wl.make_stream(L, elements=_rand_u32(rng, int(L.sum())))
+    _check(rs, [("enum_load",), ("aggregate",)], s, strategy)
+    s = wl.make_stream(L, parents=_rand_u32(rng, 2000))
+    _check(rs, [("enum_hash",), ("aggregate",)], s, strategy)
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_hashed_csr_offsets_with_parent_ids(rs, strategy):
+    """Hashed enumeration over CSR offsets that start at 1000 (element i of a region is
+    hash32(p_r, i) whatever the offset), with explicit parent ids."""
+    rng = np.random.default_rng(22)
+    L = rng.integers(0, 90, 3000).astype(np.uint64)
+    off = (1000 + np.concatenate([[0], np.cumsum(L)])).astype(np.uint32)
+    s = wl.make_stream(offsets=off, parents=_rand_u32(rng, 3000))
+    _check(rs, wl.pipeline_hash_filter_map(), s, strategy)
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_weight_filter_after_a_map(rs, strategy):
+    """A parent-weight filter at node 2: its operand comes from each item's region (the
+    parent id), not from node 1's parent records."""
+    rng = np.random.default_rng(23)
+    L = rng.integers(0, 40, 4000).astype(np.uint32)
+    s = wl.make_stream(L, elements=_rand_u32(rng, int(L.sum())), parents=_rand_u32(rng, 4000))
+    pipe = [("enum_load",), ("map_mul", 3, 1), ("filter_weight_lt", 0x5EED), ("aggregate",)]
+    _check(rs, pipe, s, strategy)
+
+
+@pytest.mark.parametrize("opts", [dict(ensemble_width=256), dict(ensemble_width=256, regions_per_unit=64, region_cost=4),
+                                  dict(ensemble_width=256, warps_per_block=1), dict(regions_per_unit=16384),
+                                  dict(regions_per_unit=1, region_cost=1)])
+def test_tag_wide_ensembles_and_unit_shapes(rs, opts):
+    """The tag strategy's own option range: ensembles of 256 items (8 per lane, two
+    slices per window) and merge-path units from 1 to 16384 steps."""
+    s = wl.cascade_stream(n_total=100_003, mean=20, seed=9)
+    _check(rs, wl.pipeline_cascade(), s, "tag", outputs=("count", "sum"), **opts)
+    s = wl.hashed_uniform_stream(3000, 64, 3)
+    _check(rs, wl.pipeline_hash_filter_map(), s, "tag", **opts)
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_count_only_output(rs, strategy):
+    s = wl.cascade_stream(n_total=1 << 16, mean=6, seed=12)
+    _check(rs, wl.pipeline_cascade(), s, strategy, outputs=("count",))
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_decreasing_offsets_are_reported(rs, strategy):
+    """CSR offsets that decrease are inconsistent input: the device flags them and the
+    host returns RS_ERR_DEVICE_INPUT; no work unit is laid out for the stream."""
+    off = np.array([0, 10, 20, 15, 30, 40], dtype=np.uint32)
+    s = wl.make_stream(offsets=off, elements=np.arange(64, dtype=np.uint32),
+                       ctx=np.zeros(5, dtype=np.uint32))
+    p = rs.Pipeline([("enum_load",), ("filter_hash_ctx", 1, 3 << 30), ("aggregate",)], strategy=strategy)
+    p.submit(rs.to_device(s), outputs=("count", "sum"))
+    p.run()
+    st = p.stats(raise_on_error=False)
+    assert st["status"] == rs.RS_ERR_DEVICE_INPUT
+    assert st["device_status"] & 8
+    p.close()
