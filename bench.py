@@ -419,7 +419,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2006_07478_b300 import rs
+    from paper_2006_07478_b300 import multi, rs
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -522,12 +522,11 @@ def main():
     kernel_ms = [p.timing_read() for p in pipes]
     statuses = [p.stats()["device_status"] for p in pipes]
     assert all(s == 0 for s in statuses), statuses
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    # every rank runs the same five streams (weak scaling): the step time is the slowest
+    # rank's, the items are summed over ranks
     items_step = N_ELEM * len(MEANS)
-    value = items_step * args.steps * world / (elapsed_ms * 1e-3)
+    elapsed_ms, items_all = multi.reduce_step(elapsed_ms, items_step * args.steps, device="cuda")
+    value = items_all / (elapsed_ms * 1e-3)
 
     # ---- roofline of the timed kernel: algorithmic bytes / kernel time, all launches ----
     peak, peak_kind = load_peaks()
@@ -599,11 +598,8 @@ def main():
         e1.record(s_out)
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": items_step * world / (e2e_ms * 1e-3), "unit": "items/s",
+        e2e_ms, e2e_items = multi.reduce_step(e2e_ms, items_step, device="cuda")
+        e2e = {"value": e2e_items / (e2e_ms * 1e-3), "unit": "items/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                "overlap": "copy-in, run and copy-out on three CUDA streams"}
 
