@@ -210,6 +210,10 @@ typedef struct {
     uint32_t block;                    /* threads per CTA (32 per processor)                */
     uint32_t smem_per_block;           /* dynamic shared memory per CTA, bytes              */
     uint32_t blocks_per_sm;            /* resident CTAs per SM (occupancy calculator)       */
+    uint32_t chunk_parents;            /* tag strategy: parents node 1 loads per chunk, 32
+                                          (one per lane) or 64 (two per lane, chosen when the
+                                          loaded streams' regions average under 3 elements);
+                                          0 for the signal strategy                         */
 } rs_stats;
 
 /* Synchronise `stream`, read the workspace counters of the last rs_run and return
@@ -327,6 +331,11 @@ const char *rs_status_string(rs_status s);
 int rs_last_cuda_error(void);
 /* Library version, for the binding's load check. */
 uint32_t rs_version(void);
+/* sizeof of the ABI structs, so a binding can check its mirrors: writes up to `max`
+ * entries in this order -- rs_stage_desc, rs_pipeline_opts, rs_stream_desc,
+ * rs_region_results, rs_stats, rs_request, rs_server_stats -- and returns how many it
+ * knows (7).  Host-only; needs no GPU. */
+uint32_t rs_struct_sizes(uint64_t *sizes, uint32_t max);
 
 #ifdef __cplusplus
 }

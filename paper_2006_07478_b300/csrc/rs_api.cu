@@ -69,7 +69,7 @@ struct rs_pipeline {
     DevStream noalloc_table[RS_NOALLOC_MAX_STREAMS];
     FixedPlan noalloc_plan;
     // launch shape of the last prepared launch (reported by rs_get_stats)
-    uint32_t last_grid = 0, last_block = 0, last_smem = 0, last_bps = 0;
+    uint32_t last_grid = 0, last_block = 0, last_smem = 0, last_bps = 0, last_cp = 0;
     // the automatic processors-per-CTA choice, for the kernel and per-processor bytes
     // it was made for
     const void *auto_key_fn = nullptr;
@@ -225,6 +225,15 @@ const char *rs_status_string(rs_status s)
 int rs_last_cuda_error(void) { return g_last_cuda; }
 
 uint32_t rs_version(void) { return RS_VERSION; }
+
+uint32_t rs_struct_sizes(uint64_t *sizes, uint32_t max)
+{
+    const uint64_t z[] = {sizeof(rs_stage_desc), sizeof(rs_pipeline_opts), sizeof(rs_stream_desc),
+                          sizeof(rs_region_results), sizeof(rs_stats), sizeof(rs_request), sizeof(rs_server_stats)};
+    const uint32_t n = (uint32_t)(sizeof z / sizeof z[0]);
+    for (uint32_t i = 0; i < n && i < max && sizes; ++i) sizes[i] = z[i];
+    return n;
+}
 
 rs_status rs_default_opts(rs_pipeline_opts *o)
 {
@@ -455,9 +464,10 @@ static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts
 // Per-processor shared memory of the tag kernel: counters, window marks (W words),
 // node 1's staging ring of four element windows (loaded enumeration only),
 // the rings of edges 1..n-2 (values and region tags, two arrays), and the parent records
-// (2 PR entries each: region id and operand, start offset, parent id).  PR >= W + 64
-// covers every record node 1 can still need (the parents of one window plus one chunk).
-static SmemLayout make_tag_layout(const rs_pipeline *p)
+// (PR entries each of {region id, operand}, start offset, and parent id for hashed
+// enumeration).  PR >= W + 64 cpl covers every record node 1 can still need: the parents
+// of one window, plus one chunk of 32 cpl loaded beyond it.
+static SmemLayout make_tag_layout(const rs_pipeline *p, uint32_t cpl)
 {
     const rs_pipeline_opts &o = p->opts;
     const uint32_t W = o.ensemble_width;
@@ -483,7 +493,7 @@ static SmemLayout make_tag_layout(const rs_pipeline *p)
     L.o_qt = (uint32_t)off;       // ring tags (region ids)
     off += (size_t)(p->n_stages - 2) * o.queue_capacity * 4;
     uint32_t pr = 128;
-    while (pr < W + 64) pr <<= 1;
+    while (pr < W + 64 * cpl) pr <<= 1;
     L.pr = pr;
     L.o_nra = (uint32_t)off;      // {region, operand} (PR entries)
     off += (size_t)pr * 8;
@@ -493,6 +503,20 @@ static SmemLayout make_tag_layout(const rs_pipeline *p)
     off += p->stages[0].kind == RS_ENUM_HASH ? (size_t)pr * 4 : 0;
     L.per_warp = (uint32_t)align_up(off, 128);
     return L;
+}
+
+// Parents per lane in the tag kernel's parent chunks: two when the loaded streams' regions
+// average fewer than 3 elements (chunk loads then recur every few windows and each one
+// carries twice the parents), else one.  Hashed streams give no element count: one.
+static uint32_t tag_chunk_cpl(const rs_pipeline *p)
+{
+    if (p->stages[0].kind != RS_ENUM_LOAD) return 1;
+    uint64_t el = 0, regions = 0;
+    for (const auto &s : p->streams) {
+        el += s.n_elements;
+        regions += s.n_regions;
+    }
+    return regions > 0 && el < 3 * regions ? 2u : 1u;
 }
 
 static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax, bool any_load, bool need_ctx,
@@ -761,7 +785,8 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
     P.budget = o.device_budget;
     P.spin_limit = 2000000000ull;   // 2 s on the global timer
-    P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p)
+    P.cpl = tag_chunk_cpl(p);
+    P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p, P.cpl)
                                       : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
     P.plan_fill = strategy == RS_STRATEGY_TAG;
     P.m16 = 1u << 16;
@@ -810,6 +835,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     p->last_grid = (uint32_t)Lc.grid;
     p->last_block = (uint32_t)Lc.block;
     p->last_smem = (uint32_t)Lc.smem;
+    p->last_cp = strategy == RS_STRATEGY_TAG ? 32 * P.cpl : 0;
     return RS_OK;
 }
 
@@ -925,6 +951,7 @@ rs_status rs_get_stats(rs_pipeline *p, const void *workspace, rs_cuda_stream str
     out->block = p->last_block;
     out->smem_per_block = p->last_smem;
     out->blocks_per_sm = p->last_bps;
+    out->chunk_parents = p->last_cp;
     if (h.status & (ST_STALL | ST_LOOKBACK_TIMEOUT | ST_COPY_TIMEOUT | ST_OVERFLOW)) return RS_ERR_STALL;
     if (h.status & ST_BAD_INPUT) return RS_ERR_DEVICE_INPUT;
     return RS_OK;
@@ -1312,7 +1339,8 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
     P.budget = o.device_budget;
     P.spin_limit = 2000000000ull;
-    P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p)
+    P.cpl = tag_chunk_cpl(p);
+    P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p, P.cpl)
                                       : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
     P.plan_fill = strategy == RS_STRATEGY_TAG;
     P.m16 = 1u << 16;

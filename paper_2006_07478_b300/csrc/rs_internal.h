@@ -150,6 +150,7 @@ struct KParams {
     unsigned long long spin_limit;
     uint32_t profile;             // accumulate the cycle breakdown
     uint32_t plan_fill;           // planner writes every region's identity result (tag strategy)
+    uint32_t cpl;                 // tag strategy: parents per lane in node 1's parent chunks (1 or 2)
     uint32_t m16, m19;            // 2^16 and 2^19: x >> 16 = umulhi(x, m16), x >> 13 = umulhi(x, m19)
                                   // (run-time values, so the shifts stay multiplies)
     SmemLayout L;
@@ -163,6 +164,6 @@ int rs_kernel_max_smem_optin(const KParams &P, size_t smem);
 int rs_kernel_occupancy(const KParams &P, int block, size_t smem, int *blocks_per_sm);
 const void *rs_kernel_entry(const KParams &P);   // the kernel a launch with P would use
 int rs_kernel_is_specialised(const KParams &P);
-// the tag strategy's kernel (rs_tag.cu)
+// the tag strategy's kernel (rs_tag.cu, rs_tag2.cu)
 const void *rs_tag_kernel_entry(const KParams &P);
 int rs_tag_kernel_is_specialised(const KParams &P);

@@ -36,8 +36,10 @@ EXPORTS = [
     "rs_fetch_region_results", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
     "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_run_noalloc",
     "rs_server_create", "rs_server_submit", "rs_server_progress", "rs_server_poll", "rs_server_get_stats",
-    "rs_server_destroy", "rs_status_string", "rs_last_cuda_error", "rs_version",
+    "rs_server_destroy", "rs_status_string", "rs_last_cuda_error", "rs_version", "rs_struct_sizes",
 ]
+# the ctypes mirrors, in the order rs_struct_sizes reports the C structs' sizes
+_MIRRORS = ("StageDesc", "Opts", "StreamDesc", "RegionResults", "Stats", "Request", "ServerStats")
 
 
 class StageDesc(ctypes.Structure):
@@ -74,7 +76,8 @@ class Stats(ctypes.Structure):
                 ("ensembles", ctypes.c_uint64 * RS_MAX_STAGES), ("items", ctypes.c_uint64 * RS_MAX_STAGES),
                 ("signals", ctypes.c_uint64 * RS_MAX_STAGES), ("firings", ctypes.c_uint64 * RS_MAX_STAGES),
                 ("cycles", ctypes.c_uint64 * 16), ("grid", ctypes.c_uint32), ("block", ctypes.c_uint32),
-                ("smem_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+                ("smem_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("chunk_parents", ctypes.c_uint32)]
     CYCLE_SLOTS = ("setup", "lookback", "tile_wait", "enumerate", "node1", "node2", "node3", "node4",
                    "node5", "flush", "total")
 
@@ -95,7 +98,7 @@ class Stats(ctypes.Structure):
                        "compact": int(self.cycles[14]), "tiles": int(self.cycles[15])},
             "active_lane_fraction": [(it / (float(W) * e)) if e else 0.0 for it, e in zip(items, ens)],
             "launch": {"grid": self.grid, "block": self.block, "smem_per_block": self.smem_per_block,
-                       "blocks_per_sm": self.blocks_per_sm},
+                       "blocks_per_sm": self.blocks_per_sm, "chunk_parents": self.chunk_parents},
         }
 
 
@@ -167,11 +170,17 @@ def lib(build_if_missing: bool = True):
             "rs_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "rs_last_cuda_error": ([], ctypes.c_int),
             "rs_version": ([], U32),
+            "rs_struct_sizes": ([ctypes.POINTER(U64), U32], U32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = res
+        c_sizes = (U64 * len(_MIRRORS))()
+        n = L.rs_struct_sizes(c_sizes, len(_MIRRORS))
+        mine = [ctypes.sizeof(globals()[m]) for m in _MIRRORS]
+        if n != len(_MIRRORS) or list(c_sizes) != mine:
+            raise RuntimeError(f"librs struct layout differs from the binding: C {list(c_sizes)[:n]} vs ctypes {mine}")
         _lib = L
     return _lib
 

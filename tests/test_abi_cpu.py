@@ -31,6 +31,18 @@ def test_every_declared_symbol_is_exported():
     assert set(rs.EXPORTS) <= declared
 
 
+def test_struct_mirrors_match_the_c_layout():
+    """rs.lib() refuses a library whose structs differ from the ctypes mirrors; check the
+    sizes it compared directly as well."""
+    L = rs.lib()
+    sizes = (ctypes.c_uint64 * 8)()
+    assert L.rs_struct_sizes(sizes, 8) == 7
+    assert list(sizes)[:7] == [ctypes.sizeof(c) for c in (rs.StageDesc, rs.Opts, rs.StreamDesc, rs.RegionResults,
+                                                         rs.Stats, rs.Request, rs.ServerStats)]
+    assert sizes[7] == 0                                   # nothing written past the known count
+    assert L.rs_struct_sizes(None, 0) == 7
+
+
 def test_version_and_status_strings():
     assert rs.lib().rs_version() >= 1
     assert rs.status_string(rs.RS_OK) == "ok"

@@ -56,7 +56,9 @@ def test_hashed_uniform_10k(rs, strategy):
 @pytest.mark.parametrize("mean", [1, 4, 32, 256, 4096])
 def test_cascade_geometric(rs, strategy, mean):
     s = wl.cascade_stream(n_total=1 << 18, mean=mean, seed=7)
-    _check(rs, wl.pipeline_cascade(), s, strategy, outputs=("count", "sum"))
+    _, st = _check(rs, wl.pipeline_cascade(), s, strategy, outputs=("count", "sum"))
+    # the tag kernel loads two parents per lane when regions average under 3 elements
+    assert st["launch"]["chunk_parents"] == (0 if strategy == "signal" else 64 if mean == 1 else 32)
 
 
 @pytest.mark.parametrize("strategy", STRATEGIES)
@@ -276,6 +278,51 @@ def test_decreasing_offsets_are_reported(rs, strategy):
     p.submit(rs.to_device(s), outputs=("count", "sum"))
     p.run()
     st = p.stats(raise_on_error=False)
+    assert st["status"] == rs.RS_ERR_DEVICE_INPUT
+    assert st["device_status"] & 8
+    p.close()
+
+
+@pytest.mark.parametrize("csr", [False, True])
+@pytest.mark.parametrize("R", [1, 2, 63, 64, 65, 129, 20001])
+def test_two_parent_chunks(rs, R, csr):
+    """Streams of short regions (0..4 elements, every fifth empty): the tag kernel's
+    64-parent chunks, two parents per lane, for odd and even region counts, ragged last
+    chunks and units that start on odd parents; CSR offsets from 7; node 1 takes its
+    operand from the context word or from the parent's weight."""
+    rng = np.random.default_rng(1000 * R + csr)
+    L = rng.integers(0, 5, R).astype(np.uint32)
+    L[::5] = 0
+    n = int(L.sum())
+    base = 7 if csr else 0
+    el = _rand_u32(rng, n + base + 1)
+    kw = dict(elements=el, ctx=_rand_u32(rng, R), parents=_rand_u32(rng, R))
+    s = (wl.make_stream(offsets=(base + np.concatenate([[0], np.cumsum(L)])).astype(np.uint32), **kw) if csr
+         else wl.make_stream(L, **kw))
+    expect_cp = 64 if el.size < 3 * R else 32
+    for pipe in (wl.pipeline_cascade(), wl.pipeline_graph_edges()):
+        for opts in (dict(), dict(regions_per_unit=1, region_cost=2), dict(ensemble_width=32, tile_elements=32),
+                     dict(ensemble_width=256)):
+            _, st = _check(rs, pipe, s, "tag", **opts)
+            assert st["launch"]["chunk_parents"] == expect_cp
+    if R == 20001:
+        assert expect_cp == 64
+
+
+@pytest.mark.parametrize("bad_at", [1, 2, 63, 64])
+def test_decreasing_offsets_in_two_parent_chunks(rs, bad_at):
+    """A decreasing CSR offset is reported whichever parent of a lane's pair it ends
+    (even or odd parent, first or second chunk)."""
+    off = 5 + np.arange(201, dtype=np.int64)           # 200 regions of one element from offset 5
+    off[bad_at] = off[bad_at - 1] - 1                   # parent bad_at - 1 ends before it starts
+    off[bad_at + 1:] += 10
+    off = off.astype(np.uint32)
+    s = wl.make_stream(offsets=off, elements=np.arange(400, dtype=np.uint32), ctx=np.zeros(200, dtype=np.uint32))
+    p = rs.Pipeline([("enum_load",), ("filter_hash_ctx", 1, 3 << 30), ("aggregate",)], strategy="tag")
+    p.submit(rs.to_device(s), outputs=("count", "sum"))
+    p.run()
+    st = p.stats(raise_on_error=False)
+    assert st["launch"]["chunk_parents"] == 64
     assert st["status"] == rs.RS_ERR_DEVICE_INPUT
     assert st["device_status"] & 8
     p.close()
