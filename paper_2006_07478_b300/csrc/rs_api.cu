@@ -463,7 +463,8 @@ static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts
 
 // Per-processor shared memory of the tag kernel: counters, window marks (W words),
 // node 1's staging ring of four element windows (loaded enumeration only),
-// the rings of edges 1..n-2 (values and region tags, two arrays), and the parent records
+// the rings of edges 1..n-3 (values and region tags, two arrays; edge n-2 too when node
+// n-2 is an expansion), and the parent records
 // (PR entries each of {region id, operand}, start offset, and parent id for hashed
 // enumeration).  PR >= W + 64 cpl covers every record node 1 can still need: the parents
 // of one window, plus one chunk of 32 cpl loaded beyond it.
@@ -488,10 +489,15 @@ static SmemLayout make_tag_layout(const rs_pipeline *p, uint32_t cpl)
     off = align_up(off, 16);
     L.o_tiles = (uint32_t)off;    // node 1's staged element windows (4 x W)
     off += p->stages[0].kind == RS_ENUM_LOAD ? (size_t)4 * W * 4 : 0;
+    // rings of edges 1..n-2, less the edge into the aggregate when its producer is not an
+    // expansion: that node folds its kept items into the aggregate directly
+    const uint32_t ns = p->n_stages;
+    const bool fused = ns >= 3 && p->stages[ns - 2].kind != RS_EXPAND;
+    const size_t rings = ns - 2 - (fused ? 1u : 0u);
     L.o_qv = (uint32_t)off;       // ring values
-    off += (size_t)(p->n_stages - 2) * o.queue_capacity * 4;
+    off += rings * o.queue_capacity * 4;
     L.o_qt = (uint32_t)off;       // ring tags (region ids)
-    off += (size_t)(p->n_stages - 2) * o.queue_capacity * 4;
+    off += rings * o.queue_capacity * 4;
     uint32_t pr = 128;
     while (pr < W + 64 * cpl) pr <<= 1;
     L.pr = pr;

@@ -141,7 +141,6 @@ struct KParams {
     uint32_t plan_tiles;          // planner tickets over all UNIT_MERGE streams
     const DevStream *streams;
     WsHeader *hdr;
-    unsigned long long *lookback; // one word per unit
     uint32_t V;                   // items per lane per ensemble (W = 32 V)
     uint32_t C, SC, TE, NT;       // queue slots, signal slots, tile elements, tiles
     uint32_t need_ctx, need_par, want_count, want_sum, want_min;

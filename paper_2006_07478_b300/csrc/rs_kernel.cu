@@ -318,6 +318,9 @@ __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint
 // parent r that contains u D (P_r = c r + offset of r, c = the stream's parent cost); positions
 // are taken relative to the tile, so locating the units costs one 32-bit division per
 // lane and round instead of two 64-bit divisions per parent.
+// A tile's look-back word holds its flag and its value in one 64-bit word and carries
+// nothing else, so it is written and read relaxed (gpu scope): no fence, so publishing
+// it never waits for the tile's identity-result stores to drain.
 
 constexpr int PLAN_ROUNDS = RS_PLAN_TILE / 128;
 
@@ -421,16 +424,16 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
         } else {
             unsigned long long *lb = S.plan_lb;
             if (tile == 0) {
-                if (lane == 0) st_release_u64(&lb[0], LB_INCL | (unsigned long long)tsum);
+                if (lane == 0) st_relaxed_u64(&lb[0], LB_INCL | (unsigned long long)tsum);
             } else {
-                if (lane == 0) st_release_u64(&lb[tile], LB_AGG | (unsigned long long)tsum);
+                if (lane == 0) st_relaxed_u64(&lb[tile], LB_AGG | (unsigned long long)tsum);
                 unsigned long long excl = 0;
                 int jt = (int)tile - 1;
                 unsigned long long t0 = global_ns();
                 uint32_t it = 0;
                 for (;;) {
                     const int idx = jt - (int)lane;
-                    const unsigned long long wv = (idx >= 0) ? ld_acquire_u64(&lb[idx]) : LB_INCL;
+                    const unsigned long long wv = (idx >= 0) ? ld_relaxed_u64(&lb[idx]) : LB_INCL;
                     const uint32_t flag = (uint32_t)(wv >> 62);
                     const uint32_t notready = __ballot_sync(FULLMASK, flag == 0u);
                     const uint32_t inclm = __ballot_sync(FULLMASK, flag == 2u);
@@ -454,7 +457,7 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
                     break;
                 }
                 E = (uint32_t)excl;
-                if (lane == 0) st_release_u64(&lb[tile], LB_INCL | (excl + tsum));
+                if (lane == 0) st_relaxed_u64(&lb[tile], LB_INCL | (excl + tsum));
             }
         }
         if (stop) break;

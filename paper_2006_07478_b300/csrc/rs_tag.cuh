@@ -689,6 +689,25 @@ struct TagEngine {
         qt[I] += n;
     }
 
+    // node I's kept items: into the ring of edge I, or, when node I is the last node
+    // before the aggregate and not an expansion, straight into the aggregate (no ring on
+    // that edge; the aggregate fires once per ensemble of node I, on its kept items)
+    template <int I, int NG, int GV>
+    __device__ __forceinline__ void emit(const bool (&keep)[V], const uint32_t (&y)[V], const uint32_t (&r)[V],
+                                         bool uni, uint32_t r0)
+    {
+        if (I == n_st() - 2) {
+            uint32_t k = 0;
+#pragma unroll
+            for (int j = 0; j < V; ++j) k += keep[j] ? 1u : 0u;
+            const uint32_t n = __reduce_add_sync(FULLMASK, k);
+            aggregate(y, r, keep, uni, r0, n);
+            count_firing(I + 1, 1u, n);
+        } else {
+            push<I, NG, GV>(keep, y, r);
+        }
+    }
+
     // expansion (0..fanout outputs per item): item x emits n = hash32(x, p0) mod
     // (fanout + 1) values hash32(x, p0 + 1 + i), i < n, in order
     template <int I, int NG, int GV>
@@ -845,7 +864,7 @@ struct TagEngine {
                     uint32_t y[V];
                     bool keep[V];
                     apply<1>(x, aux, valid, keep, y);
-                    push<1, NS, VS>(keep, y, r);
+                    emit<1, NS, VS>(keep, y, r, true, r_cur);
                 }
             }
         }
@@ -990,7 +1009,7 @@ struct TagEngine {
                     uint32_t y[V];
                     bool keep[V];
                     apply<1>(x, aux, valid, keep, y);
-                    push<1, NS, VS>(keep, y, r);
+                    emit<1, NS, VS>(keep, y, r, uni, r_cur);
                 }
             }
         }
@@ -1070,7 +1089,7 @@ struct TagEngine {
                     bool keep[V];
                     aux_of<I>(r, valid, uni, r0, aux);
                     apply<I>(x, aux, valid, keep, y);
-                    push<I, 1, V>(keep, y, r);
+                    emit<I, 1, V>(keep, y, r, uni, r0);
                 }
             }
         }
