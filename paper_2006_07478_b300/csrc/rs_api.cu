@@ -461,8 +461,9 @@ static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts
     return pl;
 }
 
-// Per-processor shared memory of the tag kernel: counters, window marks (W words),
-// node 1's staging ring of four element windows (loaded enumeration only),
+// Per-processor shared memory of the tag kernel: counters, window marks (W words, hashed
+// enumeration only: with loaded elements node 1 marks in the staging slot it has just
+// read), node 1's staging ring of four element windows (loaded enumeration only),
 // the rings of edges 1..n-3 (values and region tags, two arrays; edge n-2 too when node
 // n-2 is an expansion), and the parent records
 // (PR entries each of {region id, operand}, start offset, and parent id for hashed
@@ -484,8 +485,8 @@ static SmemLayout make_tag_layout(const rs_pipeline *p, uint32_t cpl)
     L.o_pend = (uint32_t)off;     // the next unit's description (7 words)
     off += 32;
     off = align_up(off, 16);
-    L.o_scr = (uint32_t)off;
-    off += (size_t)4 * W;
+    L.o_scr = (uint32_t)off;      // window marks, hashed enumeration only (loaded
+    off += p->stages[0].kind == RS_ENUM_LOAD ? 0 : (size_t)4 * W;   // elements: a staging slot)
     off = align_up(off, 16);
     L.o_tiles = (uint32_t)off;    // node 1's staged element windows (4 x W)
     off += p->stages[0].kind == RS_ENUM_LOAD ? (size_t)4 * W * 4 : 0;

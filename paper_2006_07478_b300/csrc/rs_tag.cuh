@@ -251,7 +251,13 @@ struct TagEngine {
     __device__ __forceinline__ SArr<uint32_t> rt() const { return sarr<uint32_t>(wb + P.L.o_qt); }   // ring tags
     __device__ __forceinline__ SArr<uint32_t> nst() const { return sarr<uint32_t>(wb + P.L.o_nst); }
     __device__ __forceinline__ SArr<uint32_t> npar() const { return sarr<uint32_t>(wb + P.L.o_npar); }
-    __device__ __forceinline__ SArr<uint32_t> marks() const { return sarr<uint32_t>(wb + P.L.o_scr); }
+    // node 1's window marks: with loaded elements, the staging slot node 1 has just read
+    // (free until the copy issued at the next window), else an array of their own
+    __device__ __forceinline__ SArr<uint32_t> marks() const
+    {
+        return hashed() ? sarr<uint32_t>(wb + P.L.o_scr)
+                        : sarr<uint32_t>(wb + P.L.o_tiles + ((wc - 1) & (NB - 1)) * W * 4);
+    }
     __device__ __forceinline__ SArr<uint32_t> stg() const { return sarr<uint32_t>(wb + P.L.o_tiles); }
     __device__ __forceinline__ SArr<uint32_t> nxs() const { return sarr<uint32_t>(wb + P.L.o_pend); }
     // ring capacity and record-ring size (powers of two), from the kernel parameters
@@ -888,6 +894,10 @@ struct TagEngine {
             }
         }
         if (a >= j1) return;
+        // the elements (getItem of Section 4); loaded ones first, so that the marks can
+        // take the staging slot they came from
+        uint32_t x[V];
+        if (!hashed()) staged_window(x);
         const uint32_t lo = max(a, j0), hi = min(a + W, j1);
         uint32_t r[V], aux[V], st[V], par[V];
         const bool uni = s_nx >= hi;
@@ -981,8 +991,6 @@ struct TagEngine {
                     valid[t * VS + i] = p >= lo && p < hi;
                 }
         }
-        // the elements (getItem of Section 4)
-        uint32_t x[V];
         if (hashed()) {
 #pragma unroll
             for (int t = 0; t < NS; ++t)
@@ -992,8 +1000,6 @@ struct TagEngine {
                     const uint32_t p = a + t * SW + VS * lane + i;
                     x[j] = valid[j] ? fmix32_m(par[j] ^ fmix32_m((p - st[j]) ^ RS_GOLD, P.m16, P.m19), P.m16, P.m19) : 0u;
                 }
-        } else {
-            staged_window(x);
         }
         const uint32_t n_valid = hi - lo;
         // node 0 and node 1 each ran one ensemble; node 1 consumed n_valid items in one firing
@@ -1256,7 +1262,9 @@ struct TagEngine {
 }  // namespace
 
 template <int V, class SG, int CPL>
-__global__ void __launch_bounds__(256, 2) rs_tag_kernel(const __grid_constant__ KParams P)
+// up to 4 items per lane: at most 80 registers, so that three CTAs of 8 processors fit
+// an SM; 8 items per lane: 128
+__global__ void __launch_bounds__(256, (V <= 4 ? 3 : 2)) rs_tag_kernel(const __grid_constant__ KParams P)
 {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t wb = warp * P.L.per_warp;
