@@ -122,6 +122,15 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
     return RS_OK;
 }
 
+// log2 x when x is a power of two, else RS_NOT_POW2 (divisions by x become shifts)
+static uint32_t log2_if_pow2(uint32_t x)
+{
+    if (x == 0 || (x & (x - 1)) != 0) return RS_NOT_POW2;
+    uint32_t k = 0;
+    while ((1u << k) != x) ++k;
+    return k;
+}
+
 static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
 {
     const uint32_t W = o->ensemble_width;
@@ -526,6 +535,16 @@ static uint32_t tag_chunk_cpl(const rs_pipeline *p)
     return regions > 0 && el < 3 * regions ? 2u : 1u;
 }
 
+// every merge-path stream of a plan has a power-of-two D (the planner then divides by
+// shifts; every tag-strategy unit shape has one)
+template <class PL>
+static uint32_t plan_pow2(const PL &pl, size_t ns)
+{
+    for (size_t i = 0; i < ns; ++i)
+        if (pl.sp[i].mode == UNIT_MERGE && log2_if_pow2(pl.sp[i].D) == RS_NOT_POW2) return 0;
+    return 1;
+}
+
 static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax, bool any_load, bool need_ctx,
                               bool need_par, bool want_min)
 {
@@ -743,6 +762,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
                 d.plan_tiles = q.plan_tiles;
                 d.plan_base = pbase;
                 d.D = q.D;
+                d.dsh = log2_if_pow2(q.D);
                 d.c = q.c;
                 pbase += q.plan_tiles;
             }
@@ -766,6 +786,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.n_streams = (uint32_t)ns;
     P.total_units = (uint32_t)pl.total_units;
     P.plan_tiles = (uint32_t)pl.plan_tiles;
+    P.plan_pow2 = plan_pow2(pl, p->streams.size());
     P.streams = (const DevStream *)(wsb + pl.table_off);
     P.hdr = (WsHeader *)wsb;
     P.V = o.ensemble_width / RS_W;
@@ -1301,6 +1322,7 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
             d.plan_tiles = q.plan_tiles;
             d.plan_base = pbase;
             d.D = q.D;
+            d.dsh = log2_if_pow2(q.D);
             d.c = q.c;
             pbase += q.plan_tiles;
         }
@@ -1321,6 +1343,7 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     P.n_streams = (uint32_t)ns;
     P.total_units = (uint32_t)pl.total_units;
     P.plan_tiles = (uint32_t)pl.plan_tiles;
+    P.plan_pow2 = plan_pow2(pl, p->streams.size());
     P.streams = (const DevStream *)(wsb + pl.table_off);
     P.hdr = (WsHeader *)wsb;
     P.V = o.ensemble_width / RS_W;

@@ -40,6 +40,7 @@ enum : uint32_t {
                         // a unit is D steps (DevStream.D); parents straddling units are split
 };
 #define RS_STEP_REGION 16u   // default merge-path steps per parent (rs_pipeline_opts.region_cost)
+#define RS_NOT_POW2 0xFFu
 #define RS_PLAN_TILE 1024u                                  // parents per planner tile
 
 // Start of merge-path unit u: i = parents whose header step lies before u*D, j = absolute
@@ -81,6 +82,7 @@ struct DevStream {
     unsigned long long *plan_lb;   // planner look-back words, one per planner tile
     uint32_t plan_tiles, plan_base;
     uint32_t D;          // merge-path steps per unit
+    uint32_t dsh;        // log2 D when D is a power of two, else RS_NOT_POW2
     uint32_t c;          // merge-path steps per parent (an element costs one)
 };
 
@@ -150,6 +152,7 @@ struct KParams {
     uint32_t profile;             // accumulate the cycle breakdown
     uint32_t plan_fill;           // planner writes every region's identity result (tag strategy)
     uint32_t cpl;                 // tag strategy: parents per lane in node 1's parent chunks (1 or 2)
+    uint32_t plan_pow2;           // every merge-path stream's D is a power of two (planner divides by shifts)
     uint32_t m16, m19;            // 2^16 and 2^19: x >> 16 = umulhi(x, m16), x >> 13 = umulhi(x, m19)
                                   // (run-time values, so the shifts stay multiplies)
     SmemLayout L;

@@ -324,13 +324,17 @@ __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint
 
 constexpr int PLAN_ROUNDS = RS_PLAN_TILE / 128;
 
-// x / d, with a 32-bit division when x < 2^32 (d = c K <= 2^16)
-__device__ __forceinline__ unsigned long long plan_div(unsigned long long x, uint32_t d)
+// x / d: a shift when every stream's d is a power of two (POW2, dsh = log2 d, as for
+// every tag-strategy unit shape), else a 32-bit division when x < 2^32 (d = c K <= 2^16)
+template <bool POW2>
+__device__ __forceinline__ unsigned long long plan_div(unsigned long long x, uint32_t d, uint32_t dsh)
 {
+    if (POW2) return x >> dsh;
     if ((x >> 32) == 0) return (uint32_t)x / d;
     return x / d;
 }
 
+template <bool POW2>
 __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KParams P)
 {
     const uint32_t lane = threadIdx.x & 31u;
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
             if (P.streams[mid].plan_base <= t) lo = mid; else hi = mid - 1;
         }
         const DevStream &S = P.streams[lo];
-        const uint32_t D = S.D, c = S.c;
+        const uint32_t D = S.D, c = S.c, dsh = S.dsh;
         const uint32_t tile = t - S.plan_base;
         const uint32_t r_lo = tile * RS_PLAN_TILE;
         const uint32_t r_hi = min(r_lo + RS_PLAN_TILE, S.R);
@@ -466,7 +470,7 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
         // tile starts at X = rem < D and unit qt + m starts at X = m D.
         bool bad = false;
         const unsigned long long Pt = (unsigned long long)c * r_lo + E;
-        const unsigned long long qt = Pt / D;
+        const unsigned long long qt = plan_div<POW2>(Pt, D, dsh);
         const uint32_t rem = (uint32_t)(Pt - qt * D);
         uint32_t pre = 0;   // elements of the tile before this round
 #pragma unroll
@@ -477,8 +481,8 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
             const uint32_t offl = pre + incl[k] - ls[k];        // its element offset in the tile
             const unsigned long long xa = rem + (unsigned long long)c * rloc + offl;
             const unsigned long long xb = xa + (unsigned long long)c * nl + ls[k];
-            unsigned long long m = plan_div(xa, D);
-            if (nl && plan_div(xb, D) > m) {
+            unsigned long long m = plan_div<POW2>(xa, D, dsh);
+            if (nl && plan_div<POW2>(xb, D, dsh) > m) {
                 unsigned long long x = xa;
                 uint32_t off = offl;
 #pragma unroll
@@ -1566,7 +1570,7 @@ int rs_launch_finalize(const KParams &P, int grid, void *stream)
 int rs_launch_planner(const KParams &P, int grid, void *stream)
 {
     void *args[] = {(void *)&P};
-    cudaError_t e = cudaLaunchKernel((const void *)rs_plan_kernel, dim3(grid), dim3(256), args, 0,
+    cudaError_t e = cudaLaunchKernel(P.plan_pow2 ? (const void *)rs_plan_kernel<true> : (const void *)rs_plan_kernel<false>, dim3(grid), dim3(256), args, 0,
                                      (cudaStream_t)stream);
     return (int)e;
 }

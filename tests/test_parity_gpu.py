@@ -107,6 +107,8 @@ def test_empty_and_degenerate_regions(rs, strategy):
     dict(regions_per_unit=2, region_cost=256), dict(ensemble_width=64, tile_elements=128, region_cost=64),
     dict(regions_per_unit=512), dict(warps_per_block=0), dict(regions_per_unit=512, warps_per_block=3),
     dict(tiles_in_flight=4), dict(tiles_in_flight=0, ensemble_width=32), dict(tiles_in_flight=0, ensemble_width=64),
+    # units of a size that is not a power of two (the planner divides instead of shifting)
+    dict(regions_per_unit=100), dict(regions_per_unit=3000, region_cost=2),
 ])
 def test_option_sweep(rs, strategy, opts):
     s = wl.cascade_stream(n_total=100_003, mean=20, seed=9)
