@@ -1133,10 +1133,10 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
         return ms / (float)trials;
     };
 
-    // Per strategy, a coordinate search from a starting point: unit shape, then ensemble
-    // width, processors per CTA and (signal strategy) tile size, each change kept when it
-    // is faster.  A strategy whose starting point is over three times the best found so
-    // far is dropped.
+    // Per strategy, a search from a starting point (128 items per ensemble, the first unit
+    // shape): unit shape and ensemble width, then processors per CTA and (signal
+    // strategy) tile size, each change kept when it is faster.  A strategy whose starting
+    // point is over three times the best found so far is dropped.
     float best_t = 1e30f;
     rs_pipeline_opts best_o = base;
     const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
@@ -1163,7 +1163,7 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
         }
         rs_pipeline_opts cur = base;
         cur.strategy = strategies[si];
-        cur.ensemble_width = (tag ? 8 : 4) * RS_W;
+        cur.ensemble_width = 4 * RS_W;
         cur.warps_per_block = 0;
         cur.tile_elements = 0;
         cur.tiles_in_flight = 0;
@@ -1171,17 +1171,23 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
         cur.region_cost = shapes[0][1];
         float cur_t = time_of(cur);
         if (cur_t > 3.f * best_t) continue;
-        for (int i = 1; i < n_shapes && result == RS_OK; ++i) {
-            rs_pipeline_opts c = cur;
-            c.regions_per_unit = shapes[i][0];
-            c.region_cost = shapes[i][1];
-            const float t = time_of(c);
-            if (t < cur_t) { cur_t = t; cur = c; }
+        // tag strategy: every unit shape at each ensemble width (128, 256, 64 items), since
+        // the best shape depends on the width; signal strategy: shapes at 128, then 64
+        const uint32_t widths[3] = {4u, 8u, 2u};
+        for (int wi = 0; wi < (tag ? 3 : 1) && result == RS_OK; ++wi) {
+            for (int i = 0; i < n_shapes && result == RS_OK; ++i) {
+                if (wi == 0 && i == 0) continue;   // the starting point, timed above
+                rs_pipeline_opts c = cur;
+                c.ensemble_width = widths[wi] * RS_W;
+                c.regions_per_unit = shapes[i][0];
+                c.region_cost = shapes[i][1];
+                const float t = time_of(c);
+                if (t < cur_t) { cur_t = t; cur = c; }
+            }
         }
-        for (uint32_t w : {4u, 2u}) {
-            if (!tag && w == 4) continue;
+        if (!tag) {
             rs_pipeline_opts c = cur;
-            c.ensemble_width = w * RS_W;
+            c.ensemble_width = 2 * RS_W;
             c.tile_elements = 0;
             const float t = time_of(c);
             if (t < cur_t) { cur_t = t; cur = c; }
