@@ -19,6 +19,7 @@ sequential definition) on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -186,8 +187,8 @@ def kernel_source_hash() -> str:
 
 
 def read_traffic():
-    """Per-launch DRAM bytes of the timed kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
+    """DRAM bytes of one run (planner + pipeline kernel, the pair the roofline times) per
+    mean, from the committed ncu summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "dram_traffic_cascade.txt")
     try:
         rows = {}
@@ -314,6 +315,10 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
     arrivals = wl.poisson_arrivals(rate, seconds, seed=4)
     srv = rs.Server(pipe, arena_bytes=int(arena_gb * (1 << 30)), strategy="tag")
     stamps, owner, lat, done_items = {}, {}, [], 0
+    # no garbage-collector pauses inside the timed loop (its objects are all still live)
+    gc_was_enabled = gc.isenabled()
+    gc.collect()
+    gc.disable()
     t0 = time.perf_counter()
     a = 0
     pending = []
@@ -345,6 +350,8 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
         if now > seconds + 30:
             break
     wall = time.perf_counter() - t0
+    if gc_was_enabled:
+        gc.enable()
     st = srv.stats()
     srv.close()
     L = np.array([x[1] for x in lat]) * 1e3
@@ -356,6 +363,8 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
             "p99_ms": float(np.percentile(L, 99)) if len(L) else None,
             "p50_ms_after_1s": float(np.percentile(Lw, 50)) if len(Lw) else None,
             "p99_ms_after_1s": float(np.percentile(Lw, 99)) if len(Lw) else None,
+            "max_ms": float(L.max()) if len(L) else None,
+            "over_5ms": int((L > 5.0).sum()) if len(L) else 0,
             "batches": st["batches"], "largest_batch": st["largest_batch"],
             "arena_peak_bytes": st["arena_peak"], "wall_s": wall}
 
