@@ -81,10 +81,11 @@ __device__ __forceinline__ uint4 ld_stream_v4(const uint32_t *p)
     return v;
 }
 
-__device__ __forceinline__ uint2 ld_stream_v2(const uint32_t *p)
+// read-only 8-byte load that allocates in L1 (the words are read again soon)
+__device__ __forceinline__ uint2 ld_nc_v2(const uint32_t *p)
 {
     uint2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
     return v;
 }
 

@@ -214,12 +214,13 @@ __device__ __forceinline__ void st_shared_if(uint32_t a, uint32_t v, uint32_t k)
 }
 
 // words p[r] and p[r + 1] of a read-only array (0 when not wanted): with VEC (r even),
-// one 8-byte load when both are wanted and the array is 8-byte aligned, else one load each
+// one 8-byte load when both are wanted and the array is 8-byte aligned, else one load each.
+// The loads allocate in L1: the downstream nodes read the same context words by region.
 template <bool VEC>
 __device__ __forceinline__ void ld_pair(const uint32_t *p, uint32_t r, bool in0, bool in1, uint32_t &a, uint32_t &b)
 {
     if (VEC && in0 && in1 && ((uintptr_t)p & 7u) == 0) {
-        const uint2 v = ld_stream_v2(p + r);
+        const uint2 v = ld_nc_v2(p + r);
         a = v.x;
         b = v.y;
     } else {
