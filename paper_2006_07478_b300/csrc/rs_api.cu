@@ -473,7 +473,7 @@ static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts
 // Per-processor shared memory of the tag kernel: counters, window marks (W words, hashed
 // enumeration only: with loaded elements node 1 marks in the staging slot it has just
 // read), node 1's staging ring of four element windows (loaded enumeration only),
-// the rings of edges 1..n-3 (values and region tags, two arrays; edge n-2 too when node
+// the rings of edges 1..n-3 (8-byte slots of {value, region tag}; edge n-2 too when node
 // n-2 is an expansion), and the parent records
 // (PR entries each of {region id, operand}, start offset, and parent id for hashed
 // enumeration).  PR >= W + 64 cpl covers every record node 1 can still need: the parents
@@ -491,8 +491,8 @@ static SmemLayout make_tag_layout(const rs_pipeline *p, uint32_t cpl)
 #endif
     L.o_cnt = (uint32_t)off;
     off += 8 * 4 * RS_MAX_STAGES;
-    L.o_pend = (uint32_t)off;     // the next unit's description (7 words)
-    off += 32;
+    L.o_pend = (uint32_t)off;     // the next unit's description (7 words) and, at byte
+    off += 48;                    // 32, the 8-byte scratch slot of the ring stores
     off = align_up(off, 16);
     L.o_scr = (uint32_t)off;      // window marks, hashed enumeration only (loaded
     off += p->stages[0].kind == RS_ENUM_LOAD ? 0 : (size_t)4 * W;   // elements: a staging slot)
@@ -504,10 +504,10 @@ static SmemLayout make_tag_layout(const rs_pipeline *p, uint32_t cpl)
     const uint32_t ns = p->n_stages;
     const bool fused = ns >= 3 && p->stages[ns - 2].kind != RS_EXPAND;
     const size_t rings = ns - 2 - (fused ? 1u : 0u);
-    L.o_qv = (uint32_t)off;       // ring values
-    off += rings * o.queue_capacity * 4;
-    L.o_qt = (uint32_t)off;       // ring tags (region ids)
-    off += rings * o.queue_capacity * 4;
+    off = align_up(off, 16);
+    L.o_qv = (uint32_t)off;       // ring slots {value, region id}, 8 bytes each
+    L.o_qt = L.o_qv;
+    off += rings * o.queue_capacity * 8;
     uint32_t pr = 128;
     while (pr < W + 64 * cpl) pr <<= 1;
     L.pr = pr;

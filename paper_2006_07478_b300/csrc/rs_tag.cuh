@@ -248,8 +248,8 @@ struct TagEngine {
     // a register
     __device__ __forceinline__ SArr<unsigned long long> cnt() const { return sarr<unsigned long long>(wb + P.L.o_cnt); }
     __device__ __forceinline__ SArr<unsigned long long> nra() const { return sarr<unsigned long long>(wb + P.L.o_nra); }
-    __device__ __forceinline__ SArr<uint32_t> rv() const { return sarr<uint32_t>(wb + P.L.o_qv); }   // ring values
-    __device__ __forceinline__ SArr<uint32_t> rt() const { return sarr<uint32_t>(wb + P.L.o_qt); }   // ring tags
+    // ring slots {value, region tag}, 8 bytes each
+    __device__ __forceinline__ SArr<uint2> rq() const { return sarr<uint2>(wb + P.L.o_qv); }
     __device__ __forceinline__ SArr<uint32_t> nst() const { return sarr<uint32_t>(wb + P.L.o_nst); }
     __device__ __forceinline__ SArr<uint32_t> npar() const { return sarr<uint32_t>(wb + P.L.o_npar); }
     // node 1's window marks: with loaded elements, the staging slot node 1 has just read
@@ -657,22 +657,21 @@ struct TagEngine {
 #pragma unroll
         for (int g = 0; g < NG; ++g) n += (tot >> (16 * g)) & 0xFFFFu;
         if (s0 + n <= C()) {
-            // kept items take consecutive slots; the others are written to a scratch word
-            // of the processor (never read), so the stores need no branch or predicate
-            const uint32_t vb = smem_addr(rv().ptr()), tb = smem_addr(rt().ptr());
-            const uint32_t trash = smem_addr(nxs().ptr() + 7);
+            // kept items take consecutive slots (one 8-byte store of {value, tag} each); the
+            // others are written to a scratch slot of the processor (never read), so the
+            // stores need no branch or predicate
+            const uint32_t qb = smem_addr(rq().ptr());
+            const uint32_t trash = smem_addr(nxs().ptr() + 8);
             uint32_t gb = rb + s0;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
-                uint32_t off = 4u * (gb + ((ex >> (16 * g)) & 0xFFFFu));
+                uint32_t off = 8u * (gb + ((ex >> (16 * g)) & 0xFFFFu));
 #pragma unroll
                 for (int i = 0; i < GV; ++i) {
                     const int j = g * GV + i;
-                    const uint32_t va = keep[j] ? vb + off : trash;
-                    const uint32_t ta = keep[j] ? tb + off : trash;
-                    asm volatile("st.shared.u32 [%0], %1;" ::"r"(va), "r"(y[j]) : "memory");
-                    asm volatile("st.shared.u32 [%0], %1;" ::"r"(ta), "r"(r[j]) : "memory");
-                    off += keep[j] ? 4u : 0u;
+                    const uint32_t qa = keep[j] ? qb + off : trash;
+                    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(qa), "r"(y[j]), "r"(r[j]) : "memory");
+                    off += keep[j] ? 8u : 0u;
                 }
                 gb += (tot >> (16 * g)) & 0xFFFFu;
             }
@@ -685,8 +684,7 @@ struct TagEngine {
                 for (int i = 0; i < GV; ++i) {
                     const int j = g * GV + i;
                     if (keep[j]) {
-                        rv()[rb + (pos & CM())] = y[j];
-                        rt()[rb + (pos & CM())] = r[j];
+                        rq()[rb + (pos & CM())] = make_uint2(y[j], r[j]);
                         ++pos;
                     }
                 }
@@ -740,8 +738,7 @@ struct TagEngine {
                 const int j = g * GV + i;
                 for (uint32_t o = 0; o < nout[j]; ++o) {
                     const uint32_t yv = fmix32(x[j] ^ fmix32((sd.p0 + 1u + o) ^ RS_GOLD));
-                    rv()[rb + (pos & CM())] = yv;
-                    rt()[rb + (pos & CM())] = r[j];
+                    rq()[rb + (pos & CM())] = make_uint2(yv, r[j]);
                     ++pos;
                 }
             }
@@ -1037,36 +1034,38 @@ struct TagEngine {
         if (FULL || (h & (V - 1)) == 0) {
             // the lane's V slots are contiguous (C is a multiple of V)
             const uint32_t s = rb + ((h + V * lane) & CM());
+            // two slots per 16-byte load (s is even: h and C are multiples of V)
             if constexpr (VS == 4) {
 #pragma unroll
                 for (int t = 0; t < NS; ++t) {
-                    const uint4 xv = *reinterpret_cast<const uint4 *>(rv().ptr() + s + 4 * t);
-                    const uint4 tv = *reinterpret_cast<const uint4 *>(rt().ptr() + s + 4 * t);
-                    x[4 * t + 0] = xv.x;
-                    x[4 * t + 1 % V] = xv.y;
-                    x[4 * t + 2 % V] = xv.z;
-                    x[4 * t + 3 % V] = xv.w;
-                    r[4 * t + 0] = tv.x;
-                    r[4 * t + 1 % V] = tv.y;
-                    r[4 * t + 2 % V] = tv.z;
-                    r[4 * t + 3 % V] = tv.w;
+                    const uint4 p0 = *reinterpret_cast<const uint4 *>(rq().ptr() + s + 4 * t);
+                    const uint4 p1 = *reinterpret_cast<const uint4 *>(rq().ptr() + s + 4 * t + 2);
+                    x[4 * t + 0] = p0.x;
+                    r[4 * t + 0] = p0.y;
+                    x[4 * t + 1 % V] = p0.z;
+                    r[4 * t + 1 % V] = p0.w;
+                    x[4 * t + 2 % V] = p1.x;
+                    r[4 * t + 2 % V] = p1.y;
+                    x[4 * t + 3 % V] = p1.z;
+                    r[4 * t + 3 % V] = p1.w;
                 }
             } else if constexpr (VS == 2) {
-                const uint2 xv = *reinterpret_cast<const uint2 *>(rv().ptr() + s);
-                const uint2 tv = *reinterpret_cast<const uint2 *>(rt().ptr() + s);
-                x[0] = xv.x;
-                x[1 % V] = xv.y;
-                r[0] = tv.x;
-                r[1 % V] = tv.y;
+                const uint4 p0 = *reinterpret_cast<const uint4 *>(rq().ptr() + s);
+                x[0] = p0.x;
+                r[0] = p0.y;
+                x[1 % V] = p0.z;
+                r[1 % V] = p0.w;
             } else {
-                x[0] = rv()[s];
-                r[0] = rt()[s];
+                const uint2 p0 = rq()[s];
+                x[0] = p0.x;
+                r[0] = p0.y;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                x[j] = rv()[rb + ((h + V * lane + j) & CM())];
-                r[j] = rt()[rb + ((h + V * lane + j) & CM())];
+                const uint2 p0 = rq()[rb + ((h + V * lane + j) & CM())];
+                x[j] = p0.x;
+                r[j] = p0.y;
             }
         }
 #pragma unroll
@@ -1075,7 +1074,7 @@ struct TagEngine {
         r0 = __shfl_sync(FULLMASK, r[0], 0);
         uint32_t rl;
         if (FULL) rl = __shfl_sync(FULLMASK, r[V - 1], 31);
-        else rl = rt()[rb + ((h + take - 1) & CM())];
+        else rl = rq()[rb + ((h + take - 1) & CM())].y;
         uni = r0 == rl;
     }
 
