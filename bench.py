@@ -304,6 +304,24 @@ def bench_batched(rs, torch):
                        "regions_per_unit": best["regions_per_unit"], "ensemble_width": best["ensemble_width"]}}
 
 
+def cgroup_cpu_stat() -> dict:
+    """This process's cgroup CPU counters (cgroup v2 cpu.stat), {} where unavailable."""
+    try:
+        with open("/sys/fs/cgroup/cpu.stat") as f:
+            return {k: int(v) for k, v in (line.split() for line in f if line.strip())}
+    except Exception:
+        return {}
+
+
+def cgroup_cpu_quota():
+    """The cgroup's CPU quota as 'max period' (cgroup v2 cpu.max), or None."""
+    try:
+        with open("/sys/fs/cgroup/cpu.max") as f:
+            return f.read().strip()
+    except Exception:
+        return None
+
+
 def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: float = 4.0):
     """Open-loop Poisson arrivals of batched-size hashed streams into the
     continuous-batching server; latency = scheduled arrival -> completion seen."""
@@ -315,6 +333,7 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
     arrivals = wl.poisson_arrivals(rate, seconds, seed=4)
     srv = rs.Server(pipe, arena_bytes=int(arena_gb * (1 << 30)), strategy="tag")
     stamps, owner, lat, done_items = {}, {}, [], 0
+    thr0 = cgroup_cpu_stat()
     # no garbage-collector pauses inside the timed loop (its objects are all still live)
     gc_was_enabled = gc.isenabled()
     gc.collect()
@@ -349,7 +368,13 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
             break
         if now > seconds + 30:
             break
+        if not owner and not pending and a < len(arrivals):
+            # nothing in flight: sleep until shortly before the next arrival
+            gap = arrivals[a] - (time.perf_counter() - t0)
+            if gap > 2e-4:
+                time.sleep(gap - 1e-4)
     wall = time.perf_counter() - t0
+    thr1 = cgroup_cpu_stat()
     if gc_was_enabled:
         gc.enable()
     st = srv.stats()
@@ -365,6 +390,9 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
             "p99_ms_after_1s": float(np.percentile(Lw, 99)) if len(Lw) else None,
             "max_ms": float(L.max()) if len(L) else None,
             "over_5ms": int((L > 5.0).sum()) if len(L) else 0,
+            "host_cpu": {"quota": cgroup_cpu_quota(),
+                         "throttled_periods": (thr1.get("nr_throttled", 0) - thr0.get("nr_throttled", 0)) if thr0 else None,
+                         "throttled_ms": ((thr1.get("throttled_usec", 0) - thr0.get("throttled_usec", 0)) / 1e3) if thr0 else None},
             "batches": st["batches"], "largest_batch": st["largest_batch"],
             "arena_peak_bytes": st["arena_peak"], "wall_s": wall}
 
@@ -612,14 +640,6 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                "overlap": "copy-in, run and copy-out on three CUDA streams"}
 
-    # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1) ----
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        threads = os.cpu_count() or 1
-        items, secs, done = time_oracle(streams, threads, budget_s=20.0)
-        cpu = {"value": items / secs, "unit": "items/s", "cores": threads, "kind": "oracle",
-               "sample": f"{done} of the 5 streams, whole ({items} elements), {threads} threads"}
-
     extras = {}
     if rank == 0 and not args.no_extras:
         for name, fn in (("graph_edges", lambda: bench_graph(rs, torch, peak)),
@@ -629,6 +649,15 @@ def main():
                 extras[name] = fn()
             except Exception as exc:   # report, do not lose the main line
                 extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1), after the
+    # GPU sections so that its host-memory churn does not overlap the serving loop ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        items, secs, done = time_oracle(streams, threads, budget_s=20.0)
+        cpu = {"value": items / secs, "unit": "items/s", "cores": threads, "kind": "oracle",
+               "sample": f"{done} of the 5 streams, whole ({items} elements), {threads} threads"}
 
     if rank == 0:
         line = {
