@@ -199,7 +199,7 @@ def read_traffic():
                 if line.startswith("kernel_source"):
                     src = line.split()[1]
                 elif line.startswith("mean="):
-                    kv = dict(tok.split("=") for tok in line.split())
+                    kv = dict(tok.split("=", 1) for tok in line.split())
                     rows[(int(kv["mean"]), kv["strategy"])] = float(kv["dram_bytes"])
         if src != kernel_source_hash():
             return None
