@@ -203,6 +203,42 @@ def cascade_stream(n_total: int = 1 << 26, mean: float = 32, seed: int = 7,
                        workload=f"cascade N={n_total} mean={mean} seed={seed}")
 
 
+def pipeline_region_sum() -> list:
+    """The paper's region-sum benchmark (Section 6, Figures figFixed and figVariable):
+    enumerate each region of an integer array and reduce it to its sum (and count)."""
+    return [("enum_load",), ("aggregate",)]
+
+
+def sized_lengths(n_total: int, size: int, seed: int = 11, variable: bool = False) -> np.ndarray:
+    """Region lengths totalling n_total: `size` each (the last one shorter), or, with
+    `variable`, uniform on 0..size (splitmix64 draws), the last one truncated."""
+    if variable:
+        sub = substream_seed(seed, 0x5A5)
+        n_est = 2 * n_total // max(size, 1) + 1024
+        lengths = (splitmix64_counter(sub, 0, n_est) % U64(size + 1)).astype(np.int64)
+        csum = np.cumsum(lengths)
+        while csum[-1] < n_total:   # draw more (never in practice: n_est is twice the mean)
+            more = (splitmix64_counter(sub, lengths.shape[0], n_est) % U64(size + 1)).astype(np.int64)
+            lengths = np.concatenate([lengths, more])
+            csum = np.cumsum(lengths)
+        last = int(np.searchsorted(csum, n_total))
+        lengths = lengths[: last + 1].copy()
+        lengths[-1] -= int(csum[last]) - n_total
+    else:
+        R = (n_total + size - 1) // size
+        lengths = np.full(R, size, dtype=np.int64)
+        lengths[-1] = n_total - size * (R - 1)
+    return lengths.astype(np.uint32)
+
+
+def sized_region_stream(n_total: int, size: int, seed: int = 11, variable: bool = False) -> dict:
+    """n_total uint32 elements (splitmix64) cut into regions by `sized_lengths`."""
+    elements = to_u32(splitmix64_counter(substream_seed(seed, 0xE1E), 0, n_total))
+    kind = "U{0.." + str(size) + "}" if variable else str(size)
+    return make_stream(sized_lengths(n_total, size, seed, variable), parents=None, elements=elements,
+                       workload=f"region-sum N={n_total} size={kind} seed={seed}")
+
+
 def zipf_degrees(V: int, E: int, s: float, cap: int, seed: int) -> np.ndarray:
     """Out-degrees with a Zipf(s) shape on 1..cap, rescaled so they sum to exactly E
     with none above cap."""

@@ -328,3 +328,24 @@ def test_decreasing_offsets_in_two_parent_chunks(rs, bad_at):
     assert st["status"] == rs.RS_ERR_DEVICE_INPUT
     assert st["device_status"] & 8
     p.close()
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+@pytest.mark.parametrize("size,variable", [(1, False), (31, False), (32, False), (33, False), (127, False),
+                                           (128, False), (129, False), (200, False), (257, False),
+                                           (64, True), (512, True)])
+def test_region_sum_sizes(rs, strategy, size, variable):
+    """The paper's region-sum benchmark (enumerate, sum per region) at fixed region sizes
+    around multiples of the ensemble width and at sizes uniform on 0..max.  Under the
+    signal strategy no ensemble spans a region boundary, so node 1's active-lane fraction
+    is at most sum L / (W sum ceil(L / W)); under tags ensembles stay (nearly) full."""
+    s = wl.sized_region_stream((1 << 16) + 37, size, seed=size, variable=variable)
+    _, st = _check(rs, wl.pipeline_region_sum(), s, strategy, outputs=("count", "sum"))
+    W = st["ensemble_width"]
+    L = s["len"].astype(np.int64)
+    bound = L.sum() / (W * np.sum((L + W - 1) // W))
+    frac = st["active_lane_fraction"][1]
+    if strategy == "signal":
+        assert frac <= bound + 1e-9, (frac, bound)
+    else:
+        assert frac >= 0.85, frac
