@@ -384,6 +384,17 @@ static void merge_shape(const rs_pipeline_opts &o, int strategy, uint32_t *c, ui
     }
 }
 
+// Parents per planner tile: with fewer than 2^20 regions over the loaded streams, tiles
+// of 128 parents (one per lane and round), so that the planner has enough warps (a
+// mean-4096 stream of 2^26 elements has only 16 K regions) to write its unit records.
+static uint32_t plan_tile_parents(const rs_pipeline *p)
+{
+    uint64_t regions = 0;
+    if (p->stages[0].kind == RS_ENUM_LOAD)
+        for (const auto &s : p->streams) regions += s.n_regions;
+    return regions < (1ull << 20) ? RS_PLAN_TILE_SMALL : RS_PLAN_TILE;
+}
+
 // the work decomposition of one stream
 static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int strategy, const rs_stream_desc &s,
                         StreamPlan &q)
@@ -394,7 +405,8 @@ static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int str
         merge_shape(o, strategy, &q.c, &q.D, &q.K);
         uint64_t steps = (uint64_t)q.c * s.n_regions + s.n_elements;
         q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
-        q.plan_tiles = (uint32_t)((s.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE);
+        const uint32_t tile = plan_tile_parents(p);
+        q.plan_tiles = (uint32_t)((s.n_regions + tile - 1) / tile);
     } else {
         q.mode = UNIT_REGIONS;
         q.K = choose_K(p, o, s, strategy);
@@ -787,6 +799,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.total_units = (uint32_t)pl.total_units;
     P.plan_tiles = (uint32_t)pl.plan_tiles;
     P.plan_pow2 = plan_pow2(pl, p->streams.size());
+    P.plan_tile = plan_tile_parents(p);
     P.streams = (const DevStream *)(wsb + pl.table_off);
     P.hdr = (WsHeader *)wsb;
     P.V = o.ensemble_width / RS_W;
@@ -1350,6 +1363,7 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     P.total_units = (uint32_t)pl.total_units;
     P.plan_tiles = (uint32_t)pl.plan_tiles;
     P.plan_pow2 = plan_pow2(pl, p->streams.size());
+    P.plan_tile = plan_tile_parents(p);
     P.streams = (const DevStream *)(wsb + pl.table_off);
     P.hdr = (WsHeader *)wsb;
     P.V = o.ensemble_width / RS_W;

@@ -42,6 +42,7 @@ enum : uint32_t {
 #define RS_STEP_REGION 16u   // default merge-path steps per parent (rs_pipeline_opts.region_cost)
 #define RS_NOT_POW2 0xFFu
 #define RS_PLAN_TILE 1024u                                  // parents per planner tile
+#define RS_PLAN_TILE_SMALL 128u                             // ... when the streams hold few regions
 
 // Start of merge-path unit u: i = parents whose header step lies before u*D, j = absolute
 // index of the unit's first element, head_off / first_off = absolute offsets of parents
@@ -153,6 +154,7 @@ struct KParams {
     uint32_t plan_fill;           // planner writes every region's identity result (tag strategy)
     uint32_t cpl;                 // tag strategy: parents per lane in node 1's parent chunks (1 or 2)
     uint32_t plan_pow2;           // every merge-path stream's D is a power of two (planner divides by shifts)
+    uint32_t plan_tile;           // parents per planner tile (RS_PLAN_TILE or RS_PLAN_TILE_SMALL)
     uint32_t m16, m19;            // 2^16 and 2^19: x >> 16 = umulhi(x, m16), x >> 13 = umulhi(x, m19)
                                   // (run-time values, so the shifts stay multiplies)
     SmemLayout L;

@@ -311,7 +311,8 @@ __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint
 // ---------------------------------------------------------------------------
 // Planner: parent offsets (a single-pass decoupled look-back scan of the lengths, or
 // the CSR offsets as given) and the merge-path unit records of every UNIT_MERGE stream.
-// One warp per tile of RS_PLAN_TILE parents, read in rounds of 128: in round k lane l
+// One warp per tile of 128 ROUNDS parents (ROUNDS = 8, or 1 when the streams hold few
+// regions, so that the tiles are many), read in rounds of 128: in round k lane l
 // holds the four parents r_lo + 128 k + 4 l .. + 3, so each load instruction of the warp
 // covers one contiguous 512-byte row, and every round's loads are issued before the
 // first is used.  Unit u starts inside the merge-path span (P_r, P_r + c + L_r] of the
@@ -322,7 +323,6 @@ __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint
 // nothing else, so it is written and read relaxed (gpu scope): no fence, so publishing
 // it never waits for the tile's identity-result stores to drain.
 
-constexpr int PLAN_ROUNDS = RS_PLAN_TILE / 128;
 
 // x / d: a shift when every stream's d is a power of two (POW2, dsh = log2 d, as for
 // every tag-strategy unit shape), else a 32-bit division when x < 2^32 (d = c K <= 2^16)
@@ -334,7 +334,7 @@ __device__ __forceinline__ unsigned long long plan_div(unsigned long long x, uin
     return x / d;
 }
 
-template <bool POW2>
+template <bool POW2, int PLAN_ROUNDS>
 __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KParams P)
 {
     const uint32_t lane = threadIdx.x & 31u;
@@ -351,8 +351,9 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
         const DevStream &S = P.streams[lo];
         const uint32_t D = S.D, c = S.c, dsh = S.dsh;
         const uint32_t tile = t - S.plan_base;
-        const uint32_t r_lo = tile * RS_PLAN_TILE;
-        const uint32_t r_hi = min(r_lo + RS_PLAN_TILE, S.R);
+        constexpr uint32_t TILE = 128u * PLAN_ROUNDS;
+        const uint32_t r_lo = tile * TILE;
+        const uint32_t r_hi = min(r_lo + TILE, S.R);
         const uint32_t base_abs = S.offsets ? S.offsets[0] : 0u;
 
         // lengths of the lane's four parents in every round (0 past the tile's end)
@@ -1567,10 +1568,19 @@ int rs_launch_finalize(const KParams &P, int grid, void *stream)
     return (int)e;
 }
 
+static const void *planner_ptr(const KParams &P)
+{
+    constexpr int BIG = RS_PLAN_TILE / 128, SMALL = RS_PLAN_TILE_SMALL / 128;
+    static_assert(SMALL == 1, "small planner tiles hold one round");
+    if (P.plan_tile == RS_PLAN_TILE_SMALL)
+        return P.plan_pow2 ? (const void *)rs_plan_kernel<true, SMALL> : (const void *)rs_plan_kernel<false, SMALL>;
+    return P.plan_pow2 ? (const void *)rs_plan_kernel<true, BIG> : (const void *)rs_plan_kernel<false, BIG>;
+}
+
 int rs_launch_planner(const KParams &P, int grid, void *stream)
 {
     void *args[] = {(void *)&P};
-    cudaError_t e = cudaLaunchKernel(P.plan_pow2 ? (const void *)rs_plan_kernel<true> : (const void *)rs_plan_kernel<false>, dim3(grid), dim3(256), args, 0,
+    cudaError_t e = cudaLaunchKernel(planner_ptr(P), dim3(grid), dim3(256), args, 0,
                                      (cudaStream_t)stream);
     return (int)e;
 }

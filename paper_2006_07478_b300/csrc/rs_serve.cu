@@ -101,7 +101,7 @@ static uint64_t stream_ws_bound(const rs_server *s, const rs_request &r)
         const uint64_t c = s->opts.region_cost ? s->opts.region_cost : RS_STEP_REGION;
         const uint64_t D = c * kp;
         const uint64_t units = (c * r.n_regions + r.n_elements + D - 1) / D;
-        const uint64_t tiles = (r.n_regions + RS_PLAN_TILE - 1) / RS_PLAN_TILE;
+        const uint64_t tiles = (r.n_regions + RS_PLAN_TILE_SMALL - 1) / RS_PLAN_TILE_SMALL;   // at most
         b += a256(units * sizeof(Slot)) + 256 + a256(tiles * 8) + a256((units + 1) * sizeof(UnitRec));
     }
     return b;
