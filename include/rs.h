@@ -291,9 +291,13 @@ rs_status rs_server_create(const rs_stage_desc *stages, uint32_t n_stages, const
 /* Queue a request (host-side only; admitted by a later rs_server_progress).
  * RS_ERR_CAPACITY if it needs more than half the arena. */
 rs_status rs_server_submit(rs_server *s, const rs_request *r, uint64_t *req_id);
-/* Non-blocking step: retire finished batches (their results are in the host outputs),
- * admit queued requests while the arena has room (copies on `stream`), and launch the
- * forming batch if fewer than max_inflight batches are running. */
+/* Non-blocking step: retire finished batches (their results are copied into the host
+ * outputs here), admit queued requests while the arena has room (copies on `stream`),
+ * and launch the forming batch if fewer than max_inflight batches are running.  A
+ * batch's results come back with one gather kernel and one device-to-host copy into a
+ * page-locked staging buffer of the server's (host memory, allocated with
+ * cudaMallocHost when a batch first needs one that large, reused afterwards); if that
+ * cannot be had, with one copy per output array. */
 rs_status rs_server_progress(rs_server *s);
 /* Ids of requests completed since the last poll (up to max; *n = how many). */
 rs_status rs_server_poll(rs_server *s, uint64_t *ids, uint32_t max, uint32_t *n);

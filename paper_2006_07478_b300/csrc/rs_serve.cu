@@ -6,11 +6,15 @@
 // running into the next batch: one rs_run over all of them.  Up to `max_inflight`
 // batches are queued on the server's CUDA stream at once, so requests that arrive while
 // others are on the GPU join the next batch and their work overlaps on the device.
-// When a batch's completion event fires, its results are already in the requests'
-// host output buffers (the copies were queued behind the batch), its arena space is
-// released and its request ids are reported by rs_server_poll.
+// A batch's results come back with one gather kernel (every member's output arrays into
+// one contiguous region of the arena) and one device-to-host copy into a page-locked
+// staging buffer of the server's; when the batch's completion event fires they are
+// copied on the host into the requests' output buffers, its arena space is released and
+// its request ids are reported by rs_server_poll.  (A batch whose results do not fit
+// that path falls back to one copy per output array.)
 //
-// Nothing here allocates device memory; the arena is the caller's.
+// Nothing here allocates device memory; the arena is the caller's.  The staging buffers
+// are host memory, allocated when a batch first needs one that large and reused.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -27,6 +31,29 @@ struct Req {
     uint64_t id;
     rs_request r;
     uint64_t off, bytes;         // arena chunk
+    uint32_t *d_count;           // the request's device outputs (in its arena chunk)
+    unsigned long long *d_sum;
+    uint32_t *d_min;
+};
+
+// one output array to gather: device source, device destination, 4-byte words
+struct GatherItem {
+    const uint4 *src;
+    uint4 *dst;
+    unsigned long long words;
+};
+
+// one output array to hand back: the request's host buffer, its offset in the staging
+// buffer, bytes
+struct Scatter {
+    void *dst;
+    uint64_t off, bytes;
+};
+
+// page-locked host staging buffer
+struct Stage {
+    unsigned char *p = nullptr;
+    uint64_t cap = 0;
 };
 
 struct Batch {
@@ -36,7 +63,21 @@ struct Batch {
     uint64_t head_after = 0;     // ring head after this batch's last allocation
     uint64_t live_bytes = 0;     // bytes this batch holds in the ring
     cudaEvent_t ev = nullptr;
+    Stage stage;                 // results staging (gathered path), returned at retire
+    std::vector<Scatter> scat;   // where each staged output array goes
 };
+
+// Each CTA copies whole items, 16 bytes per thread and step.  Sources and destinations
+// are 16-byte aligned and padded to 256 bytes in the arena, so rounding an item up to
+// 16 bytes stays inside its allocation.
+__global__ void __launch_bounds__(128) rs_gather_kernel(const GatherItem *items, uint32_t n)
+{
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const GatherItem it = items[i];
+        const unsigned long long n16 = (it.words + 3) / 4;
+        for (unsigned long long k = threadIdx.x; k < n16; k += blockDim.x) it.dst[k] = it.src[k];
+    }
+}
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -55,6 +96,8 @@ struct rs_server {
     std::vector<Req> forming_members;
     std::deque<Batch> inflight;
     std::vector<rs_pipeline *> pool;
+    std::vector<cudaEvent_t> free_events;   // completion events of retired batches, reused
+    std::vector<Stage> free_stages;         // staging buffers of retired batches, reused
     std::vector<uint64_t> completed;
     uint64_t next_id = 1;
     uint32_t max_batch = 4096, max_inflight = 2;
@@ -156,6 +199,9 @@ static rs_status admit(rs_server *s, Req &q)
     if (q.r.out_count) { d.out_count = (uint32_t *)(base + o); o += a256(R * 4); }
     if (q.r.out_sum) { d.out_sum = (uint64_t *)(base + o); o += a256(R * 8); }
     if (q.r.out_min) { d.out_min = (uint32_t *)(base + o); o += a256(R * 4); }
+    q.d_count = d.out_count;
+    q.d_sum = (unsigned long long *)d.out_sum;
+    q.d_min = d.out_min;
     d.total_elements_hint = q.r.total_elements_hint;
     uint64_t sid = 0;
     rs_status st = rs_stream_submit(s->forming.p, &d, &sid);
@@ -164,6 +210,85 @@ static rs_status admit(rs_server *s, Req &q)
     s->forming.head_after = s->head;
     s->stats.admitted++;
     return RS_OK;
+}
+
+// Queue the batch's results as one gather into an arena region and one copy into a
+// staging buffer (host side scattered at retire).  False, with nothing queued, when the
+// arena has no room or no staging buffer can be had: the caller copies per array.
+static bool gather_results(rs_server *s, Batch &b, const std::vector<Req> &members)
+{
+    std::vector<Scatter> scat;
+    uint64_t rbytes = 0;
+    size_t n_items = 0;
+    for (const Req &q : members) {
+        const uint64_t R = q.r.n_regions;
+        const void *hd[3] = {q.r.out_count, q.r.out_sum, q.r.out_min};
+        const uint64_t by[3] = {R * 4, R * 8, R * 4};
+        for (int k = 0; k < 3; ++k) {
+            if (!hd[k] || R == 0) continue;
+            scat.push_back(Scatter{const_cast<void *>(hd[k]), rbytes, by[k]});
+            rbytes += (by[k] + 15) & ~(uint64_t)15;
+            ++n_items;
+        }
+    }
+    if (n_items == 0) return true;   // nothing to hand back
+    const uint64_t tbytes = a256(n_items * sizeof(GatherItem));
+    const uint64_t total = tbytes + a256(rbytes);
+    // a staging buffer at least this large: reuse one, else allocate (rounded up to a
+    // power of two, so that few sizes are ever allocated)
+    Stage sg;
+    for (size_t i = 0; i < s->free_stages.size(); ++i) {
+        if (s->free_stages[i].cap >= total) {
+            sg = s->free_stages[i];
+            s->free_stages.erase(s->free_stages.begin() + i);
+            break;
+        }
+    }
+    if (!sg.p) {
+        uint64_t cap = 1u << 16;
+        while (cap < total) cap <<= 1;
+        if (cudaMallocHost((void **)&sg.p, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        sg.cap = cap;
+    }
+    uint64_t off = 0, charged = 0;
+    if (!ring_alloc(s, total, &off, &charged)) {
+        s->free_stages.push_back(sg);
+        return false;
+    }
+    b.head_after = s->head;
+    b.live_bytes += charged;
+    unsigned char *dev = s->arena + off;
+    GatherItem *items = reinterpret_cast<GatherItem *>(sg.p);
+    size_t k = 0;
+    for (const Req &q : members) {
+        if (q.r.n_regions == 0) continue;
+        const void *src[3] = {q.d_count, q.d_sum, q.d_min};
+        const void *hd[3] = {q.r.out_count, q.r.out_sum, q.r.out_min};
+        const uint64_t words[3] = {q.r.n_regions, 2 * q.r.n_regions, q.r.n_regions};
+        for (int j = 0; j < 3; ++j) {
+            if (!hd[j]) continue;
+            items[k].src = reinterpret_cast<const uint4 *>(src[j]);
+            items[k].dst = reinterpret_cast<uint4 *>(dev + tbytes + scat[k].off);
+            items[k].words = words[j];
+            ++k;
+        }
+    }
+    const uint32_t grid = n_items < 1024 ? (uint32_t)n_items : 1024u;
+    if (cudaMemcpyAsync(dev, sg.p, n_items * sizeof(GatherItem), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        (rs_gather_kernel<<<grid, 128, 0, s->stream>>>(reinterpret_cast<const GatherItem *>(dev), (uint32_t)n_items),
+         cudaGetLastError() != cudaSuccess) ||
+        cudaMemcpyAsync(sg.p + tbytes, dev + tbytes, rbytes, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) {
+        // the arena charge stays with the batch; the copies are not queued: fall back
+        s->free_stages.push_back(sg);
+        return false;
+    }
+    for (Scatter &c : scat) c.off += tbytes;
+    b.stage = sg;
+    b.scat.swap(scat);
+    return true;
 }
 
 // Launch the forming batch: workspace from the ring, one rs_run, result copies back
@@ -183,13 +308,19 @@ static rs_status launch(rs_server *s, std::vector<Req> &members)
     b.live_bytes += charged;
     st = rs_run(b.p, s->arena + woff, a256(wsb), (rs_cuda_stream)s->stream);
     if (st != RS_OK) return st;
-    for (size_t i = 0; i < members.size(); ++i) {
-        rs_region_results dst;
-        dst.count = members[i].r.out_count;
-        dst.sum = members[i].r.out_sum;
-        dst.min = members[i].r.out_min;
-        st = rs_fetch_region_results(b.p, i, &dst, (rs_cuda_stream)s->stream);
-        if (st != RS_OK) return st;
+    if (!gather_results(s, b, members)) {
+        for (size_t i = 0; i < members.size(); ++i) {
+            rs_region_results dst;
+            dst.count = members[i].r.out_count;
+            dst.sum = members[i].r.out_sum;
+            dst.min = members[i].r.out_min;
+            st = rs_fetch_region_results(b.p, i, &dst, (rs_cuda_stream)s->stream);
+            if (st != RS_OK) return st;
+        }
+    }
+    if (!b.ev && !s->free_events.empty()) {
+        b.ev = s->free_events.back();
+        s->free_events.pop_back();
     }
     if (!b.ev && cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) return RS_ERR_CUDA;
     if (cudaEventRecord(b.ev, s->stream) != cudaSuccess) return RS_ERR_CUDA;
@@ -261,13 +392,18 @@ rs_status rs_server_progress(rs_server *s)
         cudaError_t e = cudaEventQuery(b.ev);
         if (e == cudaErrorNotReady) break;
         if (e != cudaSuccess) return RS_ERR_CUDA;
+        // gathered results: from the staging buffer into the requests' output buffers
+        for (const Scatter &c : b.scat) memcpy(c.dst, b.stage.p + c.off, c.bytes);
+        if (b.stage.p) s->free_stages.push_back(b.stage);
+        b.stage = Stage();
+        b.scat.clear();
         for (uint64_t id : b.ids) s->completed.push_back(id);
         s->stats.completed += b.ids.size();
         // release the batch's ring space: everything up to its last allocation
         s->tail = b.head_after;
         s->live -= b.live_bytes;
         if (s->live == 0) s->head = s->tail = 0;
-        cudaEventDestroy(b.ev);
+        s->free_events.push_back(b.ev);   // reused by a later batch (no driver call per batch)
         b.ev = nullptr;
         s->pool.push_back(b.p);
         s->inflight.pop_front();
@@ -341,7 +477,12 @@ rs_status rs_server_destroy(rs_server *s)
         if (b.p) rs_pipeline_destroy(b.p);
     }
     if (s->forming.p) rs_pipeline_destroy(s->forming.p);
+    if (s->forming.ev) cudaEventDestroy(s->forming.ev);
     for (auto *p : s->pool) rs_pipeline_destroy(p);
+    for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
+    for (auto &b : s->inflight)
+        if (b.stage.p) cudaFreeHost(b.stage.p);
+    for (Stage &g : s->free_stages) cudaFreeHost(g.p);
     delete s;
     return RS_OK;
 }
