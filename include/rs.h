@@ -277,6 +277,8 @@ typedef struct {
     uint64_t submitted, admitted, completed, batches, largest_batch;
     uint64_t in_flight, queued;          /* batches on the GPU, requests waiting for memory */
     uint64_t arena_live, arena_peak;     /* bytes of the arena in use now / at most          */
+    uint64_t gathered;                   /* batches whose results came back with one gather
+                                            kernel and one copy (the rest: one copy per array) */
 } rs_server_stats;
 
 /* A server over one stage list.  `arena` (device, caller-owned, 256-byte aligned) is

@@ -308,7 +308,9 @@ static rs_status launch(rs_server *s, std::vector<Req> &members)
     b.live_bytes += charged;
     st = rs_run(b.p, s->arena + woff, a256(wsb), (rs_cuda_stream)s->stream);
     if (st != RS_OK) return st;
-    if (!gather_results(s, b, members)) {
+    if (gather_results(s, b, members)) {
+        s->stats.gathered++;
+    } else {
         for (size_t i = 0; i < members.size(); ++i) {
             rs_region_results dst;
             dst.count = members[i].r.out_count;

@@ -111,7 +111,7 @@ class Request(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "batches", "largest_batch",
-                                               "in_flight", "queued", "arena_live", "arena_peak")]
+                                               "in_flight", "queued", "arena_live", "arena_peak", "gathered")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

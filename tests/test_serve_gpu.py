@@ -49,6 +49,7 @@ def test_mix_equals_alone(rs, strategy):
     assert sorted(done) == sorted(ids)
     st = srv.stats()
     assert st["completed"] == len(ids) and st["arena_live"] == 0
+    assert st["gathered"] == st["batches"]          # the arena had room for every gather
     for r, s in zip(reqs, streams):
         _check(rs, r, s, pipe)
     # the same stream alone in its own batch gives the same result
@@ -94,6 +95,24 @@ def test_requests_arriving_during_a_batch_join_the_next(rs):
     done += _drain(srv, len(reqs) - len(done))
     st = srv.stats()
     assert st["completed"] == len(reqs) and st["batches"] >= 2
+    for r, s in zip(reqs, streams):
+        _check(rs, r, s, pipe)
+    srv.close()
+
+
+def test_results_copied_per_array_when_the_arena_is_full(rs):
+    """An arena sized so that requests fill it: some batches find no room for the
+    gathered-results region and copy each output array back on its own.  Both paths give
+    the oracle's results."""
+    pipe = wl.pipeline_hash_filter_map()
+    streams = [wl.hashed_uniform_stream(4000, 64, 40 + i) for i in range(30)]
+    reqs = [rs.host_request(s) for s in streams]
+    srv = rs.Server(pipe, arena_bytes=192 << 10, strategy="tag", max_inflight=1)
+    ids = [srv.submit(r) for r in reqs]
+    _drain(srv, len(ids))
+    st = srv.stats()
+    assert st["completed"] == len(ids) and st["arena_live"] == 0
+    assert st["gathered"] < st["batches"], st
     for r, s in zip(reqs, streams):
         _check(rs, r, s, pipe)
     srv.close()
