@@ -74,3 +74,23 @@ def test_poisson_arrivals_rate():
     t = wl.poisson_arrivals(20000.0, 2.0, 1)
     assert abs(len(t) - 40000) < 5 * np.sqrt(40000)
     assert (np.diff(t) > 0).all()
+
+
+def test_sized_region_lengths():
+    """Region-sum streams: the lengths total n_total; fixed sizes are `size` except a
+    shorter last region; variable sizes stay in 0..size with mean near size / 2; the
+    draws are deterministic in the seed."""
+    from paper_2006_07478_b300 import workloads as wl
+    n = 100_003
+    for size in (1, 7, 128, 129, 4096):
+        L = wl.sized_lengths(n, size, seed=3).astype(np.int64)
+        assert L.sum() == n
+        assert np.all(L[:-1] == size) and 1 <= L[-1] <= size
+    for size in (64, 513):
+        L = wl.sized_lengths(n, size, seed=3, variable=True).astype(np.int64)
+        assert L.sum() == n and L.min() >= 0 and L.max() <= size
+        assert abs(L[:-1].mean() - size / 2) < 0.05 * size
+        assert np.array_equal(L, wl.sized_lengths(n, size, seed=3, variable=True))
+        assert not np.array_equal(L[:100], wl.sized_lengths(n, size, seed=4, variable=True)[:100])
+    s = wl.sized_region_stream(n, 33, seed=5)
+    assert s["R"] == (n + 32) // 33 and s["elements"].shape[0] == n and s["elements"].dtype == np.uint32
