@@ -212,7 +212,7 @@ def bench_graph(rs, torch, peak):
     """Graph-edge stream: 2^22 vertices, 2^26 edges (Zipf hubs); items = edges."""
     g = wl.graph_stream()
     E, V = wl.n_elements(g), g["R"]
-    p = rs.Pipeline(wl.pipeline_graph_edges(), strategy="tag")
+    p = rs.Pipeline(wl.pipeline_graph_edges(), strategy="auto")
     out = p.submit(rs.to_device(g), outputs=("count", "min"))
     best, _ = p.autotune(trials=2)
     p.timing_enable(16)
@@ -296,7 +296,7 @@ def bench_batched(rs, torch):
     devs = [rs.to_device(s) for s in streams]
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
-        p = rs.Pipeline(pipe, strategy="tag")
+        p = rs.Pipeline(pipe, strategy="auto")
         outs = [p.submit(d) for d in devs]
         best, _ = p.autotune(trials=1)
         p.graph_capture()
@@ -535,7 +535,7 @@ def main():
     # ---- device-resident inputs, one pipeline per stream, tuned per stream ----
     pipes, outs, tuned = [], [], []
     for s in streams:
-        p = rs.Pipeline(pipe, strategy="tag")
+        p = rs.Pipeline(pipe, strategy="auto")   # the autotuner picks the strategy too
         dev = rs.to_device(s)
         out = p.submit(dev, outputs=("count", "sum"))
         pipes.append(p)
@@ -548,8 +548,8 @@ def main():
                "chosen": {"strategy": "signal" if best["strategy"] == 0 else "tag",
                           **{k: best[k] for k in ("ensemble_width", "regions_per_unit", "region_cost",
                                                   "tile_elements", "warps_per_block")}}}
-        # both strategies, kernel-only event timing: the chosen one with the tuned options,
-        # the other with its own default unit shape (the strategies' units differ in kind)
+        # both strategies, kernel-only event timing, each with the options the autotuner
+        # finds for it (the other one searched alone, its strategy fixed)
         chosen = "signal" if best["strategy"] == 0 else "tag"
         for strat in ("tag", "signal"):
             if strat == chosen:
@@ -557,6 +557,9 @@ def main():
             else:
                 p.set_opts(strategy=strat, regions_per_unit=0, region_cost=0, ensemble_width=128,
                            tile_elements=0, tiles_in_flight=0, warps_per_block=0, queue_capacity=0)
+                other, _ = p.autotune(trials=2)
+                row[strat + "_options"] = {k: other[k] for k in ("ensemble_width", "regions_per_unit",
+                                                                "region_cost", "tile_elements", "warps_per_block")}
             p.timing_enable(8)
             for _ in range(2):
                 p.run()
@@ -569,7 +572,7 @@ def main():
             kms = statistics.median(ms)
             gbs = alg_bytes(s) / (kms * 1e-3) / 1e9
             row[strat] = {"kernel_ms": kms, "items_per_s": N_ELEM / (kms * 1e-3), "alg_gbs": gbs,
-                          "options": "tuned" if strat == chosen else "strategy defaults",
+                          "options": "tuned" if strat == chosen else "tuned for this strategy alone",
                           "active_lane_fraction": [round(x, 4) for x in st["active_lane_fraction"]],
                           "launch": st["launch"]}
         p.set_opts(**{k: v for k, v in best.items() if k != "strategy"}, strategy=best["strategy"])

@@ -232,7 +232,8 @@ rs_status rs_graph_release(rs_pipeline *p);
 /* ---- autotuning (Section 5: choose per workload, from measurements) ------------ */
 
 /* Choose options by timed trials on the submitted streams (the profile-guided choice
- * of Section 5): for each strategy, a coordinate search from the defaults over the
+ * of Section 5): for each strategy (both when the pipeline's strategy option is
+ * RS_STRATEGY_AUTO, else only the one it names), a coordinate search from the defaults over the
  * unit shape (regions_per_unit x region_cost, or whole-parent unit sizes for hashed
  * streams), then ensemble width, processors per CTA and tile size, each change kept
  * when faster; a strategy starting above three times the best so far is dropped.

@@ -1154,6 +1154,8 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
     rs_pipeline_opts best_o = base;
     const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
     for (uint32_t si = 0; si < 2 && result == RS_OK; ++si) {
+        // a strategy fixed in the options is the only one searched
+        if (base.strategy != RS_STRATEGY_AUTO && strategies[si] != base.strategy) continue;
         const bool tag = strategies[si] == RS_STRATEGY_TAG;
         // (regions per unit, steps per parent)
         uint32_t shapes[8][2];

@@ -175,10 +175,16 @@ def test_fetch_to_host_and_autotune(rs):
     s = wl.cascade_stream(n_total=1 << 18, mean=64, seed=5)
     pipe = wl.pipeline_cascade()
     want = oracle.run(pipe, s)
+    for fixed, allowed in (("signal", (0,)), ("auto", (0, 1))):
+        q = rs.Pipeline(pipe, strategy=fixed)
+        q.submit(rs.to_device(s), outputs=("count", "sum"))
+        b, ms = q.autotune(trials=1)
+        assert b["strategy"] in allowed and ms > 0      # a fixed strategy is the only one searched
+        q.close()
     p = rs.Pipeline(pipe, strategy="tag")
     out = p.submit(rs.to_device(s), outputs=("count", "sum"))
     best, ms = p.autotune(trials=2)
-    assert best["strategy"] in (0, 1) and ms > 0
+    assert best["strategy"] == 1 and ms > 0
     p.run()
     hc = torch.empty(s["R"], dtype=torch.int32).pin_memory()
     hs = torch.empty(s["R"], dtype=torch.int64).pin_memory()
