@@ -712,7 +712,7 @@ def main():
             except Exception as exc:   # report, do not lose the main line
                 extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
 
-    # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1), after the
+    # ---- CPU baseline: the oracle on the host's cores (rank 0, N = 1), after the
     # GPU sections so that its host-memory churn does not overlap the serving loop ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
