@@ -180,7 +180,7 @@ def run_reference(args, rank: int, world: int):
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for fn in ("rs_tag.cuh", "rs_tag.cu", "rs_tag2.cu", "rs_kernel.cu", "rs_device.cuh", "rs_internal.h"):
+    for fn in ("rs_tag.cuh", "rs_tag.cu", "rs_tag2.cu", "rs_kernel.cu", "rs_device.cuh", "rs_internal.h", "rs_api.cu"):
         with open(os.path.join(ROOT, "paper_2006_07478_b300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -212,7 +212,7 @@ typedef struct {
     uint32_t blocks_per_sm;            /* resident CTAs per SM (occupancy calculator)       */
     uint32_t chunk_parents;            /* tag strategy: parents node 1 loads per chunk, 32
                                           (one per lane) or 64 (two per lane, chosen when the
-                                          loaded streams' regions average under 3 elements);
+                                          loaded streams' regions average under 7 elements);
                                           0 for the signal strategy                         */
 } rs_stats;
 

@@ -534,8 +534,8 @@ static SmemLayout make_tag_layout(const rs_pipeline *p, uint32_t cpl)
 }
 
 // Parents per lane in the tag kernel's parent chunks: two when the loaded streams' regions
-// average fewer than 3 elements (chunk loads then recur every few windows and each one
-// carries twice the parents), else one.  Hashed streams give no element count: one.
+// average fewer than 7 elements (chunk loads then recur every window or two and each one
+// carries twice the parents; measured faster up to a mean of 6, even from 8), else one.  Hashed streams give no element count: one.
 static uint32_t tag_chunk_cpl(const rs_pipeline *p)
 {
     if (p->stages[0].kind != RS_ENUM_LOAD) return 1;
@@ -544,7 +544,7 @@ static uint32_t tag_chunk_cpl(const rs_pipeline *p)
         el += s.n_elements;
         regions += s.n_regions;
     }
-    return regions > 0 && el < 3 * regions ? 2u : 1u;
+    return regions > 0 && el < 7 * regions ? 2u : 1u;
 }
 
 // every merge-path stream of a plan has a power-of-two D (the planner then divides by

@@ -57,8 +57,8 @@ def test_hashed_uniform_10k(rs, strategy):
 def test_cascade_geometric(rs, strategy, mean):
     s = wl.cascade_stream(n_total=1 << 18, mean=mean, seed=7)
     _, st = _check(rs, wl.pipeline_cascade(), s, strategy, outputs=("count", "sum"))
-    # the tag kernel loads two parents per lane when regions average under 3 elements
-    assert st["launch"]["chunk_parents"] == (0 if strategy == "signal" else 64 if mean == 1 else 32)
+    # the tag kernel loads two parents per lane when regions average under 7 elements
+    assert st["launch"]["chunk_parents"] == (0 if strategy == "signal" else 64 if mean < 7 else 32)
 
 
 @pytest.mark.parametrize("strategy", STRATEGIES)
@@ -307,7 +307,7 @@ def test_two_parent_chunks(rs, R, csr):
     kw = dict(elements=el, ctx=_rand_u32(rng, R), parents=_rand_u32(rng, R))
     s = (wl.make_stream(offsets=(base + np.concatenate([[0], np.cumsum(L)])).astype(np.uint32), **kw) if csr
          else wl.make_stream(L, **kw))
-    expect_cp = 64 if el.size < 3 * R else 32
+    expect_cp = 64 if el.size < 7 * R else 32
     for pipe in (wl.pipeline_cascade(), wl.pipeline_graph_edges()):
         for opts in (dict(), dict(regions_per_unit=1, region_cost=2), dict(ensemble_width=32, tile_elements=32),
                      dict(ensemble_width=256)):
