@@ -634,7 +634,8 @@ static int resolve_strategy(const rs_pipeline *p)
 
 // Unit shapes (regions_per_unit, region_cost) rs_autotune tries for the tag strategy on
 // merge-path streams.
-static const uint32_t k_tag_shapes[][2] = {{4096, 1}, {8192, 1}, {16384, 1}, {2048, 1}, {1024, 4}, {256, 16}};
+static const uint32_t k_tag_shapes[][2] = {{4096, 1}, {8192, 1}, {16384, 1}, {2048, 1}, {1024, 4}, {256, 16},
+                                            {2048, 4}, {4096, 2}};
 
 // Workspace for either strategy with the current options and for every configuration
 // rs_autotune may try, so one workspace serves them all.
@@ -1158,7 +1159,8 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
         if (base.strategy != RS_STRATEGY_AUTO && strategies[si] != base.strategy) continue;
         const bool tag = strategies[si] == RS_STRATEGY_TAG;
         // (regions per unit, steps per parent)
-        uint32_t shapes[8][2];
+        uint32_t shapes[12][2];
+        static_assert(sizeof(k_tag_shapes) / sizeof(k_tag_shapes[0]) <= 12, "unit shapes fit the search");
         int n_shapes = 0;
         if (merge && tag) {
             for (const auto &sh : k_tag_shapes) {
