@@ -151,7 +151,8 @@ struct KParams {
     unsigned long long budget;
     unsigned long long spin_limit;
     uint32_t profile;             // accumulate the cycle breakdown
-    uint32_t plan_fill;           // planner writes every region's identity result (tag strategy)
+    uint32_t plan_fill;           // tag strategy: identity results written by the planner (regions a unit
+                                  // starts inside) and by the pipeline kernel (every other region)
     uint32_t cpl;                 // tag strategy: parents per lane in node 1's parent chunks (1 or 2)
     uint32_t plan_pow2;           // every merge-path stream's D is a power of two (planner divides by shifts)
     uint32_t plan_tile;           // parents per planner tile (RS_PLAN_TILE or RS_PLAN_TILE_SMALL)

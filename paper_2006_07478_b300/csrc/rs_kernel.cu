@@ -385,33 +385,6 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
                 }
             }
         }
-        // tag strategy: every region starts at the identity result (count 0, sum 0, min
-        // 0xFFFFFFFF), written here, before the pipeline kernel folds survivors into it
-        if (P.plan_fill) {
-            // lane l fills the four parents it holds in each round: 16-byte stores when the
-            // output arrays allow them, else one store per parent
-            const bool vec = (((uintptr_t)S.out_count | (uintptr_t)S.out_sum | (uintptr_t)S.out_min) & 15u) == 0;
-#pragma unroll
-            for (int k = 0; k < PLAN_ROUNDS; ++k) {
-                const uint32_t r = r_lo + 128u * k + 4u * lane;
-                if (vec && r + 4u <= r_hi) {
-                    if (P.want_count) *reinterpret_cast<uint4 *>(S.out_count + r) = make_uint4(0u, 0u, 0u, 0u);
-                    if (P.want_sum) {
-                        *reinterpret_cast<ulonglong2 *>(S.out_sum + r) = make_ulonglong2(0ull, 0ull);
-                        *reinterpret_cast<ulonglong2 *>(S.out_sum + r + 2) = make_ulonglong2(0ull, 0ull);
-                    }
-                    if (P.want_min)
-                        *reinterpret_cast<uint4 *>(S.out_min + r) =
-                            make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-                } else {
-                    for (uint32_t j = 0; j < 4u && r + j < r_hi; ++j) {
-                        if (P.want_count) S.out_count[r + j] = 0u;
-                        if (P.want_sum) S.out_sum[r + j] = 0ull;
-                        if (P.want_min) S.out_min[r + j] = 0xFFFFFFFFu;
-                    }
-                }
-            }
-        }
         // per round: the lane's element count, its inclusive scan, the round total
         uint32_t ls[PLAN_ROUNDS], incl[PLAN_ROUNDS];
         uint32_t tsum = 0;
@@ -507,6 +480,14 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
                             rc.head_off = oa;
                             rc.first_off = oa + Lr;
                             S.rec[u] = rc;
+                            // tag strategy: a region the unit starts inside is shared by two
+                            // units; its identity result is written here, before the pipeline
+                            // kernel (every other region's by the one processor that owns it)
+                            if (P.plan_fill && je < Lr) {
+                                if (P.want_count) S.out_count[r + j] = 0u;
+                                if (P.want_sum) S.out_sum[r + j] = 0ull;
+                                if (P.want_min) S.out_min[r + j] = 0xFFFFFFFFu;
+                            }
                         }
                         x = xn;
                         off += Lr;

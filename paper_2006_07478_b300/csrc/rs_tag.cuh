@@ -131,6 +131,10 @@ struct StreamRegs {
 struct TicketUnit {
     uint32_t stream, rs, base, rend, j0, j1;
     bool valid, work, fill;
+    // identity results this unit writes (merge-path units): its parents except the one it
+    // starts inside (skip_head) and the one the next unit starts inside (skip_tail), which
+    // the planner wrote
+    bool own, skip_head, skip_tail;
 };
 
 // stream of ticket t: the last stream whose unit_base <= t, by a 32-way warp search
@@ -153,7 +157,7 @@ __device__ __forceinline__ TicketUnit describe(const KParams &P, uint32_t t, uin
 {
     TicketUnit u;
     u.valid = t < P.total_units;
-    u.work = u.fill = false;
+    u.work = u.fill = u.own = u.skip_head = u.skip_tail = false;
     u.stream = u.rs = u.base = u.rend = u.j0 = u.j1 = 0;
     if (!u.valid) return u;
     u.stream = stream_of(P, t, lane);
@@ -174,11 +178,14 @@ __device__ __forceinline__ TicketUnit describe(const KParams &P, uint32_t t, uin
     const UnitRec ra = S.rec[lu], rb = S.rec[lu + 1];
     u.j0 = ra.j;
     u.j1 = rb.j;
-    if (u.j1 <= u.j0) return u;   // no elements: the planner wrote these parents' results
     const bool head = ra.j < ra.first_off;
     u.rs = head ? ra.i - 1 : ra.i;
     u.base = head ? ra.head_off : ra.first_off;
     u.rend = min(rb.i, S.R);
+    u.own = P.plan_fill != 0;
+    u.skip_head = head;
+    u.skip_tail = rb.j < rb.first_off;
+    if (u.j1 <= u.j0) return u;   // no elements: only identity results to write
     const bool bad = rb.i < ra.i || u.rs >= u.rend || (S.elements && u.j1 > S.n_elements);
     if (bad) {
         if (lane == 0) atomicOr(&P.hdr->status, ST_BAD_INPUT);
@@ -299,6 +306,9 @@ struct TagEngine {
     // items, signals, firings), folded into shared memory after every unit
     uint32_t ctr;
     bool stop, unit_bad, fill;
+    // identity results this unit writes: none (0), or its parents in [rlo + bit 1, re - bit 2)
+    // (bit 0 set); whole-parent units write all of theirs
+    uint32_t ownf;
 
     __device__ __forceinline__ TagEngine(const KParams &P_, uint32_t lane_, uint32_t wb_)
         : P(P_), lane(lane_), wb(wb_)
@@ -320,6 +330,7 @@ struct TagEngine {
         pl0 = pl0b = pl1b = pc = pcb = pp = ppb = 0;
         ctr = 0;
         stop = unit_bad = fill = false;
+        ownf = 0;
         S.elements = S.ctx = S.meta = nullptr;
         S.n_el = 0;
         S.csr = S.vec = false;
@@ -427,9 +438,10 @@ struct TagEngine {
             st1 = st0 + L0;
             cstart += __shfl_sync(FULLMASK, incl, 31);
         }
-        if (fill) {
-            if (in0) write_identity(r);
-            if (in1) write_identity(r + 1);
+        if (ownf) {
+            const uint32_t lo_own = rlo + ((ownf >> 1) & 1u), hi_own = re - ((ownf >> 2) & 1u);
+            if (in0 && r >= lo_own && r < hi_own) write_identity(r);
+            if (in1 && r + 1 >= lo_own && r + 1 < hi_own) write_identity(r + 1);
         }
         // end of the chunk's last parent (the start of parent cb + nin)
         const uint32_t last = min(CP, re - cb) - 1;
@@ -457,7 +469,9 @@ struct TagEngine {
             if (j1 == NONE) j1 = end_last;   // a whole-parent unit ends with its last parent
             load_start = NONE;
         } else {
-            load_start = end_last >= j1 ? NONE : end_last;
+            // past the unit's last element only empty parents remain: loaded only when the
+            // unit writes their identity results
+            load_start = (end_last >= j1 && !(ownf & 1u)) ? NONE : end_last;
         }
         if (load_start != NONE) issue_chunk();
         if (s_nx == NONE && ord_cur + 1 != ord_loaded) s_nx = nst()[(ord_cur + 1) & PRM()];
@@ -499,7 +513,8 @@ struct TagEngine {
             x[3] = u.rend;
             x[4] = u.j0;
             x[5] = u.j1;
-            x[6] = (u.valid ? 1u : 0u) | (u.work ? 2u : 0u) | (u.fill ? 4u : 0u);
+            x[6] = (u.valid ? 1u : 0u) | (u.work ? 2u : 0u) | (u.fill ? 4u : 0u) | (u.own ? 8u : 0u) |
+                   (u.skip_head ? 16u : 0u) | (u.skip_tail ? 32u : 0u);
         }
         __syncwarp();
         nxt_done = true;
@@ -520,6 +535,9 @@ struct TagEngine {
         u.valid = f & 1u;
         u.work = f & 2u;
         u.fill = f & 4u;
+        u.own = f & 8u;
+        u.skip_head = f & 16u;
+        u.skip_tail = f & 32u;
         __syncwarp();
         return u;
     }
@@ -1212,14 +1230,21 @@ struct TagEngine {
         return true;
     }
 
+    // identity results of parents [lo, hi) of a unit with no elements
+    __device__ __forceinline__ void own_fill(uint32_t lo, uint32_t hi) const
+    {
+        for (uint32_t r = lo + lane; r < hi; r += 32) write_identity(r);
+    }
+
     // ---------------------------------------------------------------------------
     // one work unit: elements [rj0, rj1) of the stream (rj1 = NONE: up to the end of its
     // last parent), parents from rs (whose first element is at offset base) below rend;
     // whole-parent units (wfill) also write every parent's identity result
 
     __device__ __forceinline__ void run_unit(uint32_t rs, uint32_t base, uint32_t rend, uint32_t rj0, uint32_t rj1,
-                                             bool wfill)
+                                             bool wfill, uint32_t rownf)
     {
+        ownf = rownf;
         j0 = rj0;
         j1 = rj1;
         cb = rs & ~(CP - 1);
@@ -1252,6 +1277,8 @@ struct TagEngine {
                 atomicOr(&P.hdr->status, ST_BAD_INPUT);
             }
         }
+        // parents after the unit's last element (empty ones) still get their identity results
+        while (ownf && !fill && !unit_bad && !stop && load_start != NONE) load_chunk();
         if (!unit_bad && j1 != NONE) ctr += lane == 1 ? j1 - j0 : (lane == 3 ? 1u : 0u);
         // fast windows: one ensemble each at nodes 0 and 1, W items, one firing of node 1
         ctr += (lane == 0 || lane == 4 || lane == 7) ? nfast : (lane == 5 ? nfast * W : 0u);
@@ -1286,7 +1313,18 @@ __global__ void __launch_bounds__(256, (V <= 4 ? 3 : 2)) rs_tag_kernel(const __g
                 E.drain_all();
                 E.set_stream(u.stream);
             }
-            E.run_unit(u.rs, u.base, u.rend, u.j0, u.j1, u.fill);
+            const uint32_t ownf =
+                u.fill ? 1u : (u.own ? (1u | (u.skip_head ? 2u : 0u) | (u.skip_tail ? 4u : 0u)) : 0u);
+            E.run_unit(u.rs, u.base, u.rend, u.j0, u.j1, u.fill, ownf);
+        } else if (u.own) {
+            // a unit with no elements: only its parents' identity results
+            if (u.stream != E.sidx) {
+                E.drain_all();
+                E.set_stream(u.stream);
+            }
+            const uint32_t lo = u.rs + (u.skip_head ? 1u : 0u);
+            const uint32_t hi = u.rend >= (u.skip_tail ? 1u : 0u) ? u.rend - (u.skip_tail ? 1u : 0u) : 0u;
+            E.own_fill(lo, hi);
         }
         u = E.next_unit();
     }

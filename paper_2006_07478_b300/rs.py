@@ -510,11 +510,15 @@ def results_to_numpy(out: dict) -> dict:
 
 def run_stream(stages, stream: dict, strategy="tag", outputs=("count", "sum", "min"), **opts):
     """One-shot helper: upload a host stream, run the pipeline once, return numpy
-    results and the run's statistics."""
+    results and the run's statistics.  The output arrays start filled with a sentinel,
+    so a region the run leaves unwritten shows up in the results."""
     import torch
     p = Pipeline(stages, strategy=strategy, **opts)
     dev = to_device(stream)
     out = p.submit(dev, outputs=outputs)
+    for k in ("count", "sum", "min"):
+        if out.get(k) is not None:
+            out[k].fill_(0x5A5A5A5A)
     p.run()
     st = p.stats()
     torch.cuda.synchronize()
