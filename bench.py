@@ -246,7 +246,7 @@ def bench_graph(rs, torch, peak):
 
 
 def bench_region_sizes(rs, torch):
-    """The paper's region-sum benchmark (Section 6, Figures figFixed and figVariable): one
+    """The paper's region-sum benchmark (Section 5, Figures figFixed and figVariable): one
     2^26-element array, enumerate + sum per region, regions of a fixed size or of sizes
     uniform on 0..max; both strategies at their default options.  Per size: time per run,
     items/s and node 1's active-lane fraction (signals cut ensembles at region boundaries,

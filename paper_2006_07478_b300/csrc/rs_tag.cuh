@@ -30,9 +30,11 @@
 //   * The aggregate (Section 4.2's begin/run/end per parent) folds each ensemble into
 //     the region outputs with integer reductions: one per ensemble when it holds a
 //     single region, otherwise one per run of equal tags in a lane.  count, sum and min
-//     are associative and commutative, so the result is bit-exact in any order.  The
-//     planner has written every region's identity result before this kernel starts,
-//     which covers empty regions and regions whose elements are split between units.
+//     are associative and commutative, so the result is bit-exact in any order.  Every
+//     region's output holds the identity result before its first fold: the planner
+//     writes it for a region two units share (the one a unit starts inside), and the
+//     processor whose unit owns a region writes it when it loads that region's parent,
+//     before any fold into it; this also covers empty regions.
 //
 // Rings and the parent stream are drained when a processor moves to a unit of another
 // stream and when it runs out of units.  Nothing waits on another warp: the kernel has

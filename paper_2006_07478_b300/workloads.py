@@ -204,7 +204,7 @@ def cascade_stream(n_total: int = 1 << 26, mean: float = 32, seed: int = 7,
 
 
 def pipeline_region_sum() -> list:
-    """The paper's region-sum benchmark (Section 6, Figures figFixed and figVariable):
+    """The paper's region-sum benchmark (Section 5, Figures figFixed and figVariable):
     enumerate each region of an integer array and reduce it to its sum (and count)."""
     return [("enum_load",), ("aggregate",)]
 

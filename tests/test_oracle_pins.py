@@ -267,3 +267,141 @@ def test_invalid_pipelines_rejected():
         oracle.run([("enum_hash",), ("filter_mod", 0, 0), ("aggregate",)], s)
     with pytest.raises(ValueError):
         oracle.run([("enum_hash",), ("map_mul", 1, 0)], s)
+
+
+# ---------------------------------------------------------------------------
+# filter_weight_lt (keep edge u -> v iff w(v) < w(u), w(v) = hash32(v, salt)): pinned by
+# what a strict comparison of a bijective weight must satisfy, and tied to the pinned
+# direction of the threshold filter
+
+
+def _edge_stream(src, dst):
+    """One region per directed edge: parent id = source vertex, its only element = dst."""
+    src = np.asarray(src, dtype=np.uint32)
+    return wl.make_stream(np.ones(src.shape[0], dtype=np.uint32), parents=src,
+                          elements=np.asarray(dst, dtype=np.uint32))
+
+
+WPIPE = [("enum_load",), ("filter_weight_lt", wl.WEIGHT_SALT), ("aggregate",)]
+
+
+def test_weight_filter_self_loops_never_survive():
+    v = np.arange(5000, dtype=np.uint32) * 7919
+    res = oracle.run(WPIPE, _edge_stream(v, v))
+    assert not res["count"].any() and (res["min"] == M32).all()
+
+
+def test_weight_filter_is_antisymmetric_with_pass_rate_one_half():
+    rng = np.random.default_rng(21)
+    n = 40000
+    u = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    v = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    v[u == v] ^= 1
+    fwd = oracle.run(WPIPE, _edge_stream(u, v))["count"].astype(np.int64)
+    bwd = oracle.run(WPIPE, _edge_stream(v, u))["count"].astype(np.int64)
+    # hash32 is a bijection in its first argument, so w(u) != w(v): exactly one direction
+    assert np.array_equal(fwd + bwd, np.ones(n, dtype=np.int64))
+    assert abs(fwd.mean() - 0.5) < 5 * np.sqrt(0.25 / n)
+
+
+def test_weight_filter_ranks_a_complete_digraph():
+    """Every vertex of a complete digraph (no self-loops) keeps the out-edges to the
+    vertices of smaller weight: the counts are the weight ranks, a permutation of
+    0..n-1 (a strict total order), and min dst is the smallest id of lower rank."""
+    n = 300
+    ids = (np.arange(n, dtype=np.uint64) * 2654435761 % (1 << 32)).astype(np.uint32)
+    L = np.full(n, n - 1, dtype=np.uint32)
+    dst = np.concatenate([np.delete(ids, i) for i in range(n)])
+    res = oracle.run(WPIPE, wl.make_stream(L, parents=ids, elements=dst))
+    rank = res["count"].astype(np.int64)
+    assert np.array_equal(np.sort(rank), np.arange(n))
+    for i in range(n):
+        lower = ids[rank < rank[i]]
+        want = int(lower.min()) if lower.size else M32
+        assert int(res["min"][i]) == want
+
+
+def test_weight_filter_is_the_threshold_filter_at_the_parents_weight():
+    """keep w(x) < w(p) is the context-free threshold filter keep hash32(x, salt) < theta
+    with theta = w(p): the threshold filter's direction and rates are pinned above."""
+    rng = np.random.default_rng(22)
+    for p in (0, 1, 12345, M32, int(rng.integers(0, 1 << 32))):
+        x = rng.integers(0, 1 << 32, 3000, dtype=np.uint64).astype(np.uint32)
+        a = oracle.run(WPIPE, _edge_stream(np.full(x.shape[0], p), x))["count"]
+        theta = oracle.hash32(p, wl.WEIGHT_SALT)
+        b = oracle.run([("enum_load",), ("filter_hash_ctx", wl.WEIGHT_SALT, theta), ("aggregate",)],
+                       wl.make_stream(np.ones(x.shape[0], dtype=np.uint32), elements=x))["count"]
+        assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# expand (n = hash32(x, salt) mod (k + 1) outputs hash32(x, salt + 1 + j), j < n): pinned
+# by bounds, the uniform law of n, the modular relation between fan-outs, and the
+# independence of the output values from n
+
+
+def _single_items(n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    return wl.make_stream(np.ones(n, dtype=np.uint32), elements=x)
+
+
+def _expand_counts(s, k, salt=9):
+    return oracle.run([("enum_load",), ("expand", k, salt), ("aggregate",)], s)
+
+
+def test_expand_outputs_are_bounded_and_uniform_in_number():
+    n = 60000
+    s = _single_items(n, 23)
+    for k in (1, 2, 3, 5, 8):
+        c = _expand_counts(s, k)["count"].astype(np.int64)
+        assert c.min() >= 0 and c.max() <= k
+        # n = h mod (k + 1) of a uniform 32-bit h: every value 0..k about n / (k + 1) times
+        freq = np.bincount(c, minlength=k + 1)
+        p = 1.0 / (k + 1)
+        assert np.all(np.abs(freq - n * p) < 5 * np.sqrt(n * p * (1 - p))), (k, freq)
+        # mean yield k / 2 (variance ((k + 1)^2 - 1) / 12 per item)
+        sd = np.sqrt(((k + 1) ** 2 - 1) / 12.0 / n)
+        assert abs(c.mean() - k / 2.0) < 5 * sd
+
+
+def test_expand_counts_follow_the_modulus():
+    """h mod 2 = (h mod 4) mod 2 and h mod 4 = (h mod 8) mod 4: the counts at fan-outs 1,
+    3 and 7 are reductions of one another (a wrong modulus breaks this)."""
+    s = _single_items(30000, 24)
+    c1 = _expand_counts(s, 1)["count"].astype(np.int64)
+    c3 = _expand_counts(s, 3)["count"].astype(np.int64)
+    c7 = _expand_counts(s, 7)["count"].astype(np.int64)
+    assert np.array_equal(c1, c3 % 2)
+    assert np.array_equal(c3, c7 % 4)
+
+
+def test_expand_output_values_do_not_depend_on_the_count():
+    """The j-th output is the same value at every fan-out (the output sequence does not
+    depend on k), and it is drawn with a salt other than the count's: among items with
+    one output, that output's residue mod (k + 1) is 1 only about 1 / (k + 1) of the time."""
+    n = 40000
+    s = _single_items(n, 25)
+    r1, r3 = _expand_counts(s, 1), _expand_counts(s, 3)
+    one = (r1["count"] == 1) & (r3["count"] >= 1)
+    assert one.sum() > n // 4
+    # with one output at fan-out 1 the sum is y_0; at fan-out 3 the min is <= y_0 and
+    # with exactly one output there it equals y_0
+    assert np.all(r3["min"][one].astype(np.int64) <= r1["sum"][one].astype(np.int64))
+    both1 = (r1["count"] == 1) & (r3["count"] == 1)
+    assert np.array_equal(r1["sum"][both1], r3["sum"][both1])
+    k = 3
+    y0 = r3["sum"][r3["count"] == 1].astype(np.int64)
+    rate = np.mean(y0 % (k + 1) == 1)
+    p = 1.0 / (k + 1)
+    assert abs(rate - p) < 5 * np.sqrt(p * (1 - p) / y0.size)
+
+
+def test_expand_then_keep_all_adds_up_exactly():
+    s = wl.hashed_uniform_stream(3000, 40, 3)
+    a = oracle.run([("enum_hash",), ("expand", 4, 17), ("aggregate",)], s)
+    b = oracle.run([("enum_hash",), ("expand", 4, 17), ("filter_mod", 1, 0), ("aggregate",)], s)
+    for key in ("count", "sum", "min"):
+        assert np.array_equal(a[key], b[key])
+    # every region's count is at most k times its length
+    assert np.all(a["count"].astype(np.int64) <= 4 * s["len"].astype(np.int64))
