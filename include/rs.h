@@ -321,7 +321,9 @@ rs_status rs_server_destroy(rs_server *s);
  * The call allocates nothing: no cudaMalloc, cudaFree or cudaMallocHost, and no
  * allocating library routine.
  *   - The first call on a device (with that device current) looks up the array's
- *     device address once; make that first call before any stream capture.
+ *     device address once; make that first call before any stream capture.  The
+ *     address is kept until the process exits, so resetting a device
+ *     (cudaDeviceReset) while the library is loaded is not supported here.
  *   - RS_ERR_CAPACITY, with nothing enqueued, if the submitted streams need more than
  *     16 MiB of scratch (rs_workspace_size reports the need) or more than 64 streams
  *     are submitted.

@@ -43,6 +43,12 @@ struct FixedPlan {
     StreamPlan sp[RS_NOALLOC_MAX_STREAMS];
 };
 
+// rs_run_noalloc's stream table, passed by value as a kernel parameter (9.7 KB, within
+// the 32 KB parameter space of sm_70 and later)
+struct NoallocTable {
+    DevStream s[RS_NOALLOC_MAX_STREAMS];
+};
+
 struct rs_pipeline {
     rs_stage_desc stages[RS_MAX_STAGES];
     uint32_t n_stages;
@@ -66,7 +72,7 @@ struct rs_pipeline {
     uint32_t t_cap = 0, t_count = 0;
     // stream table and plan for rs_run_noalloc, part of the pipeline object so that call
     // needs no allocation of its own
-    DevStream noalloc_table[RS_NOALLOC_MAX_STREAMS];
+    NoallocTable noalloc_table;
     FixedPlan noalloc_plan;
     // launch shape of the last prepared launch (reported by rs_get_stats)
     uint32_t last_grid = 0, last_block = 0, last_smem = 0, last_bps = 0, last_cp = 0;
@@ -1282,6 +1288,19 @@ static rs_status noalloc_scratch(void **out)
     return RS_OK;
 }
 
+// copies the first n entries of the table (8-byte words; sizeof(DevStream) is a multiple
+// of 8) into the scratch array
+__global__ void __launch_bounds__(256) rs_noalloc_table_kernel(const __grid_constant__ NoallocTable t, DevStream *dst,
+                                                               uint32_t n)
+{
+    const uint32_t words = n * (uint32_t)(sizeof(DevStream) / 8);
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&t.s[0]);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) d[i] = src[i];
+}
+
+static_assert(sizeof(DevStream) % 8 == 0, "the table copy moves 8-byte words");
+
 static void make_plan_fixed(const rs_pipeline *p, int strategy, FixedPlan *pl)
 {
     const size_t ns = p->streams.size();
@@ -1320,7 +1339,7 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     for (size_t i = 0; i < ns; ++i) {
         const rs_stream_desc &s = p->streams[i];
         const StreamPlan &q = pl.sp[i];
-        DevStream &d = p->noalloc_table[i];
+        DevStream &d = p->noalloc_table.s[i];
         memset(&d, 0, sizeof d);
         d.parents = s.parents;
         d.len = s.region_len;
@@ -1433,9 +1452,10 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     // the scratch keeps the previous call's contents: clear the part that must start at 0
     cudaStream_t cs = (cudaStream_t)stream;
     if ((e = cudaMemsetAsync(wsb, 0, pl.zero_end, cs)) != cudaSuccess) return cuda_fail(e);
-    if ((e = cudaMemcpyAsync(wsb + pl.table_off, p->noalloc_table, ns * sizeof(DevStream), cudaMemcpyHostToDevice,
-                             cs)) != cudaSuccess)
-        return cuda_fail(e);
+    // the stream table reaches the device as the parameter of a copy kernel: no staging
+    // buffer and no copy from pageable host memory
+    rs_noalloc_table_kernel<<<1, 256, 0, cs>>>(p->noalloc_table, (DevStream *)(wsb + pl.table_off), (uint32_t)ns);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
     if (P.plan_tiles > 0) {
         int pg = (int)((P.plan_tiles + 7) / 8);
         if (pg > p->n_sm * 8) pg = p->n_sm * 8;

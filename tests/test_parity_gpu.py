@@ -355,3 +355,93 @@ def test_region_sum_sizes(rs, strategy, size, variable):
         assert frac <= bound + 1e-9, (frac, bound)
     else:
         assert frac >= 0.85, frac
+
+
+def test_device_budget_exhaustion_is_reported_and_recoverable(rs):
+    """A scheduler budget of one sweep per claimed unit cannot finish units of many
+    parents: every processor stops at its first such unit, the device reports a stall
+    (RS_ERR_STALL through rs_get_stats) and the kernel returns.  A later run with the
+    default budget on the same pipeline object is exact."""
+    import torch
+    s = wl.cascade_stream(n_total=1 << 18, mean=64, seed=9)
+    pipe = wl.pipeline_cascade()
+    p = rs.Pipeline(pipe, strategy="signal", device_budget=1, regions_per_unit=128)
+    out = p.submit(rs.to_device(s), outputs=("count", "sum"))
+    p.run()
+    st = p.stats(raise_on_error=False)
+    assert st["status"] == rs.RS_ERR_STALL and (st["device_status"] & 1)
+    p.set_opts(device_budget=0)       # back to the default budget
+    p.run()
+    st = p.stats()
+    torch.cuda.synchronize()
+    want = oracle.run(pipe, s)
+    got = rs.results_to_numpy(out)
+    assert st["device_status"] == 0
+    for k in ("count", "sum"):
+        assert np.array_equal(got[k], want[k]), k
+    p.close()
+
+
+def test_graph_full_size_sampled_with_every_hub(rs):
+    """The graph workload at its full size (2^22 vertices, 2^26 edges, out-degree capped
+    at 2^16) in the bench's launch configuration (autotuned): every vertex of degree
+    >= 2^10 (the hubs, up to 65,536 edges) and 4,000 random vertices against the oracle
+    one by one, and the count/min relation on every vertex."""
+    g = wl.graph_stream()
+    pipe = wl.pipeline_graph_edges()
+    p = rs.Pipeline(pipe, strategy="auto")
+    out = p.submit(rs.to_device(g), outputs=("count", "min"))
+    p.autotune(trials=1)
+    p.run()
+    st = p.stats()
+    got = rs.results_to_numpy(out)
+    assert st["device_status"] == 0
+    deg = np.diff(g["offsets"].astype(np.int64))
+    rng = np.random.default_rng(2)
+    idx = np.unique(np.concatenate([np.flatnonzero(deg >= 1 << 10), rng.integers(0, g["R"], 4000),
+                                    [0, g["R"] - 1]]))
+    assert deg[idx].max() == 1 << 16
+    want = oracle.run_sampled(pipe, g, idx)
+    assert np.array_equal(got["count"][idx], want["count"])
+    assert np.array_equal(got["min"][idx], want["min"])
+    cnt = got["count"].astype(np.int64)
+    assert np.all(cnt <= deg) and np.all((got["min"] == 0xFFFFFFFF) == (cnt == 0))
+    assert int(cnt.sum()) == st["items"][-1]
+    p.close()
+
+
+def test_batched_full_size_after_graph_replay(rs):
+    """The batched workload at its full size (4,096 streams, lognormal sizes with median
+    2^14, regions U{1..512}) in the bench's launch configuration: options from the
+    autotuner, one launch captured in a CUDA graph and replayed.  Per stream, its first
+    and last regions and 32 random ones against the oracle one by one."""
+    import torch
+    streams = wl.batched_streams()
+    pipe = wl.pipeline_hash_filter_map()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        p = rs.Pipeline(pipe, strategy="auto")
+        outs = [p.submit(rs.to_device(s)) for s in streams]
+        p.autotune(trials=1)
+        for o in outs:
+            for k in ("count", "sum", "min"):
+                o[k].fill_(-1)
+        p.graph_capture()
+        p.graph_launch()
+        p.graph_launch()
+    side.synchronize()
+    st = p.stats()
+    assert st["device_status"] == 0
+    rng = np.random.default_rng(4)
+    kept = 0
+    for s, o in zip(streams, outs):
+        got = rs.results_to_numpy(o)
+        R = s["R"]
+        idx = np.unique(np.concatenate([[0, R - 1], rng.integers(0, R, 32)]))
+        want = oracle.run_sampled(pipe, s, idx)
+        for k in ("count", "sum", "min"):
+            assert np.array_equal(got[k][idx], want[k]), k
+        kept += int(got["count"].astype(np.int64).sum())
+    assert kept == st["items"][-1]
+    p.graph_release()
+    p.close()

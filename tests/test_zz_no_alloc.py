@@ -58,11 +58,11 @@ def test_noalloc_equals_run_on_two_calls(rs, ci):
     p.close()
 
 
-def test_noalloc_rejects_scratch_beyond_its_fixed_size(rs):
-    """A loaded stream of 2^31 parents needs more than the fixed 16 MiB of scratch
-    under any unit shape (its planner alone keeps one 8-byte look-back word per 1024
-    parents: 16 MiB): the call returns RS_ERR_CAPACITY before enqueuing anything, so the
-    descriptor's placeholder pointers are never dereferenced."""
+def test_noalloc_scratch_need_is_reported_without_a_run(rs):
+    """The size rule on the host alone: a loaded stream of 2^31 parents needs more than
+    the fixed 16 MiB of scratch under any unit shape (its planner alone keeps one 8-byte
+    look-back word per 1024 parents).  Only host-side calls see this descriptor, whose
+    pointers are placeholders; nothing is run with it."""
     p = rs.Pipeline(wl.pipeline_cascade(), strategy="tag")
     d = rs.StreamDesc()
     d.n_regions = 1 << 31
@@ -72,7 +72,24 @@ def test_noalloc_rejects_scratch_beyond_its_fixed_size(rs):
     d.out_count = ctypes.c_void_p(0x3000)
     sid = ctypes.c_uint64()
     assert rs.lib().rs_stream_submit(p._h, ctypes.byref(d), ctypes.byref(sid)) == rs.RS_OK
-    need = p.workspace_bytes()
-    assert need > 16 << 20
+    assert p.workspace_bytes() > 16 << 20
+    p.close()
+
+
+def test_noalloc_rejects_scratch_beyond_its_fixed_size(rs):
+    """A real stream whose scratch needs more than the fixed 16 MiB: 2^22 one-element
+    regions cut into units of one parent step each (2^23 units of 16 bytes = 128 MiB of
+    unit records).  The call returns RS_ERR_CAPACITY with nothing enqueued, and the
+    outputs keep their sentinel."""
+    import torch
+    R = 1 << 22
+    lens = np.ones(R, dtype=np.uint32)
+    s = wl.make_stream(lens, elements=np.arange(R, dtype=np.uint32), ctx=np.zeros(R, dtype=np.uint32))
+    p = rs.Pipeline(wl.pipeline_cascade(), strategy="tag", regions_per_unit=1, region_cost=1)
+    out = p.submit(rs.to_device(s), outputs=("count", "sum"))
+    out["count"].fill_(-7)
+    assert p.workspace_bytes() > 16 << 20
     assert rs.lib().rs_run_noalloc(p._h, None) == rs.RS_ERR_CAPACITY
+    torch.cuda.synchronize()
+    assert bool((out["count"] == -7).all())
     p.close()
