@@ -35,6 +35,7 @@ OPS = {
     "map_mul": 20,
     "expand": 30,
     "aggregate": 40,
+    "emit": 50,
 }
 
 
@@ -71,6 +72,9 @@ def lib():
         L.ora_run_sampled.argtypes = [ctypes.POINTER(OraStage), ctypes.c_int, ctypes.c_uint64,
                                       P, P, P, P, P, P, ctypes.c_uint64, P, P, P]
         L.ora_run_sampled.restype = ctypes.c_int
+        L.ora_run_emit.argtypes = [ctypes.POINTER(OraStage), ctypes.c_int, ctypes.c_uint64,
+                                   P, P, P, P, P, ctypes.c_uint32, P, P]
+        L.ora_run_emit.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -135,3 +139,39 @@ def run_sampled(pipeline, stream: dict, idx) -> dict:
     if rc != 0:
         raise ValueError("oracle rejected the pipeline, stream or sample")
     return {"count": count, "sum": sm, "min": mn}
+
+
+def fanout_product(pipeline) -> int:
+    """F: the product of the element stages' maximum fan-outs (an expansion's k, 1
+    otherwise); region r's segment of an emit sink's output holds F * L_r values."""
+    F = 1
+    for st in pipeline[1:-1]:
+        if st[0] == "expand":
+            F *= max(1, int(st[1]))
+    return F
+
+
+def _offsets(stream: dict) -> np.ndarray:
+    if stream.get("offsets") is not None:
+        o = stream["offsets"].astype(np.int64)
+        return o - o[0]
+    return np.concatenate(([0], np.cumsum(stream["len"].astype(np.int64))))
+
+
+def run_emit(pipeline, stream: dict) -> dict:
+    """Emit sink: {count u32[R], values u32[F * N], start i64[R + 1]}; region r's
+    survivors are values[start[r] : start[r] + count[r]], in stream order
+    (start[r] = F * (off_r - off_0))."""
+    R = int(stream["R"])
+    F = fanout_product(pipeline)
+    off = _offsets(stream)
+    N = int(off[-1])
+    values = np.zeros(max(1, F * N), dtype=np.uint32)
+    count = np.empty(R, dtype=np.uint32)
+    st = _stages(pipeline)
+    rc = lib().ora_run_emit(st, len(pipeline), R, _ptr(stream.get("parents")), _ptr(stream.get("len")),
+                            _ptr(stream.get("offsets")), _ptr(stream.get("elements")), _ptr(stream.get("ctx")),
+                            F, _ptr(values), _ptr(count))
+    if rc != 0:
+        raise ValueError("oracle rejected the pipeline or stream")
+    return {"count": count, "values": values, "start": F * off}

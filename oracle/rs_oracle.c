@@ -14,7 +14,9 @@
  *   - Section 2.1: a linear pipeline; each node turns one input into 0..k outputs.
  *   - Section 4 / Figure 4: aggregation closes the parent: begin() resets the
  *     accumulator, run() folds each surviving item in, end() emits one result per
- *     parent -- including parents none of whose elements survive.
+ *     parent -- including parents none of whose elements survive.  Section 4's other
+ *     option, results derived from individual elements stripped of their parent, is
+ *     the emit sink (ora_run_emit): the survivors themselves, grouped by region.
  *   - Lemma 1 (precise delivery) says the signal/credit protocol only delivers
  *     region boundaries; it never changes which items meet which context.  So the
  *     method's result is exactly the plain definition below: walk the regions in
@@ -45,7 +47,10 @@ enum {
     ORA_FILTER_WEIGHT_LT = 12, /* keep hash32(x,salt) < hash32(p_r,salt) (p0=salt) */
     ORA_MAP_MUL = 20,       /* x <- a*x + b mod 2^32               (p0=a, p1=b) */
     ORA_EXPAND = 30,        /* n = hash32(x,salt) mod (k+1) outputs hash32(x, salt+1+j) (p0=salt, fanout=k) */
-    ORA_AGGREGATE = 40      /* count, sum (u64), min                            */
+    ORA_AGGREGATE = 40,     /* count, sum (u64), min                            */
+    ORA_EMIT = 50           /* each survivor, stripped of its parent, into the
+                               region's segment of the output array (Section 4's
+                               alternative to aggregation)                       */
 };
 
 typedef struct {
@@ -86,6 +91,7 @@ typedef struct {
     uint32_t count;
     uint64_t sum;
     uint32_t min;
+    uint32_t *seg;   /* ORA_EMIT: the region's segment of the output array, else NULL */
 } ora_acc;
 
 /* Push one item x (already produced by stage s-1) through stages s..n-1 of region r,
@@ -120,6 +126,12 @@ static void push_item(const ora_stage *st, int n, int s, uint32_t x, uint64_t r,
             acc->sum += (uint64_t)x;
             if (x < acc->min) acc->min = x;
             return;
+        case ORA_EMIT:
+            /* results derived from individual elements, in stream order; the count
+             * says how many the region produced */
+            if (acc->seg) acc->seg[acc->count] = x;
+            acc->count += 1u;
+            return;
         default:
             return;
         }
@@ -131,7 +143,7 @@ static int check_stages(const ora_stage *st, int n)
 {
     if (n < 2 || n > 8) return -1;
     if (st[0].op != ORA_ENUM_HASH && st[0].op != ORA_ENUM_LOAD) return -1;
-    if (st[n - 1].op != ORA_AGGREGATE) return -1;
+    if (st[n - 1].op != ORA_AGGREGATE && st[n - 1].op != ORA_EMIT) return -1;
     for (int s = 1; s < n - 1; ++s) {
         int op = st[s].op;
         if (op == ORA_FILTER_MOD && st[s].p0 == 0) return -1;
@@ -149,7 +161,7 @@ static void run_range(const ora_stage *st, int n, const ora_stream *s, const uin
                       uint32_t *count, uint64_t *sum, uint32_t *mn)
 {
     for (uint64_t r = r_begin; r < r_end; ++r) {
-        ora_acc acc = {0u, 0u, 0xFFFFFFFFu};               /* begin() */
+        ora_acc acc = {0u, 0u, 0xFFFFFFFFu, NULL};         /* begin() */
         uint32_t parent = s->parents ? s->parents[r] : (uint32_t)r;
         uint32_t t = s->ctx ? s->ctx[r] : 0u;
         uint64_t L = off[r + 1] - off[r];
@@ -244,6 +256,35 @@ int ora_run_sampled(const ora_stage *st, int n, uint64_t R, const uint32_t *pare
         if (count) count[k] = c1;
         if (sum) sum[k] = su1;
         if (mn) mn[k] = mi1;
+    }
+    free(off);
+    return 0;
+}
+
+/* Sink ORA_EMIT: every surviving value of region r goes, in stream order, to
+ * values[F * (off_r - off_0) + j], j = 0..count[r]-1, where off_r is the region's first
+ * element index and F the product of the element stages' maximum fan-outs (so region r
+ * owns F * L_r slots, enough for any survivors).  values holds F * N entries. */
+int ora_run_emit(const ora_stage *st, int n, uint64_t R, const uint32_t *parents,
+                 const uint32_t *len, const uint32_t *offsets, const uint32_t *elements,
+                 const uint32_t *ctx, uint32_t F, uint32_t *values, uint32_t *count)
+{
+    if (check_stages(st, n) || st[n - 1].op != ORA_EMIT) return -1;
+    if (!len && !offsets && R > 0) return -1;
+    if (st[0].op == ORA_ENUM_LOAD && !elements && R > 0) return -1;
+    ora_stream s = {R, parents, len, offsets, elements, ctx};
+    uint64_t *off = make_offsets(&s);
+    if (!off) return -1;
+    for (uint64_t r = 0; r < R; ++r) {
+        ora_acc acc = {0u, 0u, 0xFFFFFFFFu, values + (uint64_t)F * (off[r] - off[0])};
+        uint32_t parent = parents ? parents[r] : (uint32_t)r;
+        uint32_t t = ctx ? ctx[r] : 0u;
+        uint64_t L = off[r + 1] - off[r];
+        for (uint64_t i = 0; i < L; ++i) {
+            uint32_t x = (st[0].op == ORA_ENUM_HASH) ? ora_hash32(parent, (uint32_t)i) : elements[off[r] + i];
+            push_item(st, n, 1, x, r, parent, t, &acc);
+        }
+        count[r] = acc.count;
     }
     free(off);
     return 0;

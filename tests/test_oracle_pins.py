@@ -405,3 +405,58 @@ def test_expand_then_keep_all_adds_up_exactly():
         assert np.array_equal(a[key], b[key])
     # every region's count is at most k times its length
     assert np.all(a["count"].astype(np.int64) <= 4 * s["len"].astype(np.int64))
+
+
+# ---------------------------------------------------------------------------
+# emit sink (element results stripped of their parent, Section 4): pinned by the closed
+# form of the identity pipeline and by the aggregate's pinned count / sum / min
+
+
+def _as_emit(pipe):
+    return list(pipe[:-1]) + [("emit",)]
+
+
+def test_emit_identity_pipeline_returns_each_region_in_order():
+    rng = np.random.default_rng(31)
+    L = rng.integers(0, 30, 400)
+    L[::9] = 0
+    n = int(L.sum())
+    el = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    s = wl.make_stream(L, elements=el)
+    res = oracle.run_emit([("enum_load",), ("emit",)], s)
+    assert np.array_equal(res["count"], L.astype(np.uint32))
+    assert np.array_equal(res["values"][:n], el)       # F = 1: the segments tile the array
+    assert np.array_equal(res["start"], np.concatenate(([0], np.cumsum(L))))
+
+
+def _segments(res):
+    return [res["values"][res["start"][r]:res["start"][r] + int(res["count"][r])] for r in range(len(res["count"]))]
+
+
+@pytest.mark.parametrize("which", ["cascade", "hashed", "expand", "graph"])
+def test_emit_agrees_with_the_aggregate(which):
+    if which == "cascade":
+        pipe, s = wl.pipeline_cascade(), wl.cascade_stream(n_total=40000, mean=24, seed=3)
+    elif which == "hashed":
+        pipe, s = wl.pipeline_hash_filter_map(), wl.hashed_uniform_stream(2000, 64, 5)
+    elif which == "expand":
+        pipe = [("enum_hash",), ("expand", 3, 5), ("filter_mod", 3, 1), ("expand", 2, 8), ("aggregate",)]
+        s = wl.hashed_uniform_stream(1500, 20, 6)
+    else:
+        pipe, s = wl.pipeline_graph_edges(), wl.graph_stream(V=3000, E=30000, cap=2000, seed=7)
+    agg = oracle.run(pipe, s)
+    em = oracle.run_emit(_as_emit(pipe), s)
+    assert np.array_equal(em["count"], agg["count"])
+    F = oracle.fanout_product(pipe)
+    L = np.diff(em["start"]) // F
+    assert np.all(em["count"].astype(np.int64) <= F * L)
+    segs = _segments(em)
+    sums = np.array([int(x.astype(np.uint64).sum()) for x in segs], dtype=np.uint64)
+    mins = np.array([int(x.min()) if x.size else M32 for x in segs], dtype=np.uint32)
+    assert np.array_equal(sums, agg["sum"])
+    assert np.array_equal(mins, agg["min"])
+    # the slots past each region's count are untouched
+    used = np.zeros(em["values"].shape[0], dtype=bool)
+    for r in range(s["R"]):
+        used[em["start"][r]:em["start"][r] + int(em["count"][r])] = True
+    assert not em["values"][~used].any()
