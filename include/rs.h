@@ -63,7 +63,13 @@ typedef enum {
     RS_FILTER = 3,      /* 0 or 1 output per input                                        */
     RS_MAP = 4,         /* exactly 1 output per input                                     */
     RS_EXPAND = 5,      /* 0..max_fanout outputs per input                                */
-    RS_AGGREGATE = 6    /* per-region count / sum / min of the surviving values           */
+    RS_AGGREGATE = 6,   /* per-region count / sum / min of the surviving values           */
+    RS_EMIT = 7         /* the surviving values themselves, stripped of their parent
+                           (Section 4's alternative to aggregation): region r's survivors
+                           land in its own segment of the stream's out_values array,
+                           out_values[F * (off_r - off_0) ...], F = the product of the
+                           element stages' max_fanout, in an unspecified order, and
+                           out_count[r] says how many.  Needs CSR region_offsets.        */
 } rs_stage_kind;
 
 /* Operations.  hash32(a, b) = fmix32(a XOR fmix32(b XOR 0x9E3779B9)) where fmix32 is
@@ -86,7 +92,7 @@ typedef struct {
     uint32_t params[4];
 } rs_stage_desc;
 
-#define RS_MAX_STAGES 6     /* enumerate + up to 4 element stages + aggregate */
+#define RS_MAX_STAGES 6     /* enumerate + up to 4 element stages + aggregate or emit */
 
 /* ---- options ----------------------------------------------------------------- */
 
@@ -132,7 +138,7 @@ typedef struct {
 rs_status rs_default_opts(rs_pipeline_opts *opts);
 
 /* Create a pipeline from a stage list: stages[0] is RS_ENUM_HASH or RS_ENUM_LOAD,
- * stages[n-1] is RS_AGGREGATE, the ones between are FILTER / MAP / EXPAND.
+ * stages[n-1] is RS_AGGREGATE or RS_EMIT, the ones between are FILTER / MAP / EXPAND.
  * Checks (RS_ERR_INVALID): 2 <= n <= RS_MAX_STAGES; kinds/ops/params legal; FILTER
  * and MAP have max_fanout 1, EXPAND 1..8; the queue capacity holds one ensemble's
  * worst-case output (Section 3.2).  No CUDA call is made. */
@@ -159,6 +165,11 @@ typedef struct {
     uint32_t *out_min;              /* device, R; min survivor, 0xFFFFFFFF if none (or NULL) */
     uint64_t total_elements_hint;   /* sum of L_r if the caller knows it, else 0; only used to
                                        size work units (regions_per_unit = 0)               */
+    uint32_t *out_values;           /* device, RS_EMIT pipelines only (else NULL): at least
+                                       F * (offsets[R] - offsets[0]) entries; out_count is
+                                       then required and is zeroed by every run             */
+    uint64_t out_values_len;        /* entries in out_values (the device checks every write
+                                       against it and reports RS_ERR_DEVICE_INPUT beyond)   */
 } rs_stream_desc;
 
 /* Register a stream with the pipeline; it is processed by every later rs_run until

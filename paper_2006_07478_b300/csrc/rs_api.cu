@@ -110,6 +110,17 @@ static uint32_t max_fanout_of(const rs_stage_desc *st, uint32_t n)
     return k;
 }
 
+// segment slots per element of an emit sink: the product of the element stages' maximum
+// fan-outs (at most 8^4)
+static uint32_t fanout_product(const rs_stage_desc *st, uint32_t n)
+{
+    uint32_t f = 1;
+    for (uint32_t i = 1; i + 1 < n; ++i) f *= st[i].max_fanout ? st[i].max_fanout : 1u;
+    return f;
+}
+
+static bool is_emit(const rs_pipeline *p) { return p->stages[p->n_stages - 1].kind == RS_EMIT; }
+
 static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
 {
     if (o->ensemble_width == 0) o->ensemble_width = 4 * RS_W;
@@ -159,7 +170,7 @@ static rs_status check_stages(const rs_stage_desc *st, uint32_t n)
 {
     if (!st || n < 2 || n > RS_MAX_STAGES) return RS_ERR_INVALID;
     if (st[0].kind != RS_ENUM_HASH && st[0].kind != RS_ENUM_LOAD) return RS_ERR_INVALID;
-    if (st[n - 1].kind != RS_AGGREGATE) return RS_ERR_INVALID;
+    if (st[n - 1].kind != RS_AGGREGATE && st[n - 1].kind != RS_EMIT) return RS_ERR_INVALID;
     for (uint32_t i = 1; i + 1 < n; ++i) {
         const rs_stage_desc &s = st[i];
         switch (s.kind) {
@@ -197,6 +208,7 @@ static DevStage to_dev(const rs_stage_desc &s)
     case RS_ENUM_HASH: d.op = D_ENUM_HASH; break;
     case RS_ENUM_LOAD: d.op = D_ENUM_LOAD; break;
     case RS_AGGREGATE: d.op = D_AGG; break;
+    case RS_EMIT: d.op = D_EMIT; break;
     case RS_MAP: d.op = D_MAP_MULADD; break;
     case RS_EXPAND: d.op = D_EXPAND; break;
     case RS_FILTER:
@@ -324,6 +336,8 @@ rs_status rs_stream_submit(rs_pipeline *p, const rs_stream_desc *s, uint64_t *st
         if (!s->region_len && !s->region_offsets) return RS_ERR_INVALID;
         if (p->stages[0].kind == RS_ENUM_LOAD && (!s->elements || s->n_elements == 0)) return RS_ERR_INVALID;
         if (s->n_elements >= (1ull << 32) - 4096) return RS_ERR_CAPACITY;   // positions stay 32-bit
+        if (is_emit(p) && (!s->region_offsets || !s->out_count || !s->out_values || s->out_values_len == 0))
+            return RS_ERR_INVALID;   // the emit sink's segments follow the CSR offsets
         for (uint32_t i = 1; i + 1 < p->n_stages; ++i)
             if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_HASH_CTX_LT) {
                 // ctx may be NULL (t_r = 0)
@@ -766,6 +780,8 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
             d.out_count = s.out_count;
             d.out_sum = (unsigned long long *)s.out_sum;
             d.out_min = s.out_min;
+            d.out_values = s.out_values;
+            d.out_values_len = s.out_values_len;
             d.n_elements = s.n_elements;
             d.R = (uint32_t)s.n_regions;
             d.K = q.K;
@@ -827,9 +843,13 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
         if (s.n_regions == 0) continue;
         if ((wc && !s.out_count) || (wsum && !s.out_sum) || (wm && !s.out_min)) return RS_ERR_INVALID;
     }
-    P.want_count = wc;
-    P.want_sum = wsum;
-    P.want_min = wm;
+    // an emit sink claims positions with atomics on the counts, which every run zeroes
+    // first: no identity results are written
+    P.emit = is_emit(p);
+    P.emit_f = fanout_product(p->stages, p->n_stages);
+    P.want_count = wc && !P.emit;
+    P.want_sum = wsum && !P.emit;
+    P.want_min = wm && !P.emit;
     P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
     P.budget = o.device_budget;
     P.spin_limit = 2000000000ull;   // 2 s on the global timer
@@ -904,6 +924,11 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
         }
         if ((e = cudaEventRecord(p->upload_done, stream)) != cudaSuccess) return cuda_fail(e);
         p->upload_pending = true;
+    }
+    if (Lc.P.emit) {
+        for (const auto &s : p->streams)
+            if (s.n_regions && (e = cudaMemsetAsync(s.out_count, 0, s.n_regions * 4, stream)) != cudaSuccess)
+                return cuda_fail(e);
     }
     const bool timed = !capturing && p->t_cap > 0;
     const uint32_t slot = timed ? (p->t_count % p->t_cap) : 0;
@@ -1349,6 +1374,8 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
         d.out_count = s.out_count;
         d.out_sum = (unsigned long long *)s.out_sum;
         d.out_min = s.out_min;
+        d.out_values = s.out_values;
+        d.out_values_len = s.out_values_len;
         d.n_elements = s.n_elements;
         d.R = (uint32_t)s.n_regions;
         d.K = q.K;
@@ -1406,9 +1433,11 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
         if (s.n_regions == 0) continue;
         if ((wc && !s.out_count) || (wsum && !s.out_sum) || (wm && !s.out_min)) return RS_ERR_INVALID;
     }
-    P.want_count = wc;
-    P.want_sum = wsum;
-    P.want_min = wm;
+    P.emit = is_emit(p);
+    P.emit_f = fanout_product(p->stages, p->n_stages);
+    P.want_count = wc && !P.emit;
+    P.want_sum = wsum && !P.emit;
+    P.want_min = wm && !P.emit;
     P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
     P.budget = o.device_budget;
     P.spin_limit = 2000000000ull;
@@ -1456,6 +1485,11 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     // buffer and no copy from pageable host memory
     rs_noalloc_table_kernel<<<1, 256, 0, cs>>>(p->noalloc_table, (DevStream *)(wsb + pl.table_off), (uint32_t)ns);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    if (P.emit) {
+        for (const auto &s : p->streams)
+            if (s.n_regions && (e = cudaMemsetAsync(s.out_count, 0, s.n_regions * 4, cs)) != cudaSuccess)
+                return cuda_fail(e);
+    }
     if (P.plan_tiles > 0) {
         int pg = (int)((P.plan_tiles + 7) / 8);
         if (pg > p->n_sm * 8) pg = p->n_sm * 8;

@@ -22,6 +22,7 @@ enum DevOp : uint32_t {
     D_MAP_MULADD = 7,
     D_EXPAND = 8,
     D_AGG = 9,
+    D_EMIT = 10,         // sink: survivors into their region's segment of out_values
 };
 
 struct DevStage {
@@ -85,6 +86,9 @@ struct DevStream {
     uint32_t D;          // merge-path steps per unit
     uint32_t dsh;        // log2 D when D is a power of two, else RS_NOT_POW2
     uint32_t c;          // merge-path steps per parent (an element costs one)
+    // emit sink: region r's survivors go to out_values[emit_f * (offsets[r] - offsets[0]) ...]
+    uint32_t *out_values;
+    unsigned long long out_values_len;
 };
 
 // Status bits written by the device.
@@ -158,6 +162,8 @@ struct KParams {
     uint32_t plan_tile;           // parents per planner tile (RS_PLAN_TILE or RS_PLAN_TILE_SMALL)
     uint32_t m16, m19;            // 2^16 and 2^19: x >> 16 = umulhi(x, m16), x >> 13 = umulhi(x, m19)
                                   // (run-time values, so the shifts stay multiplies)
+    uint32_t emit;                // the last stage is the emit sink (results per item, not per region)
+    uint32_t emit_f;              // its segment slots per element: the product of the maximum fan-outs
     SmemLayout L;
 };
 

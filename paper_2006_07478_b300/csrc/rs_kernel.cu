@@ -630,6 +630,9 @@ struct Proc {
     uint32_t ek;     // enumerate: next parent to open (signal strategy)
     uint32_t ek1;    // node 1: parent containing its next position (tag strategy)
     bool stop;
+    // the unit's stream and its first parent (the emit sink addresses outputs by region)
+    const DevStream *ds = nullptr;
+    uint32_t r0 = 0;
 
     __device__ __forceinline__ Proc(const KParams &P_, Smem &M_, Warp &w_, Stage &g_, uint32_t lane_)
         : P(P_), M(M_), w(w_), g(g_), lane(lane_), nk(0), total(0), E0(0), ek(0), ek1(0), stop(false)
@@ -934,6 +937,30 @@ struct Proc {
         PROF_ADD(PF_COMPACT, pp);
     }
 
+    // ---- one ensemble into the emit sink (Section 4: survivors stripped of their
+    // parent): the ensemble belongs to one parent (Section 3.3), so one atomic add on the
+    // region's count claims its positions in the region's segment of the value array ----
+    __device__ __forceinline__ void emit_ensemble(const uint32_t (&x)[V], uint32_t take)
+    {
+        const uint32_t r = r0 + w.ctxk[nst() - 1];
+        uint32_t base = 0, seg = 0;
+        if (lane == 0) {
+            base = atomicAdd(ds->out_count + r, take);
+            seg = __ldg(ds->offsets + r) - __ldg(ds->offsets);
+        }
+        base = __shfl_sync(FULLMASK, base, 0);
+        seg = __shfl_sync(FULLMASK, seg, 0);
+        const unsigned long long b = (unsigned long long)P.emit_f * seg + base;
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            const uint32_t q = 32u * s + lane;
+            if (q < take) {
+                if (b + q < ds->out_values_len) ds->out_values[b + q] = x[s];
+                else atomicOr(&P.hdr->status, ST_BAD_INPUT);
+            }
+        }
+    }
+
     // ---- one ensemble into the aggregate (node I = n-1) ----
     template <int I, bool F>
     __device__ __forceinline__ void aggregate(uint32_t take)
@@ -942,6 +969,10 @@ struct Proc {
         uint32_t x[V], k[V];
         (void)gather<I, F>(take, x, k);
         if constexpr (STRAT == RS_STRATEGY_SIGNAL) {
+            if (S::generic && P.emit) {
+                emit_ensemble(x, take);
+                return;
+            }
             // the whole ensemble belongs to the current parent (Section 3.3)
             unsigned long long part = 0;
             uint32_t mn = 0xFFFFFFFFu;
@@ -1388,6 +1419,8 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
             pr.nk = nk;
             pr.total = total;
             pr.E0 = E0;
+            pr.ds = &S;
+            pr.r0 = r0;
             if (g.tma) pr.issue_tiles();
             pr.run_unit();
             pr.finish_tiles();

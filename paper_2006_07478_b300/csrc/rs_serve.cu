@@ -341,6 +341,9 @@ rs_status rs_server_create(const rs_stage_desc *stages, uint32_t n_stages, const
 {
     if (!out || !arena || arena_bytes < 4096 || ((uintptr_t)arena & 255)) return RS_ERR_INVALID;
     *out = nullptr;
+    // requests carry per-region outputs only: a pipeline ending in an emit sink is not served
+    if (!stages || n_stages < 2 || n_stages > RS_MAX_STAGES || stages[n_stages - 1].kind == RS_EMIT)
+        return RS_ERR_INVALID;
     // validate the stage list and options once, through the pipeline's own checks
     rs_pipeline *probe = nullptr;
     rs_status st = rs_pipeline_create(stages, n_stages, opts, &probe);

@@ -775,10 +775,64 @@ struct TagEngine {
         if (P.want_min) atomicMin(d.out_min + rr, mn);
     }
 
+    // one emitted value at position pos of the stream's value array (bounds-checked)
+    __device__ __forceinline__ void put_value(const DevStream &d, unsigned long long pos, uint32_t v) const
+    {
+        if (pos < d.out_values_len) d.out_values[pos] = v;
+        else atomicOr(&P.hdr->status, ST_BAD_INPUT);
+    }
+
+    // the emit sink (Section 4: results derived from single elements, stripped of their
+    // parent): each kept value goes to its region's segment of the value array, at a
+    // position claimed by an atomic add on the region's count (zeroed before the run), so
+    // a region's values keep no particular order.  A one-region ensemble claims all its
+    // positions with one atomic and places the values by a warp prefix.
+    __device__ __forceinline__ void emit_values(const uint32_t (&x)[V], const uint32_t (&r)[V],
+                                                const bool (&valid)[V], bool uni, uint32_t r0, uint32_t n_valid) const
+    {
+        const DevStream &d = D();
+        const uint32_t o0 = __ldg(d.offsets);
+        if (uni) {
+            if (n_valid == 0) return;
+            uint32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < V; ++j) c += valid[j] ? 1u : 0u;
+            const uint32_t incl = scan_add(c);
+            uint32_t base = 0, seg = 0;
+            if (lane == 0) {
+                base = atomicAdd(d.out_count + r0, n_valid);
+                seg = __ldg(d.offsets + r0) - o0;
+            }
+            base = __shfl_sync(FULLMASK, base, 0);
+            seg = __shfl_sync(FULLMASK, seg, 0);
+            unsigned long long pos = (unsigned long long)P.emit_f * seg + base + (incl - c);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                if (valid[j]) {
+                    put_value(d, pos, x[j]);
+                    ++pos;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                if (valid[j]) {
+                    const uint32_t b = atomicAdd(d.out_count + r[j], 1u);
+                    put_value(d, (unsigned long long)P.emit_f * (__ldg(d.offsets + r[j]) - o0) + b, x[j]);
+                }
+            }
+        }
+    }
+
     // the aggregate (Section 4.2): count, sum and min of each region's surviving items
+    // (or, for an emit sink, the items themselves)
     __device__ __forceinline__ void aggregate(const uint32_t (&x)[V], const uint32_t (&r)[V], const bool (&valid)[V],
                                               bool uni, uint32_t r0, uint32_t n_valid) const
     {
+        if (SG::generic && P.emit) {
+            emit_values(x, r, valid, uni, r0, n_valid);
+            return;
+        }
         if (uni) {
             uint32_t lo = 0, hi = 0, mn = NONE;
 #pragma unroll

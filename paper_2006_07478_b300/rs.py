@@ -15,6 +15,8 @@ Stage tuples (the same names the workload module uses):
     ("map_mul", a, b)                x <- a*x + b mod 2^32
     ("expand", k, salt)              0..k outputs per input
     ("aggregate",)                   count / sum / min per region
+    ("emit",)                        the survivors themselves, grouped by region (needs
+                                     CSR offsets; outputs "count" and "values")
 """
 from __future__ import annotations
 
@@ -25,7 +27,7 @@ from . import build as _build
 
 RS_OK, RS_ERR_INVALID, RS_ERR_NOMEM, RS_ERR_CUDA, RS_ERR_NOT_READY = 0, 1, 2, 3, 4
 RS_ERR_STALL, RS_ERR_CAPACITY, RS_ERR_STATE, RS_ERR_DEVICE_INPUT = 5, 6, 7, 8
-RS_ENUM_HASH, RS_ENUM_LOAD, RS_FILTER, RS_MAP, RS_EXPAND, RS_AGGREGATE = 1, 2, 3, 4, 5, 6
+RS_ENUM_HASH, RS_ENUM_LOAD, RS_FILTER, RS_MAP, RS_EXPAND, RS_AGGREGATE, RS_EMIT = 1, 2, 3, 4, 5, 6, 7
 RS_OP_NONE, RS_OP_MOD_EQ, RS_OP_HASH_CTX_LT, RS_OP_WEIGHT_LT, RS_OP_MUL_ADD, RS_OP_HASH_FANOUT = 0, 1, 2, 3, 4, 5
 STRATEGIES = {"signal": 0, "tag": 1, "auto": 2}
 RS_MAX_STAGES = 6
@@ -64,7 +66,8 @@ class StreamDesc(ctypes.Structure):
                 ("region_offsets", ctypes.c_void_p), ("elements", ctypes.c_void_p),
                 ("n_elements", ctypes.c_uint64), ("ctx", ctypes.c_void_p), ("out_count", ctypes.c_void_p),
                 ("out_sum", ctypes.c_void_p), ("out_min", ctypes.c_void_p),
-                ("total_elements_hint", ctypes.c_uint64)]
+                ("total_elements_hint", ctypes.c_uint64), ("out_values", ctypes.c_void_p),
+                ("out_values_len", ctypes.c_uint64)]
 
 
 class RegionResults(ctypes.Structure):
@@ -206,6 +209,8 @@ def stage_desc(st) -> StageDesc:
         d.kind = RS_ENUM_LOAD
     elif name == "aggregate":
         d.kind = RS_AGGREGATE
+    elif name == "emit":
+        d.kind = RS_EMIT
     elif name == "filter_mod":
         d.kind, d.op = RS_FILTER, RS_OP_MOD_EQ
         d.params[0], d.params[1] = a[0], a[1]
@@ -287,18 +292,33 @@ class Pipeline:
             setattr(o, k, int(v))
         check(lib().rs_pipeline_set_opts(self._h, ctypes.byref(o)), "rs_pipeline_set_opts")
 
+    def fanout_product(self) -> int:
+        """Segment slots per element of an emit sink (product of the maximum fan-outs)."""
+        F = 1
+        for st in self.stages[1:-1]:
+            if st[0] == "expand":
+                F *= max(1, int(st[1]))
+        return F
+
     def submit(self, dev: dict, outputs=("count", "sum", "min")) -> dict:
         """Register a device stream (dict of torch CUDA tensors: parents, len, offsets,
         elements, ctx; any may be None).  Allocates its result tensors and returns
-        them in a dict with the stream id."""
+        them in a dict with the stream id.  An emit pipeline's outputs are "count" and
+        "values" (F x the stream's element count entries)."""
         import torch
         R = int(dev["R"])
         dvc = torch.device("cuda")
+        emit = self.stages[-1][0] == "emit"
+        if emit:
+            outputs = ("count", "values")
         out = {
             "count": torch.empty(R, dtype=torch.int32, device=dvc) if "count" in outputs else None,
             "sum": torch.empty(R, dtype=torch.int64, device=dvc) if "sum" in outputs else None,
             "min": torch.empty(R, dtype=torch.int32, device=dvc) if "min" in outputs else None,
         }
+        if emit:
+            n = max(1, self.fanout_product() * int(dev.get("total_elements", 0)))
+            out["values"] = torch.empty(n, dtype=torch.int32, device=dvc)
         d = StreamDesc()
         d.n_regions = R
         d.parents = _ptr(dev.get("parents"))
@@ -312,6 +332,9 @@ class Pipeline:
         d.out_sum = _ptr(out["sum"])
         d.out_min = _ptr(out["min"])
         d.total_elements_hint = int(dev.get("total_elements", 0))
+        if out.get("values") is not None:
+            d.out_values = _ptr(out["values"])
+            d.out_values_len = int(out["values"].numel())
         sid = ctypes.c_uint64()
         check(lib().rs_stream_submit(self._h, ctypes.byref(d), ctypes.byref(sid)), "rs_stream_submit")
         self._keep.append((dev, out))
@@ -505,6 +528,8 @@ def results_to_numpy(out: dict) -> dict:
         res["sum"] = out["sum"].cpu().numpy().view(np.uint64)
     if out.get("min") is not None:
         res["min"] = out["min"].cpu().numpy().view(np.uint32)
+    if out.get("values") is not None:
+        res["values"] = out["values"].cpu().numpy().view(np.uint32)
     return res
 
 
@@ -516,7 +541,7 @@ def run_stream(stages, stream: dict, strategy="tag", outputs=("count", "sum", "m
     p = Pipeline(stages, strategy=strategy, **opts)
     dev = to_device(stream)
     out = p.submit(dev, outputs=outputs)
-    for k in ("count", "sum", "min"):
+    for k in ("count", "sum", "min", "values"):
         if out.get(k) is not None:
             out[k].fill_(0x5A5A5A5A)
     p.run()

@@ -171,3 +171,33 @@ def test_server_argument_checks_without_gpu():
     assert L.rs_server_submit(h, ctypes.byref(r), ctypes.byref(rid)) == rs.RS_OK
     st = rs.ServerStats()
     assert L.rs_server_get_stats(h, ctypes.byref(st)) == rs.RS_OK and st.submitted == 1
+
+
+def test_emit_sink_pipelines_and_streams():
+    """An emit sink is a legal last stage; its streams need CSR offsets, counts and a
+    value array; the server does not take emit pipelines (its requests carry per-region
+    outputs only)."""
+    pipe = wl.pipeline_cascade()[:-1] + [("emit",)]
+    st, h = _create(pipe)
+    assert st == rs.RS_OK
+    L = rs.lib()
+    d = rs.StreamDesc()
+    d.n_regions = 10
+    d.region_len = ctypes.c_void_p(0x1000)
+    d.elements = ctypes.c_void_p(0x2000)
+    d.n_elements = 1000
+    d.out_count = ctypes.c_void_p(0x3000)
+    sid = ctypes.c_uint64()
+    assert L.rs_stream_submit(h, ctypes.byref(d), ctypes.byref(sid)) == rs.RS_ERR_INVALID   # no offsets
+    d.region_offsets = ctypes.c_void_p(0x4000)
+    assert L.rs_stream_submit(h, ctypes.byref(d), ctypes.byref(sid)) == rs.RS_ERR_INVALID   # no values
+    d.out_values = ctypes.c_void_p(0x5000)
+    d.out_values_len = 1000
+    assert L.rs_stream_submit(h, ctypes.byref(d), ctypes.byref(sid)) == rs.RS_OK
+    assert L.rs_pipeline_destroy(h) == rs.RS_OK
+    st, h = _create([("enum_load",), ("emit",), ("aggregate",)])                             # emit is last only
+    assert st == rs.RS_ERR_INVALID
+    arr = (rs.StageDesc * len(pipe))(*[rs.stage_desc(s) for s in pipe])
+    srv = ctypes.c_void_p()
+    assert L.rs_server_create(arr, len(pipe), None, ctypes.c_void_p(0x10000), 1 << 20, 0, 0, None,
+                              ctypes.byref(srv)) == rs.RS_ERR_INVALID
