@@ -75,6 +75,9 @@ def lib():
         L.ora_run_emit.argtypes = [ctypes.POINTER(OraStage), ctypes.c_int, ctypes.c_uint64,
                                    P, P, P, P, P, ctypes.c_uint32, P, P]
         L.ora_run_emit.restype = ctypes.c_int
+        L.ora_run_tree.argtypes = [ctypes.POINTER(OraStage), P, ctypes.c_int, ctypes.c_uint64,
+                                   P, P, P, P, P, P, P, P]
+        L.ora_run_tree.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -175,3 +178,25 @@ def run_emit(pipeline, stream: dict) -> dict:
     if rc != 0:
         raise ValueError("oracle rejected the pipeline or stream")
     return {"count": count, "values": values, "start": F * off}
+
+
+def run_tree(pipeline, inputs, stream: dict) -> list:
+    """Tree topology (Figure 1(b)): stage s reads the output of stage inputs[s]
+    (inputs[0] is ignored; inputs[1] must be 0).  Returns one dict {count, sum, min}
+    per aggregate leaf, in stage order."""
+    R = int(stream["R"])
+    n = len(pipeline)
+    sinks = sum(1 for st in pipeline[1:] if st[0] == "aggregate")
+    cnt = [np.empty(R, dtype=np.uint32) for _ in range(sinks)]
+    sm = [np.empty(R, dtype=np.uint64) for _ in range(sinks)]
+    mn = [np.empty(R, dtype=np.uint32) for _ in range(sinks)]
+    up = (ctypes.c_int32 * n)(*([-1] + [int(i) for i in inputs[1:]]))
+    pc = (ctypes.c_void_p * max(1, sinks))(*[a.ctypes.data for a in cnt])
+    ps = (ctypes.c_void_p * max(1, sinks))(*[a.ctypes.data for a in sm])
+    pm = (ctypes.c_void_p * max(1, sinks))(*[a.ctypes.data for a in mn])
+    rc = lib().ora_run_tree(_stages(pipeline), up, n, R, _ptr(stream.get("parents")), _ptr(stream.get("len")),
+                            _ptr(stream.get("offsets")), _ptr(stream.get("elements")), _ptr(stream.get("ctx")),
+                            pc, ps, pm)
+    if rc != sinks:
+        raise ValueError("oracle rejected the tree or stream")
+    return [{"count": c, "sum": s_, "min": m} for c, s_, m in zip(cnt, sm, mn)]

@@ -12,6 +12,8 @@
  *     elements.  Enumeration opens parent r into elements i = 0..L_r-1 (sequential
  *     indices, Section 4.1); nodes downstream may consult the parent (getParent()).
  *   - Section 2.1: a linear pipeline; each node turns one input into 0..k outputs.
+ *     Tree topologies (Figure 1(b), ora_run_tree) replicate a stage's output stream to
+ *     each of its children; every leaf is an aggregate with results of its own.
  *   - Section 4 / Figure 4: aggregation closes the parent: begin() resets the
  *     accumulator, run() folds each surviving item in, end() emits one result per
  *     parent -- including parents none of whose elements survive.  Section 4's other
@@ -288,4 +290,107 @@ int ora_run_emit(const ora_stage *st, int n, uint64_t R, const uint32_t *parents
     }
     free(off);
     return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Tree topologies (Section 2.1, Figure 1(b)): stage s >= 1 reads the output stream of
+ * stage up[s] (up[1] = 0, the enumeration; 1 <= up[s] < s otherwise).  Every output of
+ * a stage goes to each of its children -- the stream is replicated at a branch, and so
+ * is every region boundary -- and each leaf is an aggregate with results of its own.
+ * sink_of[s] numbers the leaves in stage order. */
+
+static void push_tree(const ora_stage *st, const int *up, const int *sink_of, int n, int s, uint32_t x,
+                      uint32_t parent, uint32_t t, ora_acc *acc)
+{
+    const ora_stage *g = &st[s];
+    switch (g->op) {
+    case ORA_FILTER_MOD:
+        if (x % g->p0 != g->p1) return;
+        break;
+    case ORA_FILTER_HASH_CTX:
+        if ((ora_hash32(x, g->p0) ^ t) >= g->p1) return;
+        break;
+    case ORA_FILTER_WEIGHT_LT:
+        if (!(ora_hash32(x, g->p0) < ora_hash32(parent, g->p0))) return;
+        break;
+    case ORA_MAP_MUL:
+        x = g->p0 * x + g->p1;
+        break;
+    case ORA_EXPAND: {
+        uint32_t nout = ora_hash32(x, g->p0) % (g->fanout + 1u);
+        for (uint32_t j = 0; j < nout; ++j) {
+            uint32_t y = ora_hash32(x, g->p0 + 1u + j);
+            for (int c = s + 1; c < n; ++c)
+                if (up[c] == s) push_tree(st, up, sink_of, n, c, y, parent, t, acc);
+        }
+        return;
+    }
+    case ORA_AGGREGATE: {
+        ora_acc *a = &acc[sink_of[s]];
+        a->count += 1u;
+        a->sum += (uint64_t)x;
+        if (x < a->min) a->min = x;
+        return;
+    }
+    default:
+        return;
+    }
+    for (int c = s + 1; c < n; ++c)
+        if (up[c] == s) push_tree(st, up, sink_of, n, c, x, parent, t, acc);
+}
+
+/* Results of sink k go to count[k][r], sum[k][r], mn[k][r] (any may be NULL).
+ * Returns the number of sinks, or -1 for an invalid tree (a sink with children, an
+ * element stage without, more than 4 sinks). */
+int ora_run_tree(const ora_stage *st, const int32_t *up, int n, uint64_t R, const uint32_t *parents,
+                 const uint32_t *len, const uint32_t *offsets, const uint32_t *elements, const uint32_t *ctx,
+                 uint32_t **count, uint64_t **sum, uint32_t **mn)
+{
+    int upi[16], sink_of[16], n_sinks = 0;
+    if (n < 2 || n > 16) return -1;
+    if (st[0].op != ORA_ENUM_HASH && st[0].op != ORA_ENUM_LOAD) return -1;
+    for (int s = 1; s < n; ++s) {
+        upi[s] = up[s];
+        if (s == 1 ? up[s] != 0 : (up[s] < 1 || up[s] >= s)) return -1;
+        if (st[up[s]].op == ORA_AGGREGATE) return -1;   /* a sink has no children */
+    }
+    for (int s = 1; s < n; ++s) {
+        int kids = 0;
+        for (int c = s + 1; c < n; ++c) kids += up[c] == s;
+        const int op = st[s].op;
+        if (op == ORA_AGGREGATE) {
+            if (n_sinks >= 4) return -1;
+            sink_of[s] = n_sinks++;
+        } else {
+            if (kids == 0) return -1;                     /* every leaf is a sink */
+            if (op != ORA_FILTER_MOD && op != ORA_FILTER_HASH_CTX && op != ORA_FILTER_WEIGHT_LT &&
+                op != ORA_MAP_MUL && op != ORA_EXPAND)
+                return -1;
+            if (op == ORA_FILTER_MOD && st[s].p0 == 0) return -1;
+            sink_of[s] = -1;
+        }
+    }
+    if (!len && !offsets && R > 0) return -1;
+    if (st[0].op == ORA_ENUM_LOAD && !elements && R > 0) return -1;
+    ora_stream s = {R, parents, len, offsets, elements, ctx};
+    uint64_t *off = make_offsets(&s);
+    if (!off) return -1;
+    for (uint64_t r = 0; r < R; ++r) {
+        ora_acc acc[4];
+        for (int k = 0; k < 4; ++k) acc[k] = (ora_acc){0u, 0u, 0xFFFFFFFFu, NULL};   /* begin() per sink */
+        uint32_t parent = parents ? parents[r] : (uint32_t)r;
+        uint32_t t = ctx ? ctx[r] : 0u;
+        uint64_t L = off[r + 1] - off[r];
+        for (uint64_t i = 0; i < L; ++i) {
+            uint32_t x = (st[0].op == ORA_ENUM_HASH) ? ora_hash32(parent, (uint32_t)i) : elements[off[r] + i];
+            push_tree(st, upi, sink_of, n, 1, x, parent, t, acc);
+        }
+        for (int k = 0; k < n_sinks; ++k) {                /* end(): one result per parent and sink */
+            if (count && count[k]) count[k][r] = acc[k].count;
+            if (sum && sum[k]) sum[k][r] = acc[k].sum;
+            if (mn && mn[k]) mn[k][r] = acc[k].min;
+        }
+    }
+    free(off);
+    return n_sinks;
 }

@@ -460,3 +460,56 @@ def test_emit_agrees_with_the_aggregate(which):
     for r in range(s["R"]):
         used[em["start"][r]:em["start"][r] + int(em["count"][r])] = True
     assert not em["values"][~used].any()
+
+
+# ---------------------------------------------------------------------------
+# tree topologies (Figure 1(b)): the stream is replicated at a branch, so each leaf's
+# results are the linear pipeline along the root-to-leaf path (pinned above)
+
+
+def _path(pipeline, inputs, leaf):
+    path = [leaf]
+    while path[-1] != 0:
+        path.append(inputs[path[-1]])
+    return [pipeline[i] for i in reversed(path)]
+
+
+TREES = [
+    # enumerate -> A -> {B -> sink, sink}
+    ([("enum_load",), ("filter_hash_ctx", 1, 2147483648), ("filter_hash_ctx", 2, 1288490188), ("aggregate",),
+      ("aggregate",)], [0, 0, 1, 2, 1]),
+    # enumerate -> map -> {filter -> sink, expand -> sink}
+    ([("enum_hash",), ("map_mul", 2654435761, 7), ("filter_mod", 2, 0), ("aggregate",), ("expand", 3, 11),
+      ("aggregate",)], [0, 0, 1, 2, 1, 4]),
+    # enumerate -> expand -> {sink, sink} (the same expanded stream twice)
+    ([("enum_hash",), ("expand", 2, 5), ("aggregate",), ("aggregate",)], [0, 0, 1, 1]),
+]
+
+
+@pytest.mark.parametrize("ti", range(len(TREES)))
+def test_tree_leaves_are_their_root_to_leaf_pipelines(ti):
+    pipe, inputs = TREES[ti]
+    if pipe[0][0] == "enum_load":
+        s = wl.cascade_stream(n_total=30000, mean=12, seed=4)
+    else:
+        s = wl.hashed_uniform_stream(2000, 48, 8)
+    res = oracle.run_tree(pipe, inputs, s)
+    leaves = [i for i, st in enumerate(pipe) if st[0] == "aggregate"]
+    assert len(res) == len(leaves)
+    for k, leaf in enumerate(leaves):
+        want = oracle.run(_path(pipe, inputs, leaf), s)
+        for key in ("count", "sum", "min"):
+            assert np.array_equal(res[k][key], want[key]), (ti, leaf, key)
+    if ti == 2:
+        for key in ("count", "sum", "min"):
+            assert np.array_equal(res[0][key], res[1][key])
+
+
+def test_tree_validation():
+    s = wl.hashed_uniform_stream(10, 4, 1)
+    with pytest.raises(ValueError):          # a sink with a child
+        oracle.run_tree([("enum_hash",), ("aggregate",), ("aggregate",)], [0, 0, 1], s)
+    with pytest.raises(ValueError):          # an element stage without children
+        oracle.run_tree([("enum_hash",), ("filter_mod", 2, 0), ("map_mul", 1, 0), ("aggregate",)], [0, 0, 1, 1], s)
+    with pytest.raises(ValueError):          # an input that is not upstream
+        oracle.run_tree([("enum_hash",), ("filter_mod", 2, 0), ("aggregate",)], [0, 0, 2], s)
