@@ -90,7 +90,17 @@ typedef struct {
     uint32_t op;            /* rs_op (RS_OP_NONE for enumerate / aggregate)     */
     uint32_t max_fanout;    /* a-priori maximum outputs per input (Section 3.2) */
     uint32_t params[4];
+    uint32_t input;         /* tree topologies (Section 2.1, Figure 1(b)): index of the
+                               stage whose output this stage reads; 0 = the stage before
+                               it (a linear pipeline).  Stage 1 reads the enumeration;
+                               every other stage reads an earlier FILTER / MAP / EXPAND
+                               stage, whose output stream -- and with it every region
+                               boundary -- is replicated to each of its readers.  The
+                               leaves are the AGGREGATE stages (at most RS_MAX_SINKS;
+                               an emit sink only ends a linear pipeline).            */
 } rs_stage_desc;
+
+#define RS_MAX_SINKS 2      /* aggregate leaves of a tree */
 
 #define RS_MAX_STAGES 6     /* enumerate + up to 4 element stages + aggregate or emit */
 
@@ -132,7 +142,29 @@ typedef struct {
                                    1..256; 0 = 16                                            */
     uint64_t device_budget;     /* scheduler sweeps allowed per claimed unit before the device
                                    reports RS_ERR_STALL; 0 = 2^22                            */
+    uint32_t boundary_modes;    /* per-edge region boundaries: bits 2c..2c+1 say how stage c
+                                   (1..5) learns the region of each input item --
+                                   RS_BOUNDARY_DEFAULT (from `strategy`), _SIGNAL, _TAG or
+                                   _LANE.  0 everywhere: `strategy` decides for the whole
+                                   pipeline.  Anything else, or a tree topology, runs the
+                                   per-edge kernel (units of <= 512 parents, as the signal
+                                   strategy's).  Below a tagged edge every edge is tagged;
+                                   an EXPAND stage takes no RS_BOUNDARY_LANE input.        */
+    uint32_t reserved;
 } rs_pipeline_opts;
+
+typedef enum {
+    RS_BOUNDARY_DEFAULT = 0,
+    RS_BOUNDARY_SIGNAL = 1, /* Begin/End signals with credits; ensembles cut at each (Section 3)  */
+    RS_BOUNDARY_TAG = 2,    /* the producer tags each item with its region (Section 2.3 / 5):
+                               mixing signals upstream and tags downstream is the per-stage
+                               choice of Section 5 (the taxi application)                        */
+    RS_BOUNDARY_LANE = 3    /* signals with credits, but ensembles span them: each lane selects
+                               the context before or after a signal for its own item (the
+                               per-lane state selection proposed in Section 6)                    */
+} rs_boundary;
+
+#define RS_BOUNDARY(stage, mode) ((uint32_t)(mode) << (2 * (stage)))
 
 /* Fill *opts with the defaults above (strategy = RS_STRATEGY_TAG). */
 rs_status rs_default_opts(rs_pipeline_opts *opts);
@@ -170,6 +202,9 @@ typedef struct {
                                        then required and is zeroed by every run             */
     uint64_t out_values_len;        /* entries in out_values (the device checks every write
                                        against it and reports RS_ERR_DEVICE_INPUT beyond)   */
+    uint32_t *out2_count;           /* tree pipelines with two leaves: the second leaf's   */
+    uint64_t *out2_sum;             /* results, R entries each (the same arrays as the     */
+    uint32_t *out2_min;             /* first leaf's are required); else NULL               */
 } rs_stream_desc;
 
 /* Register a stream with the pipeline; it is processed by every later rs_run until

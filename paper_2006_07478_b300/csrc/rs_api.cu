@@ -105,10 +105,15 @@ static bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
 static uint32_t max_fanout_of(const rs_stage_desc *st, uint32_t n)
 {
     uint32_t k = 1;
-    for (uint32_t i = 1; i + 1 < n; ++i)
-        if (st[i].max_fanout > k) k = st[i].max_fanout;
+    for (uint32_t i = 1; i < n; ++i)
+        if (st[i].kind == RS_EXPAND && st[i].max_fanout > k) k = st[i].max_fanout;
     return k;
 }
+
+// the stage whose output stage i reads (0 = the enumeration)
+static uint32_t stage_input(const rs_stage_desc *st, uint32_t i) { return st[i].input ? st[i].input : i - 1; }
+
+static bool is_element_stage(uint32_t kind) { return kind == RS_FILTER || kind == RS_MAP || kind == RS_EXPAND; }
 
 // segment slots per element of an emit sink: the product of the element stages' maximum
 // fan-outs (at most 8^4)
@@ -120,6 +125,58 @@ static uint32_t fanout_product(const rs_stage_desc *st, uint32_t n)
 }
 
 static bool is_emit(const rs_pipeline *p) { return p->stages[p->n_stages - 1].kind == RS_EMIT; }
+
+// aggregate / emit leaves of the stage list
+static uint32_t n_leaves(const rs_stage_desc *st, uint32_t n)
+{
+    uint32_t k = 0;
+    for (uint32_t i = 1; i < n; ++i) k += (st[i].kind == RS_AGGREGATE || st[i].kind == RS_EMIT) ? 1u : 0u;
+    return k;
+}
+
+// Topology and per-edge boundary modes as the kernels take them.  `strategy` is the
+// resolved pipeline strategy (RS_BOUNDARY_DEFAULT edges follow it).  mix: the pipeline
+// runs on the per-edge kernel (a tree, or any mode set per edge).
+struct Topo {
+    bool mix;
+    uint32_t n_sinks;
+    uint8_t emode[RS_MAX_STAGES], up[RS_MAX_STAGES], kids[RS_MAX_STAGES], sink_of[RS_MAX_STAGES];
+};
+
+static rs_status make_topo(const rs_stage_desc *st, uint32_t n, uint32_t modes, int strategy, Topo *t)
+{
+    memset(t, 0, sizeof *t);
+    if (modes & 3u) return RS_ERR_INVALID;                     // the enumeration has no input edge
+    if (n < RS_MAX_STAGES && (modes >> (2 * n)) != 0) return RS_ERR_INVALID;   // beyond the last stage
+    bool linear = true;
+    for (uint32_t i = 1; i < n; ++i) linear = linear && stage_input(st, i) == i - 1;
+    t->mix = !linear || modes != 0;
+    for (uint32_t i = 0; i < RS_MAX_STAGES; ++i) t->sink_of[i] = 0xFF;
+    for (uint32_t c = 1; c < n; ++c) {
+        const uint32_t u = stage_input(st, c);
+        t->up[c] = (uint8_t)u;
+        t->kids[u] |= (uint8_t)(1u << c);
+        if (st[c].kind == RS_AGGREGATE || st[c].kind == RS_EMIT) t->sink_of[c] = (uint8_t)t->n_sinks++;
+        uint32_t m = (modes >> (2 * c)) & 3u;
+        if (m == RS_BOUNDARY_DEFAULT) m = strategy == RS_STRATEGY_TAG ? RS_BOUNDARY_TAG : RS_BOUNDARY_SIGNAL;
+        t->emode[c] = (uint8_t)(m == RS_BOUNDARY_TAG ? EM_TAG : m == RS_BOUNDARY_LANE ? EM_LANE : EM_SIG);
+        if (m == RS_BOUNDARY_LANE && st[c].kind == RS_EXPAND) return RS_ERR_INVALID;   // fan-out 1 only
+    }
+    // tags never turn back into signals: every reader of a tagged edge's consumer is tagged
+    for (uint32_t c = 2; c < n; ++c)
+        if (t->emode[t->up[c]] == EM_TAG && t->up[c] != 0 && t->emode[c] != EM_TAG) return RS_ERR_INVALID;
+    return RS_OK;
+}
+
+static void set_topo(KParams &P, const Topo &t)
+{
+    P.mix = t.mix;
+    P.n_sinks = t.n_sinks;
+    memcpy(P.emode, t.emode, sizeof P.emode);
+    memcpy(P.up, t.up, sizeof P.up);
+    memcpy(P.kids, t.kids, sizeof P.kids);
+    memcpy(P.sink_of, t.sink_of, sizeof P.sink_of);
+}
 
 static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
 {
@@ -166,13 +223,31 @@ static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
     return RS_OK;
 }
 
+// A linear pipeline (every stage reads the one before it) or a tree: stage 1 reads the
+// enumeration, every later stage an earlier element stage; the leaves are exactly the
+// sinks (at most RS_MAX_SINKS aggregates, or one emit sink ending a linear pipeline).
 static rs_status check_stages(const rs_stage_desc *st, uint32_t n)
 {
     if (!st || n < 2 || n > RS_MAX_STAGES) return RS_ERR_INVALID;
     if (st[0].kind != RS_ENUM_HASH && st[0].kind != RS_ENUM_LOAD) return RS_ERR_INVALID;
-    if (st[n - 1].kind != RS_AGGREGATE && st[n - 1].kind != RS_EMIT) return RS_ERR_INVALID;
-    for (uint32_t i = 1; i + 1 < n; ++i) {
+    bool linear = true;
+    uint32_t leaves = 0;
+    for (uint32_t i = 1; i < n; ++i) {
+        const uint32_t u = stage_input(st, i);
+        if (i == 1 ? u != 0 : (u < 1 || u >= i || !is_element_stage(st[u].kind))) return RS_ERR_INVALID;
+        linear = linear && u == i - 1;
+        bool read = false;
+        for (uint32_t c = i + 1; c < n; ++c) read = read || stage_input(st, c) == i;
+        const bool sink = st[i].kind == RS_AGGREGATE || st[i].kind == RS_EMIT;
+        if (read == sink) return RS_ERR_INVALID;   // sinks are exactly the leaves
+        leaves += sink ? 1u : 0u;
+    }
+    if (leaves > RS_MAX_SINKS) return RS_ERR_INVALID;
+    for (uint32_t i = 1; i < n; ++i)
+        if (st[i].kind == RS_EMIT && (!linear || i != n - 1)) return RS_ERR_INVALID;
+    for (uint32_t i = 1; i < n; ++i) {
         const rs_stage_desc &s = st[i];
+        if (s.kind == RS_AGGREGATE || s.kind == RS_EMIT) continue;
         switch (s.kind) {
         case RS_FILTER:
             if (s.max_fanout != 1) return RS_ERR_INVALID;
@@ -284,6 +359,10 @@ rs_status rs_pipeline_create(const rs_stage_desc *stages, uint32_t n_stages, con
     fill_defaults(&o, fan);
     st = check_opts(&o, fan);
     if (st != RS_OK) return st;
+    Topo topo;   // boundary modes against the strategy (RS_STRATEGY_AUTO is checked per run)
+    if (make_topo(stages, n_stages, o.boundary_modes, o.strategy == RS_STRATEGY_TAG ? RS_STRATEGY_TAG : RS_STRATEGY_SIGNAL,
+                  &topo) != RS_OK)
+        return RS_ERR_INVALID;
     rs_pipeline *p = new (std::nothrow) rs_pipeline();
     if (!p) return RS_ERR_NOMEM;
     memcpy(p->stages, stages, n_stages * sizeof(rs_stage_desc));
@@ -315,6 +394,10 @@ rs_status rs_pipeline_set_opts(rs_pipeline *p, const rs_pipeline_opts *opts)
     fill_defaults(&o, fan);
     rs_status st = check_opts(&o, fan);
     if (st != RS_OK) return st;
+    Topo topo;
+    if (make_topo(p->stages, p->n_stages, o.boundary_modes,
+                  o.strategy == RS_STRATEGY_TAG ? RS_STRATEGY_TAG : RS_STRATEGY_SIGNAL, &topo) != RS_OK)
+        return RS_ERR_INVALID;
     p->opts = o;
     p->table_dirty = true;   // regions_per_unit may change the unit split
     return RS_OK;
@@ -338,6 +421,10 @@ rs_status rs_stream_submit(rs_pipeline *p, const rs_stream_desc *s, uint64_t *st
         if (s->n_elements >= (1ull << 32) - 4096) return RS_ERR_CAPACITY;   // positions stay 32-bit
         if (is_emit(p) && (!s->region_offsets || !s->out_count || !s->out_values || s->out_values_len == 0))
             return RS_ERR_INVALID;   // the emit sink's segments follow the CSR offsets
+        // a tree's second leaf fills the same outputs as the first
+        if (n_leaves(p->stages, p->n_stages) > 1 &&
+            ((!s->out_count != !s->out2_count) || (!s->out_sum != !s->out2_sum) || (!s->out_min != !s->out2_min)))
+            return RS_ERR_INVALID;
         for (uint32_t i = 1; i + 1 < p->n_stages; ++i)
             if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_HASH_CTX_LT) {
                 // ctx may be NULL (t_r = 0)
@@ -436,11 +523,12 @@ static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int str
 
 // bytes of a stream's per-run scratch: merge slots (signal strategy only), unit count,
 // planner look-back words; then its unit records
-static size_t stream_zeroed_bytes(const StreamPlan &q, int strategy)
+static size_t stream_zeroed_bytes(const StreamPlan &q, int strategy, uint32_t nsinks)
 {
     if (q.mode != UNIT_MERGE) return 0;
     size_t b = 0;
-    if (strategy != RS_STRATEGY_TAG) b += (size_t)q.n_units * sizeof(Slot);
+    // one array of slots per leaf (a tree's second leaf merges through its own)
+    if (strategy != RS_STRATEGY_TAG) b += (size_t)q.n_units * sizeof(Slot) * (nsinks > 1 ? nsinks : 1u);
     return b;
 }
 
@@ -458,8 +546,8 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 // [header | per stream: slots, unit count, planner look-back words | per stream: unit
 //  records | stream table].  Everything before zero_end is cleared by every run.
 template <class SP>
-static void layout_plan(SP *sp, size_t ns, int strategy, uint64_t *total_units, uint64_t *plan_tiles,
-                        uint32_t *Kmax, size_t *zero_end, size_t *table_off, size_t *total)
+static void layout_plan(SP *sp, size_t ns, int strategy, uint32_t nsinks, uint64_t *total_units,
+                        uint64_t *plan_tiles, uint32_t *Kmax, size_t *zero_end, size_t *table_off, size_t *total)
 {
     *total_units = *plan_tiles = 0;
     *Kmax = 1;
@@ -471,7 +559,7 @@ static void layout_plan(SP *sp, size_t ns, int strategy, uint64_t *total_units, 
         *plan_tiles += q.plan_tiles;
         if (q.mode == UNIT_MERGE) {
             q.slots_off = off;
-            off = align256(off + stream_zeroed_bytes(q, strategy));
+            off = align256(off + stream_zeroed_bytes(q, strategy, nsinks));
             q.ucount_off = off;
             off = align256(off + 4);
             q.planlb_off = off;
@@ -496,8 +584,8 @@ static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts
     pl.hdr_bytes = align256(sizeof(WsHeader));
     pl.sp.resize(p->streams.size());
     for (size_t i = 0; i < p->streams.size(); ++i) plan_stream(p, o, strategy, p->streams[i], pl.sp[i]);
-    layout_plan(pl.sp.data(), pl.sp.size(), strategy, &pl.total_units, &pl.plan_tiles, &pl.Kmax, &pl.zero_end,
-                &pl.table_off, &pl.total);
+    layout_plan(pl.sp.data(), pl.sp.size(), strategy, n_leaves(p->stages, p->n_stages), &pl.total_units,
+                &pl.plan_tiles, &pl.Kmax, &pl.zero_end, &pl.table_off, &pl.total);
     pl.table_bytes = pl.total - pl.table_off;
     return pl;
 }
@@ -578,7 +666,7 @@ static uint32_t plan_pow2(const PL &pl, size_t ns)
 }
 
 static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax, bool any_load, bool need_ctx,
-                              bool need_par, bool want_min)
+                              bool need_par, bool want_min, const Topo &topo)
 {
     const rs_pipeline_opts &o = p->opts;
     SmemLayout L;
@@ -622,6 +710,19 @@ static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax,
     off += nacc * 4;
     L.o_rm = (uint32_t)off;
     off += want_min ? nacc * 4 : 0;
+    // a tree's second leaf: per-parent accumulators of its own
+    L.o_rs2 = L.o_rs;
+    L.o_rc2 = L.o_rc;
+    L.o_rm2 = L.o_rm;
+    if (topo.mix && topo.n_sinks > 1) {
+        off = align_up(off, 8);
+        L.o_rs2 = (uint32_t)off;
+        off += nacc * 8;
+        L.o_rc2 = (uint32_t)off;
+        off += nacc * 4;
+        L.o_rm2 = (uint32_t)off;
+        off += want_min ? nacc * 4 : 0;
+    }
     off = align_up(off, 16);
     // rings for edges 1..n-2 (edge 0 carries element positions, staged in the tiles)
     const uint32_t nr = p->n_stages - 2;
@@ -629,6 +730,8 @@ static SmemLayout make_layout(const rs_pipeline *p, int strategy, uint32_t Kmax,
     L.o_qv = (uint32_t)off;
     off += (size_t)nr * o.queue_capacity * (strategy == RS_STRATEGY_TAG ? 8 : 4);
     L.o_qt = (uint32_t)off;
+    // the per-edge kernel: a 16-bit parent tag per slot for the edges that carry tags
+    off += topo.mix ? (size_t)nr * o.queue_capacity * 2 : 0;
     off = align_up(off, 16);
     // signal rings for edges 0..n-2
     L.o_sq = (uint32_t)off;
@@ -650,6 +753,16 @@ static int resolve_strategy(const rs_pipeline *p)
     }
     double mean = R ? (double)N / (double)R : 0.0;
     return mean >= 1024.0 ? RS_STRATEGY_SIGNAL : RS_STRATEGY_TAG;
+}
+
+// The strategy a run's kernels follow: the per-edge kernel (signal-strategy units and
+// layout) for trees and per-edge boundary modes, else the resolved strategy; -1 when the
+// modes are inconsistent for the resolved strategy.  *t gets the topology.
+static int run_strategy(const rs_pipeline *p, Topo *t)
+{
+    const int strategy = resolve_strategy(p);
+    if (make_topo(p->stages, p->n_stages, p->opts.boundary_modes, strategy, t) != RS_OK) return -1;
+    return t->mix ? RS_STRATEGY_SIGNAL : strategy;
 }
 
 // Unit shapes (regions_per_unit, region_cost) rs_autotune tries for the tag strategy on
@@ -732,7 +845,9 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     if (!p || !ws) return RS_ERR_INVALID;
     if (p->streams.empty()) return RS_ERR_NOT_READY;
     Launch &Lc = *out;
-    const int strategy = resolve_strategy(p);
+    Topo topo;
+    const int strategy = run_strategy(p, &topo);
+    if (strategy < 0) return RS_ERR_INVALID;
     if (strategy != RS_STRATEGY_TAG && p->opts.ensemble_width > 4 * RS_W) return RS_ERR_INVALID;
     Lc.pl = make_plan(p, strategy, p->opts);
     const Plan &pl = Lc.pl;
@@ -782,6 +897,9 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
             d.out_min = s.out_min;
             d.out_values = s.out_values;
             d.out_values_len = s.out_values_len;
+            d.out2_count = s.out2_count;
+            d.out2_sum = (unsigned long long *)s.out2_sum;
+            d.out2_min = s.out2_min;
             d.n_elements = s.n_elements;
             d.R = (uint32_t)s.n_regions;
             d.K = q.K;
@@ -855,10 +973,11 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     P.spin_limit = 2000000000ull;   // 2 s on the global timer
     P.cpl = tag_chunk_cpl(p);
     P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p, P.cpl)
-                                      : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
+                                      : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm, topo);
     P.plan_fill = strategy == RS_STRATEGY_TAG;
     P.m16 = 1u << 16;
     P.m19 = 1u << 19;
+    set_topo(P, topo);
 
     // processors per CTA: as asked, but no more than fit the per-block shared memory;
     // 0 = the count (8, 4, 2 or 1) giving the most resident processors per SM
@@ -1160,7 +1279,9 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
         if (check_opts(&c, fan) != RS_OK) return 1e30f;
         p->opts = c;
         p->table_dirty = true;
-        const int strategy = resolve_strategy(p);
+        Topo topo;
+        const int strategy = run_strategy(p, &topo);
+        if (strategy < 0) return 1e30f;
         if (make_plan(p, strategy, c).total > workspace_bytes) return 1e30f;
         rs_status st = run_impl(p, workspace, workspace_bytes, (cudaStream_t)stream);
         if (st == RS_ERR_CAPACITY) return 1e30f;
@@ -1330,8 +1451,8 @@ static void make_plan_fixed(const rs_pipeline *p, int strategy, FixedPlan *pl)
 {
     const size_t ns = p->streams.size();
     for (size_t i = 0; i < ns; ++i) plan_stream(p, p->opts, strategy, p->streams[i], pl->sp[i]);
-    layout_plan(pl->sp, ns, strategy, &pl->total_units, &pl->plan_tiles, &pl->Kmax, &pl->zero_end, &pl->table_off,
-                &pl->total);
+    layout_plan(pl->sp, ns, strategy, n_leaves(p->stages, p->n_stages), &pl->total_units, &pl->plan_tiles,
+                &pl->Kmax, &pl->zero_end, &pl->table_off, &pl->total);
 }
 
 extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
@@ -1339,7 +1460,9 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     if (!p) return RS_ERR_INVALID;
     if (p->streams.empty()) return RS_ERR_NOT_READY;
     if (p->streams.size() > RS_NOALLOC_MAX_STREAMS) return RS_ERR_CAPACITY;
-    const int strategy = resolve_strategy(p);
+    Topo topo;
+    const int strategy = run_strategy(p, &topo);
+    if (strategy < 0) return RS_ERR_INVALID;
     if (strategy != RS_STRATEGY_TAG && p->opts.ensemble_width > 4 * RS_W) return RS_ERR_INVALID;
     FixedPlan &pl = p->noalloc_plan;
     make_plan_fixed(p, strategy, &pl);
@@ -1376,6 +1499,9 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
         d.out_min = s.out_min;
         d.out_values = s.out_values;
         d.out_values_len = s.out_values_len;
+        d.out2_count = s.out2_count;
+        d.out2_sum = (unsigned long long *)s.out2_sum;
+        d.out2_min = s.out2_min;
         d.n_elements = s.n_elements;
         d.R = (uint32_t)s.n_regions;
         d.K = q.K;
@@ -1443,10 +1569,11 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     P.spin_limit = 2000000000ull;
     P.cpl = tag_chunk_cpl(p);
     P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p, P.cpl)
-                                      : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm);
+                                      : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm, topo);
     P.plan_fill = strategy == RS_STRATEGY_TAG;
     P.m16 = 1u << 16;
     P.m19 = 1u << 19;
+    set_topo(P, topo);
     if (!p->smem_max) {
         int dev = 0, v = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);

@@ -34,6 +34,13 @@ struct DevStage {
     uint32_t pad[2];
 };
 
+// How region boundaries travel over an edge (per-edge boundary modes).
+enum : uint32_t {
+    EM_SIG = 0,    // Begin/End signals with credits; ensembles cut at every signal (Section 3)
+    EM_TAG = 1,    // every item carries its region (Section 2.3 / Section 5)
+    EM_LANE = 2,   // signals with credits, ensembles not cut: each lane selects the pre- or
+                   // post-signal context of its own item (Section 6, future work)
+};
 // Work decomposition of a stream.
 enum : uint32_t {
     UNIT_REGIONS = 0,   // a unit is K whole consecutive parents (hashed elements: no offsets needed)
@@ -89,6 +96,10 @@ struct DevStream {
     // emit sink: region r's survivors go to out_values[emit_f * (offsets[r] - offsets[0]) ...]
     uint32_t *out_values;
     unsigned long long out_values_len;
+    // tree topologies: the second leaf's per-region results
+    uint32_t *out2_count;
+    unsigned long long *out2_sum;
+    uint32_t *out2_min;
 };
 
 // Status bits written by the device.
@@ -137,6 +148,8 @@ struct SmemLayout {
     // tag kernel: rings of records of the non-empty parents node 1 is reading (PR
     // entries; the {region, operand} ring is mirrored to 2 PR)
     uint32_t o_nra, o_nst, o_npar, pr;
+    // second leaf's per-parent accumulators (tree topologies)
+    uint32_t o_rc2, o_rs2, o_rm2;
 };
 
 struct KParams {
@@ -164,6 +177,13 @@ struct KParams {
                                   // (run-time values, so the shifts stay multiplies)
     uint32_t emit;                // the last stage is the emit sink (results per item, not per region)
     uint32_t emit_f;              // its segment slots per element: the product of the maximum fan-outs
+    // per-edge boundary modes and tree topologies (the generic per-edge kernel only):
+    // node c's input edge carries region boundaries as emode[c] (EM_SIG, EM_TAG or EM_LANE);
+    // node c reads the output of node up[c]; kids[i] has bit c set for each child c of node i;
+    // sink_of[c] numbers the aggregate / emit leaves in stage order (0xFF: not a leaf)
+    uint32_t mix;
+    uint32_t n_sinks;
+    uint8_t emode[RS_MAX_STAGES], up[RS_MAX_STAGES], kids[RS_MAX_STAGES], sink_of[RS_MAX_STAGES];
     SmemLayout L;
 };
 

@@ -64,9 +64,11 @@ struct Warp {
     uint32_t sh[RS_MAX_EDGES], st[RS_MAX_EDGES], em[RS_MAX_EDGES];
     // receiver state per node: current credit counter and current parent (local index)
     uint32_t credit[RS_MAX_STAGES], ctxk[RS_MAX_STAGES];
-    // aggregate accumulator (signal strategy)
+    // aggregate accumulator (signal strategy), and the second leaf's in a tree
     uint32_t acc_c, acc_m;
     unsigned long long acc_s;
+    uint32_t acc2_c, acc2_m;
+    unsigned long long acc2_s;
 };
 
 struct Smem {
@@ -75,6 +77,8 @@ struct Smem {
     SArr<uint16_t> qtag;
     SArr<unsigned long long> q64;   // tag strategy: ring slots packing {value, tag}
     SArr<uint32_t> mraw0, mraw1, mmoff0, mmoff1, mctx0, mctx1, mpar0, mpar1;
+    SArr<uint32_t> rc2, rm2;           // the second leaf's per-parent accumulators (trees)
+    SArr<unsigned long long> rs2;
     __device__ __forceinline__ SArr<uint32_t> raw(uint32_t b) const { return b ? mraw1 : mraw0; }
     __device__ __forceinline__ SArr<uint32_t> moffb(uint32_t b) const { return b ? mmoff1 : mmoff0; }
     __device__ __forceinline__ SArr<uint32_t> ctxb(uint32_t b) const { return b ? mctx1 : mctx0; }
@@ -295,11 +299,13 @@ __device__ __forceinline__ void poll_next(Pending &pu, const KParams &P, Smem &M
 // kernel.  Integer count / sum / min are associative and commutative, so the result
 // does not depend on the order of the pieces.
 __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint32_t off_abs, uint32_t ebase,
-                                            bool owner_piece, uint32_t cnt, unsigned long long sum, uint32_t mn)
+                                            bool owner_piece, uint32_t cnt, unsigned long long sum, uint32_t mn,
+                                            uint32_t sink = 0)
 {
     const unsigned long long D = S.D, c = S.c;
     const unsigned long long Pr = c * r + (off_abs - ebase);
-    Slot *sl = &S.slots[Pr / D];
+    // a tree's second leaf merges through a second array of slots
+    Slot *sl = &S.slots[(unsigned long long)sink * S.n_units + Pr / D];
     if (cnt) {
         atomicAdd(&sl->count, cnt);
         atomicAdd(&sl->sum, sum);
@@ -615,7 +621,7 @@ __device__ __forceinline__ uint32_t parent_at(const Smem &M, uint32_t from, uint
         if (lane == 0) M.cnt[4 * (node) + (field)] += (unsigned long long)(v); \
     } while (0)
 
-template <int STRAT, int V, class S>
+template <int STRAT, int V, class S, bool MIX = false>
 struct Proc {
     static constexpr uint32_t W = 32u * V;   // ensemble width (items per firing)
     const KParams &P;
@@ -648,6 +654,21 @@ struct Proc {
         if constexpr (S::generic) return P.st[I].op;
         else return (uint32_t)S::template op<I>();
     }
+
+    // How region boundaries reach node c over its input edge, and the topology.  Without
+    // MIX every edge carries signals (tags for STRAT == TAG) along a linear pipeline; the
+    // per-edge kernel (MIX) reads both from the parameters.
+    __device__ __forceinline__ uint32_t emode(int c) const
+    {
+        if constexpr (MIX) return P.emode[c];
+        else return STRAT == RS_STRATEGY_TAG ? EM_TAG : EM_SIG;
+    }
+    __device__ __forceinline__ uint32_t kids(int i) const { return P.kids[i]; }     // MIX only
+    __device__ __forceinline__ bool is_sink(int i) const { return P.sink_of[i] != 0xFFu; }   // MIX only
+    // the per-parent accumulators of leaf q (a tree has two)
+    __device__ __forceinline__ SArr<uint32_t> rcq(uint32_t q) const { return q ? M.rc2 : M.rc; }
+    __device__ __forceinline__ SArr<unsigned long long> rsq(uint32_t q) const { return q ? M.rs2 : M.rs; }
+    __device__ __forceinline__ SArr<uint32_t> rmq(uint32_t q) const { return q ? M.rm2 : M.rm; }
 
     // ---- tile staging ----
     __device__ __forceinline__ void issue_tiles() { tiles_issue(P, M, g, lane); }
@@ -756,7 +777,7 @@ struct Proc {
             const uint32_t q0 = w.qh[0];
             const bool hashed = op<0>() == D_ENUM_HASH;
             // parent of every item
-            if (STRAT == RS_STRATEGY_TAG) {
+            if (emode(1) == EM_TAG) {
                 const uint32_t end0 = M.moff[ek1 + 1];
                 if (end0 >= q0 + take) {
                     // the whole ensemble lies in one parent
@@ -814,7 +835,7 @@ struct Proc {
             const uint32_t C = P.C, cm = C - 1;
             const uint32_t rb = (I - 2) * C;   // input edge I-1 is ring I-2
             const uint32_t h = w.qh[I - 1];
-            if (STRAT == RS_STRATEGY_TAG) {
+            if (emode(I) == EM_TAG) {
                 // tags are non-decreasing along a queue: equal ends mean one parent
                 const uint32_t k0 = M.qtag[rb + (h & cm)];
                 uni = k0 == M.qtag[rb + ((h + take - 1) & cm)];
@@ -831,7 +852,7 @@ struct Proc {
                 if (F || q < take) {
                     const uint32_t slot = rb + ((h + q) & cm);
                     x[s] = M.qv[slot];
-                    if (STRAT == RS_STRATEGY_TAG && !uni) k[s] = M.qtag[slot];
+                    if (emode(I) == EM_TAG && !uni) k[s] = M.qtag[slot];
                 }
             }
         }
@@ -842,6 +863,12 @@ struct Proc {
     template <int I, bool F>
     __device__ __forceinline__ void element_stage(uint32_t take)
     {
+        if constexpr (MIX) {
+            uint32_t x[V], k[V], bal[V];
+            const bool uni = gather<I, F>(take, x, k);
+            (void)mix_stage<I>(x, k, uni, take, bal);
+            return;
+        }
         if (F) take = W;
         const DevStage &sd = P.st[I];
         const uint32_t opc = op<I>();
@@ -967,6 +994,11 @@ struct Proc {
     {
         if (F) take = W;
         uint32_t x[V], k[V];
+        if constexpr (MIX) {
+            const bool uni = gather<I, F>(take, x, k);
+            mix_sink<I>(x, k, uni, take);
+            return;
+        }
         (void)gather<I, F>(take, x, k);
         if constexpr (STRAT == RS_STRATEGY_SIGNAL) {
             if (S::generic && P.emit) {
@@ -1052,6 +1084,7 @@ struct Proc {
     template <int I>
     __device__ __forceinline__ bool signal_phase(bool last)
     {
+        if constexpr (MIX) return mix_signal_phase<I>(last);
         const uint32_t SC = P.SC;
         bool progress = false;
         while (w.credit[I] == 0 && w.sh[I - 1] != w.st[I - 1]) {
@@ -1128,7 +1161,8 @@ struct Proc {
             if (I >= nst() || stop) return;
             const long long pt = PROF_NOW();
             (void)pt;
-            fire_body<I>(drain);
+            if constexpr (MIX) mix_fire<I>(drain);
+            else fire_body<I>(drain);
             PROF_ADD(PF_NODE0 + I, pt);
         }
     }
@@ -1205,6 +1239,564 @@ struct Proc {
         return (w.qh[e] == w.qt[e]) && (w.sh[e] == w.st[e]);
     }
 
+    // =====================================================================================
+    // The per-edge kernel (MIX): every edge carries region boundaries its own way (EM_SIG,
+    // EM_TAG or EM_LANE, as the parameters say) and a node may feed several children (a
+    // tree, Figure 1(b): its output stream, and with it every region boundary, is
+    // replicated to each child).  Tags never turn back into signals: below an EM_TAG edge
+    // every edge is EM_TAG (checked by the host).
+
+    // node I's operation on one ensemble (per-item contexts unless uni) and the push of its
+    // outputs to every child's ring, with tags for the children fed by tags.  bal[s] is the
+    // ballot of slot s's kept items (fan-out 1); returns the outputs pushed.
+    template <int I>
+    __device__ __forceinline__ uint32_t mix_stage(const uint32_t (&x)[V], const uint32_t (&k)[V], bool uni,
+                                                  uint32_t take, uint32_t (&bal)[V])
+    {
+        const DevStage &sd = P.st[I];
+        const uint32_t opc = op<I>();
+        const uint32_t C = P.C, cm = C - 1;
+        const uint32_t km = kids(I);
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int s = 0; s < V; ++s) bal[s] = 0;
+        if (opc == D_EXPAND) {
+            uint32_t total = 0;
+#pragma unroll
+            for (int s = 0; s < V; ++s) {
+                if (32u * s < take) {
+                    const bool act = 32u * s + lane < take;
+                    const uint32_t nout = act ? fmix32(x[s] ^ sd.c0) % (sd.fanout + 1u) : 0u;
+                    const uint32_t incl = warp_incl_scan_u32(nout, lane);
+                    const uint32_t tot = __shfl_sync(FULLMASK, incl, 31);
+#pragma unroll
+                    for (int c = 2; c < RS_MAX_STAGES; ++c) {
+                        if (!(km & (1u << c))) continue;
+                        const uint32_t orb = (c - 2) * C;
+                        const bool tagc = emode(c) == EM_TAG;
+                        const uint32_t base = w.qt[c - 1] + incl - nout;
+                        for (uint32_t j = 0; j < nout; ++j) {
+                            const uint32_t slot = orb + ((base + j) & cm);
+                            M.qv[slot] = fmix32(x[s] ^ fmix32((sd.p0 + 1u + j) ^ RS_GOLD));
+                            if (tagc) M.qtag[slot] = (uint16_t)k[s];
+                        }
+                        w.qt[c - 1] += tot;
+                        w.em[c - 1] += tot;
+                    }
+                    total += tot;
+                }
+            }
+            return total;
+        }
+        bool keep[V];
+        uint32_t y[V];
+        uint32_t cu = 0;
+        if (opc == D_FILT_HASH_CTX && uni) cu = M.mctx[k[0]];
+        if (opc == D_FILT_WEIGHT && uni) cu = fmix32(M.mpar[k[0]] ^ sd.c0);
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            const uint32_t xs = x[s];
+            bool kp;
+            uint32_t ys = xs;
+            switch (opc) {
+            case D_FILT_MASK: kp = (xs & sd.p0) == sd.p1; break;
+            case D_FILT_MOD: kp = (xs % sd.p0) == sd.p1; break;
+            case D_FILT_HASH_CTX: kp = (fmix32(xs ^ sd.c0) ^ (uni ? cu : M.mctx[k[s]])) < sd.p1; break;
+            case D_FILT_WEIGHT: kp = fmix32(xs ^ sd.c0) < (uni ? cu : fmix32(M.mpar[k[s]] ^ sd.c0)); break;
+            case D_MAP_MULADD: ys = xs * sd.p0 + sd.p1; kp = true; break;
+            default: kp = false; break;
+            }
+            keep[s] = kp && 32u * s + lane < take;
+            y[s] = ys;
+        }
+        uint32_t tot = 0;
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            bal[s] = 32u * s < take ? __ballot_sync(FULLMASK, keep[s]) : 0u;
+            tot += __popc(bal[s]);
+        }
+#pragma unroll
+        for (int c = 2; c < RS_MAX_STAGES; ++c) {
+            if (!(km & (1u << c))) continue;
+            const uint32_t orb = (c - 2) * C;
+            const bool tagc = emode(c) == EM_TAG;
+            uint32_t base = w.qt[c - 1];
+#pragma unroll
+            for (int s = 0; s < V; ++s) {
+                if (keep[s]) {
+                    const uint32_t slot = orb + ((base + __popc(bal[s] & lt)) & cm);
+                    M.qv[slot] = y[s];
+                    if (tagc) M.qtag[slot] = (uint16_t)k[s];
+                }
+                base += __popc(bal[s]);
+            }
+            w.qt[c - 1] = base;
+            w.em[c - 1] += tot;
+        }
+        return tot;
+    }
+
+    // the emit sink fed by tags or per-lane contexts: one position claimed per item
+    __device__ __forceinline__ void emit_items(const uint32_t (&x)[V], const uint32_t (&k)[V], uint32_t take)
+    {
+        const uint32_t o0 = __ldg(ds->offsets);
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            if (32u * s + lane < take) {
+                const uint32_t r = r0 + k[s];
+                const unsigned long long pos =
+                    (unsigned long long)P.emit_f * (__ldg(ds->offsets + r) - o0) + atomicAdd(ds->out_count + r, 1u);
+                if (pos < ds->out_values_len) ds->out_values[pos] = x[s];
+                else atomicOr(&P.hdr->status, ST_BAD_INPUT);
+            }
+        }
+    }
+
+    // leaf I (an aggregate or the emit sink) takes one ensemble: fed by signals, the whole
+    // ensemble belongs to the leaf's current parent (Section 3.3) and folds into its
+    // running accumulator; fed by tags or per-lane contexts, runs of equal parents fold
+    // into the per-parent accumulators (segmented warp reduction)
+    template <int I>
+    __device__ __forceinline__ void mix_sink(const uint32_t (&x)[V], const uint32_t (&k)[V], bool uni, uint32_t take)
+    {
+        const uint32_t q = P.sink_of[I];
+        if (emode(I) == EM_SIG) {
+            if (P.emit) {
+                emit_ensemble(x, take);
+                return;
+            }
+            unsigned long long part = 0;
+            uint32_t mn = 0xFFFFFFFFu;
+#pragma unroll
+            for (int s = 0; s < V; ++s) {
+                if (32u * s + lane < take) {
+                    part += x[s];
+                    mn = min(mn, x[s]);
+                }
+            }
+            const uint32_t lo = __reduce_add_sync(FULLMASK, (uint32_t)(part & 0xFFFFu));
+            const uint32_t hi = __reduce_add_sync(FULLMASK, (uint32_t)(part >> 16));
+            const unsigned long long sm = ((unsigned long long)hi << 16) + lo;
+            mn = __reduce_min_sync(FULLMASK, mn);
+            if (q == 0) {
+                w.acc_c += take;
+                w.acc_s += sm;
+                w.acc_m = min(w.acc_m, mn);
+            } else {
+                w.acc2_c += take;
+                w.acc2_s += sm;
+                w.acc2_m = min(w.acc2_m, mn);
+            }
+            return;
+        }
+        if (P.emit) {
+            emit_items(x, k, take);
+            return;
+        }
+        const SArr<uint32_t> rc = rcq(q), rm = rmq(q);
+        const SArr<unsigned long long> rs = rsq(q);
+        (void)uni;
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            const uint32_t sb = 32u * s;
+            if (sb >= take) break;
+            const uint32_t n = min(32u, take - sb);
+            const bool act = lane < n;
+            const uint32_t v = act ? x[s] : 0u;
+            const uint32_t kk = act ? k[s] : 0xFFFFFFFFu;
+            // runs of equal parents: per-lane contexts never decrease along the ensemble
+            const uint32_t kprev = __shfl_up_sync(FULLMASK, kk, 1);
+            const uint32_t knext = __shfl_down_sync(FULLMASK, kk, 1);
+            const bool head = lane == 0 || kk != kprev;
+            const bool tail = lane == 31 || kk != knext;
+            const uint32_t heads = __ballot_sync(FULLMASK, head);
+            const uint32_t hl = 31 - __clz(heads & ((2u << lane) - 1u));
+            unsigned long long ps = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long t = __shfl_up_sync(FULLMASK, ps, d);
+                if (lane >= (uint32_t)d) ps += t;
+            }
+            unsigned long long before = __shfl_sync(FULLMASK, ps, hl > 0 ? hl - 1 : 0);
+            if (hl == 0) before = 0;
+            uint32_t m = act ? v : 0xFFFFFFFFu;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULLMASK, m, d);
+                if (lane >= (uint32_t)d && lane - d >= hl) m = min(m, t);
+            }
+            if (act && tail) {
+                rc[kk] += lane - hl + 1;
+                rs[kk] += ps - before;
+                if (P.want_min) rm[kk] = min(rm[kk], m);
+            }
+            __syncwarp();
+        }
+    }
+
+    // the signal phase of a node fed by signals (receiver rule 2b, as signal_phase), with
+    // the signals forwarded to every child that takes signals, each with the credit of its
+    // own edge's sender rules, and an End at a leaf reporting that leaf's accumulator
+    template <int I>
+    __device__ __forceinline__ bool mix_signal_phase(bool last)
+    {
+        const uint32_t SC = P.SC;
+        const uint32_t km = kids(I);
+        const uint32_t q = last ? P.sink_of[I] : 0u;
+        bool progress = false;
+        while (w.credit[I] == 0 && w.sh[I - 1] != w.st[I - 1]) {
+            const uint32_t h = sidx(I - 1, w.sh[I - 1]);
+            const uint32_t hcr = M.sq[h + 1];
+            if (hcr > 0) {
+                w.credit[I] = hcr;
+                __syncwarp();
+                if (lane == 0) M.sq[h + 1] = 0;
+                __syncwarp();
+                progress = true;
+                break;
+            }
+            uint32_t room = 32u;
+            if (!last) {
+#pragma unroll
+                for (int c = 2; c < RS_MAX_STAGES; ++c)
+                    if ((km & (1u << c)) && emode(c) != EM_TAG) room = min(room, SC - (w.st[c - 1] - w.sh[c - 1]));
+            }
+            const uint32_t mmax = min(min(32u, w.st[I - 1] - w.sh[I - 1]), room);
+            if (mmax == 0) break;
+            const bool in = lane < mmax;
+            const uint32_t j = sidx(I - 1, w.sh[I - 1] + lane);
+            const uint32_t word = in ? M.sq[j] : 0u;
+            const uint32_t cr = in ? M.sq[j + 1] : 1u;
+            const uint32_t nz = __ballot_sync(FULLMASK, cr != 0u);
+            const uint32_t m = nz ? (uint32_t)(__ffs(nz) - 1) : 32u;
+            const bool mine = lane < m;
+            const bool is_begin = mine && !(word & SIG_END);
+            const uint32_t begins = __ballot_sync(FULLMASK, is_begin);
+            if (begins) w.ctxk[I] = __shfl_sync(FULLMASK, word, 31 - __clz(begins));
+            if (last) {
+                uint32_t ac = q ? w.acc2_c : w.acc_c, am = q ? w.acc2_m : w.acc_m;
+                unsigned long long as = q ? w.acc2_s : w.acc_s;
+                if (mine && (word & SIG_END)) {
+                    const uint32_t kk = word & ~SIG_END;
+                    const bool fresh = (begins & lanemask_lt()) != 0u;
+                    rcq(q)[kk] = fresh ? 0u : ac;
+                    rsq(q)[kk] = fresh ? 0ull : as;
+                    if (P.want_min) rmq(q)[kk] = fresh ? 0xFFFFFFFFu : am;
+                }
+                if (begins) {
+                    if (q) {
+                        w.acc2_c = 0;
+                        w.acc2_s = 0;
+                        w.acc2_m = 0xFFFFFFFFu;
+                    } else {
+                        w.acc_c = 0;
+                        w.acc_s = 0;
+                        w.acc_m = 0xFFFFFFFFu;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 2; c < RS_MAX_STAGES; ++c) {
+                    if (!(km & (1u << c)) || emode(c) == EM_TAG) continue;
+                    const uint32_t c0 = (w.sh[c - 1] == w.st[c - 1]) ? (w.qt[c - 1] - w.qh[c - 1]) : w.em[c - 1];
+                    if (mine) {
+                        const uint32_t o = sidx(c - 1, w.st[c - 1] + lane);
+                        M.sq[o] = word;
+                        M.sq[o + 1] = lane == 0 ? c0 : 0u;
+                    }
+                    w.st[c - 1] += m;
+                    w.em[c - 1] = 0;
+                }
+            }
+            __syncwarp();
+            w.sh[I - 1] += m;
+            CNT_ADD(I, 2, m);
+            progress = true;
+        }
+        return progress;
+    }
+
+    // Per-lane state selection (Section 6): node I's input edge carries signals, but its
+    // ensembles are not cut at them.  The signals whose position falls inside the
+    // ensemble are consumed with it.  Positions come from the credits: the head signal's
+    // counts the items before it (w.credit[I] holds it once taken off the ring), each later
+    // one the items since the signal before.  Every lane takes the context of the last
+    // Begin at or before its item; each consumed signal is forwarded to the children that
+    // take signals with the credit the sender rules give it at its place among the
+    // outputs (the first: |Q| or the count since the child's last signal, plus the outputs
+    // before it; the others: the outputs since the signal before).  Fan-out 1 only (the
+    // host rejects an expansion fed this way).  Returns false when nothing was consumed.
+    template <int I>
+    __device__ __forceinline__ bool lane_step(bool drain, uint32_t &took, uint32_t &nsig)
+    {
+        const uint32_t e = I - 1;
+        const uint32_t C = P.C, SC = P.SC;
+        const bool last = is_sink(I);
+        const uint32_t km = last ? 0u : kids(I);
+        uint32_t space = W, sroom = 32u;
+        bool fwd = false;
+#pragma unroll
+        for (int c = 2; c < RS_MAX_STAGES; ++c) {
+            if (!(km & (1u << c))) continue;
+            space = min(space, C - (w.qt[c - 1] - w.qh[c - 1]));
+            if (emode(c) != EM_TAG) {
+                sroom = min(sroom, SC - (w.st[c - 1] - w.sh[c - 1]));
+                fwd = true;
+            }
+        }
+        const uint32_t avail = w.qt[e] - w.qh[e];
+        uint32_t take = min(min(avail, W), space);
+        if (!drain && take < W) take = 0;   // full ensembles only until the input is drained
+        const uint32_t pend = w.st[e] - w.sh[e];
+        const uint32_t np = min(32u, pend);
+        const bool in = lane < np;
+        const uint32_t sj = sidx(e, w.sh[e] + lane);
+        const uint32_t word = in ? M.sq[sj] : 0u;
+        const uint32_t cr = in ? M.sq[sj + 1] : 0u;
+        const uint32_t pos = w.credit[I] + warp_incl_scan_u32(cr, lane);
+        uint32_t m = __popc(__ballot_sync(FULLMASK, in && pos <= take));
+        if (fwd) m = min(m, sroom);
+        // the items of this step stop at the first signal left on the ring
+        if (m < np) take = min(take, __shfl_sync(FULLMASK, pos, m));
+        else if (m > 0 && pend > np) take = min(take, __shfl_sync(FULLMASK, pos, m - 1));
+        if (take == 0 && m == 0) return false;
+        uint32_t x[V], k[V];
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+            x[s] = 0;
+            k[s] = w.ctxk[I];
+        }
+        if (take > 0) (void)gather<I, false>(take, x, k);
+        if (stop) return false;
+        // contexts: mark the item of every Begin that falls strictly inside the ensemble
+        // (the later Begin wins at one position), then a running maximum over the items
+        const bool begin = lane < m && !(word & SIG_END);
+        const uint32_t inside = __ballot_sync(FULLMASK, begin && pos < take);
+        if (inside) {
+#pragma unroll
+            for (int s = 0; s < V; ++s) M.scr[32u * s + lane] = 0u;
+            __syncwarp();
+            if (begin && pos < take) atomicMax(&M.scr[pos], lane + 1u);
+            __syncwarp();
+            uint32_t carry = 0;
+#pragma unroll
+            for (int s = 0; s < V; ++s) {
+                const uint32_t mk = M.scr[32u * s + lane];
+                uint32_t inc = mk;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) inc = max(inc, __shfl_up_sync(FULLMASK, inc, d));
+                const uint32_t rel = max(carry, inc);
+                carry = max(carry, __shfl_sync(FULLMASK, inc, 31));
+                const uint32_t kw = __shfl_sync(FULLMASK, word, rel ? rel - 1u : 0u);
+                if (rel) k[s] = kw;
+            }
+            __syncwarp();
+        }
+        const uint32_t begins = __ballot_sync(FULLMASK, begin);
+        if (last) {
+            if (take > 0) mix_sink<I>(x, k, inside == 0u, take);
+        } else {
+            // the children's queues before this step's outputs (for the first credit)
+            uint32_t first[RS_MAX_STAGES];
+#pragma unroll
+            for (int c = 2; c < RS_MAX_STAGES; ++c) {
+                first[c] = 0;
+                if ((km & (1u << c)) && emode(c) != EM_TAG)
+                    first[c] = (w.sh[c - 1] == w.st[c - 1]) ? (w.qt[c - 1] - w.qh[c - 1]) : w.em[c - 1];
+            }
+            uint32_t bal[V];
+            uint32_t tot = 0;
+            if (take > 0) tot = mix_stage<I>(x, k, inside == 0u, take, bal);
+            else {
+#pragma unroll
+                for (int s = 0; s < V; ++s) bal[s] = 0;
+            }
+            if (m > 0 && fwd) {
+                // outputs of the items before each consumed signal's position
+                uint32_t ob = 0;
+#pragma unroll
+                for (int s = 0; s < V; ++s) {
+                    const uint32_t lo = 32u * s;
+                    if (pos >= lo + 32u) ob += __popc(bal[s]);
+                    else if (pos > lo) ob += __popc(bal[s] & ((1u << (pos - lo)) - 1u));
+                }
+                const uint32_t obp = __shfl_up_sync(FULLMASK, ob, 1);
+                const uint32_t oblast = __shfl_sync(FULLMASK, ob, m - 1);
+#pragma unroll
+                for (int c = 2; c < RS_MAX_STAGES; ++c) {
+                    if (!(km & (1u << c)) || emode(c) == EM_TAG) continue;
+                    if (lane < m) {
+                        const uint32_t o = sidx(c - 1, w.st[c - 1] + lane);
+                        M.sq[o] = word;
+                        M.sq[o + 1] = lane == 0 ? first[c] + ob : ob - obp;
+                    }
+                    w.st[c - 1] += m;
+                    w.em[c - 1] = tot - oblast;
+                }
+            }
+        }
+        if (begins) w.ctxk[I] = __shfl_sync(FULLMASK, word, 31 - __clz(begins));
+        // the head left on the ring: the items still before it
+        if (m < np) {
+            const uint32_t pm = __shfl_sync(FULLMASK, pos, m);
+            if (lane == m) M.sq[sj + 1] = 0;
+            w.credit[I] = pm - take;
+        } else {
+            w.credit[I] = 0;
+        }
+        __syncwarp();
+        w.qh[e] += take;
+        w.sh[e] += m;
+        if constexpr (I == 1) {
+            if (op<0>() == D_ENUM_LOAD && E0 + w.qh[0] >= g.free_lim) release_below(E0 + w.qh[0]);
+        }
+        CNT_ADD(I, 2, m);
+        took = take;
+        nsig = m;
+        return true;
+    }
+
+    // fire node I (MIX): per-lane selection steps for an EM_LANE input, else the data and
+    // signal phases of fire_body with the children's room and modes
+    template <int I>
+    __device__ __forceinline__ void mix_fire(bool drain)
+    {
+        const uint32_t mode = emode(I);
+        const bool last = is_sink(I);
+        const uint32_t km = last ? 0u : kids(I);
+        bool fired = false;
+        uint32_t n_ens = 0, n_items = 0;
+        if (mode == EM_LANE) {
+            for (;;) {
+                uint32_t took = 0, nsig = 0;
+                if (!lane_step<I>(drain, took, nsig)) break;
+                if (!fired) {
+                    CNT_ADD(I, 3, 1);
+                    fired = true;
+                }
+                if (took) {
+                    n_ens++;
+                    n_items += took;
+                }
+                if (stop) break;
+            }
+        } else {
+            const uint32_t fan = op<I>() == D_EXPAND ? P.st[I].fanout : 1u;
+            for (;;) {
+                const bool sigp = mode == EM_SIG && w.sh[I - 1] != w.st[I - 1];
+                const uint32_t avail0 = w.qt[I - 1] - w.qh[I - 1];
+                if (!(drain ? (avail0 > 0 || sigp) : (avail0 >= W || sigp))) break;
+                if (!fired) {
+                    CNT_ADD(I, 3, 1);
+                    fired = true;
+                }
+                bool progress = false;
+                for (;;) {
+                    uint32_t want = min(w.qt[I - 1] - w.qh[I - 1], W);
+                    if (sigp) want = min(want, w.credit[I]);
+                    uint32_t take = want;
+                    if (!last) {
+                        uint32_t space = 0xFFFFFFFFu;
+#pragma unroll
+                        for (int c = 2; c < RS_MAX_STAGES; ++c)
+                            if (km & (1u << c)) space = min(space, P.C - (w.qt[c - 1] - w.qh[c - 1]));
+                        take = min(take, fan == 1u ? space : space / fan);
+                    }
+                    if (take == 0) break;
+                    if (take < want) break;                       // wait for downstream space
+                    if (!drain && !sigp && take < W) break;       // wait for a full ensemble
+                    if (last) aggregate<I, false>(take);
+                    else element_stage<I, false>(take);
+                    if (stop) break;
+                    __syncwarp();
+                    w.qh[I - 1] += take;
+                    if (sigp) w.credit[I] -= take;
+                    n_ens++;
+                    n_items += take;
+                    progress = true;
+                    if constexpr (I == 1) {
+                        if (op<0>() == D_ENUM_LOAD && E0 + w.qh[0] >= g.free_lim) release_below(E0 + w.qh[0]);
+                    }
+                }
+                if (stop) break;
+                if (mode == EM_SIG) progress |= signal_phase<I>(last);
+                if (!progress) break;
+            }
+        }
+        if (n_ens) {
+            CNT_ADD(I, 0, n_ens);
+            CNT_ADD(I, 1, n_items);
+        }
+    }
+
+    // one unit through the per-edge pipeline: the scheduler of run_unit over the tree,
+    // upstream first; a node drains once its producer has drained and its producer's
+    // input edge is empty
+    __device__ __forceinline__ void mix_run_unit()
+    {
+#pragma unroll
+        for (int i = 0; i < RS_MAX_EDGES; ++i) w.qh[i] = w.qt[i] = w.sh[i] = w.st[i] = w.em[i] = 0;
+#pragma unroll
+        for (int i = 0; i < RS_MAX_STAGES; ++i) w.credit[i] = w.ctxk[i] = 0;
+        w.acc_c = w.acc2_c = 0;
+        w.acc_s = w.acc2_s = 0;
+        w.acc_m = w.acc2_m = 0xFFFFFFFFu;
+        ek = 0;
+        const int n = nst();
+        // leaves fed by tags or per-lane contexts fold into per-parent accumulators, which
+        // start at the identity
+        for (int i = 1; i < n; ++i) {
+            if (!is_sink(i) || emode(i) == EM_SIG) continue;
+            const uint32_t q = P.sink_of[i];
+            for (uint32_t kk = lane; kk < nk; kk += 32) {
+                rcq(q)[kk] = 0u;
+                rsq(q)[kk] = 0ull;
+                rmq(q)[kk] = 0xFFFFFFFFu;
+            }
+        }
+        __syncwarp();
+        const bool tag0 = emode(1) == EM_TAG;
+        if (tag0) {
+            w.qt[0] = total;
+            CNT_ADD(0, 0, (total + W - 1) / W);
+            CNT_ADD(0, 1, total);
+            ek1 = 0;
+            if (total > 0) advance_ek1(0, 0);
+        }
+        for (unsigned long long sweep = 0;; ++sweep) {
+            CNT_ADD(0, 3, 1);
+            if (nxt_open) {
+                poll_next(*nxt, P, M, lane);
+                nxt_open = !nxt->scanned;
+            }
+            if (!tag0) enum_signal();
+            const bool done0 = tag0 || ek >= nk;
+            uint32_t dm = 0;   // bit i: node i drains
+#define RS_MIX_FIRE(I)                                                                            \
+            if (I < n) {                                                                          \
+                const uint32_t u = P.up[I];                                                       \
+                const bool d = u == 0 ? done0 : (((dm >> u) & 1u) && edge_empty((int)u - 1));     \
+                if (d) dm |= 1u << I;                                                             \
+                fire<I>(d);                                                                       \
+            }
+            RS_MIX_FIRE(1)
+            RS_MIX_FIRE(2)
+            RS_MIX_FIRE(3)
+            RS_MIX_FIRE(4)
+            RS_MIX_FIRE(5)
+#undef RS_MIX_FIRE
+            if (stop) return;
+            bool all = done0;
+            for (int e2 = 0; e2 + 1 < n; ++e2) all = all && edge_empty(e2);
+            if (all) break;
+            if (sweep >= P.budget) {
+                if (lane == 0) atomicOr(&P.hdr->status, ST_STALL);
+                stop = true;
+                return;
+            }
+        }
+    }
+
     // ---- run one unit to completion: the non-preemptive scheduler of Section 2.1 ----
     // Each sweep offers every node a firing, upstream first.
     __device__ __forceinline__ void run_unit()
@@ -1263,7 +1855,7 @@ struct Proc {
 
 // ---------------------------------------------------------------------------
 
-template <int STRAT, int V, class SG>
+template <int STRAT, int V, class SG, bool MIX = false>
 __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_constant__ KParams P)
 {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -1289,6 +1881,9 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
     M.rc = sarr<uint32_t>(wb + P.L.o_rc);
     M.rs = sarr<unsigned long long>(wb + P.L.o_rs);
     M.rm = sarr<uint32_t>(wb + P.L.o_rm);
+    M.rc2 = sarr<uint32_t>(wb + P.L.o_rc2);
+    M.rs2 = sarr<unsigned long long>(wb + P.L.o_rs2);
+    M.rm2 = sarr<uint32_t>(wb + P.L.o_rm2);
     M.qv = sarr<uint32_t>(wb + P.L.o_qv);
     M.qtag = sarr<uint16_t>(wb + P.L.o_qt);
     M.q64 = sarr<unsigned long long>(wb + P.L.o_qv);
@@ -1413,7 +2008,7 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
         PROF_ADD(PF_SETUP, pt_setup);
         bool pstop;
         {
-            Proc<STRAT, V, SG> pr(P, M, w, g, lane);
+            Proc<STRAT, V, SG, MIX> pr(P, M, w, g, lane);
             pr.nxt = pend;
             pr.nxt_open = nxt.u.valid && !nxt.scanned;
             pr.nk = nk;
@@ -1422,7 +2017,8 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
             pr.ds = &S;
             pr.r0 = r0;
             if (g.tma) pr.issue_tiles();
-            pr.run_unit();
+            if constexpr (MIX) pr.mix_run_unit();
+            else pr.run_unit();
             pr.finish_tiles();
             pstop = pr.stop;
         }
@@ -1444,6 +2040,12 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
                 if (P.want_count) S.out_count[r0 + k] = M.rc[k];
                 if (P.want_sum) S.out_sum[r0 + k] = M.rs[k];
                 if (P.want_min) S.out_min[r0 + k] = M.rm[k];
+                if (MIX && P.n_sinks > 1) {
+                    // a tree's second leaf
+                    if (P.want_count) S.out2_count[r0 + k] = M.rc2[k];
+                    if (P.want_sum) S.out2_sum[r0 + k] = M.rs2[k];
+                    if (P.want_min) S.out2_min[r0 + k] = M.rm2[k];
+                }
             }
         }
         // accumulator of the first and the last parent: index 0 and nk - 1 (signal
@@ -1456,6 +2058,14 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
             if (split_tail && !(split_head && nk == 1))
                 merge_piece(S, r0 + nk - 1, cur.tail_off, cur.u.ebase, true, M.rc[at], M.rs[at],
                             P.want_min ? M.rm[at] : 0xFFFFFFFFu);
+            if (MIX && P.n_sinks > 1) {
+                if (split_head)
+                    merge_piece(S, r0, cur.u.head_off, cur.u.ebase, false, M.rc2[ah], M.rs2[ah],
+                                P.want_min ? M.rm2[ah] : 0xFFFFFFFFu, 1);
+                if (split_tail && !(split_head && nk == 1))
+                    merge_piece(S, r0 + nk - 1, cur.tail_off, cur.u.ebase, true, M.rc2[at], M.rs2[at],
+                                P.want_min ? M.rm2[at] : 0xFFFFFFFFu, 1);
+            }
         }
         __syncwarp();
         PROF_ADD(PF_FLUSH, pt_fl);
@@ -1499,7 +2109,11 @@ struct KEntry {
     RS_KSIG(ST, 1, OE, O1, O2, O3, O4), RS_KSIG(ST, 2, OE, O1, O2, O3, O4), RS_KSIG(ST, 4, OE, O1, O2, O3, O4)
 #define RS_KBOTH(OE, O1, O2, O3, O4) RS_KALLV(RS_STRATEGY_SIGNAL, OE, O1, O2, O3, O4)
 
+// the per-edge kernel (boundary modes per edge, tree topologies): generic ops only
+#define RS_KMIX(V) {-1, V, 0, 0, 0, 0, 0, (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, V, GenericSig, true>}
+
 static const KEntry g_kernels[] = {
+    RS_KMIX(1), RS_KMIX(2), RS_KMIX(4),
     // loaded elements -> three context hash filters -> aggregate
     RS_KBOTH(D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),
     // hashed elements -> power-of-two modulus filter -> multiply-add map -> aggregate
@@ -1512,6 +2126,11 @@ static const KEntry g_kernels[] = {
 
 static const void *kernel_ptr(const KParams &P)
 {
+    if (P.mix) {
+        for (const KEntry &e : g_kernels)
+            if (e.strategy == -1 && e.V == (int)P.V) return e.fn;
+        return nullptr;
+    }
     if (P.strategy == RS_STRATEGY_TAG) return rs_tag_kernel_entry(P);
     int ops[5] = {0, 0, 0, 0, 0};
     ops[0] = (int)P.st[0].op;
@@ -1570,6 +2189,13 @@ __global__ void __launch_bounds__(256) rs_finalize_kernel(const __grid_constant_
             if (P.want_count) S.out_count[r] = sl.count;
             if (P.want_sum) S.out_sum[r] = sl.sum;
             if (P.want_min) S.out_min[r] = ~sl.min_inv;
+            if (P.mix && P.n_sinks > 1) {
+                // a tree's second leaf: its own slots, after the first leaf's
+                const Slot s2 = S.slots[S.n_units + u];
+                if (P.want_count) S.out2_count[r] = s2.count;
+                if (P.want_sum) S.out2_sum[r] = s2.sum;
+                if (P.want_min) S.out2_min[r] = ~s2.min_inv;
+            }
         }
     }
 }

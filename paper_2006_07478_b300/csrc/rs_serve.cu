@@ -344,6 +344,9 @@ rs_status rs_server_create(const rs_stage_desc *stages, uint32_t n_stages, const
     // requests carry per-region outputs only: a pipeline ending in an emit sink is not served
     if (!stages || n_stages < 2 || n_stages > RS_MAX_STAGES || stages[n_stages - 1].kind == RS_EMIT)
         return RS_ERR_INVALID;
+    // ... and a request has one leaf's results: linear pipelines only
+    for (uint32_t i = 1; i < n_stages; ++i)
+        if (stages[i].input && stages[i].input != i - 1) return RS_ERR_INVALID;
     // validate the stage list and options once, through the pipeline's own checks
     rs_pipeline *probe = nullptr;
     rs_status st = rs_pipeline_create(stages, n_stages, opts, &probe);

@@ -30,6 +30,22 @@ RS_ERR_STALL, RS_ERR_CAPACITY, RS_ERR_STATE, RS_ERR_DEVICE_INPUT = 5, 6, 7, 8
 RS_ENUM_HASH, RS_ENUM_LOAD, RS_FILTER, RS_MAP, RS_EXPAND, RS_AGGREGATE, RS_EMIT = 1, 2, 3, 4, 5, 6, 7
 RS_OP_NONE, RS_OP_MOD_EQ, RS_OP_HASH_CTX_LT, RS_OP_WEIGHT_LT, RS_OP_MUL_ADD, RS_OP_HASH_FANOUT = 0, 1, 2, 3, 4, 5
 STRATEGIES = {"signal": 0, "tag": 1, "auto": 2}
+BOUNDARIES = {"default": 0, "signal": 1, "tag": 2, "lane": 3}
+
+
+def boundary_modes(modes) -> int:
+    """Pack per-stage boundary modes ({stage: "signal" | "tag" | "lane"}, or a list
+    indexed by stage with None / "default" for the pipeline's strategy) into
+    rs_pipeline_opts.boundary_modes."""
+    if isinstance(modes, int):
+        return modes
+    items = modes.items() if isinstance(modes, dict) else enumerate(modes)
+    v = 0
+    for stage, m in items:
+        if m is None:
+            continue
+        v |= BOUNDARIES[m] << (2 * int(stage))
+    return v
 RS_MAX_STAGES = 6
 
 EXPORTS = [
@@ -46,7 +62,7 @@ _MIRRORS = ("StageDesc", "Opts", "StreamDesc", "RegionResults", "Stats", "Reques
 
 class StageDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("op", ctypes.c_uint32), ("max_fanout", ctypes.c_uint32),
-                ("params", ctypes.c_uint32 * 4)]
+                ("params", ctypes.c_uint32 * 4), ("input", ctypes.c_uint32)]
 
 
 class Opts(ctypes.Structure):
@@ -55,7 +71,8 @@ class Opts(ctypes.Structure):
                 ("regions_per_unit", ctypes.c_uint32), ("tile_elements", ctypes.c_uint32),
                 ("tiles_in_flight", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
                 ("grid", ctypes.c_uint32), ("region_cost", ctypes.c_uint32),
-                ("device_budget", ctypes.c_uint64)]
+                ("device_budget", ctypes.c_uint64), ("boundary_modes", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -67,7 +84,8 @@ class StreamDesc(ctypes.Structure):
                 ("n_elements", ctypes.c_uint64), ("ctx", ctypes.c_void_p), ("out_count", ctypes.c_void_p),
                 ("out_sum", ctypes.c_void_p), ("out_min", ctypes.c_void_p),
                 ("total_elements_hint", ctypes.c_uint64), ("out_values", ctypes.c_void_p),
-                ("out_values_len", ctypes.c_uint64)]
+                ("out_values_len", ctypes.c_uint64), ("out2_count", ctypes.c_void_p),
+                ("out2_sum", ctypes.c_void_p), ("out2_min", ctypes.c_void_p)]
 
 
 class RegionResults(ctypes.Structure):
@@ -252,11 +270,22 @@ def _cur_stream():
 
 
 class Pipeline:
-    """A stage list bound to options; streams are submitted as torch CUDA tensors."""
+    """A stage list bound to options; streams are submitted as torch CUDA tensors.
 
-    def __init__(self, stages, strategy="tag", **opts):
+    inputs: a tree topology (Figure 1(b)) -- inputs[s] is the stage whose output stage s
+    reads (inputs[0] is ignored); None is a linear pipeline.  boundary_modes: per-stage
+    boundary modes (see `boundary_modes`)."""
+
+    def __init__(self, stages, strategy="tag", inputs=None, **opts):
         self.stages = list(stages)
-        arr = (StageDesc * len(self.stages))(*[stage_desc(s) for s in self.stages])
+        self.inputs = list(inputs) if inputs is not None else None
+        descs = [stage_desc(s) for s in self.stages]
+        if self.inputs is not None:
+            for i in range(1, len(descs)):
+                descs[i].input = int(self.inputs[i])
+        arr = (StageDesc * len(self.stages))(*descs)
+        if "boundary_modes" in opts:
+            opts["boundary_modes"] = boundary_modes(opts["boundary_modes"])
         o = make_opts(strategy, **opts)
         h = ctypes.c_void_p()
         check(lib().rs_pipeline_create(arr, len(self.stages), ctypes.byref(o), ctypes.byref(h)),
@@ -288,6 +317,8 @@ class Pipeline:
         check(lib().rs_pipeline_get_opts(self._h, ctypes.byref(o)), "rs_pipeline_get_opts")
         if strategy is not None:
             o.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        if "boundary_modes" in kw:
+            kw["boundary_modes"] = boundary_modes(kw["boundary_modes"])
         for k, v in kw.items():
             setattr(o, k, int(v))
         check(lib().rs_pipeline_set_opts(self._h, ctypes.byref(o)), "rs_pipeline_set_opts")
@@ -319,6 +350,10 @@ class Pipeline:
         if emit:
             n = max(1, self.fanout_product() * int(dev.get("total_elements", 0)))
             out["values"] = torch.empty(n, dtype=torch.int32, device=dvc)
+        if sum(1 for st in self.stages[1:] if st[0] == "aggregate") > 1:
+            # a tree's second leaf
+            for k, dt in (("count", torch.int32), ("sum", torch.int64), ("min", torch.int32)):
+                out[k + "2"] = torch.empty(R, dtype=dt, device=dvc) if out[k] is not None else None
         d = StreamDesc()
         d.n_regions = R
         d.parents = _ptr(dev.get("parents"))
@@ -335,6 +370,9 @@ class Pipeline:
         if out.get("values") is not None:
             d.out_values = _ptr(out["values"])
             d.out_values_len = int(out["values"].numel())
+        d.out2_count = _ptr(out.get("count2"))
+        d.out2_sum = _ptr(out.get("sum2"))
+        d.out2_min = _ptr(out.get("min2"))
         sid = ctypes.c_uint64()
         check(lib().rs_stream_submit(self._h, ctypes.byref(d), ctypes.byref(sid)), "rs_stream_submit")
         self._keep.append((dev, out))
@@ -530,18 +568,21 @@ def results_to_numpy(out: dict) -> dict:
         res["min"] = out["min"].cpu().numpy().view(np.uint32)
     if out.get("values") is not None:
         res["values"] = out["values"].cpu().numpy().view(np.uint32)
+    for k, dt in (("count2", np.uint32), ("sum2", np.uint64), ("min2", np.uint32)):
+        if out.get(k) is not None:
+            res[k] = out[k].cpu().numpy().view(dt)
     return res
 
 
-def run_stream(stages, stream: dict, strategy="tag", outputs=("count", "sum", "min"), **opts):
+def run_stream(stages, stream: dict, strategy="tag", outputs=("count", "sum", "min"), inputs=None, **opts):
     """One-shot helper: upload a host stream, run the pipeline once, return numpy
     results and the run's statistics.  The output arrays start filled with a sentinel,
     so a region the run leaves unwritten shows up in the results."""
     import torch
-    p = Pipeline(stages, strategy=strategy, **opts)
+    p = Pipeline(stages, strategy=strategy, inputs=inputs, **opts)
     dev = to_device(stream)
     out = p.submit(dev, outputs=outputs)
-    for k in ("count", "sum", "min", "values"):
+    for k in ("count", "sum", "min", "values", "count2", "sum2", "min2"):
         if out.get(k) is not None:
             out[k].fill_(0x5A5A5A5A)
     p.run()

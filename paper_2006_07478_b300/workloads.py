@@ -203,6 +203,38 @@ def cascade_stream(n_total: int = 1 << 26, mean: float = 32, seed: int = 7,
                        workload=f"cascade N={n_total} mean={mean} seed={seed}")
 
 
+def pipeline_lines() -> list:
+    """The stand-in for the paper's taxi application (Section 5): lines of text are
+    enumerated into characters; stage 1 keeps the characters that may open a coordinate
+    pair (a context-dependent test passing about 45 of a line's 1,397 characters); stage
+    2 verifies each candidate (keeps 90%) and stage 3 parses it (a map); the aggregate
+    reduces each line's parsed pairs."""
+    return [("enum_load",), ("filter_hash_ctx", 11, LINE_THETA_OPEN), ("filter_hash_ctx", 12, LINE_THETA_VERIFY),
+            ("map_mul", 2654435761, 12345), ("aggregate",)]
+
+
+LINE_MEAN = 1397                                  # characters per line (taxi input, Section 5)
+LINE_PAIRS = 45                                   # coordinate pairs per line
+LINE_THETA_OPEN = (LINE_PAIRS << 32) // LINE_MEAN  # pass rate 45 / 1397
+LINE_THETA_VERIFY = 3865470566                    # floor(0.9 * 2^32)
+
+
+def lines_stream(n_total: int = 1 << 26, seed: int = 13) -> dict:
+    """n_total characters (splitmix64 words) cut into lines of U{1..2 * 1397 - 1}
+    characters (mean 1397), the last one truncated; one context word per line."""
+    m = int(n_total / LINE_MEAN * 1.2) + 16
+    L = uniform_int(splitmix64_counter(substream_seed(seed, 0x11E), 0, m), 1, 2 * LINE_MEAN - 1)
+    cs = np.cumsum(L)
+    last = int(np.searchsorted(cs, n_total))
+    L = L[: last + 1].copy()
+    L[-1] -= int(cs[last]) - int(n_total)
+    R = L.shape[0]
+    elements = to_u32(splitmix64_counter(substream_seed(seed, 0xC4A), 0, n_total))
+    ctx = to_u32(splitmix64_counter(substream_seed(seed, 0xC7B), 0, R))
+    return make_stream(L.astype(np.uint32), elements=elements, ctx=ctx,
+                       workload=f"lines N={n_total} L=U[1,{2 * LINE_MEAN - 1}] seed={seed}")
+
+
 def pipeline_region_sum() -> list:
     """The paper's region-sum benchmark (Section 5, Figures figFixed and figVariable):
     enumerate each region of an integer array and reduce it to its sum (and count)."""

@@ -201,3 +201,43 @@ def test_emit_sink_pipelines_and_streams():
     srv = ctypes.c_void_p()
     assert L.rs_server_create(arr, len(pipe), None, ctypes.c_void_p(0x10000), 1 << 20, 0, 0, None,
                               ctypes.byref(srv)) == rs.RS_ERR_INVALID
+
+
+def test_tree_topologies_and_boundary_modes_are_validated():
+    tree = [("enum_load",), ("filter_hash_ctx", 1, 5), ("filter_hash_ctx", 2, 5), ("aggregate",), ("aggregate",)]
+
+    def create(stages, inputs, **opts):
+        descs = [rs.stage_desc(s) for s in stages]
+        for i in range(1, len(descs)):
+            descs[i].input = inputs[i]
+        arr = (rs.StageDesc * len(stages))(*descs)
+        o = rs.make_opts("signal", **opts)
+        h = ctypes.c_void_p()
+        st = rs.lib().rs_pipeline_create(arr, len(stages), ctypes.byref(o), ctypes.byref(h))
+        if st == rs.RS_OK:
+            rs.lib().rs_pipeline_destroy(h)
+        return st
+
+    assert create(tree, [0, 0, 1, 2, 1]) == rs.RS_OK
+    assert create(tree, [0, 0, 1, 2, 3]) == rs.RS_ERR_INVALID       # reads a sink
+    assert create(tree, [0, 0, 1, 1, 1]) == rs.RS_ERR_INVALID       # stage 2 is a leaf but not a sink
+    assert create(tree, [0, 2, 1, 2, 1]) == rs.RS_ERR_INVALID       # stage 1 must read the enumeration
+    three = tree[:4] + [("aggregate",), ("aggregate",)]
+    assert create(three, [0, 0, 1, 2, 1, 1]) == rs.RS_ERR_INVALID   # more than RS_MAX_SINKS leaves
+    emit_tree = tree[:4] + [("emit",)]
+    assert create(emit_tree, [0, 0, 1, 2, 1]) == rs.RS_ERR_INVALID  # an emit sink ends a linear pipeline
+    cas = wl.pipeline_cascade()
+    lin = [0, 0, 1, 2, 3]
+    assert create(cas, lin, boundary_modes=rs.boundary_modes({1: "signal", 2: "tag", 3: "tag", 4: "tag"})) == rs.RS_OK
+    assert create(cas, lin, boundary_modes=rs.boundary_modes({1: "lane", 2: "lane", 3: "lane", 4: "lane"})) == rs.RS_OK
+    assert create(cas, lin, boundary_modes=rs.boundary_modes({1: "tag", 2: "signal", 3: "tag", 4: "tag"})) == \
+        rs.RS_ERR_INVALID                                           # signals below a tagged edge
+    assert create(cas, lin, boundary_modes=1) == rs.RS_ERR_INVALID  # the enumeration has no input edge
+    ex = [("enum_hash",), ("expand", 3, 1), ("aggregate",)]
+    assert create(ex, [0, 0, 1], boundary_modes=rs.boundary_modes({1: "lane"})) == rs.RS_ERR_INVALID
+    assert create(ex, [0, 0, 1], boundary_modes=rs.boundary_modes({1: "tag", 2: "tag"})) == rs.RS_OK
+    arr = (rs.StageDesc * 5)(*[rs.stage_desc(s) for s in tree])
+    arr[4].input = 1
+    srv = ctypes.c_void_p()
+    assert rs.lib().rs_server_create(arr, 5, None, ctypes.c_void_p(0x10000), 1 << 20, 0, 0, None,
+                                     ctypes.byref(srv)) == rs.RS_ERR_INVALID   # the server serves linear pipelines
