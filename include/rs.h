@@ -121,7 +121,8 @@ typedef struct {
                                    >= W * (max fan-out + 1) so a blocked node always leaves
                                    room for one full ensemble downstream; 0 = the smallest
                                    legal power of two >= 64                                  */
-    uint32_t signal_capacity;   /* signal-queue slots per edge; power of two >= 4; 0 = 32     */
+    uint32_t signal_capacity;   /* signal-queue slots per edge; power of two >= 4; 0 = 32 (256
+                                   when an edge selects contexts per lane)                   */
     uint32_t strategy;          /* rs_strategy                                                 */
     uint32_t regions_per_unit;  /* parents claimed per atomic step, <= 512; 0 = from the mean
                                    region length (about 2048 elements per claim)              */

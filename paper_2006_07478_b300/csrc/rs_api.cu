@@ -186,7 +186,13 @@ static rs_status fill_defaults(rs_pipeline_opts *o, uint32_t fan)
         while (c < o->ensemble_width * (fan + 1)) c <<= 1;
         o->queue_capacity = c;
     }
-    if (o->signal_capacity == 0) o->signal_capacity = 32;
+    if (o->signal_capacity == 0) {
+        // a node that selects contexts per lane consumes the signals of a whole ensemble at
+        // once: with short regions that is many signals
+        bool lane = false;
+        for (int c = 1; c < RS_MAX_STAGES; ++c) lane = lane || ((o->boundary_modes >> (2 * c)) & 3u) == RS_BOUNDARY_LANE;
+        o->signal_capacity = lane ? 256 : 32;
+    }
     if (o->tile_elements == 0) o->tile_elements = o->ensemble_width < 128 ? o->ensemble_width : 128;
     // tiles_in_flight 0: the tag strategy reads elements directly (no staging tiles);
     // the signal strategy stages 4 tiles

@@ -1518,14 +1518,22 @@ struct Proc {
 
     // Per-lane state selection (Section 6): node I's input edge carries signals, but its
     // ensembles are not cut at them.  The signals whose position falls inside the
-    // ensemble are consumed with it.  Positions come from the credits: the head signal's
-    // counts the items before it (w.credit[I] holds it once taken off the ring), each later
-    // one the items since the signal before.  Every lane takes the context of the last
-    // Begin at or before its item; each consumed signal is forwarded to the children that
-    // take signals with the credit the sender rules give it at its place among the
-    // outputs (the first: |Q| or the count since the child's last signal, plus the outputs
-    // before it; the others: the outputs since the signal before).  Fan-out 1 only (the
-    // host rejects an expansion fed this way).  Returns false when nothing was consumed.
+    // ensemble are consumed with it (up to LANE_MAX_SIG, read 32 at a time).  Positions
+    // come from the credits: the head signal's counts the items before it (w.credit[I]
+    // holds it once taken off the ring), each later one the items since the signal before.
+    // Every lane takes the context of the last Begin at or before its item; each consumed
+    // signal is forwarded to the children that take signals with the credit the sender
+    // rules give it at its place among the outputs (the first: |Q| or the count since the
+    // child's last signal, plus the outputs before it; the others: the outputs since the
+    // signal before).  Fan-out 1 only (the host rejects an expansion fed this way).
+    // Until its input is drained the node waits for full ensembles, unless its signal
+    // ring is nearly full: then the producer waits on it, and it takes what it has.
+    // Returns false when nothing was consumed.
+    static constexpr uint32_t LANE_MAX_SIG = 256;
+
+    // signal j (from the head) of edge e: its word and credit
+    __device__ __forceinline__ uint32_t sig_word(uint32_t e, uint32_t j) const { return M.sq[sidx(e, w.sh[e] + j)]; }
+
     template <int I>
     __device__ __forceinline__ bool lane_step(bool drain, uint32_t &took, uint32_t &nsig)
     {
@@ -1533,7 +1541,7 @@ struct Proc {
         const uint32_t C = P.C, SC = P.SC;
         const bool last = is_sink(I);
         const uint32_t km = last ? 0u : kids(I);
-        uint32_t space = W, sroom = 32u;
+        uint32_t space = W, sroom = SC;
         bool fwd = false;
 #pragma unroll
         for (int c = 2; c < RS_MAX_STAGES; ++c) {
@@ -1545,20 +1553,29 @@ struct Proc {
             }
         }
         const uint32_t avail = w.qt[e] - w.qh[e];
-        uint32_t take = min(min(avail, W), space);
-        if (!drain && take < W) take = 0;   // full ensembles only until the input is drained
         const uint32_t pend = w.st[e] - w.sh[e];
-        const uint32_t np = min(32u, pend);
-        const bool in = lane < np;
-        const uint32_t sj = sidx(e, w.sh[e] + lane);
-        const uint32_t word = in ? M.sq[sj] : 0u;
-        const uint32_t cr = in ? M.sq[sj + 1] : 0u;
-        const uint32_t pos = w.credit[I] + warp_incl_scan_u32(cr, lane);
-        uint32_t m = __popc(__ballot_sync(FULLMASK, in && pos <= take));
-        if (fwd) m = min(m, sroom);
+        uint32_t take = min(min(avail, W), space);
+        if (!drain && take < W && SC - pend >= 2) take = 0;
+        // pass 1: how many signals this step consumes -- those at or before the
+        // ensemble's end, as many as fit the children's signal rings
+        const uint32_t mmax = min(fwd ? sroom : SC, LANE_MAX_SIG);
+        uint32_t m = 0, stop_pos = 0xFFFFFFFFu, last_pos = 0, pbase = w.credit[I];
+        while (m < pend && m < mmax) {
+            const uint32_t np = min(32u, pend - m);
+            const bool in = lane < np;
+            const uint32_t cr = in ? M.sq[sidx(e, w.sh[e] + m + lane) + 1] : 0u;
+            const uint32_t pos = pbase + warp_incl_scan_u32(cr, lane);
+            uint32_t mc = __popc(__ballot_sync(FULLMASK, in && pos <= take));
+            mc = min(mc, mmax - m);
+            if (mc < np) stop_pos = __shfl_sync(FULLMASK, pos, mc);
+            if (mc > 0) last_pos = __shfl_sync(FULLMASK, pos, mc - 1);
+            pbase = __shfl_sync(FULLMASK, pos, 31);
+            m += mc;
+            if (mc < 32) break;
+        }
         // the items of this step stop at the first signal left on the ring
-        if (m < np) take = min(take, __shfl_sync(FULLMASK, pos, m));
-        else if (m > 0 && pend > np) take = min(take, __shfl_sync(FULLMASK, pos, m - 1));
+        if (stop_pos != 0xFFFFFFFFu) take = min(take, stop_pos);
+        else if (m < pend) take = min(take, last_pos);
         if (take == 0 && m == 0) return false;
         uint32_t x[V], k[V];
 #pragma unroll
@@ -1568,33 +1585,59 @@ struct Proc {
         }
         if (take > 0) (void)gather<I, false>(take, x, k);
         if (stop) return false;
-        // contexts: mark the item of every Begin that falls strictly inside the ensemble
-        // (the later Begin wins at one position), then a running maximum over the items
-        const bool begin = lane < m && !(word & SIG_END);
-        const uint32_t inside = __ballot_sync(FULLMASK, begin && pos < take);
-        if (inside) {
+        // pass 2: mark the item of every consumed Begin strictly inside the ensemble with
+        // its index + 1 (the later Begin wins at one position), then a running maximum over
+        // the items gives each lane the signal whose word is its context
+        uint32_t lastb = 0xFFFFFFFFu;   // index of the last consumed Begin
+        bool inside = false;
+        if (m > 0) {
+            if (take > 0) {
 #pragma unroll
-            for (int s = 0; s < V; ++s) M.scr[32u * s + lane] = 0u;
-            __syncwarp();
-            if (begin && pos < take) atomicMax(&M.scr[pos], lane + 1u);
-            __syncwarp();
-            uint32_t carry = 0;
-#pragma unroll
-            for (int s = 0; s < V; ++s) {
-                const uint32_t mk = M.scr[32u * s + lane];
-                uint32_t inc = mk;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) inc = max(inc, __shfl_up_sync(FULLMASK, inc, d));
-                const uint32_t rel = max(carry, inc);
-                carry = max(carry, __shfl_sync(FULLMASK, inc, 31));
-                const uint32_t kw = __shfl_sync(FULLMASK, word, rel ? rel - 1u : 0u);
-                if (rel) k[s] = kw;
+                for (int s = 0; s < V; ++s) M.scr[32u * s + lane] = 0u;
+                __syncwarp();
+            }
+            pbase = w.credit[I];
+            for (uint32_t b = 0; b < m; b += 32) {
+                const bool in = b + lane < m;
+                const uint32_t j = sidx(e, w.sh[e] + b + lane);
+                const uint32_t word = in ? M.sq[j] : SIG_END;
+                const uint32_t pos = pbase + warp_incl_scan_u32(in ? M.sq[j + 1] : 0u, lane);
+                const bool begin = in && !(word & SIG_END);
+                const uint32_t bb = __ballot_sync(FULLMASK, begin);
+                if (bb) lastb = b + 31 - __clz(bb);
+                if (begin && pos < take) atomicMax(&M.scr[pos], b + lane + 1u);
+                inside = inside || __any_sync(FULLMASK, begin && pos < take);
+                pbase = __shfl_sync(FULLMASK, pos, 31);
             }
             __syncwarp();
+            if (inside) {
+                uint32_t carry = 0;
+#pragma unroll
+                for (int s = 0; s < V; ++s) {
+                    uint32_t inc = M.scr[32u * s + lane];
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) inc = max(inc, __shfl_up_sync(FULLMASK, inc, d));
+                    const uint32_t rel = max(carry, inc);
+                    carry = max(carry, __shfl_sync(FULLMASK, inc, 31));
+                    if (rel && 32u * s + lane < take) k[s] = sig_word(e, rel - 1u);
+                }
+                __syncwarp();
+            }
         }
-        const uint32_t begins = __ballot_sync(FULLMASK, begin);
+        if constexpr (I == 1) {
+            // hashed enumeration: an element is a function of its parent, which the lane
+            // knows only now
+            if (op<0>() == D_ENUM_HASH && inside) {
+                const uint32_t q0 = w.qh[0];
+#pragma unroll
+                for (int s = 0; s < V; ++s) {
+                    const uint32_t q = 32u * s + lane;
+                    if (q < take) x[s] = fmix32(M.mpar[k[s]] ^ fmix32((q0 + q - M.moff[k[s]]) ^ RS_GOLD));
+                }
+            }
+        }
         if (last) {
-            if (take > 0) mix_sink<I>(x, k, inside == 0u, take);
+            if (take > 0) mix_sink<I>(x, k, !inside, take);
         } else {
             // the children's queues before this step's outputs (for the first credit)
             uint32_t first[RS_MAX_STAGES];
@@ -1606,41 +1649,56 @@ struct Proc {
             }
             uint32_t bal[V];
             uint32_t tot = 0;
-            if (take > 0) tot = mix_stage<I>(x, k, inside == 0u, take, bal);
-            else {
+            if (take > 0) {
+                tot = mix_stage<I>(x, k, !inside, take, bal);
+            } else {
 #pragma unroll
                 for (int s = 0; s < V; ++s) bal[s] = 0;
             }
             if (m > 0 && fwd) {
-                // outputs of the items before each consumed signal's position
-                uint32_t ob = 0;
+                // pass 3: forward; ob = outputs of the items before a signal's position
+                pbase = w.credit[I];
+                uint32_t ob_prev = 0;
+                for (uint32_t b = 0; b < m; b += 32) {
+                    const bool in = b + lane < m;
+                    const uint32_t j = sidx(e, w.sh[e] + b + lane);
+                    const uint32_t word = in ? M.sq[j] : 0u;
+                    const uint32_t pos = pbase + warp_incl_scan_u32(in ? M.sq[j + 1] : 0u, lane);
+                    uint32_t ob = 0;
 #pragma unroll
-                for (int s = 0; s < V; ++s) {
-                    const uint32_t lo = 32u * s;
-                    if (pos >= lo + 32u) ob += __popc(bal[s]);
-                    else if (pos > lo) ob += __popc(bal[s] & ((1u << (pos - lo)) - 1u));
+                    for (int s = 0; s < V; ++s) {
+                        const uint32_t lo = 32u * s;
+                        if (pos >= lo + 32u) ob += __popc(bal[s]);
+                        else if (pos > lo) ob += __popc(bal[s] & ((1u << (pos - lo)) - 1u));
+                    }
+                    uint32_t obp = __shfl_up_sync(FULLMASK, ob, 1);
+                    if (lane == 0) obp = ob_prev;
+#pragma unroll
+                    for (int c = 2; c < RS_MAX_STAGES; ++c) {
+                        if (!(km & (1u << c)) || emode(c) == EM_TAG) continue;
+                        if (in) {
+                            const uint32_t o = sidx(c - 1, w.st[c - 1] + b + lane);
+                            M.sq[o] = word;
+                            M.sq[o + 1] = (b + lane == 0) ? first[c] + ob : ob - obp;
+                        }
+                    }
+                    const uint32_t nin = min(32u, m - b);
+                    ob_prev = __shfl_sync(FULLMASK, ob, nin - 1);
+                    pbase = __shfl_sync(FULLMASK, pos, 31);
                 }
-                const uint32_t obp = __shfl_up_sync(FULLMASK, ob, 1);
-                const uint32_t oblast = __shfl_sync(FULLMASK, ob, m - 1);
 #pragma unroll
                 for (int c = 2; c < RS_MAX_STAGES; ++c) {
                     if (!(km & (1u << c)) || emode(c) == EM_TAG) continue;
-                    if (lane < m) {
-                        const uint32_t o = sidx(c - 1, w.st[c - 1] + lane);
-                        M.sq[o] = word;
-                        M.sq[o + 1] = lane == 0 ? first[c] + ob : ob - obp;
-                    }
                     w.st[c - 1] += m;
-                    w.em[c - 1] = tot - oblast;
+                    w.em[c - 1] = tot - ob_prev;
                 }
             }
         }
-        if (begins) w.ctxk[I] = __shfl_sync(FULLMASK, word, 31 - __clz(begins));
-        // the head left on the ring: the items still before it
-        if (m < np) {
-            const uint32_t pm = __shfl_sync(FULLMASK, pos, m);
-            if (lane == m) M.sq[sj + 1] = 0;
-            w.credit[I] = pm - take;
+        if (lastb != 0xFFFFFFFFu) w.ctxk[I] = sig_word(e, lastb);
+        // the signal now at the head: the items still before it
+        if (m < pend && stop_pos != 0xFFFFFFFFu) {
+            if (lane == 0) M.sq[sidx(e, w.sh[e] + m) + 1] = 0;
+            w.credit[I] = stop_pos - take;
         } else {
             w.credit[I] = 0;
         }
@@ -2142,7 +2200,9 @@ static const void *kernel_ptr(const KParams &P)
             generic = e.fn;
             continue;
         }
-        if (e.oe == ops[0] && e.o1 == ops[1] && e.o2 == ops[2] && e.o3 == ops[3] && e.o4 == ops[4]) return e.fn;
+        // specialised kernels end in the aggregate: an emit sink takes the generic one
+        if (!P.emit && e.oe == ops[0] && e.o1 == ops[1] && e.o2 == ops[2] && e.o3 == ops[3] && e.o4 == ops[4])
+            return e.fn;
     }
     return generic;
 }
