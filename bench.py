@@ -287,6 +287,123 @@ def bench_region_sizes(rs, torch):
             "rows": rows, "invariants_ok": inv}
 
 
+def _timed(p, torch, warm=2, reps=5):
+    """Median kernel time (planner + pipeline kernel + finalize, CUDA events on the
+    launching stream) of `reps` runs after `warm`, and the last run's statistics."""
+    p.timing_enable(warm + reps + 2)
+    for _ in range(warm):
+        p.run()
+    torch.cuda.synchronize()
+    p.timing_read()
+    for _ in range(reps):
+        p.run()
+    ms = statistics.median(p.timing_read())
+    return ms, p.stats()
+
+
+LANE4 = {1: "lane", 2: "lane", 3: "lane", 4: "lane"}
+SIG4 = {1: "signal", 2: "signal", 3: "signal", 4: "signal"}
+TAG4 = {1: "tag", 2: "tag", 3: "tag", 4: "tag"}
+
+
+def bench_modes(rs, torch, cascades):
+    """Per-stage strategy mixing (Section 5, the taxi application), per-lane state
+    selection (Section 6), a tree topology (Figure 1(b)) and the emit sink (Section 4).
+    Every variant of a workload must give the same results (compared here; exactness
+    against the oracle is tested in tests/)."""
+    res = {}
+    # ---- lines: the taxi stand-in, the paper's three variants and per-lane selection ----
+    s = wl.lines_stream(N_ELEM)
+    pipe = wl.pipeline_lines()
+    dev = rs.to_device(s)
+    variants = [
+        ("both stages enumerated: signals on every edge", "signal", SIG4),
+        ("stage 1 enumerated, tags after it (mixed)", "signal", {1: "signal", 2: "tag", 3: "tag", 4: "tag"}),
+        ("neither stage enumerated: tags on every edge", "signal", TAG4),
+        ("per-lane selection on every edge", "signal", LANE4),
+        ("per-lane selection into stage 1, tags after it", "signal", {1: "lane", 2: "tag", 3: "tag", 4: "tag"}),
+        ("tag kernel (linear pipelines, every edge tagged)", "tag", None),
+        ("signal kernel (linear pipelines, every edge signalled)", "signal", None),
+    ]
+    rows, ref, same = [], None, True
+    for name, strat, modes in variants:
+        p = rs.Pipeline(pipe, strategy=strat, boundary_modes=modes or 0)
+        o = p.submit(dev)
+        ms, st = _timed(p, torch)
+        got = rs.results_to_numpy(o)
+        if ref is None:
+            ref = got
+        same &= all(np.array_equal(got[k], ref[k]) for k in ref)
+        rows.append({"variant": name, "kernel_ms": ms, "items_per_s": N_ELEM / (ms * 1e-3),
+                     "active_lane_fraction": [round(x, 4) for x in st["active_lane_fraction"]],
+                     "ensembles": st["ensembles"], "signals": st["signals"]})
+        p.close()
+    p = rs.Pipeline(pipe, strategy="auto")
+    p.submit(dev)
+    best, best_ms = p.autotune(trials=2)
+    p.close()
+    res["lines"] = {"workload": f"{s['R']} lines of U{{1..2793}} characters (mean 1397), 2^26 in all; "
+                                "keep ~45 candidates per line (context hash), verify 90%, parse (map); "
+                                "count/sum/min per line",
+                    "variants": rows, "results_identical": bool(same),
+                    "autotuned": {"strategy": best["strategy"], "boundary_modes": best["boundary_modes"],
+                                  "ensemble_width": best["ensemble_width"], "ms": best_ms}}
+    # ---- occupancy against overhead by mean region size, on the per-edge kernel ----
+    sweep = []
+    for m, cs in cascades:
+        dv = rs.to_device(cs)
+        row, ref = {"mean": m}, None
+        for name, modes in (("signal", SIG4), ("lane", LANE4), ("tag", TAG4)):
+            p = rs.Pipeline(wl.pipeline_cascade(), strategy="signal", boundary_modes=modes)
+            o = p.submit(dv, outputs=("count", "sum"))
+            ms, st = _timed(p, torch, reps=3)
+            got = rs.results_to_numpy(o)
+            ref = got if ref is None else ref
+            row[name] = {"kernel_ms": ms, "items_per_s": N_ELEM / (ms * 1e-3),
+                         "active_lane_fraction_node1": round(st["active_lane_fraction"][1], 4),
+                         "identical": bool(all(np.array_equal(got[k], ref[k]) for k in ref))}
+            p.close()
+        sweep.append(row)
+        del dv
+    res["mean_sweep_per_edge_kernel"] = sweep
+    # ---- a tree: one filter feeding a second filter's aggregate and an aggregate of its own ----
+    m, cs = cascades[1]
+    dv = rs.to_device(cs)
+    tree = [("enum_load",), ("filter_hash_ctx", 1, wl.CASCADE_THETAS[0]), ("filter_hash_ctx", 2, wl.CASCADE_THETAS[1]),
+            ("aggregate",), ("aggregate",)]
+    inputs = [0, 0, 1, 2, 1]
+    trow, ref = {"mean": m, "inputs": inputs}, None
+    for name, modes in (("signal", SIG4), ("lane", LANE4), ("tag", TAG4)):
+        p = rs.Pipeline(tree, strategy="signal", inputs=inputs, boundary_modes=modes)
+        o = p.submit(dv, outputs=("count", "sum"))
+        ms, st = _timed(p, torch, reps=3)
+        got = rs.results_to_numpy(o)
+        ref = got if ref is None else ref
+        trow[name] = {"kernel_ms": ms, "items_per_s": N_ELEM / (ms * 1e-3),
+                      "signals_per_node": st["signals"],
+                      "identical": bool(all(np.array_equal(got[k], ref[k]) for k in ref))}
+        p.close()
+    res["tree"] = trow
+    # ---- the emit sink against the aggregate (tag kernel), CSR offsets ----
+    L = cs["len"].astype(np.int64)
+    csr = dict(cs, len=None, offsets=np.concatenate(([0], np.cumsum(L))).astype(np.uint32))
+    dvc = rs.to_device(csr)
+    erow = {"mean": m}
+    for name, pp in (("aggregate", wl.pipeline_cascade()), ("emit", wl.pipeline_cascade()[:-1] + [("emit",)])):
+        p = rs.Pipeline(pp, strategy="tag")
+        o = p.submit(dvc, outputs=("count", "sum"))
+        ms, st = _timed(p, torch, reps=3)
+        erow[name] = {"kernel_ms": ms, "items_per_s": N_ELEM / (ms * 1e-3)}
+        if name == "emit":
+            got = rs.results_to_numpy(o)
+            erow["emit_count_total"] = int(got["count"].astype(np.int64).sum())
+        else:
+            erow["aggregate_count_total"] = int(rs.results_to_numpy(o)["count"].astype(np.int64).sum())
+        p.close()
+    res["emit"] = erow
+    return res
+
+
 def bench_batched(rs, torch):
     """4,096 independent hashed streams (lognormal sizes): one persistent launch for all
     of them replayed from a CUDA graph, against one launch per stream."""
@@ -703,7 +820,9 @@ def main():
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        for name, fn in (("graph_edges", lambda: bench_graph(rs, torch, peak)),
+        for name, fn in (("modes", lambda: bench_modes(rs, torch, [(m, s) for m, s in zip(MEANS, streams)
+                                                                  if m in (4, 32, 256)])),
+                         ("graph_edges", lambda: bench_graph(rs, torch, peak)),
                          ("region_sizes", lambda: bench_region_sizes(rs, torch)),
                          ("batched", lambda: bench_batched(rs, torch)),
                          ("serving", lambda: bench_serving(rs, torch, args.serve_seconds))):

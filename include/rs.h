@@ -282,8 +282,12 @@ rs_status rs_graph_release(rs_pipeline *p);
  * of Section 5): for each strategy (both when the pipeline's strategy option is
  * RS_STRATEGY_AUTO, else only the one it names), a coordinate search from the defaults over the
  * unit shape (regions_per_unit x region_cost, or whole-parent unit sizes for hashed
- * streams), then ensemble width, processors per CTA and tile size, each change kept
- * when faster; a strategy starting above three times the best so far is dropped.
+ * streams), then ensemble width, processors per CTA, tile size and queue capacity (1, 2
+ * and 4 times the smallest legal one), each change kept when faster; a strategy starting
+ * above three times the best so far is dropped.  With RS_STRATEGY_AUTO and a linear
+ * pipeline it then tries per-edge boundary modes: signals into the first stages and tags
+ * from stage s on, for every s (the per-stage choice of Section 5), per-lane selection on
+ * every edge, and per-lane selection into stage 1 with tags after it.
  * Each trial is one warm-up and `trials` timed runs (CUDA events).  The fastest is
  * kept in the pipeline and returned in *best (mean milliseconds in *best_ms).
  * Overwrites the streams' outputs. */

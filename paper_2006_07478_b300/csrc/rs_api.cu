@@ -1278,11 +1278,17 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
     if ((e = cudaEventCreate(&ev1)) != cudaSuccess) { cudaEventDestroy(ev0); return cuda_fail(e); }
     rs_status result = RS_OK;
     // mean time of `trials` runs of configuration c; +inf when it does not fit or stalls
-    auto time_of = [&](rs_pipeline_opts c) -> float {
+    // qmul: queue capacity as a multiple of the smallest legal one for the width
+    auto time_of = [&](rs_pipeline_opts c, uint32_t qmul = 1) -> float {
         c.queue_capacity = 0;
         c.grid = 0;
         fill_defaults(&c, fan);
+        c.queue_capacity *= qmul;
         if (check_opts(&c, fan) != RS_OK) return 1e30f;
+        Topo tp;
+        if (make_topo(p->stages, p->n_stages, c.boundary_modes,
+                      c.strategy == RS_STRATEGY_TAG ? RS_STRATEGY_TAG : RS_STRATEGY_SIGNAL, &tp) != RS_OK)
+            return 1e30f;
         p->opts = c;
         p->table_dirty = true;
         Topo topo;
@@ -1311,6 +1317,7 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
     // point is over three times the best found so far is dropped.
     float best_t = 1e30f;
     rs_pipeline_opts best_o = base;
+    uint32_t best_q = 1;
     const uint32_t strategies[2] = {RS_STRATEGY_TAG, RS_STRATEGY_SIGNAL};
     for (uint32_t si = 0; si < 2 && result == RS_OK; ++si) {
         // a strategy fixed in the options is the only one searched
@@ -1382,14 +1389,68 @@ rs_status rs_autotune(rs_pipeline *p, void *workspace, uint64_t workspace_bytes,
                 if (t < cur_t) { cur_t = t; cur = c; }
             }
         }
+        // queue capacity: 2 and 4 times the smallest legal one (deeper queues let a node
+        // fire several ensembles in a row, and cost shared memory, hence occupancy)
+        uint32_t cur_q = 1;
+        for (uint32_t qm : {2u, 4u}) {
+            const float t = time_of(cur, qm);
+            if (t < cur_t) { cur_t = t; cur_q = qm; }
+        }
         if (cur_t < best_t) {
             best_t = cur_t;
             best_o = cur;
-            best_o.queue_capacity = 0;
-            best_o.grid = 0;
-            fill_defaults(&best_o, fan);
+            best_q = cur_q;
         }
     }
+    // Per-edge boundary modes (Section 5: the best representation of regional context can
+    // differ per stage, and should be chosen from measurements): for a linear pipeline,
+    // signals into the first stages and tags from stage sw on, at every switch point sw;
+    // per-lane selection (Section 6) on every edge; and per-lane selection into stage 1
+    // with tags after it.  Each at 128 and 64 items per ensemble, on the per-edge kernel.
+    bool linear = true;
+    for (uint32_t i = 1; i < p->n_stages; ++i) linear = linear && stage_input(p->stages, i) == i - 1;
+    if (base.strategy == RS_STRATEGY_AUTO && linear && p->n_stages >= 3 && result == RS_OK) {
+        const uint32_t n = p->n_stages;
+        uint32_t cand[RS_MAX_STAGES + 2];
+        int nc = 0;
+        for (uint32_t sw = 2; sw < n; ++sw) {
+            uint32_t m = 0;
+            for (uint32_t c = 1; c < n; ++c) m |= RS_BOUNDARY(c, c < sw ? RS_BOUNDARY_SIGNAL : RS_BOUNDARY_TAG);
+            cand[nc++] = m;
+        }
+        uint32_t lane_all = 0, lane_tag = 0;
+        for (uint32_t c = 1; c < n; ++c) {
+            const uint32_t lm = p->stages[c].kind == RS_EXPAND ? RS_BOUNDARY_SIGNAL : RS_BOUNDARY_LANE;
+            lane_all |= RS_BOUNDARY(c, lm);
+            lane_tag |= RS_BOUNDARY(c, c == 1 ? lm : RS_BOUNDARY_TAG);
+        }
+        cand[nc++] = lane_all;
+        cand[nc++] = lane_tag;
+        for (int i = 0; i < nc && result == RS_OK; ++i) {
+            for (uint32_t W : {4u, 2u}) {
+                rs_pipeline_opts c = base;
+                c.strategy = RS_STRATEGY_SIGNAL;
+                c.boundary_modes = cand[i];
+                c.ensemble_width = W * RS_W;
+                c.signal_capacity = 0;
+                c.regions_per_unit = 0;
+                c.region_cost = 0;
+                c.warps_per_block = 0;
+                c.tile_elements = 0;
+                c.tiles_in_flight = 0;
+                const float t = time_of(c);
+                if (t < best_t) {
+                    best_t = t;
+                    best_o = c;
+                    best_q = 1;
+                }
+            }
+        }
+    }
+    best_o.queue_capacity = 0;
+    best_o.grid = 0;
+    fill_defaults(&best_o, fan);
+    best_o.queue_capacity *= best_q;
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     p->opts = best_o;

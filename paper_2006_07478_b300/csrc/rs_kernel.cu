@@ -1527,7 +1527,8 @@ struct Proc {
     // child's last signal, plus the outputs before it; the others: the outputs since the
     // signal before).  Fan-out 1 only (the host rejects an expansion fed this way).
     // Until its input is drained the node waits for full ensembles, unless its signal
-    // ring is nearly full: then the producer waits on it, and it takes what it has.
+    // ring is nearly full: then the producer waits on it, and it takes what it has.  An
+    // ensemble waits for room for all of it in every child's ring.
     // Returns false when nothing was consumed.
     static constexpr uint32_t LANE_MAX_SIG = 256;
 
@@ -1554,7 +1555,10 @@ struct Proc {
         }
         const uint32_t avail = w.qt[e] - w.qh[e];
         const uint32_t pend = w.st[e] - w.sh[e];
-        uint32_t take = min(min(avail, W), space);
+        // an ensemble fires only when the children have room for all of it (like the
+        // data phase of fire_body, which waits for downstream space rather than cut it)
+        uint32_t take = min(avail, W);
+        if (space < take) take = 0;
         if (!drain && take < W && SC - pend >= 2) take = 0;
         // pass 1: how many signals this step consumes -- those at or before the
         // ensemble's end, as many as fit the children's signal rings
