@@ -768,7 +768,7 @@ def main():
     if args.e2e_steps > 0:
         host_in, dev_in = [], []
         for p in pipes:
-            dev, _ = p._keep[0]
+            dev = p._keep[0][0]
             hi = {k: dev[k].cpu().pin_memory() for k in ("len", "elements", "ctx") if dev.get(k) is not None}
             host_in.append(hi)
             dev_in.append(dev)

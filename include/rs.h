@@ -214,6 +214,37 @@ typedef struct {
 rs_status rs_stream_submit(rs_pipeline *p, const rs_stream_desc *s, uint64_t *stream_id);
 rs_status rs_clear_streams(rs_pipeline *p);
 
+/* ---- sliced runs over resident per-stream state (bounded launches) ------------------
+ * A stream's work is a sequence of n_units merge-path units (whole-parent units for
+ * hashed enumeration); every unit can run in any launch once the stream is planned,
+ * because the aggregate folds each unit's items into the region outputs with integer
+ * reductions (Section 4's begin/run/end, merged across pieces).  A sliced run keeps the
+ * stream's planning state -- its unit records, planner words and merge slots -- in a
+ * caller-owned device buffer that outlives the launch, and each launch processes a
+ * bounded number of the stream's units.  This is the serving form: many streams advance
+ * a slice at a time and new ones join between launches. */
+
+/* Bytes of resident state a sliced run of stream s needs (0 for hashed enumeration, which
+ * needs none) and its number of units, under the pipeline's current options (units of
+ * loaded streams are an upper bound: the planner may use fewer; units past the last one
+ * are skipped).  Host-only. */
+rs_status rs_stream_state_size(const rs_pipeline *p, const rs_stream_desc *s, uint64_t *state_bytes,
+                               uint64_t *n_units);
+
+/* Submit stream s for the next rs_run with only its units [unit_begin, unit_begin +
+ * unit_count) (clamped to the stream's units).  `state` (device, 256-byte aligned,
+ * caller-owned, at least rs_stream_state_size bytes; may be NULL for hashed enumeration)
+ * must be the same buffer for every slice of the stream and must not change in between.
+ * unit_begin == 0 plans the stream: the run clears the state and writes the stream's unit
+ * records (and the identity results the planner owns) before its units run.  The
+ * region results are complete once every unit has run (the signal strategy writes the
+ * merged results of split parents in the run holding the last unit); the options must not
+ * change between slices of one stream.  Sliced streams cannot be captured in a graph
+ * (RS_ERR_STATE): each slice is a submission of its own.  Errors as rs_stream_submit;
+ * rs_run returns RS_ERR_CAPACITY if a state is too small. */
+rs_status rs_stream_submit_slice(rs_pipeline *p, const rs_stream_desc *s, void *state, uint64_t state_bytes,
+                                 uint64_t unit_begin, uint64_t unit_count, uint64_t *stream_id);
+
 /* Bytes of caller-owned device workspace rs_run needs for the streams submitted so
  * far (work cursor, look-back words, stream table, counters, status word). */
 rs_status rs_workspace_size(const rs_pipeline *p, uint64_t *bytes);

@@ -33,6 +33,21 @@ static rs_status cuda_fail(cudaError_t e)
 struct StreamPlan {
     uint32_t mode, K, n_units, plan_tiles, D, c;
     size_t slots_off, ucount_off, planlb_off, rec_off;
+    // this run's share of the stream: units [slice_lo, slice_lo + slice_n) of full_units,
+    // run_tiles planner tiles (all of them, or none when a sliced stream was planned
+    // earlier); a sliced stream's scratch lives in its own state (offsets above relative to
+    // it): st_zero bytes cleared when it is planned, st_total bytes in all
+    uint32_t full_units, slice_lo, slice_n, run_tiles;
+    bool sliced, plan_now;
+    size_t st_zero, st_total;
+};
+
+// A stream submitted for a sliced run (rs_stream_submit_slice): its resident state and the
+// units the next run takes.
+struct SliceInfo {
+    bool on = false;
+    void *state = nullptr;
+    uint64_t state_bytes = 0, begin = 0, count = 0;
 };
 
 // The workspace layout of make_plan in fixed arrays, for rs_run_noalloc (no allocation).
@@ -54,6 +69,7 @@ struct rs_pipeline {
     uint32_t n_stages;
     rs_pipeline_opts opts;
     std::vector<rs_stream_desc> streams;
+    std::vector<SliceInfo> slices;   // one per stream
     std::vector<uint32_t> stream_K;
     // pinned copy of the device stream table
     DevStream *table_host = nullptr;
@@ -438,7 +454,9 @@ rs_status rs_stream_submit(rs_pipeline *p, const rs_stream_desc *s, uint64_t *st
     }
     try {
         p->streams.push_back(*s);
+        p->slices.push_back(SliceInfo());
     } catch (...) {
+        if (p->streams.size() > p->slices.size()) p->streams.pop_back();
         return RS_ERR_NOMEM;
     }
     p->table_dirty = true;
@@ -451,7 +469,44 @@ rs_status rs_clear_streams(rs_pipeline *p)
     if (!p) return RS_ERR_INVALID;
     if (p->graph) return RS_ERR_STATE;
     p->streams.clear();
+    p->slices.clear();
     p->table_dirty = true;
+    return RS_OK;
+}
+
+}  // extern "C"
+
+static rs_status state_need(const rs_pipeline *p, const rs_stream_desc *s, uint64_t *bytes, uint64_t *n_units);
+
+extern "C" {
+
+rs_status rs_stream_state_size(const rs_pipeline *p, const rs_stream_desc *s, uint64_t *state_bytes,
+                               uint64_t *n_units)
+{
+    if (!p || !s) return RS_ERR_INVALID;
+    uint64_t b = 0, u = 0;
+    rs_status st = state_need(p, s, &b, &u);
+    if (st != RS_OK) return st;
+    if (state_bytes) *state_bytes = b;
+    if (n_units) *n_units = u;
+    return RS_OK;
+}
+
+rs_status rs_stream_submit_slice(rs_pipeline *p, const rs_stream_desc *s, void *state, uint64_t state_bytes,
+                                 uint64_t unit_begin, uint64_t unit_count, uint64_t *stream_id)
+{
+    if (!p || !s) return RS_ERR_INVALID;
+    if (state && ((uintptr_t)state & 255) != 0) return RS_ERR_INVALID;
+    uint64_t id = 0;
+    rs_status st = rs_stream_submit(p, s, &id);
+    if (st != RS_OK) return st;
+    SliceInfo &si = p->slices.back();
+    si.on = true;
+    si.state = state;
+    si.state_bytes = state_bytes;
+    si.begin = unit_begin;
+    si.count = unit_count;
+    if (stream_id) *stream_id = id;
     return RS_OK;
 }
 
@@ -561,9 +616,9 @@ static void layout_plan(SP *sp, size_t ns, int strategy, uint32_t nsinks, uint64
     for (size_t i = 0; i < ns; ++i) {
         StreamPlan &q = sp[i];
         if (q.K > *Kmax) *Kmax = q.K;
-        *total_units += q.n_units;
-        *plan_tiles += q.plan_tiles;
-        if (q.mode == UNIT_MERGE) {
+        *total_units += q.slice_n;
+        *plan_tiles += q.run_tiles;
+        if (q.mode == UNIT_MERGE && !q.sliced) {   // a sliced stream's scratch is its state
             q.slots_off = off;
             off = align256(off + stream_zeroed_bytes(q, strategy, nsinks));
             q.ucount_off = off;
@@ -575,7 +630,7 @@ static void layout_plan(SP *sp, size_t ns, int strategy, uint32_t nsinks, uint64
     *zero_end = off;
     for (size_t i = 0; i < ns; ++i) {
         StreamPlan &q = sp[i];
-        if (q.mode == UNIT_MERGE) {
+        if (q.mode == UNIT_MERGE && !q.sliced) {
             q.rec_off = off;
             off = align256(off + ((size_t)q.n_units + 1) * sizeof(UnitRec));
         }
@@ -584,16 +639,76 @@ static void layout_plan(SP *sp, size_t ns, int strategy, uint32_t nsinks, uint64
     *total = off + align256(ns * sizeof(DevStream));
 }
 
+// A sliced stream's state: merge slots, unit count and planner words (cleared when the
+// stream is planned), then its unit records.
+static void state_layout(StreamPlan &q, int strategy, uint32_t nsinks)
+{
+    q.st_zero = q.st_total = 0;
+    if (q.mode != UNIT_MERGE) return;
+    size_t off = 0;
+    q.slots_off = off;
+    off = align256(off + stream_zeroed_bytes(q, strategy, nsinks));
+    q.ucount_off = off;
+    off = align256(off + 4);
+    q.planlb_off = off;
+    off = align256(off + (size_t)q.plan_tiles * 8);
+    q.st_zero = off;
+    q.rec_off = off;
+    off = align256(off + ((size_t)q.n_units + 1) * sizeof(UnitRec));
+    q.st_total = off;
+}
+
+// this run's share of a stream (all of it unless it was submitted for a sliced run)
+static void apply_slice(const SliceInfo &si, StreamPlan &q, int strategy, uint32_t nsinks)
+{
+    q.full_units = q.n_units;
+    q.sliced = si.on;
+    q.slice_lo = 0;
+    q.slice_n = q.n_units;
+    q.plan_now = true;
+    q.run_tiles = q.plan_tiles;
+    if (!si.on) return;
+    const uint64_t b = si.begin < q.n_units ? si.begin : q.n_units;
+    const uint64_t n = si.count < q.n_units - b ? si.count : q.n_units - b;
+    q.slice_lo = (uint32_t)b;
+    q.slice_n = (uint32_t)n;
+    q.plan_now = b == 0;
+    q.run_tiles = q.plan_now ? q.plan_tiles : 0u;
+    state_layout(q, strategy, nsinks);
+}
+
 static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts &o)
 {
     Plan pl;
     pl.hdr_bytes = align256(sizeof(WsHeader));
     pl.sp.resize(p->streams.size());
-    for (size_t i = 0; i < p->streams.size(); ++i) plan_stream(p, o, strategy, p->streams[i], pl.sp[i]);
+    const uint32_t nsinks = n_leaves(p->stages, p->n_stages);
+    for (size_t i = 0; i < p->streams.size(); ++i) {
+        plan_stream(p, o, strategy, p->streams[i], pl.sp[i]);
+        apply_slice(p->slices[i], pl.sp[i], strategy, nsinks);
+    }
     layout_plan(pl.sp.data(), pl.sp.size(), strategy, n_leaves(p->stages, p->n_stages), &pl.total_units,
                 &pl.plan_tiles, &pl.Kmax, &pl.zero_end, &pl.table_off, &pl.total);
     pl.table_bytes = pl.total - pl.table_off;
     return pl;
+}
+
+static int run_strategy(const rs_pipeline *p, Topo *t);
+
+// the state a sliced run of stream s needs under the current options, and its units
+static rs_status state_need(const rs_pipeline *p, const rs_stream_desc *s, uint64_t *bytes, uint64_t *n_units)
+{
+    Topo topo;
+    const int strategy = run_strategy(p, &topo);
+    if (strategy < 0) return RS_ERR_INVALID;
+    StreamPlan q;
+    plan_stream(p, p->opts, strategy, *s, q);
+    SliceInfo si;
+    si.on = true;
+    apply_slice(si, q, strategy, n_leaves(p->stages, p->n_stages));
+    *bytes = q.st_total;
+    *n_units = q.full_units;
+    return RS_OK;
 }
 
 // Per-processor shared memory of the tag kernel: counters, window marks (W words, hashed
@@ -837,6 +952,82 @@ static rs_status auto_wpb(rs_pipeline *p, const KParams &P, uint32_t *out)
     return RS_OK;
 }
 
+// The device stream table of a run: the streams' arrays, their unit split and this run's
+// share of their units, and their scratch in the workspace wsd (a sliced stream's in its
+// own state).
+static void fill_table(const rs_pipeline *p, const StreamPlan *sp, size_t ns, unsigned char *wsd, DevStream *out)
+{
+    uint32_t base = 0, pbase = 0;
+    for (size_t i = 0; i < ns; ++i) {
+        const rs_stream_desc &s = p->streams[i];
+        const StreamPlan &q = sp[i];
+        DevStream &d = out[i];
+        memset(&d, 0, sizeof d);
+        d.parents = s.parents;
+        d.len = s.region_len;
+        d.offsets = s.region_offsets;
+        d.elements = s.elements;
+        d.ctx = s.ctx;
+        d.out_count = s.out_count;
+        d.out_sum = (unsigned long long *)s.out_sum;
+        d.out_min = s.out_min;
+        d.out_values = s.out_values;
+        d.out_values_len = s.out_values_len;
+        d.out2_count = s.out2_count;
+        d.out2_sum = (unsigned long long *)s.out2_sum;
+        d.out2_min = s.out2_min;
+        d.n_elements = s.n_elements;
+        d.R = (uint32_t)s.n_regions;
+        d.K = q.K;
+        d.n_units = q.slice_n;
+        d.slice_lo = q.slice_lo;
+        d.slot_units = q.full_units;
+        d.finalize = q.slice_lo + q.slice_n >= q.full_units ? 1u : 0u;
+        d.unit_base = base;
+        d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
+        d.mode = q.mode;
+        if (q.mode == UNIT_MERGE) {
+            unsigned char *b = q.sliced ? (unsigned char *)p->slices[i].state : wsd;
+            d.rec = (UnitRec *)(b + q.rec_off);
+            d.slots = (Slot *)(b + q.slots_off);
+            d.u_count = (uint32_t *)(b + q.ucount_off);
+            d.plan_lb = (unsigned long long *)(b + q.planlb_off);
+            d.plan_tiles = q.run_tiles;
+            d.plan_base = pbase;
+            d.D = q.D;
+            d.dsh = log2_if_pow2(q.D);
+            d.c = q.c;
+            pbase += q.run_tiles;
+        }
+        base += d.n_units;
+    }
+}
+
+// every sliced stream's state holds its layout under the current options
+static rs_status check_states(const rs_pipeline *p, const StreamPlan *sp, size_t ns)
+{
+    for (size_t i = 0; i < ns; ++i) {
+        const StreamPlan &q = sp[i];
+        if (!q.sliced || q.mode != UNIT_MERGE) continue;
+        const SliceInfo &si = p->slices[i];
+        if (!si.state || ((uintptr_t)si.state & 255) != 0) return RS_ERR_INVALID;
+        if (si.state_bytes < q.st_total) return RS_ERR_CAPACITY;
+    }
+    return RS_OK;
+}
+
+// clear the scratch of the sliced streams this run plans
+static rs_status clear_states(const rs_pipeline *p, const StreamPlan *sp, size_t ns, cudaStream_t stream)
+{
+    for (size_t i = 0; i < ns; ++i) {
+        const StreamPlan &q = sp[i];
+        if (!q.sliced || !q.plan_now || q.mode != UNIT_MERGE || q.slice_n == 0) continue;
+        const cudaError_t e = cudaMemsetAsync(p->slices[i].state, 0, q.st_zero, stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return RS_OK;
+}
+
 struct Launch {
     KParams P;
     Plan pl;
@@ -858,6 +1049,8 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     Lc.pl = make_plan(p, strategy, p->opts);
     const Plan &pl = Lc.pl;
     if (ws_bytes < pl.total) return RS_ERR_CAPACITY;
+    rs_status sst = check_states(p, pl.sp.data(), pl.sp.size());
+    if (sst != RS_OK) return sst;
     if (((uintptr_t)ws & 255) != 0) return RS_ERR_INVALID;
     if (pl.total_units >= (1ull << 31)) return RS_ERR_CAPACITY;
     cudaError_t e;
@@ -886,47 +1079,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
                 return cuda_fail(e);
             p->table_cap = cap;
         }
-        uint32_t base = 0, pbase = 0;
-        unsigned char *wsd = (unsigned char *)ws;
-        for (size_t i = 0; i < ns; ++i) {
-            const rs_stream_desc &s = p->streams[i];
-            const StreamPlan &q = pl.sp[i];
-            DevStream &d = p->table_host[i];
-            memset(&d, 0, sizeof d);
-            d.parents = s.parents;
-            d.len = s.region_len;
-            d.offsets = s.region_offsets;
-            d.elements = s.elements;
-            d.ctx = s.ctx;
-            d.out_count = s.out_count;
-            d.out_sum = (unsigned long long *)s.out_sum;
-            d.out_min = s.out_min;
-            d.out_values = s.out_values;
-            d.out_values_len = s.out_values_len;
-            d.out2_count = s.out2_count;
-            d.out2_sum = (unsigned long long *)s.out2_sum;
-            d.out2_min = s.out2_min;
-            d.n_elements = s.n_elements;
-            d.R = (uint32_t)s.n_regions;
-            d.K = q.K;
-            d.n_units = q.n_units;
-            d.unit_base = base;
-            d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
-            d.mode = q.mode;
-            if (q.mode == UNIT_MERGE) {
-                d.rec = (UnitRec *)(wsd + q.rec_off);
-                d.slots = (Slot *)(wsd + q.slots_off);
-                d.u_count = (uint32_t *)(wsd + q.ucount_off);
-                d.plan_lb = (unsigned long long *)(wsd + q.planlb_off);
-                d.plan_tiles = q.plan_tiles;
-                d.plan_base = pbase;
-                d.D = q.D;
-                d.dsh = log2_if_pow2(q.D);
-                d.c = q.c;
-                pbase += q.plan_tiles;
-            }
-            base += d.n_units;
-        }
+        fill_table(p, pl.sp.data(), ns, (unsigned char *)ws, p->table_host);
         p->table_dirty = false;
         p->table_ws = ws;
     }
@@ -1055,6 +1208,8 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
             if (s.n_regions && (e = cudaMemsetAsync(s.out_count, 0, s.n_regions * 4, stream)) != cudaSuccess)
                 return cuda_fail(e);
     }
+    rs_status cst = clear_states(p, Lc.pl.sp.data(), Lc.pl.sp.size(), stream);
+    if (cst != RS_OK) return cst;
     const bool timed = !capturing && p->t_cap > 0;
     const uint32_t slot = timed ? (p->t_count % p->t_cap) : 0;
     if (timed && (e = cudaEventRecord(p->tev[2 * slot], stream)) != cudaSuccess) return cuda_fail(e);
@@ -1159,6 +1314,8 @@ rs_status rs_graph_capture(rs_pipeline *p, void *workspace, uint64_t workspace_b
 {
     if (!p || !stream) return RS_ERR_INVALID;
     if (p->graph) return RS_ERR_STATE;
+    for (const SliceInfo &si : p->slices)
+        if (si.on) return RS_ERR_STATE;   // a slice runs once; its successor is another submission
     cudaError_t e;
     // the table upload inside the graph reads the pinned buffer at every replay:
     // build it now, outside the capture
@@ -1517,7 +1674,11 @@ static_assert(sizeof(DevStream) % 8 == 0, "the table copy moves 8-byte words");
 static void make_plan_fixed(const rs_pipeline *p, int strategy, FixedPlan *pl)
 {
     const size_t ns = p->streams.size();
-    for (size_t i = 0; i < ns; ++i) plan_stream(p, p->opts, strategy, p->streams[i], pl->sp[i]);
+    const uint32_t nsinks = n_leaves(p->stages, p->n_stages);
+    for (size_t i = 0; i < ns; ++i) {
+        plan_stream(p, p->opts, strategy, p->streams[i], pl->sp[i]);
+        apply_slice(p->slices[i], pl->sp[i], strategy, nsinks);
+    }
     layout_plan(pl->sp, ns, strategy, n_leaves(p->stages, p->n_stages), &pl->total_units, &pl->plan_tiles,
                 &pl->Kmax, &pl->zero_end, &pl->table_off, &pl->total);
 }
@@ -1531,9 +1692,11 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     const int strategy = run_strategy(p, &topo);
     if (strategy < 0) return RS_ERR_INVALID;
     if (strategy != RS_STRATEGY_TAG && p->opts.ensemble_width > 4 * RS_W) return RS_ERR_INVALID;
+    rs_status st0;
     FixedPlan &pl = p->noalloc_plan;
     make_plan_fixed(p, strategy, &pl);
     if (pl.total > RS_NOALLOC_WS_BYTES) return RS_ERR_CAPACITY;   // beyond the fixed scratch
+    if ((st0 = check_states(p, pl.sp, p->streams.size())) != RS_OK) return st0;
     if (pl.total_units >= (1ull << 31)) return RS_ERR_CAPACITY;
     void *ws = nullptr;
     rs_status st = noalloc_scratch(&ws);
@@ -1550,46 +1713,7 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
     const size_t ns = p->streams.size();
 
     // stream table in the pipeline's own host memory (pointers into the scratch array)
-    uint32_t base = 0, pbase = 0;
-    for (size_t i = 0; i < ns; ++i) {
-        const rs_stream_desc &s = p->streams[i];
-        const StreamPlan &q = pl.sp[i];
-        DevStream &d = p->noalloc_table.s[i];
-        memset(&d, 0, sizeof d);
-        d.parents = s.parents;
-        d.len = s.region_len;
-        d.offsets = s.region_offsets;
-        d.elements = s.elements;
-        d.ctx = s.ctx;
-        d.out_count = s.out_count;
-        d.out_sum = (unsigned long long *)s.out_sum;
-        d.out_min = s.out_min;
-        d.out_values = s.out_values;
-        d.out_values_len = s.out_values_len;
-        d.out2_count = s.out2_count;
-        d.out2_sum = (unsigned long long *)s.out2_sum;
-        d.out2_min = s.out2_min;
-        d.n_elements = s.n_elements;
-        d.R = (uint32_t)s.n_regions;
-        d.K = q.K;
-        d.n_units = q.n_units;
-        d.unit_base = base;
-        d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
-        d.mode = q.mode;
-        if (q.mode == UNIT_MERGE) {
-            d.rec = (UnitRec *)(wsb + q.rec_off);
-            d.slots = (Slot *)(wsb + q.slots_off);
-            d.u_count = (uint32_t *)(wsb + q.ucount_off);
-            d.plan_lb = (unsigned long long *)(wsb + q.planlb_off);
-            d.plan_tiles = q.plan_tiles;
-            d.plan_base = pbase;
-            d.D = q.D;
-            d.dsh = log2_if_pow2(q.D);
-            d.c = q.c;
-            pbase += q.plan_tiles;
-        }
-        base += d.n_units;
-    }
+    fill_table(p, pl.sp, ns, wsb, p->noalloc_table.s);
     if (pl.total_units == 0) return RS_OK;
 
     KParams P;
@@ -1684,6 +1808,7 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
             if (s.n_regions && (e = cudaMemsetAsync(s.out_count, 0, s.n_regions * 4, cs)) != cudaSuccess)
                 return cuda_fail(e);
     }
+    if ((st0 = clear_states(p, pl.sp, ns, cs)) != RS_OK) return st0;
     if (P.plan_tiles > 0) {
         int pg = (int)((P.plan_tiles + 7) / 8);
         if (pg > p->n_sm * 8) pg = p->n_sm * 8;

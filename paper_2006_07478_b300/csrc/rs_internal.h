@@ -100,6 +100,11 @@ struct DevStream {
     uint32_t *out2_count;
     unsigned long long *out2_sum;
     uint32_t *out2_min;
+    // sliced runs: this run processes units [slice_lo, slice_lo + n_units) of the stream;
+    // slot_units = the stream's whole unit count (the length of each leaf's slot array);
+    // finalize: this run holds the stream's last unit (the signal strategy then writes the
+    // merged results of the parents processed in pieces)
+    uint32_t slice_lo, slot_units, finalize;
 };
 
 // Status bits written by the device.

@@ -140,7 +140,7 @@ __device__ __forceinline__ Unit describe_unit(const KParams &P, uint32_t ticket)
     }
     const DevStream &S = P.streams[lo];
     u.stream = lo;
-    u.lu = ticket - S.unit_base;
+    u.lu = ticket - S.unit_base + S.slice_lo;
     if (S.mode == UNIT_MERGE) {
         if (u.lu >= *S.u_count) {   // beyond the units the planner laid out
             u.skip = true;
@@ -160,6 +160,10 @@ __device__ __forceinline__ Unit describe_unit(const KParams &P, uint32_t ticket)
         if (u.nk > S.D / S.c + 1 || u.j1 < u.j0 || u.i1 < u.i0) u.skip = true;   // inconsistent records
     } else {
         u.r0 = u.lu * S.K;
+        if (u.r0 >= S.R) {
+            u.skip = true;
+            return u;
+        }
         u.nk = min(S.K, S.R - u.r0);
     }
     return u;
@@ -305,7 +309,7 @@ __device__ __forceinline__ void merge_piece(const DevStream &S, uint32_t r, uint
     const unsigned long long D = S.D, c = S.c;
     const unsigned long long Pr = c * r + (off_abs - ebase);
     // a tree's second leaf merges through a second array of slots
-    Slot *sl = &S.slots[(unsigned long long)sink * S.n_units + Pr / D];
+    Slot *sl = &S.slots[(unsigned long long)sink * S.slot_units + Pr / D];
     if (cnt) {
         atomicAdd(&sl->count, cnt);
         atomicAdd(&sl->sum, sum);
@@ -2244,7 +2248,7 @@ __global__ void __launch_bounds__(256) rs_finalize_kernel(const __grid_constant_
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     for (uint32_t si = 0; si < P.n_streams; ++si) {
         const DevStream &S = P.streams[si];
-        if (S.mode != UNIT_MERGE || S.R == 0) continue;
+        if (S.mode != UNIT_MERGE || S.R == 0 || !S.finalize) continue;   // a sliced stream: after its last slice
         const uint32_t U = *S.u_count;
         for (uint32_t u = tid; u < U; u += nth) {
             const Slot sl = S.slots[u];
@@ -2255,7 +2259,7 @@ __global__ void __launch_bounds__(256) rs_finalize_kernel(const __grid_constant_
             if (P.want_min) S.out_min[r] = ~sl.min_inv;
             if (P.mix && P.n_sinks > 1) {
                 // a tree's second leaf: its own slots, after the first leaf's
-                const Slot s2 = S.slots[S.n_units + u];
+                const Slot s2 = S.slots[S.slot_units + u];
                 if (P.want_count) S.out2_count[r] = s2.count;
                 if (P.want_sum) S.out2_sum[r] = s2.sum;
                 if (P.want_min) S.out2_min[r] = ~s2.min_inv;

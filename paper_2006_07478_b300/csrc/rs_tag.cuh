@@ -164,7 +164,7 @@ __device__ __forceinline__ TicketUnit describe(const KParams &P, uint32_t t, uin
     if (!u.valid) return u;
     u.stream = stream_of(P, t, lane);
     const DevStream &S = P.streams[u.stream];
-    const uint32_t lu = t - S.unit_base;
+    const uint32_t lu = t - S.unit_base + S.slice_lo;
     if (S.mode == UNIT_REGIONS) {
         // K whole parents; their elements end where the last one ends
         u.rs = lu * S.K;

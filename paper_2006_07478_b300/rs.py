@@ -51,6 +51,7 @@ RS_MAX_STAGES = 6
 EXPORTS = [
     "rs_default_opts", "rs_pipeline_create", "rs_pipeline_destroy", "rs_pipeline_set_opts",
     "rs_pipeline_get_opts", "rs_stream_submit", "rs_clear_streams", "rs_workspace_size", "rs_run",
+    "rs_stream_state_size", "rs_stream_submit_slice",
     "rs_fetch_region_results", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
     "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_run_noalloc",
     "rs_server_create", "rs_server_submit", "rs_server_progress", "rs_server_poll", "rs_server_get_stats",
@@ -168,6 +169,10 @@ def lib(build_if_missing: bool = True):
             "rs_pipeline_set_opts": ([P, ctypes.POINTER(Opts)], ctypes.c_int),
             "rs_pipeline_get_opts": ([P, ctypes.POINTER(Opts)], ctypes.c_int),
             "rs_stream_submit": ([P, ctypes.POINTER(StreamDesc), ctypes.POINTER(U64)], ctypes.c_int),
+            "rs_stream_state_size": ([P, ctypes.POINTER(StreamDesc), ctypes.POINTER(U64), ctypes.POINTER(U64)],
+                                     ctypes.c_int),
+            "rs_stream_submit_slice": ([P, ctypes.POINTER(StreamDesc), P, U64, U64, U64, ctypes.POINTER(U64)],
+                                       ctypes.c_int),
             "rs_clear_streams": ([P], ctypes.c_int),
             "rs_workspace_size": ([P, ctypes.POINTER(U64)], ctypes.c_int),
             "rs_run": ([P, P, U64, P], ctypes.c_int),
@@ -331,12 +336,19 @@ class Pipeline:
                 F *= max(1, int(st[1]))
         return F
 
-    def submit(self, dev: dict, outputs=("count", "sum", "min")) -> dict:
+    def submit(self, dev: dict, outputs=("count", "sum", "min"), out=None, state=None, unit_begin=0,
+               unit_count=None) -> dict:
         """Register a device stream (dict of torch CUDA tensors: parents, len, offsets,
-        elements, ctx; any may be None).  Allocates its result tensors and returns
-        them in a dict with the stream id.  An emit pipeline's outputs are "count" and
-        "values" (F x the stream's element count entries)."""
+        elements, ctx; any may be None).  Allocates its result tensors (or reuses `out`,
+        the dict an earlier submit returned) and returns them in a dict with the stream
+        id.  An emit pipeline's outputs are "count" and "values" (F x the stream's element
+        count entries).  With unit_count set, the stream is submitted for a sliced run of
+        its units [unit_begin, unit_begin + unit_count) with `state` (a uint8 CUDA tensor
+        of at least state_size(dev)[0] bytes, kept by the caller across slices)."""
         import torch
+        if out is not None:
+            d = self._desc(dev, out)
+            return self._register(dev, out, d, state, unit_begin, unit_count)
         R = int(dev["R"])
         dvc = torch.device("cuda")
         emit = self.stages[-1][0] == "emit"
@@ -373,12 +385,51 @@ class Pipeline:
         d.out2_count = _ptr(out.get("count2"))
         d.out2_sum = _ptr(out.get("sum2"))
         d.out2_min = _ptr(out.get("min2"))
+        return self._register(dev, out, d, state, unit_begin, unit_count)
+
+    def _desc(self, dev: dict, out: dict):
+        d = StreamDesc()
+        d.n_regions = int(dev["R"])
+        d.parents = _ptr(dev.get("parents"))
+        d.region_len = _ptr(dev.get("len"))
+        d.region_offsets = _ptr(dev.get("offsets"))
+        el = dev.get("elements")
+        d.elements = _ptr(el)
+        d.n_elements = 0 if el is None else int(el.numel())
+        d.ctx = _ptr(dev.get("ctx"))
+        d.out_count = _ptr(out.get("count"))
+        d.out_sum = _ptr(out.get("sum"))
+        d.out_min = _ptr(out.get("min"))
+        d.total_elements_hint = int(dev.get("total_elements", 0))
+        if out.get("values") is not None:
+            d.out_values = _ptr(out["values"])
+            d.out_values_len = int(out["values"].numel())
+        d.out2_count = _ptr(out.get("count2"))
+        d.out2_sum = _ptr(out.get("sum2"))
+        d.out2_min = _ptr(out.get("min2"))
+        return d
+
+    def _register(self, dev, out, d, state, unit_begin, unit_count):
         sid = ctypes.c_uint64()
-        check(lib().rs_stream_submit(self._h, ctypes.byref(d), ctypes.byref(sid)), "rs_stream_submit")
-        self._keep.append((dev, out))
+        if unit_count is None:
+            check(lib().rs_stream_submit(self._h, ctypes.byref(d), ctypes.byref(sid)), "rs_stream_submit")
+        else:
+            st_ptr = None if state is None else ctypes.c_void_p(state.data_ptr())
+            st_len = 0 if state is None else int(state.numel())
+            check(lib().rs_stream_submit_slice(self._h, ctypes.byref(d), st_ptr, st_len, int(unit_begin),
+                                               int(unit_count), ctypes.byref(sid)), "rs_stream_submit_slice")
+        self._keep.append((dev, out, state))
         out["id"] = int(sid.value)
         self.streams.append(out)
         return out
+
+    def state_size(self, dev: dict) -> tuple:
+        """(bytes of resident state, units) of a sliced run of the device stream `dev`."""
+        d = self._desc(dev, {})
+        b, u = ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().rs_stream_state_size(self._h, ctypes.byref(d), ctypes.byref(b), ctypes.byref(u)),
+              "rs_stream_state_size")
+        return int(b.value), int(u.value)
 
     def clear(self):
         check(lib().rs_clear_streams(self._h), "rs_clear_streams")
