@@ -491,18 +491,21 @@ def cgroup_cpu_quota():
         return None
 
 
-def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: float = 4.0):
+def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: float = 40.0, slice_units: int = 16,
+                  warm_requests: int = 64):
     """Open-loop Poisson arrivals of batched-size hashed streams into the
-    continuous-batching server; latency = scheduled arrival -> completion seen."""
+    continuous-batching server (requests advanced `slice_units` work units per launch over
+    their resident state, admission by free arena memory); latency = scheduled arrival ->
+    completion seen."""
     pool = wl.batched_streams()
     pipe = wl.pipeline_hash_filter_map()
     reqs = [rs.host_request(s) for s in pool]
     sizes = [wl.n_elements(s) for s in pool]
     busy = [False] * len(pool)
     arrivals = wl.poisson_arrivals(rate, seconds, seed=4)
-    srv = rs.Server(pipe, arena_bytes=int(arena_gb * (1 << 30)), strategy="tag")
-    # untimed warm-up: a few batches through the server (first launches, staging buffers)
-    warm = [srv.submit(reqs[i]) for i in range(64)]
+    srv = rs.Server(pipe, arena_bytes=int(arena_gb * (1 << 30)), strategy="tag", slice_units=slice_units)
+    # untimed warm-up: a few launches through the server (first launches, staging buffers)
+    warm = [srv.submit(reqs[i]) for i in range(warm_requests)]
     left = set(warm)
     t_w = time.perf_counter()
     while left and time.perf_counter() - t_w < 30.0:
@@ -558,7 +561,9 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
     L = np.array([x[1] for x in lat]) * 1e3
     Lw = np.array([x[1] for x in lat if x[0] >= 1.0]) * 1e3
     return {"workload": f"Poisson {rate:.0f} streams/s for {seconds:.0f} s, batched-size hashed streams, "
-                        f"arena {arena_gb:.0f} GiB",
+                        f"arena {arena_gb:.0f} GiB, {slice_units} units per request per launch",
+            "offered_items_per_s": rate * float(np.mean(sizes)),
+            "launches": st["batches"], "largest_launch": st["largest_batch"],
             "requests": int(len(lat)), "items_per_s": done_items / wall,
             "p50_ms": float(np.percentile(L, 50)) if len(L) else None,
             "p99_ms": float(np.percentile(L, 99)) if len(L) else None,
@@ -571,6 +576,24 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
                          "throttled_ms": ((thr1.get("throttled_usec", 0) - thr0.get("throttled_usec", 0)) / 1e3) if thr0 else None},
             "batches": st["batches"], "largest_batch": st["largest_batch"],
             "arena_peak_bytes": st["arena_peak"], "wall_s": wall}
+
+
+def bench_serving_sweep(rs, torch, rates=(20000, 40000, 80000, 160000, 320000), seconds=3.0):
+    """Arrival rates doubling from the configured 20,000 streams/s: throughput and p99 per
+    rate; the saturation rate is the first whose p99 exceeds twice the lightest load's, or
+    whose completions fall below 95% of the offered items."""
+    rows = []
+    for r in rates:
+        x = bench_serving(rs, torch, seconds, rate=float(r), warm_requests=16)
+        rows.append({"rate": r, "items_per_s": x["items_per_s"], "offered_items_per_s": x["offered_items_per_s"],
+                     "p50_ms": x["p50_ms"], "p99_ms": x["p99_ms"], "launches": x["launches"]})
+    base = rows[0]["p99_ms"] or 0.0
+    sat = None
+    for row in rows:
+        if (row["p99_ms"] or 0.0) > 2 * base or row["items_per_s"] < 0.95 * row["offered_items_per_s"]:
+            sat = row["rate"]
+            break
+    return {"seconds_per_rate": seconds, "rows": rows, "saturation_rate": sat}
 
 
 def run_case(args, rs, torch):
@@ -614,7 +637,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="also sweep arrival rates to find where p99 turns up (about 20 s more)")
     ap.add_argument("--no-extras", action="store_true", help="skip the graph, batched and serving sections")
     ap.add_argument("--case", default=None,
                     help="MEAN:STRATEGY[:N_LOG2[:OPT=V,...]] -- one stream, fixed strategy and options "
@@ -825,7 +850,8 @@ def main():
                          ("graph_edges", lambda: bench_graph(rs, torch, peak)),
                          ("region_sizes", lambda: bench_region_sizes(rs, torch)),
                          ("batched", lambda: bench_batched(rs, torch)),
-                         ("serving", lambda: bench_serving(rs, torch, args.serve_seconds))):
+                         ("serving", lambda: bench_serving(rs, torch, args.serve_seconds)),
+                         ("serving_sweep", lambda: bench_serving_sweep(rs, torch) if args.serve_sweep else None)):
             try:
                 extras[name] = fn()
             except Exception as exc:   # report, do not lose the main line

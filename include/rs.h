@@ -357,32 +357,45 @@ typedef struct {
 } rs_request;
 
 typedef struct {
-    uint64_t submitted, admitted, completed, batches, largest_batch;
-    uint64_t in_flight, queued;          /* batches on the GPU, requests waiting for memory */
+    uint64_t submitted, admitted, completed;
+    uint64_t batches, largest_batch;     /* launches (slices), most requests in one          */
+    uint64_t in_flight, queued;          /* launches queued on the GPU, requests waiting for
+                                            memory                                           */
     uint64_t arena_live, arena_peak;     /* bytes of the arena in use now / at most          */
-    uint64_t gathered;                   /* batches whose results came back with one gather
-                                            kernel and one copy (the rest: one copy per array) */
+    uint64_t gathered;                   /* launches whose finished requests' results came
+                                            back with one gather kernel and one copy        */
+    uint64_t per_array;                  /* ... with one copy per output array (no room)    */
 } rs_server_stats;
 
-/* A server over one stage list.  `arena` (device, caller-owned, 256-byte aligned) is
- * the device memory budget: a request is admitted only when its inputs and outputs fit
- * in the arena's free part (a ring), and every batch's workspace comes from it too.
- * Up to max_batch requests (0 = 4096) form one batch = one rs_run; up to max_inflight
- * (0 = 2) batches are queued on `stream` at once, so arrivals during a batch join the
- * next one.  No CUDA call is made here. */
+/* A server over one linear stage list (not ending in an emit sink).  `arena` (device,
+ * caller-owned, 256-byte aligned) is the device memory budget: a request is admitted only
+ * when its inputs, outputs and resident state (rs_stream_state_size) fit in the arena's
+ * free part, and stays there until it finishes; every launch's workspace comes from it
+ * too.  Each launch (a slice) advances every active request -- up to max_batch of them
+ * (0 = 4096) -- by at most the slice budget of work units (rs_server_set_slice_units),
+ * so requests arriving meanwhile join the next launch.  Up to max_inflight (0 = 2)
+ * launches are queued on `stream`; admissions' copies and finished requests' result
+ * copies run on two streams of the server's own, so they overlap the launches on the
+ * device.  RS_STRATEGY_AUTO serves with the tag strategy (a request's units are sized
+ * once, at submission).  No CUDA call is made here. */
 rs_status rs_server_create(const rs_stage_desc *stages, uint32_t n_stages, const rs_pipeline_opts *opts,
                            void *arena, uint64_t arena_bytes, uint32_t max_batch, uint32_t max_inflight,
                            rs_cuda_stream stream, rs_server **out);
+/* Work units each active request runs per launch (default 16); 0 runs every request to
+ * completion in the launch it joins. */
+rs_status rs_server_set_slice_units(rs_server *s, uint32_t units);
 /* Queue a request (host-side only; admitted by a later rs_server_progress).
  * RS_ERR_CAPACITY if it needs more than half the arena. */
 rs_status rs_server_submit(rs_server *s, const rs_request *r, uint64_t *req_id);
-/* Non-blocking step: retire finished batches (their results are copied into the host
- * outputs here), admit queued requests while the arena has room (copies on `stream`),
- * and launch the forming batch if fewer than max_inflight batches are running.  A
- * batch's results come back with one gather kernel and one device-to-host copy into a
- * page-locked staging buffer of the server's (host memory, allocated with
- * cudaMallocHost when a batch first needs one that large, reused afterwards); if that
- * cannot be had, with one copy per output array. */
+/* Non-blocking step: retire launches whose finished requests' results have landed
+ * (copied into the requests' host outputs here; their arena space is freed), admit queued
+ * requests while the arena has room (their inputs copied on the server's copy-in stream),
+ * and launch slices while fewer than max_inflight are queued.  The results of the
+ * requests a launch finishes come back with one gather kernel and one device-to-host copy
+ * into a page-locked staging buffer of the server's (host memory, allocated with
+ * cudaMallocHost when a launch first needs one that large, reused afterwards); if that
+ * cannot be had, with one copy per output array.  The first call creates the two copy
+ * streams. */
 rs_status rs_server_progress(rs_server *s);
 /* Ids of requests completed since the last poll (up to max; *n = how many). */
 rs_status rs_server_poll(rs_server *s, uint64_t *ids, uint32_t max, uint32_t *n);

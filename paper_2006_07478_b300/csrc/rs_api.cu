@@ -39,6 +39,7 @@ struct StreamPlan {
     // it): st_zero bytes cleared when it is planned, st_total bytes in all
     uint32_t full_units, slice_lo, slice_n, run_tiles;
     bool sliced, plan_now;
+    bool scan2;   // the planner reads a two-pass prefix of the lengths (many tiles)
     size_t st_zero, st_total;
 };
 
@@ -575,6 +576,7 @@ static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int str
         q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
         const uint32_t tile = plan_tile_parents(p);
         q.plan_tiles = (uint32_t)((s.n_regions + tile - 1) / tile);
+        q.scan2 = !s.region_offsets && q.plan_tiles >= RS_SCAN2_TILES;
     } else {
         q.mode = UNIT_REGIONS;
         q.K = choose_K(p, o, s, strategy);
@@ -983,6 +985,7 @@ static void fill_table(const rs_pipeline *p, const StreamPlan *sp, size_t ns, un
         d.slice_lo = q.slice_lo;
         d.slot_units = q.full_units;
         d.finalize = q.slice_lo + q.slice_n >= q.full_units ? 1u : 0u;
+        d.scan2 = q.scan2 ? 1u : 0u;
         d.unit_base = base;
         d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
         d.mode = q.mode;
@@ -1001,6 +1004,14 @@ static void fill_table(const rs_pipeline *p, const StreamPlan *sp, size_t ns, un
         }
         base += d.n_units;
     }
+}
+
+// some stream this run plans takes the two-pass prefix
+static bool any_scan2(const StreamPlan *sp, size_t ns)
+{
+    for (size_t i = 0; i < ns; ++i)
+        if (sp[i].scan2 && sp[i].run_tiles > 0) return true;
+    return false;
 }
 
 // every sliced stream's state holds its layout under the current options
@@ -1219,6 +1230,10 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
         int cap = p->n_sm * 8;
         if (pg > cap) pg = cap;
         if (pg < 1) pg = 1;
+        if (any_scan2(Lc.pl.sp.data(), Lc.pl.sp.size())) {
+            int le2 = rs_launch_prefix(Lc.P, pg, (void *)stream);
+            if (le2 != 0) return cuda_fail((cudaError_t)le2);
+        }
         int le = rs_launch_planner(Lc.P, pg, (void *)stream);
         if (le != 0) return cuda_fail((cudaError_t)le);
     }
@@ -1813,6 +1828,10 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
         int pg = (int)((P.plan_tiles + 7) / 8);
         if (pg > p->n_sm * 8) pg = p->n_sm * 8;
         if (pg < 1) pg = 1;
+        if (any_scan2(pl.sp, ns)) {
+            int le2 = rs_launch_prefix(P, pg, (void *)cs);
+            if (le2 != 0) return cuda_fail((cudaError_t)le2);
+        }
         int le = rs_launch_planner(P, pg, (void *)cs);
         if (le != 0) return cuda_fail((cudaError_t)le);
     }

@@ -1,25 +1,30 @@
 // rs_serve.cu -- continuous-batching server over the pipeline (the serving form).
 //
-// Requests (one stream each, in host memory) arrive at any time.  The server admits a
-// request when its inputs and outputs fit in the free part of a caller-provided device
-// arena (a ring), copies it in, and groups every admitted request that is not yet
-// running into the next batch: one rs_run over all of them.  Up to `max_inflight`
-// batches are queued on the server's CUDA stream at once, so requests that arrive while
-// others are on the GPU join the next batch and their work overlaps on the device.
-// A batch's results come back with one gather kernel (every member's output arrays into
-// one contiguous region of the arena) and one device-to-host copy into a page-locked
-// staging buffer of the server's; when the batch's completion event fires they are
-// copied on the host into the requests' output buffers, its arena space is released and
-// its request ids are reported by rs_server_poll.  (A batch whose results do not fit
-// that path falls back to one copy per output array.)
+// Requests (one stream each, in host memory) arrive at any time.  A request is admitted
+// when its inputs, outputs and resident state fit in the free part of a caller-provided
+// device arena; its inputs are copied in on a copy stream of the server's own.  From
+// then on the request is active: its data and its planning state stay on the device
+// until it finishes.  The server advances every active request a slice at a time: one
+// launch (rs_run over the active requests, each submitted with rs_stream_submit_slice)
+// runs at most `slice_units` work units of each, so a request that arrives while others
+// are on the GPU joins the next launch, and a long request holds a short one back by at
+// most one slice.  Up to `max_inflight` slices are queued on the server's compute stream
+// and the copies overlap them on the device: admissions' inputs go up on one copy
+// stream, and the results of the requests a slice finishes come back on another (one
+// gather kernel packing their output arrays into one arena region, one device-to-host
+// copy into a page-locked staging buffer, scattered into the requests' host buffers when
+// the copy has landed; when that path has no room, one copy per array).
 //
-// Nothing here allocates device memory; the arena is the caller's.  The staging buffers
-// are host memory, allocated when a batch first needs one that large and reused.
+// Nothing here allocates device memory; the arena is the caller's (a first-fit free
+// list, so requests may finish in any order).  The staging buffers are host memory,
+// allocated when a slice first needs one that large and reused.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <deque>
+#include <iterator>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -27,13 +32,61 @@
 
 namespace {
 
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// first-fit free list over [0, cap) with coalescing
+struct FreeList {
+    std::map<uint64_t, uint64_t> free;   // offset -> bytes
+    uint64_t live = 0, peak = 0;
+    void reset(uint64_t cap)
+    {
+        free.clear();
+        if (cap) free[0] = cap;
+        live = peak = 0;
+    }
+    bool alloc(uint64_t b, uint64_t *off)
+    {
+        for (auto it = free.begin(); it != free.end(); ++it) {
+            if (it->second < b) continue;
+            *off = it->first;
+            const uint64_t rest = it->second - b;
+            const uint64_t o2 = it->first + b;
+            free.erase(it);
+            if (rest) free[o2] = rest;
+            live += b;
+            if (live > peak) peak = live;
+            return true;
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t b)
+    {
+        live -= b;
+        auto it = free.emplace(off, b).first;
+        auto nx = std::next(it);
+        if (nx != free.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free.erase(nx);
+        }
+        if (it != free.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free.erase(it);
+            }
+        }
+    }
+};
+
 struct Req {
-    uint64_t id;
+    uint64_t id = 0;
     rs_request r;
-    uint64_t off, bytes;         // arena chunk
-    uint32_t *d_count;           // the request's device outputs (in its arena chunk)
-    unsigned long long *d_sum;
-    uint32_t *d_min;
+    uint64_t off = 0, bytes = 0;        // arena chunk: inputs, outputs, resident state
+    rs_stream_desc d;                   // device view of the request
+    void *state = nullptr;
+    uint64_t state_bytes = 0;
+    uint64_t units = 0, next = 0;       // its work units; the next one to run
+    uint64_t round = 0;                 // admission round (whose copy-in event covers it)
 };
 
 // one output array to gather: device source, device destination, 4-byte words
@@ -56,15 +109,14 @@ struct Stage {
     uint64_t cap = 0;
 };
 
-struct Batch {
+// one launch, and the requests whose last unit it runs
+struct Slice {
     rs_pipeline *p = nullptr;
-    std::vector<uint64_t> ids;
-    uint64_t ws_bound = 0;       // workspace this batch will need, bounded from above
-    uint64_t head_after = 0;     // ring head after this batch's last allocation
-    uint64_t live_bytes = 0;     // bytes this batch holds in the ring
-    cudaEvent_t ev = nullptr;
-    Stage stage;                 // results staging (gathered path), returned at retire
-    std::vector<Scatter> scat;   // where each staged output array goes
+    uint64_t ws_off = 0, ws_bytes = 0, res_off = 0, res_bytes = 0;   // arena chunks of the slice
+    std::vector<Req> finishing;
+    cudaEvent_t done = nullptr;       // their results have landed in host memory
+    Stage stage;
+    std::vector<Scatter> scat;
 };
 
 // Each CTA copies whole items, 16 bytes per thread and step.  Sources and destinations
@@ -79,8 +131,6 @@ __global__ void __launch_bounds__(128) rs_gather_kernel(const GatherItem *items,
     }
 }
 
-size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
-
 }  // namespace
 
 struct rs_server {
@@ -89,68 +139,37 @@ struct rs_server {
     rs_pipeline_opts opts;
     unsigned char *arena = nullptr;
     uint64_t cap = 0;
-    // ring allocator: live bytes occupy [tail, head) modulo cap
-    uint64_t head = 0, tail = 0, live = 0, peak = 0;
+    FreeList fl;
     std::deque<Req> queued;
-    Batch forming;
-    std::vector<Req> forming_members;
-    std::deque<Batch> inflight;
+    std::vector<Req> active;
+    std::deque<Slice> inflight;
     std::vector<rs_pipeline *> pool;
-    std::vector<cudaEvent_t> free_events;   // completion events of retired batches, reused
-    std::vector<Stage> free_stages;         // staging buffers of retired batches, reused
+    rs_pipeline *probe = nullptr;           // sizes requests' resident state
+    std::vector<cudaEvent_t> free_events;
+    std::vector<Stage> free_stages;
     std::vector<uint64_t> completed;
+    // admission rounds not yet waited on by the compute stream: {round, copy-in event}
+    std::deque<std::pair<uint64_t, cudaEvent_t>> rounds;
+    uint64_t round = 0;
     uint64_t next_id = 1;
     uint32_t max_batch = 4096, max_inflight = 2;
-    cudaStream_t stream = nullptr;
+    uint32_t slice_units = 16;
+    cudaStream_t stream = nullptr;                // slices (the caller's stream)
+    cudaStream_t cin = nullptr, cout = nullptr;   // copy-in, results
     rs_server_stats stats;
 };
 
-// Contiguous allocation of b bytes from the ring.  Live bytes occupy [tail, head)
-// modulo cap.  When the end of the arena is too short, the allocation wraps to 0 and
-// the skipped end is charged to the caller (*charged) until the tail passes it.
-static bool ring_alloc(rs_server *s, uint64_t b, uint64_t *off, uint64_t *charged)
+static rs_status take_event(rs_server *s, cudaEvent_t *e)
 {
-    if (b > s->cap) return false;
-    if (s->live == 0) s->head = s->tail = 0;
-    uint64_t skip = 0;
-    if (s->live == 0 || s->head > s->tail) {
-        if (s->cap - s->head >= b) {
-            *off = s->head;
-        } else if (s->tail >= b) {
-            skip = s->cap - s->head;
-            *off = 0;
-        } else {
-            return false;
-        }
-    } else {   // wrapped (head < tail) or full (head == tail, live > 0)
-        if (s->tail - s->head >= b) *off = s->head;
-        else return false;
+    if (!s->free_events.empty()) {
+        *e = s->free_events.back();
+        s->free_events.pop_back();
+        return RS_OK;
     }
-    s->head = *off + b;
-    s->live += b + skip;
-    if (s->live > s->peak) s->peak = s->live;
-    *charged = b + skip;
-    return true;
+    return cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
-// Upper bound of the workspace bytes one more stream adds to a batch (the layout of
-// rs_workspace_size: merge slots, unit count, planner words and unit records for loaded
-// streams, one stream-table entry for every stream, each piece 256-byte aligned).
-static uint64_t stream_ws_bound(const rs_server *s, const rs_request &r)
-{
-    uint64_t b = a256(sizeof(DevStream)) + 256;
-    if (s->st[0].kind == RS_ENUM_LOAD && r.n_regions) {
-        const uint64_t kp = s->opts.regions_per_unit ? s->opts.regions_per_unit : 128;
-        const uint64_t c = s->opts.region_cost ? s->opts.region_cost : RS_STEP_REGION;
-        const uint64_t D = c * kp;
-        const uint64_t units = (c * r.n_regions + r.n_elements + D - 1) / D;
-        const uint64_t tiles = (r.n_regions + RS_PLAN_TILE_SMALL - 1) / RS_PLAN_TILE_SMALL;   // at most
-        b += a256(units * sizeof(Slot)) + 256 + a256(tiles * 8) + a256((units + 1) * sizeof(UnitRec));
-    }
-    return b;
-}
-
-static uint64_t request_bytes(const rs_server *s, const rs_request &r)
+static uint64_t request_io_bytes(const rs_request &r)
 {
     const uint64_t R = r.n_regions;
     uint64_t b = 0;
@@ -161,66 +180,64 @@ static uint64_t request_bytes(const rs_server *s, const rs_request &r)
     if (r.out_count) b += a256(R * 4);
     if (r.out_sum) b += a256(R * 8);
     if (r.out_min) b += a256(R * 4);
-    (void)s;
     return b < 256 ? 256 : b;
 }
 
-// Copy a request into its arena chunk and register it with the forming batch.
-static rs_status admit(rs_server *s, Req &q)
+// the request's device view: inputs and outputs laid out in its chunk, then its state
+static void layout_request(rs_server *s, Req &q)
 {
-    if (!s->forming.p) {
-        if (!s->pool.empty()) {
-            s->forming.p = s->pool.back();
-            s->pool.pop_back();
-            rs_clear_streams(s->forming.p);
-        } else {
-            rs_status st = rs_pipeline_create(s->st, s->n_stages, &s->opts, &s->forming.p);
-            if (st != RS_OK) return st;
-        }
-    }
     unsigned char *base = s->arena + q.off;
     size_t o = 0;
-    rs_stream_desc d;
+    rs_stream_desc &d = q.d;
     memset(&d, 0, sizeof d);
     d.n_regions = q.r.n_regions;
     const uint64_t R = q.r.n_regions;
-    auto put = [&](const void *src, size_t bytes, const void **dst) -> bool {
-        *dst = base + o;
-        if (bytes && cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
-            return false;
+    auto put = [&](const void *src, size_t bytes) -> void * {
+        if (!src) return nullptr;
+        void *p = base + o;
         o += a256(bytes);
-        return true;
+        return p;
     };
-    if (q.r.parents && !put(q.r.parents, R * 4, (const void **)&d.parents)) return RS_ERR_CUDA;
-    if (q.r.region_len && !put(q.r.region_len, R * 4, (const void **)&d.region_len)) return RS_ERR_CUDA;
-    if (q.r.elements && !put(q.r.elements, q.r.n_elements * 4, (const void **)&d.elements)) return RS_ERR_CUDA;
-    if (q.r.ctx && !put(q.r.ctx, R * 4, (const void **)&d.ctx)) return RS_ERR_CUDA;
+    d.parents = (const uint32_t *)put(q.r.parents, R * 4);
+    d.region_len = (const uint32_t *)put(q.r.region_len, R * 4);
+    d.elements = (const uint32_t *)put(q.r.elements, q.r.n_elements * 4);
+    d.ctx = (const uint32_t *)put(q.r.ctx, R * 4);
     d.n_elements = q.r.elements ? q.r.n_elements : 0;
-    if (q.r.out_count) { d.out_count = (uint32_t *)(base + o); o += a256(R * 4); }
-    if (q.r.out_sum) { d.out_sum = (uint64_t *)(base + o); o += a256(R * 8); }
-    if (q.r.out_min) { d.out_min = (uint32_t *)(base + o); o += a256(R * 4); }
-    q.d_count = d.out_count;
-    q.d_sum = (unsigned long long *)d.out_sum;
-    q.d_min = d.out_min;
+    d.out_count = (uint32_t *)put(q.r.out_count, R * 4);
+    d.out_sum = (uint64_t *)put(q.r.out_sum, R * 8);
+    d.out_min = (uint32_t *)put(q.r.out_min, R * 4);
     d.total_elements_hint = q.r.total_elements_hint;
-    uint64_t sid = 0;
-    rs_status st = rs_stream_submit(s->forming.p, &d, &sid);
-    if (st != RS_OK) return st;
-    s->forming.ids.push_back(q.id);
-    s->forming.head_after = s->head;
-    s->stats.admitted++;
+    q.state = base + a256(o);
+}
+
+static rs_status copy_in(rs_server *s, const Req &q)
+{
+    const uint64_t R = q.r.n_regions;
+    struct {
+        const void *src;
+        const void *dst;
+        uint64_t bytes;
+    } c[4] = {{q.r.parents, q.d.parents, R * 4},
+              {q.r.region_len, q.d.region_len, R * 4},
+              {q.r.elements, q.d.elements, q.r.n_elements * 4},
+              {q.r.ctx, q.d.ctx, R * 4}};
+    for (auto &x : c)
+        if (x.src && x.bytes &&
+            cudaMemcpyAsync(const_cast<void *>(x.dst), x.src, x.bytes, cudaMemcpyHostToDevice, s->cin) != cudaSuccess)
+            return RS_ERR_CUDA;
     return RS_OK;
 }
 
-// Queue the batch's results as one gather into an arena region and one copy into a
-// staging buffer (host side scattered at retire).  False, with nothing queued, when the
-// arena has no room or no staging buffer can be had: the caller copies per array.
-static bool gather_results(rs_server *s, Batch &b, const std::vector<Req> &members)
+// Queue the finishing requests' results back to the host on the results stream: one
+// gather into an arena region and one copy into a staging buffer (scattered on the host
+// at retire).  False, with nothing queued, when no arena room or staging buffer can be
+// had: the caller copies each array.
+static bool gather_results(rs_server *s, Slice &b)
 {
     std::vector<Scatter> scat;
     uint64_t rbytes = 0;
     size_t n_items = 0;
-    for (const Req &q : members) {
+    for (const Req &q : b.finishing) {
         const uint64_t R = q.r.n_regions;
         const void *hd[3] = {q.r.out_count, q.r.out_sum, q.r.out_min};
         const uint64_t by[3] = {R * 4, R * 8, R * 4};
@@ -231,11 +248,9 @@ static bool gather_results(rs_server *s, Batch &b, const std::vector<Req> &membe
             ++n_items;
         }
     }
-    if (n_items == 0) return true;   // nothing to hand back
+    if (n_items == 0) return true;
     const uint64_t tbytes = a256(n_items * sizeof(GatherItem));
     const uint64_t total = tbytes + a256(rbytes);
-    // a staging buffer at least this large: reuse one, else allocate (rounded up to a
-    // power of two, so that few sizes are ever allocated)
     Stage sg;
     for (size_t i = 0; i < s->free_stages.size(); ++i) {
         if (s->free_stages[i].cap >= total) {
@@ -253,19 +268,17 @@ static bool gather_results(rs_server *s, Batch &b, const std::vector<Req> &membe
         }
         sg.cap = cap;
     }
-    uint64_t off = 0, charged = 0;
-    if (!ring_alloc(s, total, &off, &charged)) {
+    uint64_t off = 0;
+    if (!s->fl.alloc(a256(total), &off)) {
         s->free_stages.push_back(sg);
         return false;
     }
-    b.head_after = s->head;
-    b.live_bytes += charged;
     unsigned char *dev = s->arena + off;
     GatherItem *items = reinterpret_cast<GatherItem *>(sg.p);
     size_t k = 0;
-    for (const Req &q : members) {
+    for (const Req &q : b.finishing) {
         if (q.r.n_regions == 0) continue;
-        const void *src[3] = {q.d_count, q.d_sum, q.d_min};
+        const void *src[3] = {q.d.out_count, q.d.out_sum, q.d.out_min};
         const void *hd[3] = {q.r.out_count, q.r.out_sum, q.r.out_min};
         const uint64_t words[3] = {q.r.n_regions, 2 * q.r.n_regions, q.r.n_regions};
         for (int j = 0; j < 3; ++j) {
@@ -277,59 +290,121 @@ static bool gather_results(rs_server *s, Batch &b, const std::vector<Req> &membe
         }
     }
     const uint32_t grid = n_items < 1024 ? (uint32_t)n_items : 1024u;
-    if (cudaMemcpyAsync(dev, sg.p, n_items * sizeof(GatherItem), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-        (rs_gather_kernel<<<grid, 128, 0, s->stream>>>(reinterpret_cast<const GatherItem *>(dev), (uint32_t)n_items),
+    if (cudaMemcpyAsync(dev, sg.p, n_items * sizeof(GatherItem), cudaMemcpyHostToDevice, s->cout) != cudaSuccess ||
+        (rs_gather_kernel<<<grid, 128, 0, s->cout>>>(reinterpret_cast<const GatherItem *>(dev), (uint32_t)n_items),
          cudaGetLastError() != cudaSuccess) ||
-        cudaMemcpyAsync(sg.p + tbytes, dev + tbytes, rbytes, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) {
-        // the arena charge stays with the batch; the copies are not queued: fall back
+        cudaMemcpyAsync(sg.p + tbytes, dev + tbytes, rbytes, cudaMemcpyDeviceToHost, s->cout) != cudaSuccess) {
+        s->fl.release(off, a256(total));
         s->free_stages.push_back(sg);
         return false;
     }
     for (Scatter &c : scat) c.off += tbytes;
     b.stage = sg;
     b.scat.swap(scat);
+    b.res_off = off;
+    b.res_bytes = a256(total);
     return true;
 }
 
-// Launch the forming batch: workspace from the ring, one rs_run, result copies back
-// to each request's host buffers, then a completion event.
-static rs_status launch(rs_server *s, std::vector<Req> &members)
+// Launch one slice over the active requests: each runs its next slice_units units (all of
+// them when slice_units is 0).  RS_ERR_NOT_READY when the arena has no room for the
+// slice's workspace now.
+static rs_status launch_slice(rs_server *s)
 {
-    Batch &b = s->forming;
+    Slice b;
+    if (!s->pool.empty()) {
+        b.p = s->pool.back();
+        s->pool.pop_back();
+        rs_clear_streams(b.p);
+    } else {
+        rs_status st = rs_pipeline_create(s->st, s->n_stages, &s->opts, &b.p);
+        if (st != RS_OK) return st;
+    }
+    std::vector<size_t> members;
+    uint64_t need_round = 0;
+    for (size_t i = 0; i < s->active.size() && members.size() < s->max_batch; ++i) {
+        Req &q = s->active[i];
+        if (q.next >= q.units) continue;
+        const uint64_t n = s->slice_units ? s->slice_units : q.units;
+        rs_status st = rs_stream_submit_slice(b.p, &q.d, q.state, q.state_bytes, q.next, n, nullptr);
+        if (st != RS_OK) {
+            s->pool.push_back(b.p);
+            return st;
+        }
+        members.push_back(i);
+        if (q.round > need_round) need_round = q.round;
+    }
+    if (members.empty()) {
+        s->pool.push_back(b.p);
+        return RS_OK;
+    }
     uint64_t wsb = 0;
     rs_status st = rs_workspace_size(b.p, &wsb);
-    if (st != RS_OK) return st;
-    uint64_t woff = 0, charged = 0;
-    if (!ring_alloc(s, a256(wsb), &woff, &charged)) {
-        // no room for the workspace: wait for a batch to finish, unless none is running
+    if (st != RS_OK) {
+        s->pool.push_back(b.p);
+        return st;
+    }
+    uint64_t woff = 0;
+    if (!s->fl.alloc(a256(wsb), &woff)) {
+        s->pool.push_back(b.p);
         return s->inflight.empty() ? RS_ERR_CAPACITY : RS_ERR_NOT_READY;
     }
-    b.head_after = s->head;
-    b.live_bytes += charged;
-    st = rs_run(b.p, s->arena + woff, a256(wsb), (rs_cuda_stream)s->stream);
+    b.ws_off = woff;
+    b.ws_bytes = a256(wsb);
+    // the slice reads the inputs of every admission round up to its newest member's
+    // (an event may be recorded again once a wait on it is enqueued)
+    while (!s->rounds.empty() && s->rounds.front().first <= need_round) {
+        if (cudaStreamWaitEvent(s->stream, s->rounds.front().second, 0) != cudaSuccess) return RS_ERR_CUDA;
+        s->free_events.push_back(s->rounds.front().second);
+        s->rounds.pop_front();
+    }
+    st = rs_run(b.p, s->arena + woff, b.ws_bytes, (rs_cuda_stream)s->stream);
     if (st != RS_OK) return st;
-    if (gather_results(s, b, members)) {
-        s->stats.gathered++;
-    } else {
-        for (size_t i = 0; i < members.size(); ++i) {
-            rs_region_results dst;
-            dst.count = members[i].r.out_count;
-            dst.sum = members[i].r.out_sum;
-            dst.min = members[i].r.out_min;
-            st = rs_fetch_region_results(b.p, i, &dst, (rs_cuda_stream)s->stream);
-            if (st != RS_OK) return st;
+    // requests whose last unit ran: their results go back on the results stream
+    std::vector<Req> keep;
+    keep.reserve(s->active.size());
+    size_t mi = 0;
+    for (size_t i = 0; i < s->active.size(); ++i) {
+        Req &q = s->active[i];
+        if (mi < members.size() && members[mi] == i) {
+            ++mi;
+            q.next += s->slice_units ? s->slice_units : q.units;
+            if (q.next >= q.units) {
+                b.finishing.push_back(q);
+                continue;
+            }
+        }
+        keep.push_back(q);
+    }
+    s->active.swap(keep);
+    cudaEvent_t ran;
+    if (take_event(s, &ran) != RS_OK) return RS_ERR_CUDA;
+    if (cudaEventRecord(ran, s->stream) != cudaSuccess) return RS_ERR_CUDA;
+    if (cudaStreamWaitEvent(s->cout, ran, 0) != cudaSuccess) return RS_ERR_CUDA;
+    s->free_events.push_back(ran);
+    if (!b.finishing.empty()) {
+        if (gather_results(s, b)) {
+            s->stats.gathered++;
+        } else {
+            s->stats.per_array++;
+            for (const Req &q : b.finishing) {
+                const uint64_t R = q.r.n_regions;
+                if (!R) continue;
+                if ((q.r.out_count && cudaMemcpyAsync(q.r.out_count, q.d.out_count, R * 4, cudaMemcpyDeviceToHost,
+                                                      s->cout) != cudaSuccess) ||
+                    (q.r.out_sum && cudaMemcpyAsync(q.r.out_sum, q.d.out_sum, R * 8, cudaMemcpyDeviceToHost,
+                                                    s->cout) != cudaSuccess) ||
+                    (q.r.out_min && cudaMemcpyAsync(q.r.out_min, q.d.out_min, R * 4, cudaMemcpyDeviceToHost,
+                                                    s->cout) != cudaSuccess))
+                    return RS_ERR_CUDA;
+            }
         }
     }
-    if (!b.ev && !s->free_events.empty()) {
-        b.ev = s->free_events.back();
-        s->free_events.pop_back();
-    }
-    if (!b.ev && cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) return RS_ERR_CUDA;
-    if (cudaEventRecord(b.ev, s->stream) != cudaSuccess) return RS_ERR_CUDA;
+    if (take_event(s, &b.done) != RS_OK) return RS_ERR_CUDA;
+    if (cudaEventRecord(b.done, s->cout) != cudaSuccess) return RS_ERR_CUDA;
     s->stats.batches++;
-    s->stats.largest_batch = b.ids.size() > s->stats.largest_batch ? b.ids.size() : s->stats.largest_batch;
+    if (members.size() > s->stats.largest_batch) s->stats.largest_batch = members.size();
     s->inflight.push_back(b);
-    s->forming = Batch();
     return RS_OK;
 }
 
@@ -347,9 +422,13 @@ rs_status rs_server_create(const rs_stage_desc *stages, uint32_t n_stages, const
     // ... and a request has one leaf's results: linear pipelines only
     for (uint32_t i = 1; i < n_stages; ++i)
         if (stages[i].input && stages[i].input != i - 1) return RS_ERR_INVALID;
-    // validate the stage list and options once, through the pipeline's own checks
+    // validate the stage list and options once, through the pipeline's own checks; a
+    // request's units and state are sized for one strategy, so AUTO becomes TAG
+    rs_pipeline_opts o;
+    if (opts) o = *opts; else rs_default_opts(&o);
+    if (o.strategy == RS_STRATEGY_AUTO) o.strategy = RS_STRATEGY_TAG;
     rs_pipeline *probe = nullptr;
-    rs_status st = rs_pipeline_create(stages, n_stages, opts, &probe);
+    rs_status st = rs_pipeline_create(stages, n_stages, &o, &probe);
     if (st != RS_OK) return st;
     rs_server *s = new (std::nothrow) rs_server();
     if (!s) {
@@ -359,14 +438,22 @@ rs_status rs_server_create(const rs_stage_desc *stages, uint32_t n_stages, const
     memcpy(s->st, stages, n_stages * sizeof(rs_stage_desc));
     s->n_stages = n_stages;
     rs_pipeline_get_opts(probe, &s->opts);
-    s->pool.push_back(probe);
+    s->probe = probe;
     s->arena = (unsigned char *)arena;
     s->cap = arena_bytes & ~(uint64_t)255;
+    s->fl.reset(s->cap);
     s->max_batch = max_batch ? max_batch : 4096;
     s->max_inflight = max_inflight ? max_inflight : 2;
     s->stream = (cudaStream_t)stream;
     memset(&s->stats, 0, sizeof s->stats);
     *out = s;
+    return RS_OK;
+}
+
+rs_status rs_server_set_slice_units(rs_server *s, uint32_t units)
+{
+    if (!s) return RS_ERR_INVALID;
+    s->slice_units = units;
     return RS_OK;
 }
 
@@ -378,15 +465,28 @@ rs_status rs_server_submit(rs_server *s, const rs_request *r, uint64_t *req_id)
     Req q;
     q.id = s->next_id++;
     q.r = *r;
-    q.off = 0;
-    q.bytes = a256(request_bytes(s, *r));
+    // the resident state this request's sliced runs need, sized like its device stream
+    rs_stream_desc d;
+    memset(&d, 0, sizeof d);
+    d.n_regions = r->n_regions;
+    d.region_len = r->region_len;
+    d.n_elements = r->elements ? r->n_elements : 0;
+    d.total_elements_hint = r->total_elements_hint;
+    rs_status st = rs_stream_state_size(s->probe, &d, &q.state_bytes, &q.units);
+    if (st != RS_OK) return st;
+    q.bytes = a256(request_io_bytes(*r)) + a256(q.state_bytes);
     if (q.bytes > s->cap / 2) return RS_ERR_CAPACITY;   // could never be admitted beside a workspace
     try {
-        s->queued.push_back(q);
+        if (q.units == 0) s->completed.push_back(q.id);   // nothing to run: done at once
+        else s->queued.push_back(q);
     } catch (...) {
         return RS_ERR_NOMEM;
     }
     s->stats.submitted++;
+    if (q.units == 0) {
+        s->stats.admitted++;
+        s->stats.completed++;
+    }
     if (req_id) *req_id = q.id;
     return RS_OK;
 }
@@ -394,65 +494,64 @@ rs_status rs_server_submit(rs_server *s, const rs_request *r, uint64_t *req_id)
 rs_status rs_server_progress(rs_server *s)
 {
     if (!s) return RS_ERR_INVALID;
-    // 1. retire finished batches (in order)
+    // the copy streams, made on first use (creating the server makes no CUDA call)
+    if (!s->cin && cudaStreamCreateWithFlags(&s->cin, cudaStreamNonBlocking) != cudaSuccess) return RS_ERR_CUDA;
+    if (!s->cout && cudaStreamCreateWithFlags(&s->cout, cudaStreamNonBlocking) != cudaSuccess) return RS_ERR_CUDA;
+    // 1. retire slices whose finished requests' results have landed (in launch order)
     while (!s->inflight.empty()) {
-        Batch &b = s->inflight.front();
-        cudaError_t e = cudaEventQuery(b.ev);
+        Slice &b = s->inflight.front();
+        cudaError_t e = cudaEventQuery(b.done);
         if (e == cudaErrorNotReady) break;
         if (e != cudaSuccess) return RS_ERR_CUDA;
-        // gathered results: from the staging buffer into the requests' output buffers
         for (const Scatter &c : b.scat) memcpy(c.dst, b.stage.p + c.off, c.bytes);
         if (b.stage.p) s->free_stages.push_back(b.stage);
-        b.stage = Stage();
-        b.scat.clear();
-        for (uint64_t id : b.ids) s->completed.push_back(id);
-        s->stats.completed += b.ids.size();
-        // release the batch's ring space: everything up to its last allocation
-        s->tail = b.head_after;
-        s->live -= b.live_bytes;
-        if (s->live == 0) s->head = s->tail = 0;
-        s->free_events.push_back(b.ev);   // reused by a later batch (no driver call per batch)
-        b.ev = nullptr;
+        for (const Req &q : b.finishing) {
+            s->completed.push_back(q.id);
+            s->fl.release(q.off, q.bytes);
+        }
+        s->stats.completed += b.finishing.size();
+        if (b.res_bytes) s->fl.release(b.res_off, b.res_bytes);
+        s->fl.release(b.ws_off, b.ws_bytes);
+        s->free_events.push_back(b.done);
         s->pool.push_back(b.p);
         s->inflight.pop_front();
     }
-    // 2. admit queued requests while the arena has room
-    while (!s->queued.empty() && s->forming.ids.size() < s->max_batch) {
+    // 2. admit queued requests while the arena has room for them; their inputs go up on
+    //    the copy-in stream, and one event per round marks the copies done
+    bool admitted = false;
+    while (!s->queued.empty() && s->active.size() < s->max_batch) {
         Req &q = s->queued.front();
-        // admission by free device memory: the request and the batch's grown workspace
-        // must both fit (the workspace is taken from the ring when the batch launches)
-        const uint64_t ws_next = s->forming.ws_bound + stream_ws_bound(s, q.r) + 512;
-        const uint64_t h0 = s->head, t0 = s->tail, l0 = s->live, p0 = s->peak;
-        uint64_t off = 0, charged = 0, woff = 0, wch = 0;
-        if (!ring_alloc(s, q.bytes, &off, &charged)) break;
-        const uint64_t h1 = s->head, t1 = s->tail, l1 = s->live, p1 = s->peak;
-        const bool ws_fits = ring_alloc(s, a256(ws_next), &woff, &wch);
-        if (!ws_fits) {
-            s->head = h0; s->tail = t0; s->live = l0; s->peak = p0;   // undo the request's allocation
-            break;
-        }
-        s->head = h1; s->tail = t1; s->live = l1; s->peak = p1;       // keep only the request's
+        uint64_t off = 0;
+        if (!s->fl.alloc(q.bytes, &off)) break;
         q.off = off;
-        s->forming.live_bytes += charged;
-        s->forming.ws_bound = ws_next - 512;
-        rs_status st = admit(s, q);
+        q.round = s->round + 1;
+        layout_request(s, q);
+        rs_status st = copy_in(s, q);
         if (st != RS_OK) return st;
-        s->forming_members.push_back(q);
+        s->active.push_back(q);
         s->queued.pop_front();
+        s->stats.admitted++;
+        admitted = true;
     }
-    // 3. launch the forming batch if a slot is free
-    if (!s->forming.ids.empty() && s->inflight.size() < s->max_inflight) {
-        rs_status st = launch(s, s->forming_members);
-        if (st == RS_OK) {
-            s->forming_members.clear();
-        } else if (st != RS_ERR_NOT_READY) {
-            return st;
-        }
+    if (admitted) {
+        cudaEvent_t ev;
+        if (take_event(s, &ev) != RS_OK) return RS_ERR_CUDA;
+        if (cudaEventRecord(ev, s->cin) != cudaSuccess) return RS_ERR_CUDA;
+        s->rounds.push_back({++s->round, ev});
+    }
+    // 3. launch slices while fewer than max_inflight are queued
+    while (s->inflight.size() < s->max_inflight) {
+        bool work = false;
+        for (const Req &q : s->active) work = work || q.next < q.units;
+        if (!work) break;
+        rs_status st = launch_slice(s);
+        if (st == RS_ERR_NOT_READY) break;
+        if (st != RS_OK) return st;
     }
     s->stats.in_flight = s->inflight.size();
     s->stats.queued = s->queued.size();
-    s->stats.arena_live = s->live;
-    s->stats.arena_peak = s->peak;
+    s->stats.arena_live = s->fl.live;
+    s->stats.arena_peak = s->fl.peak;
     return RS_OK;
 }
 
@@ -480,17 +579,20 @@ rs_status rs_server_destroy(rs_server *s)
 {
     if (!s) return RS_ERR_INVALID;
     cudaStreamSynchronize(s->stream);
+    if (s->cin) cudaStreamSynchronize(s->cin);
+    if (s->cout) cudaStreamSynchronize(s->cout);
     for (auto &b : s->inflight) {
-        if (b.ev) cudaEventDestroy(b.ev);
+        if (b.done) cudaEventDestroy(b.done);
         if (b.p) rs_pipeline_destroy(b.p);
-    }
-    if (s->forming.p) rs_pipeline_destroy(s->forming.p);
-    if (s->forming.ev) cudaEventDestroy(s->forming.ev);
-    for (auto *p : s->pool) rs_pipeline_destroy(p);
-    for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
-    for (auto &b : s->inflight)
         if (b.stage.p) cudaFreeHost(b.stage.p);
+    }
+    for (auto *p : s->pool) rs_pipeline_destroy(p);
+    if (s->probe) rs_pipeline_destroy(s->probe);
+    for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
+    for (auto &r : s->rounds) cudaEventDestroy(r.second);
     for (Stage &g : s->free_stages) cudaFreeHost(g.p);
+    if (s->cin) cudaStreamDestroy(s->cin);
+    if (s->cout) cudaStreamDestroy(s->cout);
     delete s;
     return RS_OK;
 }

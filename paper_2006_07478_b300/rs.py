@@ -54,7 +54,7 @@ EXPORTS = [
     "rs_stream_state_size", "rs_stream_submit_slice",
     "rs_fetch_region_results", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
     "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_run_noalloc",
-    "rs_server_create", "rs_server_submit", "rs_server_progress", "rs_server_poll", "rs_server_get_stats",
+    "rs_server_create", "rs_server_set_slice_units", "rs_server_submit", "rs_server_progress", "rs_server_poll", "rs_server_get_stats",
     "rs_server_destroy", "rs_status_string", "rs_last_cuda_error", "rs_version", "rs_struct_sizes",
 ]
 # the ctypes mirrors, in the order rs_struct_sizes reports the C structs' sizes
@@ -133,7 +133,8 @@ class Request(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "completed", "batches", "largest_batch",
-                                               "in_flight", "queued", "arena_live", "arena_peak", "gathered")]
+                                               "in_flight", "queued", "arena_live", "arena_peak", "gathered",
+                                               "per_array")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -188,6 +189,7 @@ def lib(build_if_missing: bool = True):
             "rs_run_noalloc": ([P, P], ctypes.c_int),
             "rs_server_create": ([ctypes.POINTER(StageDesc), U32, ctypes.POINTER(Opts), P, U64, U32, U32, P,
                                   ctypes.POINTER(P)], ctypes.c_int),
+            "rs_server_set_slice_units": ([P, U32], ctypes.c_int),
             "rs_server_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(U64)], ctypes.c_int),
             "rs_server_progress": ([P], ctypes.c_int),
             "rs_server_poll": ([P, ctypes.POINTER(U64), U32, ctypes.POINTER(U32)], ctypes.c_int),
@@ -509,7 +511,8 @@ class Server:
     Requests are host streams: dicts of pinned int32/int64 CPU tensors (see
     `host_request`); their outputs are filled in place when poll() reports the id."""
 
-    def __init__(self, stages, arena_bytes, strategy="tag", max_batch=0, max_inflight=0, stream=None, **opts):
+    def __init__(self, stages, arena_bytes, strategy="tag", max_batch=0, max_inflight=0, stream=None,
+                 slice_units=None, **opts):
         import torch
         self.stages = list(stages)
         arr = (StageDesc * len(self.stages))(*[stage_desc(s) for s in self.stages])
@@ -524,6 +527,8 @@ class Server:
                                      int(max_batch), int(max_inflight), ctypes.c_void_p(self.stream.cuda_stream),
                                      ctypes.byref(h)), "rs_server_create")
         self._h = h
+        if slice_units is not None:
+            check(lib().rs_server_set_slice_units(h, int(slice_units)), "rs_server_set_slice_units")
         self._live = {}
         self._ids = (ctypes.c_uint64 * 4096)()
 
