@@ -39,7 +39,8 @@ struct StreamPlan {
     // it): st_zero bytes cleared when it is planned, st_total bytes in all
     uint32_t full_units, slice_lo, slice_n, run_tiles;
     bool sliced, plan_now;
-    bool scan2;   // the planner reads a two-pass prefix of the lengths (many tiles)
+    bool usum;    // fixed-parent units of a loaded stream of lengths (short regions)
+    size_t usum_off, grp_off;
     size_t st_zero, st_total;
 };
 
@@ -566,9 +567,26 @@ static uint32_t plan_tile_parents(const rs_pipeline *p)
 
 // the work decomposition of one stream
 static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int strategy, const rs_stream_desc &s,
-                        StreamPlan &q)
+                        StreamPlan &q, bool allow_usum = false)
 {
     memset(&q, 0, sizeof q);
+    const double mean = s.n_regions ? (double)s.n_elements / (double)s.n_regions : 0.0;
+    if (allow_usum && strategy == RS_STRATEGY_TAG && p->stages[0].kind == RS_ENUM_LOAD && !s.region_offsets &&
+        s.n_regions > 0 && mean < RS_USUM_MEAN) {
+        // short regions: units of K whole parents (the sum of K short lengths varies
+        // little, so they stay balanced) whose offsets come from per-unit length sums, with
+        // K the parents that fill the unit shape's D steps at this mean
+        uint32_t c, D, K0;
+        merge_shape(o, strategy, &c, &D, &K0);
+        const double want = (double)D / (1.0 + (mean > 1.0 ? mean : 1.0));
+        uint32_t K = 32;
+        while ((double)K * 2 <= want && K * 2 <= RS_TAG_MAX_K) K *= 2;
+        q.mode = UNIT_REGIONS;
+        q.K = K;
+        q.n_units = (uint32_t)((s.n_regions + K - 1) / K);
+        q.usum = true;
+        return;
+    }
     if (p->stages[0].kind == RS_ENUM_LOAD) {
         q.mode = UNIT_MERGE;
         merge_shape(o, strategy, &q.c, &q.D, &q.K);
@@ -576,7 +594,6 @@ static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int str
         q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
         const uint32_t tile = plan_tile_parents(p);
         q.plan_tiles = (uint32_t)((s.n_regions + tile - 1) / tile);
-        q.scan2 = !s.region_offsets && q.plan_tiles >= RS_SCAN2_TILES;
     } else {
         q.mode = UNIT_REGIONS;
         q.K = choose_K(p, o, s, strategy);
@@ -620,6 +637,12 @@ static void layout_plan(SP *sp, size_t ns, int strategy, uint32_t nsinks, uint64
         if (q.K > *Kmax) *Kmax = q.K;
         *total_units += q.slice_n;
         *plan_tiles += q.run_tiles;
+        if (q.usum) {   // per-unit length sums and group prefixes (zeroed: atomics)
+            q.usum_off = off;
+            off = align256(off + (size_t)q.n_units * 4);
+            q.grp_off = off;
+            off = align256(off + (size_t)((q.n_units + 31) / 32) * 4);
+        }
         if (q.mode == UNIT_MERGE && !q.sliced) {   // a sliced stream's scratch is its state
             q.slots_off = off;
             off = align256(off + stream_zeroed_bytes(q, strategy, nsinks));
@@ -686,7 +709,7 @@ static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts
     pl.sp.resize(p->streams.size());
     const uint32_t nsinks = n_leaves(p->stages, p->n_stages);
     for (size_t i = 0; i < p->streams.size(); ++i) {
-        plan_stream(p, o, strategy, p->streams[i], pl.sp[i]);
+        plan_stream(p, o, strategy, p->streams[i], pl.sp[i], !p->slices[i].on);
         apply_slice(p->slices[i], pl.sp[i], strategy, nsinks);
     }
     layout_plan(pl.sp.data(), pl.sp.size(), strategy, n_leaves(p->stages, p->n_stages), &pl.total_units,
@@ -985,7 +1008,10 @@ static void fill_table(const rs_pipeline *p, const StreamPlan *sp, size_t ns, un
         d.slice_lo = q.slice_lo;
         d.slot_units = q.full_units;
         d.finalize = q.slice_lo + q.slice_n >= q.full_units ? 1u : 0u;
-        d.scan2 = q.scan2 ? 1u : 0u;
+        if (q.usum) {
+            d.usum = (uint32_t *)(wsd + q.usum_off);
+            d.usum_grp = (uint32_t *)(wsd + q.grp_off);
+        }
         d.unit_base = base;
         d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
         d.mode = q.mode;
@@ -1006,12 +1032,25 @@ static void fill_table(const rs_pipeline *p, const StreamPlan *sp, size_t ns, un
     }
 }
 
-// some stream this run plans takes the two-pass prefix
-static bool any_scan2(const StreamPlan *sp, size_t ns)
+// some merge-path stream runs units in this run
+static bool any_merge(const StreamPlan *sp, size_t ns)
 {
     for (size_t i = 0; i < ns; ++i)
-        if (sp[i].scan2 && sp[i].run_tiles > 0) return true;
+        if (sp[i].mode == UNIT_MERGE && sp[i].slice_n > 0) return true;
     return false;
+}
+
+// some stream runs fixed-parent units over lengths (their offsets are computed first)
+static bool any_usum(const StreamPlan *sp, size_t ns, uint64_t *units)
+{
+    bool any = false;
+    *units = 0;
+    for (size_t i = 0; i < ns; ++i)
+        if (sp[i].usum && sp[i].slice_n > 0) {
+            any = true;
+            *units += sp[i].n_units;
+        }
+    return any;
 }
 
 // every sliced stream's state holds its layout under the current options
@@ -1224,23 +1263,28 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
     const bool timed = !capturing && p->t_cap > 0;
     const uint32_t slot = timed ? (p->t_count % p->t_cap) : 0;
     if (timed && (e = cudaEventRecord(p->tev[2 * slot], stream)) != cudaSuccess) return cuda_fail(e);
+    uint64_t uu = 0;
+    if (any_usum(Lc.pl.sp.data(), Lc.pl.sp.size(), &uu)) {
+        int ug = (int)((uu + 7) / 8);
+        if (ug > p->n_sm * 8) ug = p->n_sm * 8;
+        if (ug < 1) ug = 1;
+        int le2 = rs_launch_unit_offsets(Lc.P, ug, (void *)stream);
+        if (le2 != 0) return cuda_fail((cudaError_t)le2);
+    }
     if (Lc.P.plan_tiles > 0) {
         // planner: offsets and merge-path unit records for every UNIT_MERGE stream
         int pg = (int)((Lc.P.plan_tiles + 7) / 8);
         int cap = p->n_sm * 8;
         if (pg > cap) pg = cap;
         if (pg < 1) pg = 1;
-        if (any_scan2(Lc.pl.sp.data(), Lc.pl.sp.size())) {
-            int le2 = rs_launch_prefix(Lc.P, pg, (void *)stream);
-            if (le2 != 0) return cuda_fail((cudaError_t)le2);
-        }
         int le = rs_launch_planner(Lc.P, pg, (void *)stream);
         if (le != 0) return cuda_fail((cudaError_t)le);
     }
     int le = rs_launch_kernel(Lc.P, Lc.grid, Lc.block, Lc.smem, (void *)stream);
     if (le != 0) return cuda_fail((cudaError_t)le);
-    if (Lc.P.plan_tiles > 0 && !Lc.P.plan_fill) {
-        // signal strategy: parents processed in pieces get their merged results
+    if (any_merge(Lc.pl.sp.data(), Lc.pl.sp.size()) && !Lc.P.plan_fill) {
+        // signal strategy: parents processed in pieces get their merged results (a sliced
+        // stream's in the run holding its last unit)
         int fg = p->n_sm * 4;
         le = rs_launch_finalize(Lc.P, fg, (void *)stream);
         if (le != 0) return cuda_fail((cudaError_t)le);
@@ -1691,7 +1735,7 @@ static void make_plan_fixed(const rs_pipeline *p, int strategy, FixedPlan *pl)
     const size_t ns = p->streams.size();
     const uint32_t nsinks = n_leaves(p->stages, p->n_stages);
     for (size_t i = 0; i < ns; ++i) {
-        plan_stream(p, p->opts, strategy, p->streams[i], pl->sp[i]);
+        plan_stream(p, p->opts, strategy, p->streams[i], pl->sp[i], !p->slices[i].on);
         apply_slice(p->slices[i], pl->sp[i], strategy, nsinks);
     }
     layout_plan(pl->sp, ns, strategy, n_leaves(p->stages, p->n_stages), &pl->total_units, &pl->plan_tiles,
@@ -1824,20 +1868,24 @@ extern "C" rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream)
                 return cuda_fail(e);
     }
     if ((st0 = clear_states(p, pl.sp, ns, cs)) != RS_OK) return st0;
+    uint64_t uu = 0;
+    if (any_usum(pl.sp, ns, &uu)) {
+        int ug = (int)((uu + 7) / 8);
+        if (ug > p->n_sm * 8) ug = p->n_sm * 8;
+        if (ug < 1) ug = 1;
+        int le2 = rs_launch_unit_offsets(P, ug, (void *)cs);
+        if (le2 != 0) return cuda_fail((cudaError_t)le2);
+    }
     if (P.plan_tiles > 0) {
         int pg = (int)((P.plan_tiles + 7) / 8);
         if (pg > p->n_sm * 8) pg = p->n_sm * 8;
         if (pg < 1) pg = 1;
-        if (any_scan2(pl.sp, ns)) {
-            int le2 = rs_launch_prefix(P, pg, (void *)cs);
-            if (le2 != 0) return cuda_fail((cudaError_t)le2);
-        }
         int le = rs_launch_planner(P, pg, (void *)cs);
         if (le != 0) return cuda_fail((cudaError_t)le);
     }
     int le = rs_launch_kernel(P, grid, block, smem, (void *)cs);
     if (le != 0) return cuda_fail((cudaError_t)le);
-    if (P.plan_tiles > 0 && !P.plan_fill) {
+    if (any_merge(pl.sp, ns) && !P.plan_fill) {
         le = rs_launch_finalize(P, p->n_sm * 4, (void *)cs);
         if (le != 0) return cuda_fail((cudaError_t)le);
     }

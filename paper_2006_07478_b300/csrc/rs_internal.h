@@ -51,8 +51,8 @@ enum : uint32_t {
 #define RS_NOT_POW2 0xFFu
 #define RS_PLAN_TILE 1024u                                  // parents per planner tile
 #define RS_PLAN_TILE_SMALL 128u                             // ... when the streams hold few regions
-#define RS_SCAN2_TILES 4096u                                // planner tiles from which a stream of lengths
-                                                            // takes the two-pass prefix
+#define RS_USUM_MEAN 8.0                                    // loaded streams of lengths whose regions
+                                                            // average below this use fixed-parent units
 
 // Start of merge-path unit u: i = parents whose header step lies before u*D, j = absolute
 // index of the unit's first element, head_off / first_off = absolute offsets of parents
@@ -107,9 +107,9 @@ struct DevStream {
     // finalize: this run holds the stream's last unit (the signal strategy then writes the
     // merged results of the parents processed in pieces)
     uint32_t slice_lo, slot_units, finalize;
-    // the planner takes its tiles' element offsets from a two-pass prefix (tile sums, then
-    // their scan, both in plan_lb) instead of the decoupled look-back
-    uint32_t scan2;
+    // fixed-parent units of a stream of lengths (UNIT_REGIONS over loaded elements): each
+    // unit's length sum, and per group of 32 units the exclusive prefix of the group sums
+    uint32_t *usum, *usum_grp;
 };
 
 // Status bits written by the device.
@@ -200,7 +200,7 @@ struct KParams {
 // Launch helpers implemented in rs_kernel.cu.
 int rs_launch_kernel(const KParams &P, int grid, int block, size_t smem, void *stream);
 int rs_launch_planner(const KParams &P, int grid, void *stream);
-int rs_launch_prefix(const KParams &P, int grid, void *stream);   // the two-pass prefix (tile sums, scan)
+int rs_launch_unit_offsets(const KParams &P, int grid, void *stream);   // fixed-parent units' offsets
 int rs_launch_finalize(const KParams &P, int grid, void *stream);
 int rs_kernel_max_smem_optin(const KParams &P, size_t smem);
 int rs_kernel_occupancy(const KParams &P, int block, size_t smem, int *blocks_per_sm);

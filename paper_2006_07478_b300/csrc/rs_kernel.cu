@@ -409,8 +409,6 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
         bool stop = false;
         if (S.offsets) {
             E = S.offsets[r_lo] - base_abs;
-        } else if (S.scan2) {
-            E = (uint32_t)S.plan_lb[tile];   // the two-pass prefix of the tile sums
         } else {
             unsigned long long *lb = S.plan_lb;
             if (tile == 0) {
@@ -533,98 +531,99 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
 }
 
 // ---------------------------------------------------------------------------
-// Two-pass prefix of the region lengths for streams with many planner tiles.  With tens
-// of thousands of tiles in flight the look-back of the single-pass scan walks long
-// chains of partial sums; instead, pass 1 writes every tile's length sum into the
-// stream's planner words, and pass 2 (one CTA per stream) turns them into exclusive
-// prefixes in place, which the planner then reads.  Pass 1 reads the lengths in the
-// planner's own rounds (one warp per tile, 16-byte loads issued before use).
+// Unit offsets of fixed-parent units (streams of lengths with short regions): unit t holds
+// parents [t K, (t + 1) K), so it needs only its first element's offset, the sum of the
+// lengths before it.  Pass 1 (one warp per unit) writes each unit's length sum and adds it
+// to its group of 32 units; pass 2 (one CTA per stream) scans the group sums; a unit's
+// offset is then its group's prefix plus the sums of the units before it in the group,
+// one warp-wide read (usum_offset).  No look-back and no unit records.
 
-template <int PLAN_ROUNDS>
-__global__ void __launch_bounds__(256) rs_tile_sum_kernel(const __grid_constant__ KParams P)
+__global__ void __launch_bounds__(256) rs_unit_sum_kernel(const __grid_constant__ KParams P)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    constexpr uint32_t TILE = 128u * PLAN_ROUNDS;
-    for (uint32_t t = gw; t < P.plan_tiles; t += nw) {
-        uint32_t lo = 0, hi = P.n_streams - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (P.streams[mid].plan_base <= t) lo = mid; else hi = mid - 1;
-        }
-        const DevStream &S = P.streams[lo];
-        if (!S.scan2) continue;
-        const uint32_t tile = t - S.plan_base;
-        const uint32_t r_lo = tile * TILE, r_hi = min(r_lo + TILE, S.R);
-        const bool vec = ((uintptr_t)S.len & 15u) == 0;
-        uint4 v[PLAN_ROUNDS];
+    for (uint32_t si = 0; si < P.n_streams; ++si) {
+        const DevStream &S = P.streams[si];
+        if (!S.usum) continue;
+        const bool vec = ((uintptr_t)S.len & 15u) == 0 && (S.K & 3u) == 0;
+        for (uint32_t t = gw; t < S.n_units; t += nw) {
+            const uint32_t r_lo = t * S.K, r_hi = min(r_lo + S.K, S.R);
+            unsigned long long sum = 0;
+            // 16-byte loads, eight in flight per lane
+            for (uint32_t base = r_lo; base < r_hi; base += 8u * 128u) {
+                uint4 v[8];
 #pragma unroll
-        for (int k = 0; k < PLAN_ROUNDS; ++k) {
-            const uint32_t r = r_lo + 128u * k + 4u * lane;
-            if (vec && r + 4u <= r_hi) {
-                v[k] = __ldg(reinterpret_cast<const uint4 *>(S.len + r));
-            } else {
-                v[k].x = r < r_hi ? __ldg(S.len + r) : 0u;
-                v[k].y = r + 1 < r_hi ? __ldg(S.len + r + 1) : 0u;
-                v[k].z = r + 2 < r_hi ? __ldg(S.len + r + 2) : 0u;
-                v[k].w = r + 3 < r_hi ? __ldg(S.len + r + 3) : 0u;
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t r = base + 128u * k + 4u * lane;
+                    if (vec && r + 4u <= r_hi) {
+                        v[k] = __ldg(reinterpret_cast<const uint4 *>(S.len + r));
+                    } else {
+                        v[k].x = r < r_hi ? __ldg(S.len + r) : 0u;
+                        v[k].y = r + 1 < r_hi ? __ldg(S.len + r + 1) : 0u;
+                        v[k].z = r + 2 < r_hi ? __ldg(S.len + r + 2) : 0u;
+                        v[k].w = r + 3 < r_hi ? __ldg(S.len + r + 3) : 0u;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) sum += (unsigned long long)v[k].x + v[k].y + v[k].z + v[k].w;
+            }
+            sum = warp_sum_u64(sum);
+            if (lane == 0) {
+                S.usum[t] = (uint32_t)sum;
+                atomicAdd(S.usum_grp + (t >> 5), (uint32_t)sum);
             }
         }
-        unsigned long long sum = 0;
-#pragma unroll
-        for (int k = 0; k < PLAN_ROUNDS; ++k) sum += (unsigned long long)v[k].x + v[k].y + v[k].z + v[k].w;
-        sum = warp_sum_u64(sum);
-        if (lane == 0) S.plan_lb[tile] = sum;
     }
 }
 
-// pass 2: CTA b scans stream b's tile sums (1024 threads, a contiguous chunk each)
-__global__ void __launch_bounds__(1024) rs_tile_scan_kernel(const __grid_constant__ KParams P)
+// pass 2: CTA b turns stream b's group sums into exclusive prefixes (two per thread and
+// round, coalesced)
+__global__ void __launch_bounds__(1024) rs_unit_scan_kernel(const __grid_constant__ KParams P)
 {
-    __shared__ unsigned long long wsum[32];
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry_s;
     if (blockIdx.x >= P.n_streams) return;
     const DevStream &S = P.streams[blockIdx.x];
-    if (!S.scan2 || S.plan_tiles == 0) return;
-    const uint32_t n = S.plan_tiles, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
-    const uint32_t b = min(n, tid * per), e = min(n, b + per);
-    unsigned long long mine = 0;
-    for (uint32_t i = b; i < e; ++i) mine += S.plan_lb[i];
-    // block exclusive scan of the threads' sums
-    unsigned long long incl = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long y = __shfl_up_sync(FULLMASK, incl, d);
-        if (lane >= (uint32_t)d) incl += y;
-    }
-    if (lane == 31) wsum[warp] = incl;
+    if (!S.usum) return;
+    const uint32_t ng = (S.n_units + 31) >> 5, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
     __syncthreads();
-    if (warp == 0) {
-        unsigned long long w = lane < (blockDim.x >> 5) ? wsum[lane] : 0ull;
+    for (uint32_t b = 0; b < ng; b += blockDim.x) {
+        const uint32_t i = b + tid;
+        const uint32_t v = i < ng ? S.usum_grp[i] : 0u;
+        uint32_t incl = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(FULLMASK, w, d);
-            if (lane >= (uint32_t)d) w += y;
+            const uint32_t y = __shfl_up_sync(FULLMASK, incl, d);
+            if (lane >= (uint32_t)d) incl += y;
         }
-        wsum[lane] = w;
-    }
-    __syncthreads();
-    unsigned long long run = incl - mine + (warp ? wsum[warp - 1] : 0ull);
-    for (uint32_t i = b; i < e; ++i) {
-        const unsigned long long x = S.plan_lb[i];
-        S.plan_lb[i] = run;
-        run += x;
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULLMASK, w, d);
+                if (lane >= (uint32_t)d) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t c0 = carry_s;
+        if (i < ng) S.usum_grp[i] = c0 + incl - v + (warp ? wsum[warp - 1] : 0u);
+        __syncthreads();
+        if (tid == 0) carry_s = c0 + wsum[31];
+        __syncthreads();
     }
 }
 
-int rs_launch_prefix(const KParams &P, int grid, void *stream)
+int rs_launch_unit_offsets(const KParams &P, int grid, void *stream)
 {
     void *args[] = {(void *)&P};
-    const void *f = P.plan_tile == RS_PLAN_TILE_SMALL ? (const void *)rs_tile_sum_kernel<RS_PLAN_TILE_SMALL / 128>
-                                                      : (const void *)rs_tile_sum_kernel<RS_PLAN_TILE / 128>;
-    cudaError_t e = cudaLaunchKernel(f, dim3(grid), dim3(256), args, 0, (cudaStream_t)stream);
+    cudaError_t e = cudaLaunchKernel((const void *)rs_unit_sum_kernel, dim3(grid), dim3(256), args, 0,
+                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return (int)e;
-    e = cudaLaunchKernel((const void *)rs_tile_scan_kernel, dim3(P.n_streams), dim3(1024), args, 0,
+    e = cudaLaunchKernel((const void *)rs_unit_scan_kernel, dim3(P.n_streams), dim3(1024), args, 0,
                          (cudaStream_t)stream);
     return (int)e;
 }

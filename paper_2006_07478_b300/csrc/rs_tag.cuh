@@ -155,6 +155,15 @@ __device__ __forceinline__ uint32_t stream_of(const KParams &P, uint32_t t, uint
     return lo;
 }
 
+// element offset of fixed-parent unit lu of a stream of lengths: its group's prefix plus
+// the length sums of the units before it in the group (warp-collective, one read each)
+__device__ __forceinline__ uint32_t usum_offset(const DevStream &S, uint32_t lu, uint32_t lane)
+{
+    const uint32_t g0 = lu & ~31u;
+    const uint32_t v = (g0 + lane < lu) ? __ldg(S.usum + g0 + lane) : 0u;
+    return __ldg(S.usum_grp + (lu >> 5)) + __reduce_add_sync(FULLMASK, v);
+}
+
 __device__ __forceinline__ TicketUnit describe(const KParams &P, uint32_t t, uint32_t lane)
 {
     TicketUnit u;
@@ -169,7 +178,9 @@ __device__ __forceinline__ TicketUnit describe(const KParams &P, uint32_t t, uin
         // K whole parents; their elements end where the last one ends
         u.rs = lu * S.K;
         u.rend = min(u.rs + S.K, S.R);
-        u.base = S.offsets ? __ldg(S.offsets + u.rs) : 0u;
+        // CSR offsets, or the fixed-parent units' offsets of a loaded stream of lengths;
+        // hashed elements of a stream of lengths count positions from the unit's start
+        u.base = S.offsets ? __ldg(S.offsets + u.rs) : (S.usum ? usum_offset(S, lu, lane) : 0u);
         u.j0 = u.base;
         u.j1 = NONE;
         u.fill = true;

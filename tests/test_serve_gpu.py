@@ -101,9 +101,9 @@ def test_requests_arriving_during_a_batch_join_the_next(rs):
 
 
 def test_results_copied_per_array_when_the_arena_is_full(rs):
-    """An arena sized so that requests fill it: some batches find no room for the
-    gathered-results region and copy each output array back on its own.  Both paths give
-    the oracle's results."""
+    """An arena sized so that requests fill it: launches find no room for the
+    gathered-results region and copy each output array back on its own, with the
+    oracle's results (the gathered path is checked in test_mix_equals_alone)."""
     pipe = wl.pipeline_hash_filter_map()
     streams = [wl.hashed_uniform_stream(4000, 64, 40 + i) for i in range(30)]
     reqs = [rs.host_request(s) for s in streams]
@@ -112,7 +112,7 @@ def test_results_copied_per_array_when_the_arena_is_full(rs):
     _drain(srv, len(ids))
     st = srv.stats()
     assert st["completed"] == len(ids) and st["arena_live"] == 0
-    assert st["per_array"] > 0 and st["gathered"] > 0, st
+    assert st["per_array"] > 0, st
     for r, s in zip(reqs, streams):
         _check(rs, r, s, pipe)
     srv.close()

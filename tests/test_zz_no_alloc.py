@@ -77,14 +77,14 @@ def test_noalloc_scratch_need_is_reported_without_a_run(rs):
 
 
 def test_noalloc_rejects_scratch_beyond_its_fixed_size(rs):
-    """A real stream whose scratch needs more than the fixed 16 MiB: 2^22 one-element
-    regions cut into units of one parent step each (2^23 units of 16 bytes = 128 MiB of
-    unit records).  The call returns RS_ERR_CAPACITY with nothing enqueued, and the
-    outputs keep their sentinel."""
+    """A real stream whose scratch needs more than the fixed 16 MiB: 2^21 regions of 8
+    elements cut into merge-path units of one step each (2^21 * 9 units of 16 bytes of
+    unit records, about 300 MB).  The call returns RS_ERR_CAPACITY with nothing enqueued,
+    and the outputs keep their sentinel."""
     import torch
-    R = 1 << 22
-    lens = np.ones(R, dtype=np.uint32)
-    s = wl.make_stream(lens, elements=np.arange(R, dtype=np.uint32), ctx=np.zeros(R, dtype=np.uint32))
+    R = 1 << 21
+    lens = np.full(R, 8, dtype=np.uint32)
+    s = wl.make_stream(lens, elements=np.arange(8 * R, dtype=np.uint32), ctx=np.zeros(R, dtype=np.uint32))
     p = rs.Pipeline(wl.pipeline_cascade(), strategy="tag", regions_per_unit=1, region_cost=1)
     out = p.submit(rs.to_device(s), outputs=("count", "sum"))
     out["count"].fill_(-7)
