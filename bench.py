@@ -56,7 +56,7 @@ def alg_bytes(stream) -> int:
     """Algorithmic HBM bytes of one pass: every element read once (4 B), and per
     region its length and context word read and its count (4 B) and sum (8 B)
     written."""
-    return 4 * N_ELEM + 20 * int(stream["R"])
+    return 4 * wl.n_elements(stream) + 20 * int(stream["R"])
 
 
 def make_streams():
@@ -447,6 +447,23 @@ def bench_batched(rs, torch):
         side.synchronize()
         per_ms = e0.elapsed_time(e1)
         per_wall = (time.perf_counter() - t0) * 1e3
+        # the same one-launch-per-stream work with little host time between launches: each
+        # stream's run captured in a graph of its own, the 4096 graphs replayed back to back
+        for q in singles:
+            q.graph_capture()
+        for q in singles[:64]:
+            q.graph_launch()
+        side.synchronize()
+        t1 = time.perf_counter()
+        e0.record(side)
+        for q in singles:
+            q.graph_launch()
+        e1.record(side)
+        side.synchronize()
+        per_graph_ms = e0.elapsed_time(e1)
+        per_graph_wall = (time.perf_counter() - t1) * 1e3
+        for q in singles:
+            q.graph_release()
     # invariants of the results (exactness against the oracle is tested in tests/): no
     # region keeps more items than it has, and the counts over all streams add up to the
     # items the aggregate consumed in the last batched run
@@ -468,7 +485,9 @@ def bench_batched(rs, torch):
     return {"workload": "4096 hashed streams, sizes lognormal(median 2^14, sigma 1.5, cap 2^22), regions U{1..512}",
             "items": items, "batched_graph_ms": one_ms, "batched_items_per_s": items / (one_ms * 1e-3),
             "per_stream_launch_ms": per_ms, "per_stream_items_per_s": items / (per_ms * 1e-3),
-            "per_stream_host_wall_ms": per_wall, "speedup": per_ms / one_ms, "invariants_ok": bool(exact),
+            "per_stream_host_wall_ms": per_wall, "speedup": per_ms / one_ms,
+            "per_stream_graphs_ms": per_graph_ms, "per_stream_graphs_host_wall_ms": per_graph_wall,
+            "speedup_vs_per_stream_graphs": per_graph_ms / one_ms, "invariants_ok": bool(exact),
             "chosen": {"strategy": "signal" if best["strategy"] == 0 else "tag",
                        "regions_per_unit": best["regions_per_unit"], "ensemble_width": best["ensemble_width"]}}
 
@@ -641,6 +660,9 @@ def main():
     ap.add_argument("--serve-sweep", action="store_true",
                     help="also sweep arrival rates to find where p99 turns up (about 20 s more)")
     ap.add_argument("--no-extras", action="store_true", help="skip the graph, batched and serving sections")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split each stream's regions across the ranks (strong scaling) instead of "
+                         "running the same five streams on every rank (weak scaling)")
     ap.add_argument("--case", default=None,
                     help="MEAN:STRATEGY[:N_LOG2[:OPT=V,...]] -- one stream, fixed strategy and options "
                          "(a small fixed launch sequence for profilers)")
@@ -672,6 +694,10 @@ def main():
         return
 
     streams = make_streams()
+    if args.shard:
+        # this rank's region range of every stream, balanced on merge-path cost; no data
+        # crosses ranks (regions are independent), the step's items are summed over ranks
+        streams = [multi.shard_stream(s, world, rank) for s in streams]
     pipe = wl.pipeline_cascade()
 
     # ---- device-resident inputs, one pipeline per stream, tuned per stream ----
@@ -713,7 +739,7 @@ def main():
             st = p.stats()
             kms = statistics.median(ms)
             gbs = alg_bytes(s) / (kms * 1e-3) / 1e9
-            row[strat] = {"kernel_ms": kms, "items_per_s": N_ELEM / (kms * 1e-3), "alg_gbs": gbs,
+            row[strat] = {"kernel_ms": kms, "items_per_s": wl.n_elements(s) / (kms * 1e-3), "alg_gbs": gbs,
                           "options": "tuned" if strat == chosen else "tuned for this strategy alone",
                           "active_lane_fraction": [round(x, 4) for x in st["active_lane_fraction"]],
                           "launch": st["launch"]}
@@ -764,7 +790,7 @@ def main():
     assert all(s == 0 for s in statuses), statuses
     # every rank runs the same five streams (weak scaling): the step time is the slowest
     # rank's, the items are summed over ranks
-    items_step = N_ELEM * len(MEANS)
+    items_step = sum(wl.n_elements(s) for s in streams)
     elapsed_ms, items_all = multi.reduce_step(elapsed_ms, items_step * args.steps, device="cuda")
     value = items_all / (elapsed_ms * 1e-3)
 
@@ -820,8 +846,7 @@ def main():
                 if started[i]:
                     s_in.wait_event(ev_run[i])     # the previous run of this stream has read its inputs
                 with torch.cuda.stream(s_in):
-                    for k, t in hi.items():
-                        dev[k].copy_(t, non_blocking=True)
+                    p.upload(out["id"], hi)      # rs_stream_upload: host buffers -> the stream's arrays
                 ev_in[i].record(s_in)
                 s_run.wait_event(ev_in[i])
                 if started[i]:
@@ -841,7 +866,8 @@ def main():
         e2e_ms, e2e_items = multi.reduce_step(e2e_ms, items_step, device="cuda")
         e2e = {"value": e2e_items / (e2e_ms * 1e-3), "unit": "items/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-               "overlap": "copy-in, run and copy-out on three CUDA streams"}
+               "overlap": "copy-in, run and copy-out on three CUDA streams",
+               "path": "C ABI: rs_stream_upload -> rs_run -> rs_fetch_region_results, page-locked host buffers"}
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -870,11 +896,12 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "items/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+            "scaling": "strong" if args.shard else "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded)",
             "config": {"workload": "cascade: 5 streams x 2^26 u32 elements, geometric regions mean 1/4/32/256/4096, "
                                    "3 context hash filters (pass 0.5/0.3/0.1), count+sum per region",
                        "seed": SEED, "l2": "inputs larger than L2 (256 MiB per stream), streams alternate",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"region shards x{world}" if args.shard else f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                          "frac_of_8tbs_spec": achieved / SPEC_HBM_GBS,

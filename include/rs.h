@@ -255,6 +255,23 @@ rs_status rs_workspace_size(const rs_pipeline *p, uint64_t *bytes);
  * RS_ERR_NOT_READY if nothing is submitted, RS_ERR_CUDA on a launch failure. */
 rs_status rs_run(rs_pipeline *p, void *workspace, uint64_t workspace_bytes, rs_cuda_stream stream);
 
+/* Host copies of a submitted stream's inputs (any may be NULL: not copied). */
+typedef struct {
+    const uint32_t *parents;         /* R entries     */
+    const uint32_t *region_len;      /* R entries     */
+    const uint32_t *region_offsets;  /* R + 1 entries */
+    const uint32_t *elements;        /* n_elements    */
+    const uint32_t *ctx;             /* R entries     */
+} rs_host_inputs;
+
+/* Enqueue host-to-device copies of stream `stream_id`'s inputs from `src` into the device
+ * arrays it was submitted with (sizes from its description), on `stream`: with
+ * rs_run and rs_fetch_region_results, one pass from host buffers to host results through
+ * this ABI.  Page-locked sources make the copies asynchronous (the cudaMemcpyAsync rule:
+ * keep them unchanged until the copies have run).  RS_ERR_INVALID for an array the
+ * stream was submitted without. */
+rs_status rs_stream_upload(rs_pipeline *p, uint64_t stream_id, const rs_host_inputs *src, rs_cuda_stream stream);
+
 typedef struct {
     uint32_t *count;    /* destination (host or device), R entries, or NULL */
     uint64_t *sum;

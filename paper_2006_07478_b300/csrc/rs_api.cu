@@ -1341,6 +1341,31 @@ rs_status rs_fetch_region_results(rs_pipeline *p, uint64_t stream_id, const rs_r
     return RS_OK;
 }
 
+rs_status rs_stream_upload(rs_pipeline *p, uint64_t stream_id, const rs_host_inputs *src, rs_cuda_stream stream)
+{
+    if (!p || !src || stream_id >= p->streams.size()) return RS_ERR_INVALID;
+    const rs_stream_desc &s = p->streams[stream_id];
+    const uint64_t R = s.n_regions;
+    struct {
+        const uint32_t *from;
+        const uint32_t *to;
+        uint64_t n;
+    } c[5] = {{src->parents, s.parents, R},
+              {src->region_len, s.region_len, R},
+              {src->region_offsets, s.region_offsets, R ? R + 1 : 0},
+              {src->elements, s.elements, s.n_elements},
+              {src->ctx, s.ctx, R}};
+    for (auto &x : c) {
+        if (!x.from) continue;
+        if (!x.to) return RS_ERR_INVALID;
+        if (!x.n) continue;
+        const cudaError_t e = cudaMemcpyAsync(const_cast<uint32_t *>(x.to), x.from, x.n * 4, cudaMemcpyHostToDevice,
+                                              (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return RS_OK;
+}
+
 rs_status rs_get_stats(rs_pipeline *p, const void *workspace, rs_cuda_stream stream, rs_stats *out)
 {
     if (!p || !workspace || !out) return RS_ERR_INVALID;

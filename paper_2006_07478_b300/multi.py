@@ -44,6 +44,37 @@ def shard_regions(lengths: np.ndarray, world: int, rank: int, region_cost: int =
     return start(rank), start(rank + 1)
 
 
+def shard_stream(stream: dict, world: int, rank: int, region_cost: int = 1) -> dict:
+    """The part of a host stream (numpy arrays) that `rank` runs: its contiguous region
+    range from `shard_regions`, with the matching lengths or CSR offsets, context words,
+    parent ids (the global region ordinal when the stream has none, so hashed elements are
+    unchanged) and element slice.  Regions are independent, so the shards' per-region
+    results, concatenated in rank order, are the whole stream's."""
+    if stream.get("len") is not None:
+        L = np.asarray(stream["len"], dtype=np.int64)
+        off = np.concatenate([[0], np.cumsum(L)])
+    else:
+        o = np.asarray(stream["offsets"], dtype=np.int64)
+        off = o - o[0]
+        L = np.diff(o)
+    lo, hi = shard_regions(L, world, rank, region_cost)
+    out = {"R": hi - lo, "len": None, "offsets": None, "parents": None, "elements": None, "ctx": None,
+           "shard": (lo, hi)}
+    if stream.get("len") is not None:
+        out["len"] = np.ascontiguousarray(stream["len"][lo:hi])
+    else:
+        out["offsets"] = np.ascontiguousarray((off[lo:hi + 1] - off[lo]).astype(np.uint32))
+    if stream.get("parents") is not None:
+        out["parents"] = np.ascontiguousarray(stream["parents"][lo:hi])
+    else:
+        out["parents"] = np.arange(lo, hi, dtype=np.uint64).astype(np.uint32)
+    if stream.get("ctx") is not None:
+        out["ctx"] = np.ascontiguousarray(stream["ctx"][lo:hi])
+    if stream.get("elements") is not None:
+        out["elements"] = np.ascontiguousarray(stream["elements"][off[lo]:off[hi]])
+    return out
+
+
 def reduce_step(elapsed_ms: float, items: int, device=None) -> tuple:
     """(slowest rank's time, items over all ranks) by torch.distributed all-reduces;
     the identity when no process group is initialised."""

@@ -52,7 +52,7 @@ EXPORTS = [
     "rs_default_opts", "rs_pipeline_create", "rs_pipeline_destroy", "rs_pipeline_set_opts",
     "rs_pipeline_get_opts", "rs_stream_submit", "rs_clear_streams", "rs_workspace_size", "rs_run",
     "rs_stream_state_size", "rs_stream_submit_slice",
-    "rs_fetch_region_results", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
+    "rs_fetch_region_results", "rs_stream_upload", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
     "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_run_noalloc",
     "rs_server_create", "rs_server_set_slice_units", "rs_server_submit", "rs_server_progress", "rs_server_poll", "rs_server_get_stats",
     "rs_server_destroy", "rs_status_string", "rs_last_cuda_error", "rs_version", "rs_struct_sizes",
@@ -87,6 +87,11 @@ class StreamDesc(ctypes.Structure):
                 ("total_elements_hint", ctypes.c_uint64), ("out_values", ctypes.c_void_p),
                 ("out_values_len", ctypes.c_uint64), ("out2_count", ctypes.c_void_p),
                 ("out2_sum", ctypes.c_void_p), ("out2_min", ctypes.c_void_p)]
+
+
+class HostInputs(ctypes.Structure):
+    _fields_ = [("parents", ctypes.c_void_p), ("region_len", ctypes.c_void_p), ("region_offsets", ctypes.c_void_p),
+                ("elements", ctypes.c_void_p), ("ctx", ctypes.c_void_p)]
 
 
 class RegionResults(ctypes.Structure):
@@ -178,6 +183,7 @@ def lib(build_if_missing: bool = True):
             "rs_workspace_size": ([P, ctypes.POINTER(U64)], ctypes.c_int),
             "rs_run": ([P, P, U64, P], ctypes.c_int),
             "rs_fetch_region_results": ([P, U64, ctypes.POINTER(RegionResults), P], ctypes.c_int),
+            "rs_stream_upload": ([P, U64, ctypes.POINTER(HostInputs), P], ctypes.c_int),
             "rs_get_stats": ([P, P, P, ctypes.POINTER(Stats)], ctypes.c_int),
             "rs_graph_capture": ([P, P, U64, P], ctypes.c_int),
             "rs_graph_launch": ([P, P], ctypes.c_int),
@@ -474,6 +480,13 @@ class Pipeline:
         r = RegionResults(_ptr(count), _ptr(sum), _ptr(min))
         check(lib().rs_fetch_region_results(self._h, sid, ctypes.byref(r), _cur_stream()),
               "rs_fetch_region_results")
+
+    def upload(self, sid: int, host: dict):
+        """Copy a stream's inputs from host tensors (keys parents, len, offsets, elements,
+        ctx; page-locked for asynchronous copies) into its device arrays (rs_stream_upload)."""
+        src = HostInputs(_ptr(host.get("parents")), _ptr(host.get("len")), _ptr(host.get("offsets")),
+                         _ptr(host.get("elements")), _ptr(host.get("ctx")))
+        check(lib().rs_stream_upload(self._h, sid, ctypes.byref(src), _cur_stream()), "rs_stream_upload")
 
     def graph_capture(self):
         ws = self.workspace()

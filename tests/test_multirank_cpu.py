@@ -73,3 +73,18 @@ def test_region_shards_balance_merge_path_cost(world):
     cost = np.array([(hi - lo) + L[lo:hi].sum() for lo, hi in cuts])
     # balanced up to the one region a cut cannot split
     assert cost.max() - cost.min() <= 2 * (L.max() + 1)
+
+
+@pytest.mark.parametrize("world", [2, 3, 5])
+def test_stream_shards_concatenate_to_the_whole(world):
+    """Each rank's shard (regions, lengths or offsets, context, parent ids, elements) run by
+    the oracle; the results, concatenated in rank order, are the whole stream's."""
+    from oracle import oracle
+    cases = [(wl.pipeline_cascade(), wl.cascade_stream(n_total=1 << 16, mean=6, seed=3)),
+             (wl.pipeline_graph_edges(), wl.graph_stream(V=4000, E=40000, cap=3000, seed=7)),
+             (wl.pipeline_hash_filter_map(), wl.hashed_uniform_stream(3000, 64, 4))]
+    for pipe, s in cases:
+        whole = oracle.run(pipe, s)
+        parts = [oracle.run(pipe, multi.shard_stream(s, world, r)) for r in range(world)]
+        for k in ("count", "sum", "min"):
+            assert np.array_equal(np.concatenate([p[k] for p in parts]), whole[k]), k

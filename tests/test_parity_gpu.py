@@ -488,3 +488,20 @@ def test_emit_sink_sorted_multisets_per_region(rs, strategy, which):
     else:
         pipe, s = wl.pipeline_region_sum(), _csr(wl.sized_region_stream(1 << 17, 100, variable=True))
     _check_emit(rs, pipe, s, strategy)
+
+
+def test_region_shards_through_the_library_concatenate(rs):
+    """The multi-GPU split run one shard after another on one GPU: each rank's region
+    range of a bench-shaped stream through the library, the shards' results concatenated
+    in rank order equal the whole stream's run and the oracle's."""
+    from paper_2006_07478_b300 import multi
+    s = wl.cascade_stream(n_total=1 << 20, mean=6, seed=7)
+    pipe = wl.pipeline_cascade()
+    whole, _ = rs.run_stream(pipe, s, strategy="tag", outputs=("count", "sum"))
+    want = oracle.run(pipe, s)
+    for world in (2, 3):
+        parts = [rs.run_stream(pipe, multi.shard_stream(s, world, r), strategy="tag", outputs=("count", "sum"))[0]
+                 for r in range(world)]
+        for k in ("count", "sum"):
+            cat = np.concatenate([p[k] for p in parts])
+            assert np.array_equal(cat, whole[k]) and np.array_equal(cat, want[k]), (world, k)
