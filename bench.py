@@ -510,7 +510,7 @@ def cgroup_cpu_quota():
         return None
 
 
-def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: float = 40.0, slice_units: int = 16,
+def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: float = 40.0, slice_units: int = 64,
                   warm_requests: int = 64):
     """Open-loop Poisson arrivals of batched-size hashed streams into the
     continuous-batching server (requests advanced `slice_units` work units per launch over
@@ -558,7 +558,7 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
         srv.progress()
         for rid in srv.poll():
             tdone = time.perf_counter() - t0
-            lat.append((stamps[rid], tdone - stamps[rid]))
+            lat.append((stamps[rid], tdone - stamps[rid], sizes[owner[rid]]))
             slot = owner.pop(rid)
             busy[slot] = False
             done_items += sizes[slot]
@@ -579,6 +579,8 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
     srv.close()
     L = np.array([x[1] for x in lat]) * 1e3
     Lw = np.array([x[1] for x in lat if x[0] >= 1.0]) * 1e3
+    med = float(np.median(sizes))
+    Ls = np.array([x[1] for x in lat if x[2] <= med]) * 1e3     # requests up to the median size
     return {"workload": f"Poisson {rate:.0f} streams/s for {seconds:.0f} s, batched-size hashed streams, "
                         f"arena {arena_gb:.0f} GiB, {slice_units} units per request per launch",
             "offered_items_per_s": rate * float(np.mean(sizes)),
@@ -588,6 +590,7 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
             "p99_ms": float(np.percentile(L, 99)) if len(L) else None,
             "p50_ms_after_1s": float(np.percentile(Lw, 50)) if len(Lw) else None,
             "p99_ms_after_1s": float(np.percentile(Lw, 99)) if len(Lw) else None,
+            "p99_ms_requests_up_to_median_size": float(np.percentile(Ls, 99)) if len(Ls) else None,
             "max_ms": float(L.max()) if len(L) else None,
             "over_5ms": int((L > 5.0).sum()) if len(L) else 0,
             "host_cpu": {"quota": cgroup_cpu_quota(),
@@ -605,7 +608,8 @@ def bench_serving_sweep(rs, torch, rates=(20000, 40000, 80000, 160000, 320000), 
     for r in rates:
         x = bench_serving(rs, torch, seconds, rate=float(r), warm_requests=16)
         rows.append({"rate": r, "items_per_s": x["items_per_s"], "offered_items_per_s": x["offered_items_per_s"],
-                     "p50_ms": x["p50_ms"], "p99_ms": x["p99_ms"], "launches": x["launches"]})
+                     "p50_ms": x["p50_ms"], "p99_ms": x["p99_ms"],
+                     "p99_ms_small": x["p99_ms_requests_up_to_median_size"], "launches": x["launches"]})
     base = rows[0]["p99_ms"] or 0.0
     sat = None
     for row in rows:

@@ -398,7 +398,7 @@ typedef struct {
 rs_status rs_server_create(const rs_stage_desc *stages, uint32_t n_stages, const rs_pipeline_opts *opts,
                            void *arena, uint64_t arena_bytes, uint32_t max_batch, uint32_t max_inflight,
                            rs_cuda_stream stream, rs_server **out);
-/* Work units each active request runs per launch (default 16); 0 runs every request to
+/* Work units each active request runs per launch (default 64); 0 runs every request to
  * completion in the launch it joins. */
 rs_status rs_server_set_slice_units(rs_server *s, uint32_t units);
 /* Queue a request (host-side only; admitted by a later rs_server_progress).

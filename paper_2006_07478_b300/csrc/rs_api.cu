@@ -941,6 +941,16 @@ static size_t workspace_need(const rs_pipeline *p)
     return need;
 }
 
+rs_status rs_run_workspace_bytes(const rs_pipeline *p, uint64_t *bytes)
+{
+    if (!p || !bytes) return RS_ERR_INVALID;
+    Topo topo;
+    const int strategy = run_strategy(p, &topo);
+    if (strategy < 0) return RS_ERR_INVALID;
+    *bytes = make_plan(p, strategy, p->opts).total;
+    return RS_OK;
+}
+
 extern "C" rs_status rs_workspace_size(const rs_pipeline *p, uint64_t *bytes)
 {
     if (!p || !bytes) return RS_ERR_INVALID;

@@ -197,6 +197,10 @@ struct KParams {
     SmemLayout L;
 };
 
+// Workspace bytes of the next rs_run alone (rs_workspace_size also covers every option
+// set the autotuner may try); used by the server for each launch (rs_api.cu).
+rs_status rs_run_workspace_bytes(const rs_pipeline *p, uint64_t *bytes);
+
 // Launch helpers implemented in rs_kernel.cu.
 int rs_launch_kernel(const KParams &P, int grid, int block, size_t smem, void *stream);
 int rs_launch_planner(const KParams &P, int grid, void *stream);

@@ -153,7 +153,7 @@ struct rs_server {
     uint64_t round = 0;
     uint64_t next_id = 1;
     uint32_t max_batch = 4096, max_inflight = 2;
-    uint32_t slice_units = 16;
+    uint32_t slice_units = 64;
     cudaStream_t stream = nullptr;                // slices (the caller's stream)
     cudaStream_t cin = nullptr, cout = nullptr;   // copy-in, results
     rs_server_stats stats;
@@ -339,7 +339,7 @@ static rs_status launch_slice(rs_server *s)
         return RS_OK;
     }
     uint64_t wsb = 0;
-    rs_status st = rs_workspace_size(b.p, &wsb);
+    rs_status st = rs_run_workspace_bytes(b.p, &wsb);
     if (st != RS_OK) {
         s->pool.push_back(b.p);
         return st;
