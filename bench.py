@@ -881,6 +881,8 @@ def main():
                          ("region_sizes", lambda: bench_region_sizes(rs, torch)),
                          ("batched", lambda: bench_batched(rs, torch)),
                          ("serving", lambda: bench_serving(rs, torch, args.serve_seconds)),
+                         ("serving_whole_requests",
+                          lambda: bench_serving(rs, torch, min(10.0, args.serve_seconds), slice_units=0)),
                          ("serving_sweep", lambda: bench_serving_sweep(rs, torch) if args.serve_sweep else None)):
             try:
                 extras[name] = fn()
