@@ -151,8 +151,14 @@ typedef struct {
                                    per-edge kernel (units of <= 512 parents, as the signal
                                    strategy's).  Below a tagged edge every edge is tagged;
                                    an EXPAND stage takes no RS_BOUNDARY_LANE input.        */
-    uint32_t reserved;
+    uint32_t flags;             /* RS_FLAG_* below                                              */
 } rs_pipeline_opts;
+
+/* The tag strategy with a persistent grid (grid = 0) and one stream: the unit count is
+ * rounded down to a whole number of rounds over the resident processors (units grow a
+ * little), so that the last round does not leave most processors idle.  This flag keeps
+ * the unit shape as given. */
+#define RS_FLAG_UNBALANCED_UNITS 1u
 
 typedef enum {
     RS_BOUNDARY_DEFAULT = 0,

@@ -78,6 +78,7 @@ struct rs_pipeline {
     size_t table_cap = 0;
     bool table_dirty = true;
     void *table_ws = nullptr;      // workspace the table's pointers refer to
+    uint64_t table_bal = 0;        // balanced unit count the table was built for (0: none)
     cudaEvent_t upload_done = nullptr;
     bool upload_pending = false;
     // graph
@@ -567,7 +568,7 @@ static uint32_t plan_tile_parents(const rs_pipeline *p)
 
 // the work decomposition of one stream
 static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int strategy, const rs_stream_desc &s,
-                        StreamPlan &q, bool allow_usum = false)
+                        StreamPlan &q, bool allow_usum = false, uint64_t bal = 0)
 {
     memset(&q, 0, sizeof q);
     const double mean = s.n_regions ? (double)s.n_elements / (double)s.n_regions : 0.0;
@@ -581,6 +582,8 @@ static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int str
         const double want = (double)D / (1.0 + (mean > 1.0 ? mean : 1.0));
         uint32_t K = 32;
         while ((double)K * 2 <= want && K * 2 <= RS_TAG_MAX_K) K *= 2;
+        // balanced units: bal units in all (at most as many as the shape gives)
+        if (bal && bal < (s.n_regions + K - 1) / K) K = (uint32_t)((s.n_regions + bal - 1) / bal);
         q.mode = UNIT_REGIONS;
         q.K = K;
         q.n_units = (uint32_t)((s.n_regions + K - 1) / K);
@@ -591,6 +594,10 @@ static void plan_stream(const rs_pipeline *p, const rs_pipeline_opts &o, int str
         q.mode = UNIT_MERGE;
         merge_shape(o, strategy, &q.c, &q.D, &q.K);
         uint64_t steps = (uint64_t)q.c * s.n_regions + s.n_elements;
+        // balanced units: D grows so that the stream has bal units (never more than the
+        // shape gives: the workspace was sized for those)
+        if (bal && bal < (steps + q.D - 1) / q.D && (steps + bal - 1) / bal < (1ull << 32))
+            q.D = (uint32_t)((steps + bal - 1) / bal);
         q.n_units = s.n_regions ? (uint32_t)((steps + q.D - 1) / q.D) : 0u;
         const uint32_t tile = plan_tile_parents(p);
         q.plan_tiles = (uint32_t)((s.n_regions + tile - 1) / tile);
@@ -702,14 +709,14 @@ static void apply_slice(const SliceInfo &si, StreamPlan &q, int strategy, uint32
     state_layout(q, strategy, nsinks);
 }
 
-static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts &o)
+static Plan make_plan(const rs_pipeline *p, int strategy, const rs_pipeline_opts &o, uint64_t bal = 0)
 {
     Plan pl;
     pl.hdr_bytes = align256(sizeof(WsHeader));
     pl.sp.resize(p->streams.size());
     const uint32_t nsinks = n_leaves(p->stages, p->n_stages);
     for (size_t i = 0; i < p->streams.size(); ++i) {
-        plan_stream(p, o, strategy, p->streams[i], pl.sp[i], !p->slices[i].on);
+        plan_stream(p, o, strategy, p->streams[i], pl.sp[i], !p->slices[i].on, bal);
         apply_slice(p->slices[i], pl.sp[i], strategy, nsinks);
     }
     layout_plan(pl.sp.data(), pl.sp.size(), strategy, n_leaves(p->stages, p->n_stages), &pl.total_units,
@@ -1097,6 +1104,28 @@ struct Launch {
 
 // Host-only preparation: stream table in pinned memory, kernel parameters, grid.
 // Makes no stream-ordered call, so it may run before a stream capture begins.
+// The balanced unit count for a run (0: none): with the tag kernel on a persistent grid and
+// one stream, the units are rounded down to a whole number of rounds over the resident
+// processors `procs`, so that the last round does not leave most of them idle.  Returns
+// `bal` itself when the plan made with it already is whole rounds.
+static uint64_t balanced_units(const rs_pipeline *p, int strategy, const Topo &topo, const Plan &pl, uint64_t procs,
+                               uint64_t bal)
+{
+    if (strategy != RS_STRATEGY_TAG || topo.mix || p->opts.grid != 0 || (p->opts.flags & RS_FLAG_UNBALANCED_UNITS))
+        return 0;
+    int with_units = 0;
+    for (const StreamPlan &q : pl.sp) {
+        if (q.slice_n == 0) continue;
+        if (q.sliced) return 0;
+        ++with_units;
+    }
+    if (with_units != 1 || procs == 0) return 0;
+    const uint64_t n = pl.total_units;
+    if (n <= procs) return 0;
+    const uint64_t t = (n / procs) * procs;
+    return t == n ? bal : t;
+}
+
 static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *out)
 {
     if (!p || !ws) return RS_ERR_INVALID;
@@ -1106,26 +1135,131 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
     const int strategy = run_strategy(p, &topo);
     if (strategy < 0) return RS_ERR_INVALID;
     if (strategy != RS_STRATEGY_TAG && p->opts.ensemble_width > 4 * RS_W) return RS_ERR_INVALID;
-    Lc.pl = make_plan(p, strategy, p->opts);
-    const Plan &pl = Lc.pl;
-    if (ws_bytes < pl.total) return RS_ERR_CAPACITY;
-    rs_status sst = check_states(p, pl.sp.data(), pl.sp.size());
-    if (sst != RS_OK) return sst;
-    if (((uintptr_t)ws & 255) != 0) return RS_ERR_INVALID;
-    if (pl.total_units >= (1ull << 31)) return RS_ERR_CAPACITY;
+    // a balanced unit count decided by an earlier run on the same streams and options
+    uint64_t bal = (p->table_dirty || p->table_ws != ws) ? 0 : p->table_bal;
     cudaError_t e;
-    if (!p->n_sm) {
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
-        if ((e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-            return cuda_fail(e);
-    }
     const rs_pipeline_opts &o = p->opts;
     unsigned char *wsb = (unsigned char *)ws;
+    const size_t ns = p->streams.size();
+    for (int pass = 0;; ++pass) {
+        Lc.pl = make_plan(p, strategy, p->opts, bal);
+        const Plan &pl = Lc.pl;
+        if (ws_bytes < pl.total) return RS_ERR_CAPACITY;
+        rs_status sst = check_states(p, pl.sp.data(), pl.sp.size());
+        if (sst != RS_OK) return sst;
+        if (((uintptr_t)ws & 255) != 0) return RS_ERR_INVALID;
+        if (pl.total_units >= (1ull << 31)) return RS_ERR_CAPACITY;
+        if (!p->n_sm) {
+            int dev = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+            if ((e = cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                return cuda_fail(e);
+        }
+
+        // ---- kernel parameters ----
+        KParams &P = Lc.P;
+        memset(&P, 0, sizeof P);
+        bool need_ctx = false, need_par = p->stages[0].kind == RS_ENUM_HASH;
+        for (uint32_t i = 0; i < p->n_stages; ++i) {
+            P.st[i] = to_dev(p->stages[i]);
+            if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_HASH_CTX_LT) need_ctx = true;
+            if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_WEIGHT_LT) need_par = true;
+        }
+        P.n_stages = (int)p->n_stages;
+        P.strategy = strategy;
+        P.n_streams = (uint32_t)ns;
+        P.total_units = (uint32_t)pl.total_units;
+        P.plan_tiles = (uint32_t)pl.plan_tiles;
+        P.plan_pow2 = plan_pow2(pl, p->streams.size());
+        P.plan_tile = plan_tile_parents(p);
+        P.streams = (const DevStream *)(wsb + pl.table_off);
+        P.hdr = (WsHeader *)wsb;
+        P.V = o.ensemble_width / RS_W;
+        P.C = o.queue_capacity;
+        P.SC = o.signal_capacity;
+        P.TE = o.tile_elements;
+        P.NT = o.tiles_in_flight;
+        P.need_ctx = need_ctx;
+        P.need_par = need_par;
+        bool wc = false, wsum = false, wm = false;
+        for (const auto &s : p->streams) {
+            wc |= s.out_count != nullptr;
+            wsum |= s.out_sum != nullptr;
+            wm |= s.out_min != nullptr;
+        }
+        // every non-empty stream must provide each output any stream asks for
+        for (const auto &s : p->streams) {
+            if (s.n_regions == 0) continue;
+            if ((wc && !s.out_count) || (wsum && !s.out_sum) || (wm && !s.out_min)) return RS_ERR_INVALID;
+        }
+        // an emit sink claims positions with atomics on the counts, which every run zeroes
+        // first: no identity results are written
+        P.emit = is_emit(p);
+        P.emit_f = fanout_product(p->stages, p->n_stages);
+        P.want_count = wc && !P.emit;
+        P.want_sum = wsum && !P.emit;
+        P.want_min = wm && !P.emit;
+        P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
+        P.budget = o.device_budget;
+        P.spin_limit = 2000000000ull;   // 2 s on the global timer
+        P.cpl = tag_chunk_cpl(p);
+        P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p, P.cpl)
+                                          : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm, topo);
+        P.plan_fill = strategy == RS_STRATEGY_TAG;
+        P.m16 = 1u << 16;
+        P.m19 = 1u << 19;
+        set_topo(P, topo);
+
+        // processors per CTA: as asked, but no more than fit the per-block shared memory;
+        // 0 = the count (8, 4, 2 or 1) giving the most resident processors per SM
+        uint32_t wpb = o.warps_per_block;
+        if (!p->smem_max) {
+            int dev = 0, v = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+            if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+                return cuda_fail(e);
+            p->smem_max = (size_t)v;
+        }
+        if (wpb == 0) {
+            rs_status ws = auto_wpb(p, P, &wpb);
+            if (ws != RS_OK) return ws;
+        }
+        while (wpb > 1 && (size_t)P.L.per_warp * wpb > p->smem_max) --wpb;
+        if ((size_t)P.L.per_warp * wpb > p->smem_max) return RS_ERR_CAPACITY;
+        Lc.block = (int)wpb * 32;
+        Lc.smem = (size_t)P.L.per_warp * wpb;
+        Lc.grid = (int)o.grid;
+        if (pl.total_units == 0) break;   // only empty streams: nothing to launch
+        if (Lc.grid == 0) {
+            int bps = 0;
+            int ce = rs_kernel_occupancy(P, Lc.block, Lc.smem, &bps);
+            if (ce != 0) return cuda_fail((cudaError_t)ce);
+            if (bps == 0) return RS_ERR_CAPACITY;
+            p->last_bps = (uint32_t)bps;
+            Lc.grid = bps * p->n_sm;
+            uint64_t warps = (uint64_t)Lc.grid * wpb;   // no more processors than units
+            if (warps > pl.total_units) {
+                Lc.grid = (int)((pl.total_units + wpb - 1) / wpb);
+                if (Lc.grid < 1) Lc.grid = 1;
+            }
+        } else {
+            int ce = rs_kernel_max_smem_optin(P, Lc.smem);
+            if (ce != 0) return cuda_fail((cudaError_t)ce);
+            int bps = 0;
+            ce = rs_kernel_occupancy(P, Lc.block, Lc.smem, &bps);
+            if (ce != 0) return cuda_fail((cudaError_t)ce);
+            p->last_bps = (uint32_t)bps;
+        }
+
+        const uint64_t want =
+            balanced_units(p, strategy, topo, Lc.pl, (uint64_t)Lc.grid * (uint64_t)(Lc.block / 32), bal);
+        if (pass == 1 || want == bal) break;
+        bal = want;
+    }
+    const Plan &pl = Lc.pl;
 
     // ---- stream table (pinned host copy, uploaded by every run) ----
-    const size_t ns = p->streams.size();
-    if (p->table_dirty || !p->table_host || p->table_ws != ws) {
+    if (p->table_dirty || !p->table_host || p->table_ws != ws || p->table_bal != bal) {
         if (p->upload_pending) {
             if ((e = cudaEventSynchronize(p->upload_done)) != cudaSuccess) return cuda_fail(e);
             p->upload_pending = false;
@@ -1142,106 +1276,13 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
         fill_table(p, pl.sp.data(), ns, (unsigned char *)ws, p->table_host);
         p->table_dirty = false;
         p->table_ws = ws;
+        p->table_bal = bal;
     }
 
-    // ---- kernel parameters ----
-    KParams &P = Lc.P;
-    memset(&P, 0, sizeof P);
-    bool need_ctx = false, need_par = p->stages[0].kind == RS_ENUM_HASH;
-    for (uint32_t i = 0; i < p->n_stages; ++i) {
-        P.st[i] = to_dev(p->stages[i]);
-        if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_HASH_CTX_LT) need_ctx = true;
-        if (p->stages[i].kind == RS_FILTER && p->stages[i].op == RS_OP_WEIGHT_LT) need_par = true;
-    }
-    P.n_stages = (int)p->n_stages;
-    P.strategy = strategy;
-    P.n_streams = (uint32_t)ns;
-    P.total_units = (uint32_t)pl.total_units;
-    P.plan_tiles = (uint32_t)pl.plan_tiles;
-    P.plan_pow2 = plan_pow2(pl, p->streams.size());
-    P.plan_tile = plan_tile_parents(p);
-    P.streams = (const DevStream *)(wsb + pl.table_off);
-    P.hdr = (WsHeader *)wsb;
-    P.V = o.ensemble_width / RS_W;
-    P.C = o.queue_capacity;
-    P.SC = o.signal_capacity;
-    P.TE = o.tile_elements;
-    P.NT = o.tiles_in_flight;
-    P.need_ctx = need_ctx;
-    P.need_par = need_par;
-    bool wc = false, wsum = false, wm = false;
-    for (const auto &s : p->streams) {
-        wc |= s.out_count != nullptr;
-        wsum |= s.out_sum != nullptr;
-        wm |= s.out_min != nullptr;
-    }
-    // every non-empty stream must provide each output any stream asks for
-    for (const auto &s : p->streams) {
-        if (s.n_regions == 0) continue;
-        if ((wc && !s.out_count) || (wsum && !s.out_sum) || (wm && !s.out_min)) return RS_ERR_INVALID;
-    }
-    // an emit sink claims positions with atomics on the counts, which every run zeroes
-    // first: no identity results are written
-    P.emit = is_emit(p);
-    P.emit_f = fanout_product(p->stages, p->n_stages);
-    P.want_count = wc && !P.emit;
-    P.want_sum = wsum && !P.emit;
-    P.want_min = wm && !P.emit;
-    P.any_load = p->stages[0].kind == RS_ENUM_LOAD;
-    P.budget = o.device_budget;
-    P.spin_limit = 2000000000ull;   // 2 s on the global timer
-    P.cpl = tag_chunk_cpl(p);
-    P.L = strategy == RS_STRATEGY_TAG ? make_tag_layout(p, P.cpl)
-                                      : make_layout(p, strategy, pl.Kmax, P.any_load, need_ctx, need_par, wm, topo);
-    P.plan_fill = strategy == RS_STRATEGY_TAG;
-    P.m16 = 1u << 16;
-    P.m19 = 1u << 19;
-    set_topo(P, topo);
-
-    // processors per CTA: as asked, but no more than fit the per-block shared memory;
-    // 0 = the count (8, 4, 2 or 1) giving the most resident processors per SM
-    uint32_t wpb = o.warps_per_block;
-    if (!p->smem_max) {
-        int dev = 0, v = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
-        if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
-            return cuda_fail(e);
-        p->smem_max = (size_t)v;
-    }
-    if (wpb == 0) {
-        rs_status ws = auto_wpb(p, P, &wpb);
-        if (ws != RS_OK) return ws;
-    }
-    while (wpb > 1 && (size_t)P.L.per_warp * wpb > p->smem_max) --wpb;
-    if ((size_t)P.L.per_warp * wpb > p->smem_max) return RS_ERR_CAPACITY;
-    Lc.block = (int)wpb * 32;
-    Lc.smem = (size_t)P.L.per_warp * wpb;
-    Lc.grid = (int)o.grid;
-    if (pl.total_units == 0) return RS_OK;
-    if (Lc.grid == 0) {
-        int bps = 0;
-        int ce = rs_kernel_occupancy(P, Lc.block, Lc.smem, &bps);
-        if (ce != 0) return cuda_fail((cudaError_t)ce);
-        if (bps == 0) return RS_ERR_CAPACITY;
-        p->last_bps = (uint32_t)bps;
-        Lc.grid = bps * p->n_sm;
-        uint64_t warps = (uint64_t)Lc.grid * wpb;   // no more processors than units
-        if (warps > pl.total_units) {
-            Lc.grid = (int)((pl.total_units + wpb - 1) / wpb);
-            if (Lc.grid < 1) Lc.grid = 1;
-        }
-    } else {
-        int ce = rs_kernel_max_smem_optin(P, Lc.smem);
-        if (ce != 0) return cuda_fail((cudaError_t)ce);
-        int bps = 0;
-        ce = rs_kernel_occupancy(P, Lc.block, Lc.smem, &bps);
-        if (ce != 0) return cuda_fail((cudaError_t)ce);
-        p->last_bps = (uint32_t)bps;
-    }
     p->last_grid = (uint32_t)Lc.grid;
     p->last_block = (uint32_t)Lc.block;
     p->last_smem = (uint32_t)Lc.smem;
-    p->last_cp = strategy == RS_STRATEGY_TAG ? 32 * P.cpl : 0;
+    p->last_cp = strategy == RS_STRATEGY_TAG ? 32 * Lc.P.cpl : 0;
     return RS_OK;
 }
 

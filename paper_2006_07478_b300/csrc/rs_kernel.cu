@@ -1341,6 +1341,17 @@ struct Proc {
         return (w.qh[e] == w.qt[e]) && (w.sh[e] == w.st[e]);
     }
 
+    // edge_empty for a run-time edge index, by a compile-time select over the edges (so the
+    // queue cursors stay in registers)
+    __device__ __forceinline__ bool edge_empty_at(uint32_t e) const
+    {
+        bool r = true;
+#pragma unroll
+        for (int j = 0; j < RS_MAX_EDGES; ++j)
+            if ((uint32_t)j == e) r = edge_empty(j);
+        return r;
+    }
+
     // =====================================================================================
     // The per-edge kernel (MIX): every edge carries region boundaries its own way (EM_SIG,
     // EM_TAG or EM_LANE, as the parameters say) and a node may feed several children (a
@@ -1939,7 +1950,7 @@ struct Proc {
 #define RS_MIX_FIRE(I)                                                                            \
             if (I < n) {                                                                          \
                 const uint32_t u = P.up[I];                                                       \
-                const bool d = u == 0 ? done0 : (((dm >> u) & 1u) && edge_empty((int)u - 1));     \
+                const bool d = u == 0 ? done0 : (((dm >> u) & 1u) && edge_empty_at(u - 1));       \
                 if (d) dm |= 1u << I;                                                             \
                 fire<I>(d);                                                                       \
             }
@@ -1951,7 +1962,9 @@ struct Proc {
 #undef RS_MIX_FIRE
             if (stop) return;
             bool all = done0;
-            for (int e2 = 0; e2 + 1 < n; ++e2) all = all && edge_empty(e2);
+#pragma unroll
+            for (int e2 = 0; e2 < RS_MAX_EDGES; ++e2)
+                if (e2 + 1 < n) all = all && edge_empty(e2);
             if (all) break;
             if (sweep >= P.budget) {
                 if (lane == 0) atomicOr(&P.hdr->status, ST_STALL);

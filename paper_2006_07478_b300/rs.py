@@ -73,7 +73,7 @@ class Opts(ctypes.Structure):
                 ("tiles_in_flight", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
                 ("grid", ctypes.c_uint32), ("region_cost", ctypes.c_uint32),
                 ("device_budget", ctypes.c_uint64), ("boundary_modes", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
