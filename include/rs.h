@@ -154,10 +154,11 @@ typedef struct {
     uint32_t flags;             /* RS_FLAG_* below                                              */
 } rs_pipeline_opts;
 
-/* The tag strategy with a persistent grid (grid = 0) and one stream: the unit count is
- * rounded down to a whole number of rounds over the resident processors (units grow a
- * little), so that the last round does not leave most processors idle.  This flag keeps
- * the unit shape as given. */
+/* The tag strategy with a persistent grid (grid = 0) and one stream: when the stream has at
+ * least two rounds of units over the resident processors, the unit count is rounded down to
+ * a whole number of rounds (units grow a little), so that the last round does not leave
+ * most processors idle.  The count is decided by the first run after a submit or an option
+ * change and kept by the runs after it.  This flag keeps the unit shape as given. */
 #define RS_FLAG_UNBALANCED_UNITS 1u
 
 typedef enum {

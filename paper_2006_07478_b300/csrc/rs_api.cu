@@ -1105,11 +1105,13 @@ struct Launch {
 // Host-only preparation: stream table in pinned memory, kernel parameters, grid.
 // Makes no stream-ordered call, so it may run before a stream capture begins.
 // The balanced unit count for a run (0: none): with the tag kernel on a persistent grid and
-// one stream, the units are rounded down to a whole number of rounds over the resident
-// processors `procs`, so that the last round does not leave most of them idle.  Returns
-// `bal` itself when the plan made with it already is whole rounds.
-static uint64_t balanced_units(const rs_pipeline *p, int strategy, const Topo &topo, const Plan &pl, uint64_t procs,
-                               uint64_t bal)
+// one stream, the units of the plan made without balancing (n of them) are regrouped into
+// r = floor(n / procs) whole rounds over the resident processors `procs`, so that the last
+// round does not leave most of them idle.  Needs r >= 2: with one round every processor
+// holds a single large unit and nothing evens out the processors' speeds.  Derived once,
+// from the unbalanced plan; a plan made with the count may hold a few units fewer (each
+// unit takes ceil(regions / count) parents), which the caller keeps as it is.
+static uint64_t balanced_units(const rs_pipeline *p, int strategy, const Topo &topo, const Plan &pl, uint64_t procs)
 {
     if (strategy != RS_STRATEGY_TAG || topo.mix || p->opts.grid != 0 || (p->opts.flags & RS_FLAG_UNBALANCED_UNITS))
         return 0;
@@ -1121,9 +1123,9 @@ static uint64_t balanced_units(const rs_pipeline *p, int strategy, const Topo &t
     }
     if (with_units != 1 || procs == 0) return 0;
     const uint64_t n = pl.total_units;
-    if (n <= procs) return 0;
-    const uint64_t t = (n / procs) * procs;
-    return t == n ? bal : t;
+    const uint64_t r = n / procs;
+    if (r < 2 || r * procs == n) return 0;
+    return r * procs;
 }
 
 static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *out)
@@ -1251,9 +1253,12 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
             p->last_bps = (uint32_t)bps;
         }
 
+        // a count taken from an earlier run, or this pass's, stands: it is never derived
+        // again from a plan made with it
+        if (pass == 1 || bal != 0) break;
         const uint64_t want =
-            balanced_units(p, strategy, topo, Lc.pl, (uint64_t)Lc.grid * (uint64_t)(Lc.block / 32), bal);
-        if (pass == 1 || want == bal) break;
+            balanced_units(p, strategy, topo, Lc.pl, (uint64_t)Lc.grid * (uint64_t)(Lc.block / 32));
+        if (want == 0) break;
         bal = want;
     }
     const Plan &pl = Lc.pl;

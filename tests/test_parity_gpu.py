@@ -269,6 +269,44 @@ def test_tag_wide_ensembles_and_unit_shapes(rs, opts):
     _check(rs, wl.pipeline_hash_filter_map(), s, "tag", **opts)
 
 
+def test_balanced_unit_count_is_kept_by_later_runs(rs):
+    """The tag kernel on one stream regroups its fixed-parent units into whole rounds over
+    the resident processors: the first run decides the count and every later run keeps it
+    (a count re-derived from a balanced plan would drift down a round per run), with exact
+    results in each run."""
+    import torch
+    s = wl.cascade_stream(n_total=1 << 20, mean=1, seed=11)
+    pipe = wl.pipeline_cascade()
+    want = oracle.run(pipe, s)
+    units, procs = {}, 0
+    for flags in (0, 1):   # 1 = RS_FLAG_UNBALANCED_UNITS
+        p = rs.Pipeline(pipe, strategy="tag", regions_per_unit=64, region_cost=2, flags=flags)
+        out = p.submit(rs.to_device(s), outputs=("count", "sum"))
+        seen = []
+        for _ in range(6):
+            for k in ("count", "sum"):
+                out[k].fill_(0x5A5A5A5A)
+            p.run()
+            st = p.stats()
+            torch.cuda.synchronize()
+            assert st["device_status"] == 0, st
+            got = rs.results_to_numpy(out)
+            for k in ("count", "sum"):
+                assert np.array_equal(got[k], want[k]), (flags, k)
+            seen.append(st["units"])
+        assert len(set(seen)) == 1, (flags, seen)
+        units[flags] = seen[0]
+        procs = st["launch"]["grid"] * st["launch"]["block"] // 32
+        p.close()
+    n = units[1]
+    r = n // procs
+    if r >= 2 and n % procs:
+        # r whole rounds; a unit takes ceil(regions / count) parents, so a few fewer
+        assert (r - 1) * procs < units[0] <= r * procs, (units, procs)
+    else:
+        assert units[0] == n, (units, procs)
+
+
 @pytest.mark.parametrize("strategy", STRATEGIES)
 def test_count_only_output(rs, strategy):
     s = wl.cascade_stream(n_total=1 << 16, mean=6, seed=12)
