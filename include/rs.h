@@ -160,6 +160,14 @@ typedef struct {
  * most processors idle.  The count is decided by the first run after a submit or an option
  * change and kept by the runs after it.  This flag keeps the unit shape as given. */
 #define RS_FLAG_UNBALANCED_UNITS 1u
+/* The caller gives rs_run the workspace of this pipeline alone: nothing else writes into it
+ * between two runs of the pipeline.  A run then leaves in place the stream table (the
+ * per-stream array pointers and unit split that every run reads) an earlier run uploaded
+ * into the same workspace, and uploads it again only after a submit, an option change or a
+ * change of workspace.  Without the flag every run copies the table from host memory first.
+ * Graph capture always records the copy.  Breaking the promise is undefined behaviour: the
+ * kernels would follow whatever pointers the workspace then holds where the table was. */
+#define RS_FLAG_PRIVATE_WORKSPACE 2u
 
 typedef enum {
     RS_BOUNDARY_DEFAULT = 0,

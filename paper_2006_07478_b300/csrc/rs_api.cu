@@ -79,6 +79,7 @@ struct rs_pipeline {
     bool table_dirty = true;
     void *table_ws = nullptr;      // workspace the table's pointers refer to
     uint64_t table_bal = 0;        // balanced unit count the table was built for (0: none)
+    void *table_in_ws = nullptr;   // workspace holding the current table (private workspaces)
     cudaEvent_t upload_done = nullptr;
     bool upload_pending = false;
     // graph
@@ -245,6 +246,7 @@ static rs_status check_opts(const rs_pipeline_opts *o, uint32_t fan)
     if (o->tiles_in_flight != 0 && o->tiles_in_flight != 2 && o->tiles_in_flight != 4) return RS_ERR_INVALID;
     if (o->warps_per_block > 8) return RS_ERR_INVALID;   // 0: chosen per launch
     if (o->region_cost != 0 && (!is_pow2(o->region_cost) || o->region_cost > 256)) return RS_ERR_INVALID;
+    if (o->flags & ~(RS_FLAG_UNBALANCED_UNITS | RS_FLAG_PRIVATE_WORKSPACE)) return RS_ERR_INVALID;
     return RS_OK;
 }
 
@@ -1279,6 +1281,7 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
             p->table_cap = cap;
         }
         fill_table(p, pl.sp.data(), ns, (unsigned char *)ws, p->table_host);
+        p->table_in_ws = nullptr;
         p->table_dirty = false;
         p->table_ws = ws;
         p->table_bal = bal;
@@ -1298,16 +1301,21 @@ static rs_status enqueue(rs_pipeline *p, void *ws, const Launch &Lc, cudaStream_
     cudaError_t e;
     unsigned char *wsb = (unsigned char *)ws;
     if ((e = cudaMemsetAsync(wsb, 0, Lc.pl.zero_end, stream)) != cudaSuccess) return cuda_fail(e);
-    if ((e = cudaMemcpyAsync(wsb + Lc.pl.table_off, p->table_host, p->streams.size() * sizeof(DevStream),
-                             cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-        return cuda_fail(e);
-    if (!capturing) {
-        if (!p->upload_done) {
-            if ((e = cudaEventCreateWithFlags(&p->upload_done, cudaEventDisableTiming)) != cudaSuccess)
-                return cuda_fail(e);
+    // a private workspace keeps the table an earlier run uploaded, until it is rebuilt
+    const bool priv = (p->opts.flags & RS_FLAG_PRIVATE_WORKSPACE) != 0;
+    if (capturing || !priv || p->table_in_ws != ws) {
+        if ((e = cudaMemcpyAsync(wsb + Lc.pl.table_off, p->table_host, p->streams.size() * sizeof(DevStream),
+                                 cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+            return cuda_fail(e);
+        if (!capturing) {
+            if (!p->upload_done) {
+                if ((e = cudaEventCreateWithFlags(&p->upload_done, cudaEventDisableTiming)) != cudaSuccess)
+                    return cuda_fail(e);
+            }
+            if ((e = cudaEventRecord(p->upload_done, stream)) != cudaSuccess) return cuda_fail(e);
+            p->upload_pending = true;
+            p->table_in_ws = priv ? ws : nullptr;
         }
-        if ((e = cudaEventRecord(p->upload_done, stream)) != cudaSuccess) return cuda_fail(e);
-        p->upload_pending = true;
     }
     if (Lc.P.emit) {
         for (const auto &s : p->streams)

@@ -263,6 +263,10 @@ def stage_desc(st) -> StageDesc:
     return d
 
 
+FLAG_UNBALANCED_UNITS = 1      # RS_FLAG_UNBALANCED_UNITS
+FLAG_PRIVATE_WORKSPACE = 2     # RS_FLAG_PRIVATE_WORKSPACE
+
+
 def make_opts(strategy="tag", **kw) -> Opts:
     o = Opts()
     check(lib().rs_default_opts(ctypes.byref(o)), "rs_default_opts")
@@ -299,6 +303,8 @@ class Pipeline:
         arr = (StageDesc * len(self.stages))(*descs)
         if "boundary_modes" in opts:
             opts["boundary_modes"] = boundary_modes(opts["boundary_modes"])
+        # the workspace is this object's own tensor: runs may keep the stream table in it
+        opts["flags"] = int(opts.get("flags", 0)) | FLAG_PRIVATE_WORKSPACE
         o = make_opts(strategy, **opts)
         h = ctypes.c_void_p()
         check(lib().rs_pipeline_create(arr, len(self.stages), ctypes.byref(o), ctypes.byref(h)),
@@ -332,6 +338,8 @@ class Pipeline:
             o.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
         if "boundary_modes" in kw:
             kw["boundary_modes"] = boundary_modes(kw["boundary_modes"])
+        if "flags" in kw:
+            kw["flags"] = int(kw["flags"]) | FLAG_PRIVATE_WORKSPACE
         for k, v in kw.items():
             setattr(o, k, int(v))
         check(lib().rs_pipeline_set_opts(self._h, ctypes.byref(o)), "rs_pipeline_set_opts")

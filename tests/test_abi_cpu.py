@@ -100,6 +100,12 @@ def test_queue_capacity_must_hold_worst_case_output():
     st, h = _create(wl.pipeline_cascade(), region_cost=1, regions_per_unit=256)
     assert st == rs.RS_OK
     rs.lib().rs_pipeline_destroy(h)
+    # flags: RS_FLAG_UNBALANCED_UNITS | RS_FLAG_PRIVATE_WORKSPACE, nothing else
+    st, h = _create(wl.pipeline_cascade(), flags=rs.FLAG_UNBALANCED_UNITS | rs.FLAG_PRIVATE_WORKSPACE)
+    assert st == rs.RS_OK
+    rs.lib().rs_pipeline_destroy(h)
+    st, _ = _create(wl.pipeline_cascade(), flags=4)
+    assert st == rs.RS_ERR_INVALID
 
 
 def test_stream_submit_validation_and_workspace_size():
@@ -138,6 +144,10 @@ def test_opts_round_trip():
     assert o["strategy"] == 0 and o["queue_capacity"] == 512 and o["regions_per_unit"] == 16
     p.set_opts(strategy="tag", warps_per_block=8)
     assert p.opts["strategy"] == 1 and p.opts["warps_per_block"] == 8
+    # the binding's workspace is the pipeline's own tensor: the flag stays set
+    assert p.opts["flags"] == rs.FLAG_PRIVATE_WORKSPACE
+    p.set_opts(flags=rs.FLAG_UNBALANCED_UNITS)
+    assert p.opts["flags"] == rs.FLAG_UNBALANCED_UNITS | rs.FLAG_PRIVATE_WORKSPACE
     with pytest.raises(rs.RsError):
         p.set_opts(warps_per_block=16)
     with pytest.raises(rs.RsError):

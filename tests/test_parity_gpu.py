@@ -170,6 +170,44 @@ def test_batched_streams_one_launch_and_graph_replay(rs, strategy):
     p.close()
 
 
+def test_private_workspace_table_follows_submits_options_and_workspace(rs):
+    """RS_FLAG_PRIVATE_WORKSPACE (always set by the binding, whose workspace is the
+    pipeline's own tensor): runs keep the stream table in the workspace, and a submit, an
+    option change or a new workspace must each bring a fresh one, with exact results."""
+    import torch
+    pipe = wl.pipeline_cascade()
+    streams = [wl.cascade_stream(n_total=1 << 17, mean=m, seed=20 + i) for i, m in enumerate((3, 40, 700))]
+    wants = [oracle.run(pipe, s) for s in streams]
+    p = rs.Pipeline(pipe, strategy="tag")
+    assert p.opts["flags"] & rs.FLAG_PRIVATE_WORKSPACE
+
+    def check(outs):
+        for o in outs:
+            for k in ("count", "sum"):
+                o[k].fill_(0x5A5A5A5A)
+        p.run()
+        p.run()
+        assert p.stats()["device_status"] == 0
+        torch.cuda.synchronize()
+        for o, want in zip(outs, wants):
+            got = rs.results_to_numpy(o)
+            for k in ("count", "sum"):
+                assert np.array_equal(got[k], want[k]), k
+
+    outs = [p.submit(rs.to_device(streams[0]), outputs=("count", "sum"))]
+    check(outs)
+    outs.append(p.submit(rs.to_device(streams[1]), outputs=("count", "sum")))   # submit
+    check(outs)
+    p.set_opts(regions_per_unit=1024, region_cost=4)                           # options
+    check(outs)
+    p._ws = None                                                                # new workspace
+    check(outs)
+    outs.append(p.submit(rs.to_device(streams[2]), outputs=("count", "sum")))
+    p.set_opts(strategy="signal")
+    check(outs)
+    p.close()
+
+
 def test_fetch_to_host_and_autotune(rs):
     import torch
     s = wl.cascade_stream(n_total=1 << 18, mean=64, seed=5)
