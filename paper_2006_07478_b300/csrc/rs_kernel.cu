@@ -1754,8 +1754,9 @@ struct Proc {
             }
         }
         if (last) {
-            if (take > 0) mix_sink<I>(x, k, !inside, take);
-        } else {
+            if constexpr (S::template maybe_last<I>())
+                if (take > 0) mix_sink<I>(x, k, !inside, take);
+        } else if constexpr (S::template maybe_elem<I>()) {
             // the children's queues before this step's outputs (for the first credit)
             uint32_t first[RS_MAX_STAGES];
 #pragma unroll
@@ -1880,8 +1881,11 @@ struct Proc {
                     if (take == 0) break;
                     if (take < want) break;                       // wait for downstream space
                     if (!drain && !sigp && take < W) break;       // wait for a full ensemble
-                    if (last) aggregate<I, false>(take);
-                    else element_stage<I, false>(take);
+                    if (last) {
+                        if constexpr (S::template maybe_last<I>()) aggregate<I, false>(take);
+                    } else {
+                        if constexpr (S::template maybe_elem<I>()) element_stage<I, false>(take);
+                    }
                     if (stop) break;
                     __syncwarp();
                     w.qh[I - 1] += take;
@@ -2286,11 +2290,19 @@ struct KEntry {
     RS_KSIG(ST, 1, OE, O1, O2, O3, O4), RS_KSIG(ST, 2, OE, O1, O2, O3, O4), RS_KSIG(ST, 4, OE, O1, O2, O3, O4)
 #define RS_KBOTH(OE, O1, O2, O3, O4) RS_KALLV(RS_STRATEGY_SIGNAL, OE, O1, O2, O3, O4)
 
-// the per-edge kernel (boundary modes per edge, tree topologies): generic ops only
+// the per-edge kernel (boundary modes per edge, tree topologies): generic ops, and the
+// workloads' linear pipelines at 128 items per ensemble specialised (the generic one's
+// code overflows the instruction cache)
 #define RS_KMIX(V) {-1, V, 0, 0, 0, 0, 0, (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, V, GenericSig, true>}
+#define RS_KMIXS(V, OE, O1, O2, O3, O4) \
+    {-1, V, OE, O1, O2, O3, O4, (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, V, Sig<OE, O1, O2, O3, O4>, true>}
 
 static const KEntry g_kernels[] = {
     RS_KMIX(1), RS_KMIX(2), RS_KMIX(4),
+    // the cascade (three context hash filters) and the lines pipeline (two context hash
+    // filters and a multiply-add map)
+    RS_KMIXS(4, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),
+    RS_KMIXS(4, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_MAP_MULADD, 0),
     // loaded elements -> three context hash filters -> aggregate
     RS_KBOTH(D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),
     // hashed elements -> power-of-two modulus filter -> multiply-add map -> aggregate
@@ -2303,15 +2315,23 @@ static const KEntry g_kernels[] = {
 
 static const void *kernel_ptr(const KParams &P)
 {
-    if (P.mix) {
-        for (const KEntry &e : g_kernels)
-            if (e.strategy == -1 && e.V == (int)P.V) return e.fn;
-        return nullptr;
-    }
-    if (P.strategy == RS_STRATEGY_TAG) return rs_tag_kernel_entry(P);
     int ops[5] = {0, 0, 0, 0, 0};
     ops[0] = (int)P.st[0].op;
     for (int i = 1; i < P.n_stages - 1 && i < 5; ++i) ops[i] = (int)P.st[i].op;
+    if (P.mix) {
+        // a specialised per-edge kernel serves a linear pipeline ending in the aggregate
+        bool linear = P.n_sinks <= 1 && !P.emit;
+        for (int i = 1; i < P.n_stages; ++i) linear = linear && P.up[i] == i - 1;
+        const void *generic = nullptr;
+        for (const KEntry &e : g_kernels) {
+            if (e.strategy != -1 || e.V != (int)P.V) continue;
+            if (e.oe == 0) generic = e.fn;
+            else if (linear && e.oe == ops[0] && e.o1 == ops[1] && e.o2 == ops[2] && e.o3 == ops[3] && e.o4 == ops[4])
+                return e.fn;
+        }
+        return generic;
+    }
+    if (P.strategy == RS_STRATEGY_TAG) return rs_tag_kernel_entry(P);
     const void *generic = nullptr;
     for (const KEntry &e : g_kernels) {
         if (e.strategy != P.strategy || e.V != (int)P.V) continue;

@@ -55,9 +55,17 @@ CASCADE_MODES = [
 @pytest.mark.parametrize("mi", range(len(CASCADE_MODES)))
 @pytest.mark.parametrize("mean", [1, 4, 32, 300])
 def test_cascade_per_edge_modes(rs, mi, mean):
+    # 128 items per ensemble: the per-edge kernel specialised for the cascade's ops
     s = wl.cascade_stream(n_total=1 << 18, mean=mean, seed=7)
     st = _check(rs, wl.pipeline_cascade(), s, CASCADE_MODES[mi], outputs=("count", "sum"))
     assert st["items"][1] == 1 << 18
+
+
+@pytest.mark.parametrize("mi", [0, 5, 6])
+def test_cascade_per_edge_modes_generic_kernel(rs, mi):
+    # 64 items per ensemble: the generic per-edge kernel on the same stage list
+    s = wl.cascade_stream(n_total=1 << 17, mean=24, seed=8)
+    _check(rs, wl.pipeline_cascade(), s, CASCADE_MODES[mi], outputs=("count", "sum"), ensemble_width=64)
 
 
 @pytest.mark.parametrize("W", [32, 64, 128])
