@@ -404,6 +404,51 @@ def bench_modes(rs, torch, cascades):
     return res
 
 
+def bench_calibration(rs, torch, dev, peak, tag_ms_4096):
+    """The calibration kernel (rs_calibrate_cascade): the cascade's three filters, queues
+    and compaction on the bench's 2^26 elements as ONE region, with no region handling --
+    an upper bound for the pipeline kernels on these elements -- beside the tag kernel on
+    the same one-region stream and on the mean-4096 stream."""
+    el = dev["elements"]
+    n = int(el.numel())
+    pipe = wl.pipeline_cascade()
+    salts = [st[1] for st in pipe[1:4]]
+    thetas = [st[2] for st in pipe[1:4]]
+    ctx = 0x1234ABCD
+    out = torch.empty(2, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        rs.calibrate_cascade(el, ctx, salts, thetas, out=out)
+    ms = []
+    for _ in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rs.calibrate_cascade(el, ctx, salts, thetas, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    cal_ms = statistics.median(ms)
+    cal = out.cpu().numpy().astype(np.uint64)
+    # the tag kernel on the same elements as one region with the same context word
+    one = {"R": 1, "len": torch.tensor([n], dtype=torch.int32, device="cuda"), "offsets": None, "parents": None,
+           "elements": el, "ctx": torch.tensor([ctx - (1 << 32) if ctx >= 1 << 31 else ctx], dtype=torch.int32,
+                                               device="cuda"), "total_elements": n}
+    p = rs.Pipeline(pipe, strategy="tag")
+    o = p.submit(one, outputs=("count", "sum"))
+    p.autotune(trials=2)
+    one_ms, _ = _timed(p, torch, reps=5)
+    got = rs.results_to_numpy(o)
+    p.close()
+    b = 4 * n
+    return {"elements": n, "ctx": ctx,
+            "calibration_ms": cal_ms, "calibration_gbs": b / (cal_ms * 1e-3) / 1e9,
+            "calibration_frac_of_measured_hbm": b / (cal_ms * 1e-3) / 1e9 / peak,
+            "tag_kernel_one_region_ms": one_ms,
+            "tag_kernel_one_region_gbs": b / (one_ms * 1e-3) / 1e9,
+            "tag_kernel_mean4096_ms": tag_ms_4096,
+            "same_results": bool(int(cal[0]) == int(got["count"][0]) and int(cal[1]) == int(got["sum"][0]))}
+
+
 def bench_batched(rs, torch):
     """4,096 independent hashed streams (lognormal sizes): one persistent launch for all
     of them replayed from a CUDA graph, against one launch per stream."""
@@ -875,7 +920,9 @@ def main():
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        for name, fn in (("modes", lambda: bench_modes(rs, torch, [(m, s) for m, s in zip(MEANS, streams)
+        for name, fn in (("calibration", lambda: bench_calibration(rs, torch, pipes[MEANS.index(4096)]._keep[0][0], peak,
+                                                                   per_mean[MEANS.index(4096)]["timed_kernel_ms_median"])),
+                         ("modes", lambda: bench_modes(rs, torch, [(m, s) for m, s in zip(MEANS, streams)
                                                                   if m in (4, 32, 256)])),
                          ("graph_edges", lambda: bench_graph(rs, torch, peak)),
                          ("region_sizes", lambda: bench_region_sizes(rs, torch)),
@@ -917,8 +964,11 @@ def main():
             "clocks": sampler.summary(t_start, t_end),
             "e2e": e2e,
             "cpu_baseline": cpu,
-            # per run: planner + pipeline kernel, plus the finalize kernel for the signal strategy
-            "gpu_launches": sum(len(k) * (2 if t["strategy"] == 1 else 3) for k, t in zip(kernel_ms, tuned)),
+            # per run: the tag strategy's unit sums + group scan (loaded streams of mean under 8)
+            # or planner, and the pipeline kernel; the signal strategy's planner, pipeline
+            # kernel and finalize kernel
+            "gpu_launches": sum(len(k) * (3 if t["strategy"] != 1 or wl.n_elements(s) < 8 * s["R"] else 2)
+                                for k, t, s in zip(kernel_ms, tuned, streams)),
             **extras,
         }
         print(json.dumps(line), flush=True)

@@ -460,6 +460,22 @@ rs_status rs_server_destroy(rs_server *s);
  *   - rs_get_stats reads a caller workspace and does not apply to these runs. */
 rs_status rs_run_noalloc(rs_pipeline *p, rs_cuda_stream stream);
 
+/* ---- calibration ---------------------------------------------------------------- */
+
+/* A measurement aid, not part of the pipeline: the cascade's element arithmetic over ONE
+ * region with no region handling at all.  elements[0..n) (device memory, any alignment;
+ * 16-byte aligned arrays are read with vector loads) pass three filters in a row, each
+ * keeping x when (hash32(x, salts[i]) XOR ctx) < thetas[i] -- the context-hash filter of
+ * Section 5's cascade, every element under the one context word ctx -- with the ensemble
+ * queues and compaction of the pipeline kernels between them; out[0] (device, 8-byte
+ * aligned, two words) receives the survivors' count and out[1] their sum (zeroed first
+ * on `stream`).  The results equal a pipeline run on a stream of one region of n elements
+ * with context word ctx; the time bounds from above what the pipeline kernels can reach
+ * on the same elements.  salts and thetas are host arrays of 3.  RS_ERR_INVALID on a null
+ * or misaligned argument, RS_ERR_CUDA on a launch failure. */
+rs_status rs_calibrate_cascade(const uint32_t *elements, uint64_t n, uint32_t ctx, const uint32_t *salts,
+                               const uint32_t *thetas, uint64_t *out, rs_cuda_stream stream);
+
 /* ---- misc ---------------------------------------------------------------------- */
 
 const char *rs_status_string(rs_status s);

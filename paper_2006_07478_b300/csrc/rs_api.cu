@@ -351,6 +351,25 @@ const char *rs_status_string(rs_status s)
     return "unknown status";
 }
 
+rs_status rs_calibrate_cascade(const uint32_t *elements, uint64_t n, uint32_t ctx, const uint32_t *salts,
+                               const uint32_t *thetas, uint64_t *out, rs_cuda_stream stream)
+{
+    if (!out || !salts || !thetas || (n > 0 && !elements)) return RS_ERR_INVALID;
+    if (((uintptr_t)out & 7u) != 0) return RS_ERR_INVALID;
+    int dev = 0, n_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemsetAsync(out, 0, 2 * sizeof(uint64_t), (cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e);
+    if (n == 0) return RS_OK;
+    uint32_t c0[3];
+    for (int i = 0; i < 3; ++i) c0[i] = host_fmix32(salts[i] ^ RS_GOLD);
+    const int le = rs_launch_calib(elements, (unsigned long long)n, ctx, c0, thetas, (unsigned long long *)out, n_sm,
+                                   (void *)stream);
+    if (le != 0) return cuda_fail((cudaError_t)le);
+    return RS_OK;
+}
+
 int rs_last_cuda_error(void) { return g_last_cuda; }
 
 uint32_t rs_version(void) { return RS_VERSION; }
@@ -764,10 +783,12 @@ static SmemLayout make_tag_layout(const rs_pipeline *p, uint32_t cpl)
 #ifdef RS_PROFILE
     off += 8 * RS_PROF_SLOTS;
 #endif
-    L.o_cnt = (uint32_t)off;
-    off += 8 * 4 * RS_MAX_STAGES;
-    L.o_pend = (uint32_t)off;     // the next unit's description (7 words) and, at byte
-    off += 48;                    // 32, the 8-byte scratch slot of the ring stores
+    L.o_cnt = (uint32_t)off;      // 32-bit node statistics
+    off += 4 * 4 * RS_MAX_STAGES;
+    off = align_up(off, 16);
+    L.o_pend = (uint32_t)off;     // the next unit's description (7 words), at byte 32 the
+    off += 72;                    // 8-byte scratch slot of the ring stores, at byte 48 the
+                                  // aggregate's pending fold (3 words, the sum at byte 64)
     off = align_up(off, 16);
     L.o_scr = (uint32_t)off;      // window marks, hashed enumeration only (loaded
     off += p->stages[0].kind == RS_ENUM_LOAD ? 0 : (size_t)4 * W;   // elements: a staging slot)

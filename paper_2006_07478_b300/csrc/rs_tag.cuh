@@ -266,7 +266,15 @@ struct TagEngine {
     const uint32_t wb;   // this processor's byte offset in dynamic shared memory
     // shared-memory arrays: byte offsets from the kernel parameters, so only wb lives in
     // a register
-    __device__ __forceinline__ SArr<unsigned long long> cnt() const { return sarr<unsigned long long>(wb + P.L.o_cnt); }
+    // node statistics (32-bit per processor; a field about to pass 2^31 goes to the
+    // header's 64-bit counters at once)
+    __device__ __forceinline__ SArr<uint32_t> cnt() const { return sarr<uint32_t>(wb + P.L.o_cnt); }
+    // the aggregate's pending fold (lane 0): region (NONE: none), count, min, then the sum
+    __device__ __forceinline__ SArr<uint32_t> accw() const { return sarr<uint32_t>(wb + P.L.o_pend + 48); }
+    __device__ __forceinline__ SArr<unsigned long long> accs() const
+    {
+        return sarr<unsigned long long>(wb + P.L.o_pend + 64);
+    }
     __device__ __forceinline__ SArr<unsigned long long> nra() const { return sarr<unsigned long long>(wb + P.L.o_nra); }
     // ring slots {value, region tag}, 8 bytes each
     __device__ __forceinline__ SArr<uint2> rq() const { return sarr<uint2>(wb + P.L.o_qv); }
@@ -373,7 +381,16 @@ struct TagEngine {
 
     __device__ __forceinline__ void flush_counters()
     {
-        if (lane < 4 * RS_MAX_STAGES) cnt()[lane] += ctr;
+        if (lane < 4 * RS_MAX_STAGES) {
+            uint32_t v = cnt()[lane];
+            if (v + (unsigned long long)ctr >= (1ull << 31)) {
+                atomicAdd(&P.hdr->counters[lane], (unsigned long long)v + ctr);
+                v = 0;
+            } else {
+                v += ctr;
+            }
+            cnt()[lane] = v;
+        }
         ctr = 0;
     }
 
@@ -786,6 +803,41 @@ struct TagEngine {
         if (P.want_min) atomicMin(d.out_min + rr, mn);
     }
 
+    // One-region ensembles fold into the processor's pending fold (lane 0, shared memory),
+    // which goes to the region's outputs when an ensemble of another region arrives and
+    // before the processor changes stream or finishes: a region long enough to span many
+    // ensembles costs one atomic per output per processor and run of its ensembles, not
+    // one per ensemble (with one region in a whole stream, every processor's folds would
+    // otherwise meet on one address).  Deferring a fold keeps it after the region's
+    // identity result: the owner writes that when it loads the parent, before any item
+    // of it, and the planner before the kernel for a region two units share.
+    __device__ __forceinline__ void acc_add(uint32_t rr, uint32_t n, unsigned long long s, uint32_t mn) const
+    {
+        const uint32_t ar = accw()[0];
+        if (ar == rr) {
+            accw()[1] += n;
+            accs()[0] += s;
+            accw()[2] = min(accw()[2], mn);
+        } else {
+            if (ar != NONE) fold(ar, accw()[1], accs()[0], accw()[2]);
+            accw()[0] = rr;
+            accw()[1] = n;
+            accs()[0] = s;
+            accw()[2] = mn;
+        }
+    }
+
+    // the pending fold to the outputs (warp-collective; lane 0 holds it)
+    __device__ __forceinline__ void acc_flush() const
+    {
+        if (lane == 0) {
+            const uint32_t ar = accw()[0];
+            if (ar != NONE) fold(ar, accw()[1], accs()[0], accw()[2]);
+            accw()[0] = NONE;
+        }
+        __syncwarp();
+    }
+
     // one emitted value at position pos of the stream's value array (bounds-checked)
     __device__ __forceinline__ void put_value(const DevStream &d, unsigned long long pos, uint32_t v) const
     {
@@ -859,7 +911,7 @@ struct TagEngine {
                 hi = __reduce_add_sync(FULLMASK, hi);
             }
             if (P.want_min) mn = __reduce_min_sync(FULLMASK, mn);
-            if (lane == 0 && n_valid) fold(r0, n_valid, ((unsigned long long)hi << 16) + lo, mn);
+            if (lane == 0 && n_valid) acc_add(r0, n_valid, ((unsigned long long)hi << 16) + lo, mn);
         } else {
             // runs of equal tags within the lane (tags never decrease along the lane's items)
             uint32_t cr = NONE, cn = 0, cm = NONE;
@@ -1364,6 +1416,7 @@ __global__ void __launch_bounds__(256, (V <= 4 ? 3 : 2)) rs_tag_kernel(const __g
     const uint32_t wb = warp * P.L.per_warp;
     TagEngine<V, SG, CPL> E(P, lane, wb);
     if (lane < 4 * RS_MAX_STAGES) E.cnt()[lane] = 0;
+    if (lane == 0) E.accw()[0] = NONE;
     __syncwarp();
 
     uint32_t t = 0;
@@ -1378,6 +1431,7 @@ __global__ void __launch_bounds__(256, (V <= 4 ? 3 : 2)) rs_tag_kernel(const __g
         if (u.work) {
             if (u.stream != E.sidx) {
                 E.drain_all();
+                E.acc_flush();
                 E.set_stream(u.stream);
             }
             const uint32_t ownf =
@@ -1387,6 +1441,7 @@ __global__ void __launch_bounds__(256, (V <= 4 ? 3 : 2)) rs_tag_kernel(const __g
             // a unit with no elements: only its parents' identity results
             if (u.stream != E.sidx) {
                 E.drain_all();
+                E.acc_flush();
                 E.set_stream(u.stream);
             }
             const uint32_t lo = u.rs + (u.skip_head ? 1u : 0u);
@@ -1396,12 +1451,13 @@ __global__ void __launch_bounds__(256, (V <= 4 ? 3 : 2)) rs_tag_kernel(const __g
         u = E.next_unit();
     }
     if (!E.stop) E.drain_all();
+    E.acc_flush();
     E.flush_counters();
 
     __syncwarp();
     if (lane == 0) {
         atomicAdd(&P.hdr->units, units);
-        for (int i = 0; i < 4 * P.n_stages; ++i) atomicAdd(&P.hdr->counters[i], E.cnt()[i]);
+        for (int i = 0; i < 4 * P.n_stages; ++i) atomicAdd(&P.hdr->counters[i], (unsigned long long)E.cnt()[i]);
     }
 }
 

@@ -55,7 +55,8 @@ EXPORTS = [
     "rs_fetch_region_results", "rs_stream_upload", "rs_get_stats", "rs_graph_capture", "rs_graph_launch",
     "rs_graph_release", "rs_autotune", "rs_timing_enable", "rs_timing_read", "rs_run_noalloc",
     "rs_server_create", "rs_server_set_slice_units", "rs_server_submit", "rs_server_progress", "rs_server_poll", "rs_server_get_stats",
-    "rs_server_destroy", "rs_status_string", "rs_last_cuda_error", "rs_version", "rs_struct_sizes",
+    "rs_server_destroy", "rs_calibrate_cascade", "rs_status_string", "rs_last_cuda_error", "rs_version",
+    "rs_struct_sizes",
 ]
 # the ctypes mirrors, in the order rs_struct_sizes reports the C structs' sizes
 _MIRRORS = ("StageDesc", "Opts", "StreamDesc", "RegionResults", "Stats", "Request", "ServerStats")
@@ -201,6 +202,7 @@ def lib(build_if_missing: bool = True):
             "rs_server_poll": ([P, ctypes.POINTER(U64), U32, ctypes.POINTER(U32)], ctypes.c_int),
             "rs_server_get_stats": ([P, ctypes.POINTER(ServerStats)], ctypes.c_int),
             "rs_server_destroy": ([P], ctypes.c_int),
+            "rs_calibrate_cascade": ([P, U64, U32, ctypes.POINTER(U32), ctypes.POINTER(U32), P, P], ctypes.c_int),
             "rs_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "rs_last_cuda_error": ([], ctypes.c_int),
             "rs_version": ([], U32),
@@ -523,6 +525,20 @@ class Pipeline:
         check(lib().rs_autotune(self._h, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _cur_stream(), trials,
                                 ctypes.byref(best), ctypes.byref(ms)), "rs_autotune")
         return best.as_dict(), float(ms.value)
+
+
+def calibrate_cascade(elements, ctx: int, salts, thetas, out=None):
+    """rs_calibrate_cascade: the cascade's three context-hash filters over ONE region of
+    `elements` (a CUDA uint32/int32 tensor), no region handling; a measurement aid.  Returns
+    the device int64 tensor [count, sum] (filled asynchronously on the current stream)."""
+    import torch
+    if out is None:
+        out = torch.empty(2, dtype=torch.int64, device=elements.device)
+    s3 = (ctypes.c_uint32 * 3)(*[int(v) & 0xFFFFFFFF for v in salts])
+    t3 = (ctypes.c_uint32 * 3)(*[int(v) & 0xFFFFFFFF for v in thetas])
+    check(lib().rs_calibrate_cascade(_ptr(elements), int(elements.numel()), int(ctx) & 0xFFFFFFFF, s3, t3,
+                                     _ptr(out), _cur_stream()), "rs_calibrate_cascade")
+    return out
 
 
 class Server:

@@ -138,6 +138,16 @@ def test_stream_submit_validation_and_workspace_size():
     assert L.rs_pipeline_destroy(h) == rs.RS_OK
 
 
+def test_calibration_argument_checks_without_gpu():
+    L = rs.lib()
+    s3 = (ctypes.c_uint32 * 3)(1, 2, 3)
+    # no output array, or elements missing for n > 0: argument errors before any CUDA call
+    assert L.rs_calibrate_cascade(None, 0, 0, s3, s3, None, None) == rs.RS_ERR_INVALID
+    assert L.rs_calibrate_cascade(None, 10, 0, s3, s3, ctypes.c_void_p(0x1000), None) == rs.RS_ERR_INVALID
+    assert L.rs_calibrate_cascade(ctypes.c_void_p(0x2000), 10, 0, s3, s3, ctypes.c_void_p(0x1004), None) == \
+        rs.RS_ERR_INVALID
+
+
 def test_opts_round_trip():
     p = rs.Pipeline(wl.pipeline_cascade(), strategy="signal", queue_capacity=512, regions_per_unit=16)
     o = p.opts
