@@ -668,6 +668,28 @@ def run_case(args, rs, torch):
     """One stream, one fixed strategy: warm-up launches then `steps` timed launches.
     Used to give profilers a small, fixed launch sequence."""
     parts = args.case.split(":")
+    if parts[0] == "calib":
+        # the calibration kernel on 2^lg elements of the cascade stream: calib:lg
+        n = 1 << int(parts[1])
+        el = rs.to_device(wl.cascade_stream(n_total=n, mean=4096, seed=SEED))["elements"]
+        pipe = wl.pipeline_cascade()
+        salts, thetas = [st[1] for st in pipe[1:4]], [st[2] for st in pipe[1:4]]
+        out = torch.empty(2, dtype=torch.int64, device="cuda")
+        stream = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            rs.calibrate_cascade(el, 0x1234ABCD, salts, thetas, out=out)
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs.calibrate_cascade(el, 0x1234ABCD, salts, thetas, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        kms = statistics.median(ms)
+        print(json.dumps({"case": args.case, "n": n, "kernel_ms": kms, "items_per_s": n / (kms * 1e-3),
+                          "gbs": 4 * n / (kms * 1e-3) / 1e9, "result": out.cpu().tolist()}), flush=True)
+        return
     mean, strat = float(parts[0]), parts[1]
     n = 1 << int(parts[2]) if len(parts) > 2 and parts[2] else N_ELEM
     opts = {}

@@ -80,6 +80,8 @@ struct CalibWarp {
         }
     }
 
+    // node 1 on window w (FULL: all of its 128 positions hold elements)
+    template <bool FULL>
     __device__ __forceinline__ void node1(const uint4 v, unsigned long long w)
     {
         const uint32_t x[4] = {v.x, v.y, v.z, v.w};
@@ -87,7 +89,7 @@ struct CalibWarp {
         bool k[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            k[i] = e + i < P.n && (hash_c(x[i], P.c0s[0], P.m16, P.m19) ^ P.ctx) < P.theta[0];
+            k[i] = (FULL || e + i < P.n) && (hash_c(x[i], P.c0s[0], P.m16, P.m19) ^ P.ctx) < P.theta[0];
         push(q1, t1, x, k);
     }
 
@@ -158,7 +160,8 @@ __global__ void __launch_bounds__(256, 4) rs_calib_kernel(const __grid_constant_
         const uint4 cur = v0;
         v0 = v1;
         v1 = w + 2 * tw < nwin ? load_window(P, w + 2 * tw, lane, vec) : make_uint4(0u, 0u, 0u, 0u);
-        C.node1(cur, w);
+        if ((w + 1) * CW <= P.n) C.node1<true>(cur, w);
+        else C.node1<false>(cur, w);
         __syncwarp();
         C.pump();
     }

@@ -344,6 +344,9 @@ __device__ __forceinline__ unsigned long long plan_div(unsigned long long x, uin
     return x / d;
 }
 
+// a parent with more unit starts than this has its unit records written by the whole warp
+constexpr unsigned long long PLAN_HEAVY = 4;
+
 template <bool POW2, int PLAN_ROUNDS>
 __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KParams P)
 {
@@ -466,6 +469,7 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
             const unsigned long long xa = rem + (unsigned long long)c * rloc + offl;
             const unsigned long long xb = xa + (unsigned long long)c * nl + ls[k];
             unsigned long long m = plan_div<POW2>(xa, D, dsh);
+            uint32_t heavy = 0;   // bit j: parent j holds more than PLAN_HEAVY unit starts
             if (nl && plan_div<POW2>(xb, D, dsh) > m) {
                 unsigned long long x = xa;
                 uint32_t off = offl;
@@ -474,6 +478,12 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
                     if ((uint32_t)j < nl) {
                         const uint32_t Lr = L[k][j];
                         const unsigned long long xn = x + c + Lr;
+                        const unsigned long long mend = plan_div<POW2>(xn, D, dsh);
+                        if (mend - m > PLAN_HEAVY) {
+                            // many units start inside this parent: the warp writes them below
+                            heavy |= 1u << j;
+                            m = mend;
+                        }
                         while ((m + 1) * D <= xn) {
                             ++m;
                             const unsigned long long u = qt + m;
@@ -502,6 +512,51 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(const __grid_constant__ KP
                         x = xn;
                         off += Lr;
                     }
+                }
+            }
+            // the parents with many unit starts (a region much longer than a unit): the
+            // whole warp writes each one's records, one per lane, instead of its lane alone
+            for (uint32_t hv = __ballot_sync(FULLMASK, heavy != 0); hv; hv &= hv - 1) {
+                const uint32_t src = __ffs(hv) - 1;
+                const uint32_t hs = __shfl_sync(FULLMASK, heavy, src);
+                unsigned long long xj = xa;
+                uint32_t offj = offl;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t Lj = L[k][j];
+                    const unsigned long long xs = __shfl_sync(FULLMASK, xj, src);
+                    const uint32_t os = __shfl_sync(FULLMASK, offj, src);
+                    const uint32_t Ls = __shfl_sync(FULLMASK, Lj, src);
+                    if ((hs >> j) & 1u) {
+                        const unsigned long long m0 = plan_div<POW2>(xs, D, dsh);
+                        const unsigned long long me = plan_div<POW2>(xs + c + Ls, D, dsh);
+                        const uint32_t rj = r_lo + 128u * k + 4u * src + j;
+                        const uint32_t oa = base_abs + E + os;
+                        for (unsigned long long mm = m0 + 1 + lane; mm <= me; mm += 32) {
+                            const unsigned long long u = qt + mm;
+                            if (u > S.slot_units) {
+                                bad = true;
+                                break;
+                            }
+                            const long long into = (long long)(mm * D) - (long long)(xs + c);
+                            const uint32_t je = (uint32_t)(into <= 0 ? 0 : (into >= (long long)Ls ? Ls : into));
+                            UnitRec rc;
+                            rc.i = rj + 1;
+                            rc.j = oa + je;
+                            rc.head_off = oa;
+                            rc.first_off = oa + Ls;
+                            S.rec[u] = rc;
+                            // the first unit start decides whether a unit starts inside the
+                            // region (only the last can start exactly at its end)
+                            if (P.plan_fill && mm == m0 + 1 && je < Ls) {
+                                if (P.want_count) S.out_count[rj] = 0u;
+                                if (P.want_sum) S.out_sum[rj] = 0ull;
+                                if (P.want_min) S.out_min[rj] = 0xFFFFFFFFu;
+                            }
+                        }
+                    }
+                    xj += c + Lj;
+                    offj += Lj;
                 }
             }
             pre += __shfl_sync(FULLMASK, incl[k], 31);

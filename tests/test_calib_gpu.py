@@ -43,9 +43,34 @@ def test_calibration_equals_one_region_pipeline(rs, n, offset):
     got = out.cpu().numpy().astype(np.uint64)
     assert int(got[0]) == int(want["count"][0]) and int(got[1]) == int(want["sum"][0]), (got, want)
     if n >= 1 << 20:
-        # the pipeline kernel on the same one-region stream agrees
-        res, st = rs.run_stream(pipe, _one_region(el, ctx), strategy="tag", outputs=("count", "sum"))
-        assert int(res["count"][0]) == int(got[0]) and int(res["sum"][0]) == int(got[1])
+        # the pipeline kernels on the same one-region stream agree: one region spans
+        # hundreds of work units, whose records the planner's warp writes together
+        for strategy in ("tag", "signal"):
+            res, st = rs.run_stream(pipe, _one_region(el, ctx), strategy=strategy, outputs=("count", "sum"))
+            assert st["device_status"] == 0, st
+            assert int(res["count"][0]) == int(got[0]) and int(res["sum"][0]) == int(got[1]), strategy
+
+
+@pytest.mark.parametrize("strategy", ["tag", "signal"])
+def test_long_regions_among_short_ones(rs, strategy):
+    """Regions of up to 2^18 elements (hundreds of units each) between short ones, as
+    lengths and as CSR offsets: the planner writes a long region's unit records with the
+    whole warp, a short one's with its lane."""
+    rng = np.random.default_rng(17)
+    L = rng.integers(0, 40, size=3000).astype(np.uint32)
+    L[[5, 6, 700, 2999]] = [1 << 18, 100_000, 77_777, 1 << 17]
+    el = wl.cascade_stream(n_total=int(L.sum()), mean=4096, seed=6)["elements"]
+    ctx = rng.integers(0, 1 << 32, size=L.shape[0], dtype=np.uint64).astype(np.uint32)
+    s = wl.make_stream(L, elements=el, ctx=ctx)
+    pipe = wl.pipeline_cascade()
+    want = oracle.run(pipe, s)
+    off = np.concatenate(([0], np.cumsum(L.astype(np.int64)))).astype(np.uint32)
+    for stream in (s, wl.make_stream(offsets=off, elements=el, ctx=ctx)):
+        for rpu in ((64, 1024) if strategy == "tag" else (64, 256)):
+            res, st = rs.run_stream(pipe, stream, strategy=strategy, outputs=("count", "sum"), regions_per_unit=rpu)
+            assert st["device_status"] == 0, st
+            for k in ("count", "sum"):
+                assert np.array_equal(res[k], want[k]), (k, rpu)
 
 
 def test_calibration_argument_checks(rs):
