@@ -778,7 +778,7 @@ __device__ __forceinline__ uint32_t parent_at(const Smem &M, uint32_t from, uint
         if (lane == 0) M.cnt[4 * (node) + (field)] += (unsigned long long)(v); \
     } while (0)
 
-template <int STRAT, int V, class S, bool MIX = false>
+template <int STRAT, int V, class S, bool MIX = false, int UM = -1>
 struct Proc {
     static constexpr uint32_t W = 32u * V;   // ensemble width (items per firing)
     const KParams &P;
@@ -814,11 +814,16 @@ struct Proc {
 
     // How region boundaries reach node c over its input edge, and the topology.  Without
     // MIX every edge carries signals (tags for STRAT == TAG) along a linear pipeline; the
-    // per-edge kernel (MIX) reads both from the parameters.
+    // per-edge kernel (MIX) reads both from the parameters, except that a per-edge kernel
+    // compiled for one mode on every edge (UM >= 0) has it at compile time.
     __device__ __forceinline__ uint32_t emode(int c) const
     {
-        if constexpr (MIX) return P.emode[c];
-        else return STRAT == RS_STRATEGY_TAG ? EM_TAG : EM_SIG;
+        if constexpr (MIX) {
+            if constexpr (UM >= 0) return (uint32_t)UM;
+            else return P.emode[c];
+        } else {
+            return STRAT == RS_STRATEGY_TAG ? EM_TAG : EM_SIG;
+        }
     }
     __device__ __forceinline__ uint32_t kids(int i) const { return P.kids[i]; }     // MIX only
     __device__ __forceinline__ bool is_sink(int i) const { return P.sink_of[i] != 0xFFu; }   // MIX only
@@ -2091,7 +2096,7 @@ struct Proc {
 
 // ---------------------------------------------------------------------------
 
-template <int STRAT, int V, class SG, bool MIX = false>
+template <int STRAT, int V, class SG, bool MIX = false, int UM = -1>
 __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_constant__ KParams P)
 {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -2244,7 +2249,7 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
         PROF_ADD(PF_SETUP, pt_setup);
         bool pstop;
         {
-            Proc<STRAT, V, SG, MIX> pr(P, M, w, g, lane);
+            Proc<STRAT, V, SG, MIX, UM> pr(P, M, w, g, lane);
             pr.nxt = pend;
             pr.nxt_open = nxt.u.valid && !nxt.scanned;
             pr.nk = nk;
@@ -2337,10 +2342,11 @@ __global__ void __launch_bounds__(256, 2) rs_pipeline_kernel(const __grid_consta
 struct KEntry {
     int strategy, V, oe, o1, o2, o3, o4;
     const void *fn;
+    int um;   // per-edge kernels: the mode of every edge, compiled in (-1: read per edge)
 };
 
 #define RS_KSIG(ST, V, OE, O1, O2, O3, O4) \
-    {ST, V, OE, O1, O2, O3, O4, (const void *)rs_pipeline_kernel<ST, V, Sig<OE, O1, O2, O3, O4>>}
+    {ST, V, OE, O1, O2, O3, O4, (const void *)rs_pipeline_kernel<ST, V, Sig<OE, O1, O2, O3, O4>>, -1}
 #define RS_KALLV(ST, OE, O1, O2, O3, O4) \
     RS_KSIG(ST, 1, OE, O1, O2, O3, O4), RS_KSIG(ST, 2, OE, O1, O2, O3, O4), RS_KSIG(ST, 4, OE, O1, O2, O3, O4)
 #define RS_KBOTH(OE, O1, O2, O3, O4) RS_KALLV(RS_STRATEGY_SIGNAL, OE, O1, O2, O3, O4)
@@ -2348,9 +2354,12 @@ struct KEntry {
 // the per-edge kernel (boundary modes per edge, tree topologies): generic ops, and the
 // workloads' linear pipelines at 128 items per ensemble specialised (the generic one's
 // code overflows the instruction cache)
-#define RS_KMIX(V) {-1, V, 0, 0, 0, 0, 0, (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, V, GenericSig, true>}
+#define RS_KMIX(V) {-1, V, 0, 0, 0, 0, 0, (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, V, GenericSig, true>, -1}
 #define RS_KMIXS(V, OE, O1, O2, O3, O4) \
-    {-1, V, OE, O1, O2, O3, O4, (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, V, Sig<OE, O1, O2, O3, O4>, true>}
+    {-1, V, OE, O1, O2, O3, O4, (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, V, Sig<OE, O1, O2, O3, O4>, true>, -1}
+#define RS_KMIXU(V, UM, OE, O1, O2, O3, O4)                                                                          \
+    {-1, V, OE, O1, O2, O3, O4, (const void *)rs_pipeline_kernel<RS_STRATEGY_SIGNAL, V, Sig<OE, O1, O2, O3, O4>, true, UM>, \
+     UM}
 
 static const KEntry g_kernels[] = {
     RS_KMIX(1), RS_KMIX(2), RS_KMIX(4),
@@ -2358,6 +2367,9 @@ static const KEntry g_kernels[] = {
     // filters and a multiply-add map)
     RS_KMIXS(4, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),
     RS_KMIXS(4, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_MAP_MULADD, 0),
+    // ... with per-lane selection on every edge
+    RS_KMIXU(4, EM_LANE, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),
+    RS_KMIXU(4, EM_LANE, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_MAP_MULADD, 0),
     // loaded elements -> three context hash filters -> aggregate
     RS_KBOTH(D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),
     // hashed elements -> power-of-two modulus filter -> multiply-add map -> aggregate
@@ -2377,14 +2389,22 @@ static const void *kernel_ptr(const KParams &P)
         // a specialised per-edge kernel serves a linear pipeline ending in the aggregate
         bool linear = P.n_sinks <= 1 && !P.emit;
         for (int i = 1; i < P.n_stages; ++i) linear = linear && P.up[i] == i - 1;
-        const void *generic = nullptr;
+        // one mode on every edge: the kernel compiled for it, if any
+        int um = P.n_stages > 1 ? (int)P.emode[1] : -1;
+        for (int i = 2; i < P.n_stages; ++i)
+            if ((int)P.emode[i] != um) um = -1;
+        const void *generic = nullptr, *spec = nullptr;
         for (const KEntry &e : g_kernels) {
             if (e.strategy != -1 || e.V != (int)P.V) continue;
-            if (e.oe == 0) generic = e.fn;
-            else if (linear && e.oe == ops[0] && e.o1 == ops[1] && e.o2 == ops[2] && e.o3 == ops[3] && e.o4 == ops[4])
-                return e.fn;
+            if (e.oe == 0) {
+                generic = e.fn;
+            } else if (linear && e.oe == ops[0] && e.o1 == ops[1] && e.o2 == ops[2] && e.o3 == ops[3] &&
+                       e.o4 == ops[4]) {
+                if (e.um >= 0 && e.um == um) return e.fn;
+                if (e.um < 0) spec = e.fn;
+            }
         }
-        return generic;
+        return spec ? spec : generic;
     }
     if (P.strategy == RS_STRATEGY_TAG) return rs_tag_kernel_entry(P);
     const void *generic = nullptr;
