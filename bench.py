@@ -638,6 +638,9 @@ def bench_serving(rs, torch, seconds: float, rate: float = 20000.0, arena_gb: fl
             "p99_ms_requests_up_to_median_size": float(np.percentile(Ls, 99)) if len(Ls) else None,
             "max_ms": float(L.max()) if len(L) else None,
             "over_5ms": int((L > 5.0).sum()) if len(L) else 0,
+            # completions of the requests over 5 ms, grouped by the 10-ms window they landed
+            # in: few windows mean host stalls that delayed many requests at once
+            "over_5ms_windows": int(len({int((x[0] + x[1]) * 100) for x in lat if x[1] > 5e-3})),
             "host_cpu": {"quota": cgroup_cpu_quota(),
                          "throttled_periods": (thr1.get("nr_throttled", 0) - thr0.get("nr_throttled", 0)) if thr0 else None,
                          "throttled_ms": ((thr1.get("throttled_usec", 0) - thr0.get("throttled_usec", 0)) / 1e3) if thr0 else None},

@@ -1151,6 +1151,33 @@ static uint64_t balanced_units(const rs_pipeline *p, int strategy, const Topo &t
     return r * procs;
 }
 
+// Room for n streams in the pinned host copy of the stream table, grown to a power of two
+// (at least 16): freeing page-locked memory waits for the device, so it happens seldom.
+static rs_status reserve_table(rs_pipeline *p, size_t n)
+{
+    if (p->table_cap >= n) return RS_OK;
+    cudaError_t e;
+    if (p->upload_pending) {
+        if ((e = cudaEventSynchronize(p->upload_done)) != cudaSuccess) return cuda_fail(e);
+        p->upload_pending = false;
+    }
+    if (p->table_host) cudaFreeHost(p->table_host);
+    p->table_host = nullptr;
+    p->table_cap = 0;
+    p->table_dirty = true;
+    size_t cap = 16;
+    while (cap < n) cap <<= 1;
+    if ((e = cudaMallocHost((void **)&p->table_host, cap * sizeof(DevStream))) != cudaSuccess) return cuda_fail(e);
+    p->table_cap = cap;
+    return RS_OK;
+}
+
+rs_status rs_pipeline_reserve_streams(rs_pipeline *p, uint64_t n_streams)
+{
+    if (!p) return RS_ERR_INVALID;
+    return reserve_table(p, (size_t)n_streams);
+}
+
 static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *out)
 {
     if (!p || !ws) return RS_ERR_INVALID;
@@ -1293,13 +1320,8 @@ static rs_status prepare(rs_pipeline *p, void *ws, uint64_t ws_bytes, Launch *ou
             p->upload_pending = false;
         }
         if (p->table_cap < ns) {
-            if (p->table_host) cudaFreeHost(p->table_host);
-            p->table_host = nullptr;
-            p->table_cap = 0;
-            size_t cap = ns < 16 ? 16 : ns;
-            if ((e = cudaMallocHost((void **)&p->table_host, cap * sizeof(DevStream))) != cudaSuccess)
-                return cuda_fail(e);
-            p->table_cap = cap;
+            const rs_status rst = reserve_table(p, ns);
+            if (rst != RS_OK) return rst;
         }
         fill_table(p, pl.sp.data(), ns, (unsigned char *)ws, p->table_host);
         p->table_in_ws = nullptr;

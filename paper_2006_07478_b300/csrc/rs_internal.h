@@ -205,6 +205,9 @@ rs_status rs_run_workspace_bytes(const rs_pipeline *p, uint64_t *bytes);
 int rs_launch_kernel(const KParams &P, int grid, int block, size_t smem, void *stream);
 int rs_launch_planner(const KParams &P, int grid, void *stream);
 int rs_launch_unit_offsets(const KParams &P, int grid, void *stream);   // fixed-parent units' offsets
+// pinned room for the stream table of n streams, ahead of the first run that needs it
+// (the server reserves its batch size, so no run frees page-locked memory mid-stream)
+rs_status rs_pipeline_reserve_streams(rs_pipeline *p, uint64_t n_streams);
 // the calibration kernel (rs_calib.cu): the cascade's element arithmetic over one region
 int rs_launch_calib(const uint32_t *elements, unsigned long long n, uint32_t ctx, const uint32_t c0[3],
                     const uint32_t theta[3], unsigned long long *out, int n_sm, void *stream);

@@ -319,6 +319,12 @@ static rs_status launch_slice(rs_server *s)
     } else {
         rs_status st = rs_pipeline_create(s->st, s->n_stages, &s->opts, &b.p);
         if (st != RS_OK) return st;
+        // the stream table's pinned copy for a whole batch now, not grown mid-stream
+        st = rs_pipeline_reserve_streams(b.p, s->max_batch);
+        if (st != RS_OK) {
+            rs_pipeline_destroy(b.p);
+            return st;
+        }
     }
     std::vector<size_t> members;
     uint64_t need_round = 0;
