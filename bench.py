@@ -984,7 +984,8 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                          "frac_of_8tbs_spec": achieved / SPEC_HBM_GBS,
                          "kernel": "planner + pipeline kernel (rs_tag_kernel for the tag strategy) of "
-                                   "every run in the timed region"},
+                                   "every run in the timed region",
+                         "kernel_source": kernel_source_hash()},
             "per_mean": per_mean,
             "clocks": sampler.summary(t_start, t_end),
             "e2e": e2e,
