@@ -24,9 +24,12 @@
 //     max-scan of these marks gives every position its parent.
 //   * Nodes 2.. fire on full ensembles of W items taken from shared-memory rings of
 //     64-bit {value, region} slots (Section 2.1's queues; a node fires only when its
-//     output ring can take W times its maximum fan-out, Section 3.2).  The 0..k outputs
-//     of an ensemble are compacted by one warp scan of the lanes' output counts, in
-//     item order, so tags never decrease along a ring.
+//     output ring can take W times its maximum fan-out, Section 3.2).  The 0..1 outputs
+//     of a filter or map are compacted slot by slot: each of the lane's V item slots is
+//     placed by its own ballot, so a ring holds an ensemble's kept items in slot-major
+//     order (an expansion's 0..k outputs keep item order, by one warp scan of the lanes'
+//     output counts).  Tags along a ring are therefore not ordered; a one-region ensemble
+//     is recognised by a warp vote.
 //   * The aggregate (Section 4.2's begin/run/end per parent) folds each ensemble into
 //     the region outputs with integer reductions: one per ensemble when it holds a
 //     single region, otherwise one per run of equal tags in a lane.  count, sum and min
@@ -93,21 +96,6 @@ __device__ __forceinline__ uint32_t scan_add(uint32_t v)
             : "r"(d));
     }
     return v;
-}
-
-// exclusive warp prefix sum of a small per-lane count c < 2^NB: each bit of c is one
-// ballot, and the prefix is the weighted popcount of the lower lanes' bits.
-// The NB chains are independent, so the latency is that of one ballot and one popcount
-// instead of five dependent shuffles.
-template <int NB>
-__device__ __forceinline__ void prefix_small(uint32_t c, uint32_t lt, uint32_t &ex)
-{
-    ex = 0;
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const uint32_t m = __ballot_sync(FULLMASK, (c >> b) & 1u);
-        ex += (uint32_t)__popc(m & lt) << b;
-    }
 }
 
 // inclusive warp scan (max); a lane with no source lane gets its own value back,
@@ -673,73 +661,27 @@ struct TagEngine {
         }
     }
 
-    // Append kept items to the ring of edge I in item order.  The lane's V items form NG
-    // groups of GV; items of group g follow all lanes' items of group g - 1.  One warp
-    // scan of the lanes' group counts (16-bit fields) places them all.  When the run of
-    // slots does not wrap past the ring's end (the common case), slots are written with
-    // one index increment each.
-    template <int I, int NG, int GV>
+    // Append kept items to the ring of edge I, slot by slot: the kept items of slot j of
+    // all lanes take the next consecutive slots, in lane order, placed by one ballot (the
+    // lanes' earlier kept items of that slot) and one popcount (all of them).  The caller
+    // guarantees room for W items.
+    template <int I>
     __device__ __forceinline__ void push(const bool (&keep)[V], const uint32_t (&y)[V], const uint32_t (&r)[V])
     {
-        const uint32_t rb = (I - 1) * C();
-        uint32_t c = 0;
+        const uint32_t lt = lanemask_lt();
+        const uint32_t qb = smem_addr(rq().ptr()) + 8u * (I - 1) * C();
+        const uint32_t cm = CM();
+        uint32_t t = qt[I];
 #pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            uint32_t m = 0;
-#pragma unroll
-            for (int i = 0; i < GV; ++i) m |= (keep[g * GV + i] ? 1u : 0u) << i;
-            c += (uint32_t)__popc(m) << (16 * g);
-        }
-        uint32_t ex, tot;
-        if constexpr (NG == 1 && GV <= 7) {
-            // a count of at most 7: bit-sliced ballots give the prefix, one shuffle the total
-            prefix_small<GV <= 1 ? 1 : (GV <= 3 ? 2 : 3)>(c, lanemask_lt(), ex);
-            tot = __shfl_sync(FULLMASK, ex + c, 31);
-        } else {
-            const uint32_t incl = scan_add(c);
-            tot = __shfl_sync(FULLMASK, incl, 31);
-            ex = incl - c;
-        }
-        const uint32_t s0 = qt[I] & CM();
-        uint32_t n = 0;
-#pragma unroll
-        for (int g = 0; g < NG; ++g) n += (tot >> (16 * g)) & 0xFFFFu;
-        if (s0 + n <= C()) {
-            // kept items take consecutive slots (one 8-byte store of {value, tag} each); the
-            // others are written to a scratch slot of the processor (never read), so the
-            // stores need no branch or predicate
-            const uint32_t qb = smem_addr(rq().ptr());
-            const uint32_t trash = smem_addr(nxs().ptr() + 8);
-            uint32_t gb = rb + s0;
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                uint32_t off = 8u * (gb + ((ex >> (16 * g)) & 0xFFFFu));
-#pragma unroll
-                for (int i = 0; i < GV; ++i) {
-                    const int j = g * GV + i;
-                    const uint32_t qa = keep[j] ? qb + off : trash;
-                    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(qa), "r"(y[j]), "r"(r[j]) : "memory");
-                    off += keep[j] ? 8u : 0u;
-                }
-                gb += (tot >> (16 * g)) & 0xFFFFu;
+        for (int j = 0; j < V; ++j) {
+            const uint32_t b = __ballot_sync(FULLMASK, keep[j]);
+            if (keep[j]) {
+                const uint32_t qa = qb + 8u * ((t + __popc(b & lt)) & cm);
+                asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(qa), "r"(y[j]), "r"(r[j]) : "memory");
             }
-        } else {
-            uint32_t gb = s0;
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                uint32_t pos = gb + ((ex >> (16 * g)) & 0xFFFFu);
-#pragma unroll
-                for (int i = 0; i < GV; ++i) {
-                    const int j = g * GV + i;
-                    if (keep[j]) {
-                        rq()[rb + (pos & CM())] = make_uint2(y[j], r[j]);
-                        ++pos;
-                    }
-                }
-                gb += (tot >> (16 * g)) & 0xFFFFu;
-            }
+            t += __popc(b);
         }
-        qt[I] += n;
+        qt[I] = t;
     }
 
     // node I's kept items: into the ring of edge I, or, when node I is the last node
@@ -757,7 +699,7 @@ struct TagEngine {
             aggregate(y, r, keep, uni, r0, n);
             count_firing(I + 1, 1u, n);
         } else {
-            push<I, NG, GV>(keep, y, r);
+            push<I>(keep, y, r);
         }
     }
 
@@ -913,7 +855,8 @@ struct TagEngine {
             if (P.want_min) mn = __reduce_min_sync(FULLMASK, mn);
             if (lane == 0 && n_valid) acc_add(r0, n_valid, ((unsigned long long)hi << 16) + lo, mn);
         } else {
-            // runs of equal tags within the lane (tags never decrease along the lane's items)
+            // runs of equal consecutive tags among the lane's items (any order of regions:
+            // the reductions commute)
             uint32_t cr = NONE, cn = 0, cm = NONE;
             unsigned long long cs = 0;
 #pragma unroll
@@ -1207,12 +1150,13 @@ struct TagEngine {
         }
 #pragma unroll
         for (int j = 0; j < V; ++j) valid[j] = FULL || V * lane + j < take;
-        // tags never decrease along a ring: equal first and last tags mean one region
+        // one region: every valid item carries the first item's tag (a warp vote; tags along
+        // a ring are in slot-major order of each pushed ensemble, not sorted)
         r0 = __shfl_sync(FULLMASK, r[0], 0);
-        uint32_t rl;
-        if (FULL) rl = __shfl_sync(FULLMASK, r[V - 1], 31);
-        else rl = rq()[rb + ((h + take - 1) & CM())].y;
-        uni = r0 == rl;
+        bool same = true;
+#pragma unroll
+        for (int j = 0; j < V; ++j) same = same && (!valid[j] || r[j] == r0);
+        uni = __all_sync(FULLMASK, same);
     }
 
     template <int I, bool FULL>
