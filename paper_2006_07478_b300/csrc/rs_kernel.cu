@@ -825,8 +825,30 @@ struct Proc {
             return STRAT == RS_STRATEGY_TAG ? EM_TAG : EM_SIG;
         }
     }
-    __device__ __forceinline__ uint32_t kids(int i) const { return P.kids[i]; }     // MIX only
-    __device__ __forceinline__ bool is_sink(int i) const { return P.sink_of[i] != 0xFFu; }   // MIX only
+    // The topology (MIX only): node i's children, whether it is a sink and which, its
+    // producer.  A specialised per-edge kernel serves linear pipelines only (the host
+    // checks), so there they are compile-time facts and the loops over children fold.
+    static constexpr bool LIN = MIX && !S::generic;
+    __device__ __forceinline__ uint32_t kids(int i) const
+    {
+        if constexpr (LIN) return i + 1 < S::n ? (1u << (i + 1)) : 0u;
+        else return P.kids[i];
+    }
+    __device__ __forceinline__ bool is_sink(int i) const
+    {
+        if constexpr (LIN) return i == S::n - 1;
+        else return P.sink_of[i] != 0xFFu;
+    }
+    __device__ __forceinline__ uint32_t sink_idx(int i) const
+    {
+        if constexpr (LIN) return 0u;
+        else return P.sink_of[i];
+    }
+    __device__ __forceinline__ uint32_t up_of(int i) const
+    {
+        if constexpr (LIN) return (uint32_t)(i - 1);
+        else return P.up[i];
+    }
     // the per-parent accumulators of leaf q (a tree has two)
     __device__ __forceinline__ SArr<uint32_t> rcq(uint32_t q) const { return q ? M.rc2 : M.rc; }
     __device__ __forceinline__ SArr<unsigned long long> rsq(uint32_t q) const { return q ? M.rs2 : M.rs; }
@@ -1532,7 +1554,7 @@ struct Proc {
     template <int I>
     __device__ __forceinline__ void mix_sink(const uint32_t (&x)[V], const uint32_t (&k)[V], bool uni, uint32_t take)
     {
-        const uint32_t q = P.sink_of[I];
+        const uint32_t q = sink_idx(I);
         if (emode(I) == EM_SIG) {
             if (P.emit) {
                 emit_ensemble(x, take);
@@ -1615,7 +1637,7 @@ struct Proc {
     {
         const uint32_t SC = P.SC;
         const uint32_t km = kids(I);
-        const uint32_t q = last ? P.sink_of[I] : 0u;
+        const uint32_t q = last ? sink_idx(I) : 0u;
         bool progress = false;
         while (w.credit[I] == 0 && w.sh[I - 1] != w.st[I - 1]) {
             const uint32_t h = sidx(I - 1, w.sh[I - 1]);
@@ -1986,7 +2008,7 @@ struct Proc {
         // start at the identity
         for (int i = 1; i < n; ++i) {
             if (!is_sink(i) || emode(i) == EM_SIG) continue;
-            const uint32_t q = P.sink_of[i];
+            const uint32_t q = sink_idx(i);
             for (uint32_t kk = lane; kk < nk; kk += 32) {
                 rcq(q)[kk] = 0u;
                 rsq(q)[kk] = 0ull;
@@ -2013,7 +2035,7 @@ struct Proc {
             uint32_t dm = 0;   // bit i: node i drains
 #define RS_MIX_FIRE(I)                                                                            \
             if (I < n) {                                                                          \
-                const uint32_t u = P.up[I];                                                       \
+                const uint32_t u = up_of(I);                                                      \
                 const bool d = u == 0 ? done0 : (((dm >> u) & 1u) && edge_empty_at(u - 1));       \
                 if (d) dm |= 1u << I;                                                             \
                 fire<I>(d);                                                                       \
