@@ -172,14 +172,16 @@ __device__ __forceinline__ unsigned long long warp_sum_u32_wide(uint32_t v)
 // kernel, which reads every op from the parameters at run time.  A specialised
 // kernel carries only the code its own nodes execute, which keeps its hot loop small
 // enough for the instruction cache.
-template <int OE_, int O1_, int O2_, int O3_, int O4_>
+template <int OE_, int O1_, int O2_, int O3_, int O4_, int SK_ = D_AGG>
 struct Sig {
     static constexpr bool generic = OE_ == 0;
+    // the sink: an aggregate, or an emit sink (Section 4's results stripped of context)
+    static constexpr bool emit = !generic && SK_ == D_EMIT;
     static constexpr int n = generic ? 0 : 2 + (O1_ != 0) + (O2_ != 0) + (O3_ != 0) + (O4_ != 0);
     template <int I>
     __host__ __device__ static constexpr int op()
     {
-        return I == 0 ? OE_ : (I == n - 1 ? (int)D_AGG : (I == 1 ? O1_ : I == 2 ? O2_ : I == 3 ? O3_ : O4_));
+        return I == 0 ? OE_ : (I == n - 1 ? SK_ : (I == 1 ? O1_ : I == 2 ? O2_ : I == 3 ? O3_ : O4_));
     }
     template <int I>
     __host__ __device__ static constexpr bool present() { return generic ? (I < RS_MAX_STAGES) : (I < n); }

@@ -23,8 +23,9 @@ const void *rs_tag_kernel_entry(const KParams &P)
             generic = e.fn;
             continue;
         }
-        // specialised kernels end in the aggregate: an emit sink takes the generic one
-        if (!P.emit && e.oe == ops[0] && e.o1 == ops[1] && e.o2 == ops[2] && e.o3 == ops[3] && e.o4 == ops[4])
+        // a specialised kernel ends in the sink it was compiled for
+        if ((e.emit != 0) == (P.emit != 0) && e.oe == ops[0] && e.o1 == ops[1] && e.o2 == ops[2] &&
+            e.o3 == ops[3] && e.o4 == ops[4])
             return e.fn;
     }
     return generic;

@@ -834,7 +834,7 @@ struct TagEngine {
     __device__ __forceinline__ void aggregate(const uint32_t (&x)[V], const uint32_t (&r)[V], const bool (&valid)[V],
                                               bool uni, uint32_t r0, uint32_t n_valid) const
     {
-        if (SG::generic && P.emit) {
+        if ((SG::generic && P.emit) || SG::emit) {
             emit_values(x, r, valid, uni, r0, n_valid);
             return;
         }
@@ -1412,16 +1412,21 @@ __global__ void __launch_bounds__(256, (V <= 4 ? 3 : 2)) rs_tag_kernel(const __g
 struct TagEntry {
     int V, oe, o1, o2, o3, o4;
     const void *fn;
+    int emit;   // the stage list ends in an emit sink, not an aggregate
 };
 
 #define RS_TSIG(V, CPL, OE, O1, O2, O3, O4) \
-    {V, OE, O1, O2, O3, O4, (const void *)rs_tag_kernel<V, Sig<OE, O1, O2, O3, O4>, CPL>}
+    {V, OE, O1, O2, O3, O4, (const void *)rs_tag_kernel<V, Sig<OE, O1, O2, O3, O4>, CPL>, 0}
+#define RS_TSIGE(V, CPL, OE, O1, O2, O3, O4) \
+    {V, OE, O1, O2, O3, O4, (const void *)rs_tag_kernel<V, Sig<OE, O1, O2, O3, O4, D_EMIT>, CPL>, 1}
 #define RS_TALLV(CPL, OE, O1, O2, O3, O4)                                                          \
     RS_TSIG(1, CPL, OE, O1, O2, O3, O4), RS_TSIG(2, CPL, OE, O1, O2, O3, O4),                      \
         RS_TSIG(4, CPL, OE, O1, O2, O3, O4), RS_TSIG(8, CPL, OE, O1, O2, O3, O4)
 #define RS_TAG_TABLE(CPL)                                                                           \
     {/* loaded elements -> three context hash filters -> aggregate */                               \
      RS_TALLV(CPL, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),              \
+     /* ... ending in an emit sink instead, at 128 items per ensemble */                             \
+     RS_TSIGE(4, CPL, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),            \
      /* hashed elements -> power-of-two modulus filter -> multiply-add map -> aggregate */          \
      RS_TALLV(CPL, D_ENUM_HASH, D_FILT_MASK, D_MAP_MULADD, 0, 0),                                    \
      /* loaded elements (edges) -> weight comparison -> aggregate */                                 \
