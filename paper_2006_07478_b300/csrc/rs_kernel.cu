@@ -2005,14 +2005,15 @@ struct Proc {
         ek = 0;
         const int n = nst();
         // leaves fed by tags or per-lane contexts fold into per-parent accumulators, which
-        // start at the identity
+        // start at the identity; an emit sink uses none, and the minima exist only when a
+        // stream asks for them (the layout gives them no room otherwise)
         for (int i = 1; i < n; ++i) {
-            if (!is_sink(i) || emode(i) == EM_SIG) continue;
+            if (!is_sink(i) || emode(i) == EM_SIG || P.emit) continue;
             const uint32_t q = sink_idx(i);
             for (uint32_t kk = lane; kk < nk; kk += 32) {
                 rcq(q)[kk] = 0u;
                 rsq(q)[kk] = 0ull;
-                rmq(q)[kk] = 0xFFFFFFFFu;
+                if (P.want_min) rmq(q)[kk] = 0xFFFFFFFFu;
             }
         }
         __syncwarp();

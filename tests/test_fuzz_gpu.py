@@ -1,0 +1,121 @@
+"""Seeded random pipelines on the GPU vs the CPU oracle, bit-exact.
+
+Each case draws a linear stage list (loaded or hashed enumeration; one to three element
+stages among the modulus, context-hash and weight filters, the multiply-add map and the
+expansion; an aggregate or an emit sink), a strategy, a boundary mode per edge, an ensemble
+width and a unit shape, and a stream of geometric region lengths (empty regions included),
+then compares every region's results (a random subset of count, sum and min) with oracle.run /
+oracle.run_emit.  A drawn combination the library rejects at creation (an illegal mode
+sequence, say) is drawn again; every case runs."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2006_07478_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2006_07478_b300 import rs as _rs
+    _rs.lib()
+    return _rs
+
+
+def _stream(rng, hashed, want_offsets):
+    mean = float(rng.choice([0.5, 2, 9, 40, 300]))
+    R = int(rng.integers(50, 3000))
+    L = rng.geometric(1.0 / (1.0 + mean), size=R).astype(np.int64) - 1   # support from 0
+    L = np.minimum(L, 5000).astype(np.uint32)
+    N = int(L.sum())
+    parents = rng.integers(0, 1 << 32, size=R, dtype=np.uint64).astype(np.uint32)
+    ctx = rng.integers(0, 1 << 32, size=R, dtype=np.uint64).astype(np.uint32)
+    elements = None if hashed else rng.integers(0, 1 << 32, size=max(N, 1), dtype=np.uint64).astype(np.uint32)[:N]
+    if want_offsets:
+        off = np.concatenate(([0], np.cumsum(L.astype(np.int64)))).astype(np.uint32)
+        return wl.make_stream(offsets=off, parents=parents, elements=elements, ctx=ctx)
+    return wl.make_stream(L, parents=parents, elements=elements, ctx=ctx)
+
+
+def _stage(rng, k):
+    kind = rng.choice(["mod", "hctx", "weight", "map", "expand"])
+    salt = int(rng.integers(1, 1 << 31))
+    if kind == "mod":
+        m = int(rng.choice([2, 3, 4, 7, 16]))
+        return ("filter_mod", m, int(rng.integers(0, m)))
+    if kind == "hctx":
+        return ("filter_hash_ctx", salt, int(rng.integers(1 << 29, 1 << 32)))
+    if kind == "weight":
+        return ("filter_weight_lt", salt)
+    if kind == "map":
+        return ("map_mul", int(rng.integers(1, 1 << 32)), int(rng.integers(0, 1 << 32)))
+    return ("expand", int(rng.integers(0, 4)), salt)
+
+
+def _modes(rng, n_stages, stages):
+    modes, tagged = {}, False
+    for e in range(1, n_stages):
+        if tagged:
+            m = "tag"
+        else:
+            choices = ["signal", "tag"] + ([] if stages[e][0] == "expand" else ["lane"])
+            m = str(rng.choice(choices))
+        tagged = tagged or m == "tag"
+        modes[e] = m
+    return modes
+
+
+def _draw(rng):
+    hashed = bool(rng.random() < 0.3)
+    emit = bool(rng.random() < 0.3)
+    stages = [("enum_hash",) if hashed else ("enum_load",)]
+    for k in range(int(rng.integers(1, 4))):
+        stages.append(_stage(rng, k))
+    stages.append(("emit",) if emit else ("aggregate",))
+    strategy = str(rng.choice(["tag", "signal"]))
+    opts = {"ensemble_width": int(rng.choice([64, 128, 256] if strategy == "tag" else [32, 64, 128]))}
+    if rng.random() < 0.5:
+        opts["regions_per_unit"] = int(rng.choice([16, 128, 512] if strategy == "signal" else [64, 1024, 8192]))
+    if strategy == "signal" and rng.random() < 0.6:
+        opts["boundary_modes"] = _modes(rng, len(stages), stages)
+    return stages, strategy, opts, hashed, emit
+
+
+@pytest.mark.parametrize("seed", range(96))
+def test_random_pipeline_matches_oracle(rs, seed):
+    rng = np.random.default_rng(1000 + seed)
+    for _ in range(50):
+        stages, strategy, opts, hashed, emit = _draw(rng)
+        try:
+            rs.Pipeline(stages, strategy=strategy, **opts).close()
+        except rs.RsError:
+            continue   # a combination the library rejects: draw again
+        break
+    else:
+        pytest.fail("no accepted combination drawn")
+    s = _stream(rng, hashed, want_offsets=emit)
+    case = (stages, strategy, opts)
+    if emit:
+        want = oracle.run_emit(stages, s)
+        got, st = rs.run_stream(stages, s, strategy=strategy, **opts)
+        assert st["device_status"] == 0, (case, st)
+        assert np.array_equal(got["count"], want["count"]), case
+        start = want["start"]
+        for r in np.flatnonzero(want["count"]):
+            a = np.sort(got["values"][start[r]:start[r] + int(want["count"][r])])
+            b = np.sort(want["values"][start[r]:start[r] + int(want["count"][r])])
+            assert np.array_equal(a, b), (case, r)
+    else:
+        # a random subset of the outputs (the kernels size and use per-parent minima only
+        # when a stream asks for them)
+        outputs = [("count", "sum", "min"), ("count", "sum"), ("count",), ("sum", "min")][int(rng.integers(0, 4))]
+        want = oracle.run(stages, s)
+        got, st = rs.run_stream(stages, s, strategy=strategy, outputs=outputs, **opts)
+        assert st["device_status"] == 0, (case, st)
+        for k in outputs:
+            bad = np.flatnonzero(got[k] != want[k])
+            assert bad.size == 0, (case, k, bad[:5])
