@@ -119,3 +119,65 @@ def test_random_pipeline_matches_oracle(rs, seed):
         for k in outputs:
             bad = np.flatnonzero(got[k] != want[k])
             assert bad.size == 0, (case, k, bad[:5])
+
+
+def _draw_tree(rng):
+    """A tree (Figure 1(b)): the enumeration feeds one element stage; below it two
+    branches of zero to two element stages each end in an aggregate, forking at a random
+    element stage of the trunk."""
+    hashed = bool(rng.random() < 0.4)
+    stages = [("enum_hash",) if hashed else ("enum_load",)]
+    inputs = [0]
+    trunk = [len(stages)]
+    stages.append(_stage(rng, 0))
+    inputs.append(0)
+    for _ in range(int(rng.integers(0, 2))):
+        inputs.append(len(stages) - 1)
+        trunk.append(len(stages))
+        stages.append(_stage(rng, 0))
+    fork = int(rng.choice(trunk))
+    for _ in range(2):
+        prev = fork
+        for _ in range(int(rng.integers(0, 3))):
+            inputs.append(prev)
+            prev = len(stages)
+            stages.append(_stage(rng, 0))
+        inputs.append(prev)
+        stages.append(("aggregate",))
+    modes, tagged = {}, set()
+    for c in range(1, len(stages)):
+        if inputs[c] in tagged and inputs[c] != 0:
+            m = "tag"
+        else:
+            m = str(rng.choice(["signal", "tag"] + ([] if stages[c][0] == "expand" else ["lane"])))
+        if m == "tag":
+            tagged.add(c)
+        modes[c] = m
+    if rng.random() < 0.25:
+        modes = {c: "signal" for c in range(1, len(stages))}
+    return stages, inputs, modes, hashed
+
+
+@pytest.mark.parametrize("seed", range(48))
+def test_random_tree_matches_oracle(rs, seed):
+    rng = np.random.default_rng(5000 + seed)
+    for _ in range(50):
+        stages, inputs, modes, hashed = _draw_tree(rng)
+        w = int(rng.choice([32, 64, 128]))
+        try:
+            rs.Pipeline(stages, strategy="signal", inputs=inputs, boundary_modes=modes, ensemble_width=w).close()
+        except rs.RsError:
+            continue
+        break
+    else:
+        pytest.fail("no accepted tree drawn")
+    s = _stream(rng, hashed, want_offsets=False)
+    outputs = [("count", "sum", "min"), ("count", "sum"), ("min",)][int(rng.integers(0, 3))]
+    case = (stages, inputs, modes, w)
+    want = oracle.run_tree(stages, inputs, s)
+    got, st = rs.run_stream(stages, s, strategy="signal", inputs=inputs, boundary_modes=modes, ensemble_width=w,
+                            outputs=outputs)
+    assert st["device_status"] == 0, (case, st)
+    for k in outputs:
+        assert np.array_equal(got[k], want[0][k]), (case, k, 0)
+        assert np.array_equal(got[k + "2"], want[1][k]), (case, k, 1)
