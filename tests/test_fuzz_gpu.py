@@ -181,3 +181,49 @@ def test_random_tree_matches_oracle(rs, seed):
     for k in outputs:
         assert np.array_equal(got[k], want[0][k]), (case, k, 0)
         assert np.array_equal(got[k + "2"], want[1][k]), (case, k, 1)
+
+
+@pytest.mark.parametrize("seed", range(32))
+def test_random_pipeline_sliced_matches_oracle(rs, seed):
+    """The same random linear pipelines (aggregate sinks) run a few work units per launch
+    over resident per-stream state until done: the results equal the oracle's."""
+    import torch
+    rng = np.random.default_rng(9000 + seed)
+    for _ in range(50):
+        stages, strategy, opts, hashed, emit = _draw(rng)
+        if emit:
+            continue
+        try:
+            rs.Pipeline(stages, strategy=strategy, **opts).close()
+        except rs.RsError:
+            continue
+        break
+    else:
+        pytest.fail("no accepted combination drawn")
+    s = _stream(rng, hashed, want_offsets=bool(rng.random() < 0.5))
+    budget = int(rng.integers(1, 5))
+    outputs = ("count", "sum", "min")
+    case = (stages, strategy, opts, budget)
+    want = oracle.run(stages, s)
+    p = rs.Pipeline(stages, strategy=strategy, **opts)
+    dev = rs.to_device(s)
+    out = p.submit(dev, outputs=outputs)
+    for k in outputs:
+        out[k].fill_(0x5A5A5A5A)
+    nbytes, units = p.state_size(dev)
+    state = torch.empty(max(256, nbytes) + 256, dtype=torch.uint8, device="cuda")
+    state = state[(-state.data_ptr()) % 256:]
+    begin = 0
+    while begin < units:
+        p.clear()
+        p.submit(dev, out=out, state=state, unit_begin=begin, unit_count=budget)
+        p.run()
+        st = p.stats()
+        assert st["device_status"] == 0, (case, st)
+        begin += budget
+    torch.cuda.synchronize()
+    got = rs.results_to_numpy(out)
+    for k in outputs:
+        bad = np.flatnonzero(got[k] != want[k])
+        assert bad.size == 0, (case, k, bad[:5])
+    p.close()
