@@ -227,3 +227,41 @@ def test_random_pipeline_sliced_matches_oracle(rs, seed):
         bad = np.flatnonzero(got[k] != want[k])
         assert bad.size == 0, (case, k, bad[:5])
     p.close()
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_pipeline_served_matches_oracle(rs, seed):
+    """Random linear pipelines (aggregate sinks) served: a dozen random streams submitted to
+    the continuous-batching server with a random slice budget, each result equal to the
+    oracle's."""
+    import time
+    rng = np.random.default_rng(13000 + seed)
+    for _ in range(50):
+        stages, strategy, opts, hashed, emit = _draw(rng)
+        opts.pop("boundary_modes", None)
+        if emit:
+            continue
+        try:
+            rs.Pipeline(stages, strategy=strategy, **opts).close()
+        except rs.RsError:
+            continue
+        break
+    else:
+        pytest.fail("no accepted combination drawn")
+    streams = [_stream(rng, hashed, want_offsets=False) for _ in range(12)]
+    slice_units = int(rng.choice([0, 1, 4, 64]))
+    srv = rs.Server(stages, arena_bytes=256 << 20, strategy=strategy, slice_units=slice_units, **opts)
+    reqs = [rs.host_request(s) for s in streams]
+    ids = [srv.submit(r) for r in reqs]
+    done, t0 = [], time.time()
+    while len(done) < len(ids):
+        srv.progress()
+        done += srv.poll()
+        assert time.time() - t0 < 60.0, srv.stats()
+    srv.close()
+    for r, s in zip(reqs, streams):
+        want = oracle.run(stages, s)
+        got = rs.results_to_numpy({k: r[k] for k in ("count", "sum", "min")})
+        for k in got:
+            bad = np.flatnonzero(got[k] != want[k])
+            assert bad.size == 0, (stages, strategy, opts, slice_units, k, bad[:5])
