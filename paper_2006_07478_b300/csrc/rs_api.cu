@@ -1053,6 +1053,10 @@ static void fill_table(const rs_pipeline *p, const StreamPlan *sp, size_t ns, un
             d.usum_grp = (uint32_t *)(wsd + q.grp_off);
         }
         d.unit_base = base;
+        // every stream's planner-tile base, planned or not, so that the tiles' bases never
+        // decrease along the table (the planner finds a tile's stream by binary search: a
+        // stream without tiles holds the base of the next one that has some)
+        d.plan_base = pbase;
         d.tma_ok = s.elements && (((uintptr_t)s.elements & 15) == 0);
         d.mode = q.mode;
         if (q.mode == UNIT_MERGE) {

@@ -265,3 +265,69 @@ def test_random_pipeline_served_matches_oracle(rs, seed):
         for k in got:
             bad = np.flatnonzero(got[k] != want[k])
             assert bad.size == 0, (stages, strategy, opts, slice_units, k, bad[:5])
+
+
+def _check_results(got, want, outputs, case):
+    for k in outputs:
+        bad = np.flatnonzero(got[k] != want[k])
+        assert bad.size == 0, (case, k, bad[:5])
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_batch_graph_replay_and_noalloc_match_oracle(rs, seed):
+    """Random linear pipelines over two to six random streams in one launch: the plain run,
+    two replays of a captured CUDA graph (on a side stream, outputs clobbered before) and
+    the workspace-free entry point all give the oracle's results for every stream."""
+    import torch
+    rng = np.random.default_rng(17000 + seed)
+    for _ in range(50):
+        stages, strategy, opts, hashed, emit = _draw(rng)
+        if emit:
+            continue
+        try:
+            rs.Pipeline(stages, strategy=strategy, **opts).close()
+        except rs.RsError:
+            continue
+        break
+    else:
+        pytest.fail("no accepted combination drawn")
+    streams = [_stream(rng, hashed, want_offsets=bool(rng.random() < 0.5)) for _ in range(int(rng.integers(2, 7)))]
+    outputs = ("count", "sum", "min")
+    case = (stages, strategy, opts, len(streams))
+    wants = [oracle.run(stages, s) for s in streams]
+    p = rs.Pipeline(stages, strategy=strategy, **opts)
+    outs = [p.submit(rs.to_device(s), outputs=outputs) for s in streams]
+
+    def clobber():
+        for o in outs:
+            for k in outputs:
+                o[k].fill_(0x5A5A5A5A)
+
+    def verify():
+        torch.cuda.synchronize()
+        for o, want in zip(outs, wants):
+            _check_results(rs.results_to_numpy(o), want, outputs, case)
+
+    clobber()
+    p.run()
+    assert p.stats()["device_status"] == 0, case
+    verify()
+    clobber()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        p.graph_capture()
+        p.graph_launch()
+        p.graph_launch()
+    side.synchronize()
+    verify()
+    p.graph_release()
+    clobber()
+    try:
+        p.run_noalloc()
+    except rs.RsError as e:
+        # beyond the fixed scratch array (16 MiB, 64 streams): refused, nothing ran
+        assert e.status == rs.RS_ERR_CAPACITY, (case, e)
+    else:
+        verify()
+    p.close()

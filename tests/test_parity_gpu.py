@@ -208,6 +208,34 @@ def test_private_workspace_table_follows_submits_options_and_workspace(rs):
     p.close()
 
 
+def test_fixed_parent_and_merge_path_streams_in_one_launch(rs):
+    """One tag-strategy launch over streams planned both ways: streams of lengths with short
+    regions take fixed-parent units (no planner tiles), CSR and long-region streams
+    merge-path units.  The planner finds each tile's stream by the tiles' bases, which every
+    stream carries (a fixed-parent stream the base of the next planned one)."""
+    pipe = wl.pipeline_cascade()
+    streams = []
+    for i, (mean, csr) in enumerate([(40, True), (0.6, False), (300, False), (2, False), (1, True), (0.5, False)]):
+        s = wl.cascade_stream(n_total=1 << 15, mean=mean, seed=60 + i)
+        if csr:
+            L = s["len"].astype(np.int64)
+            s = dict(s, len=None, offsets=np.concatenate(([0], np.cumsum(L))).astype(np.uint32))
+        streams.append(s)
+    p = rs.Pipeline(pipe, strategy="tag")
+    outs = [p.submit(rs.to_device(s), outputs=("count", "sum")) for s in streams]
+    for o in outs:
+        for k in ("count", "sum"):
+            o[k].fill_(0x5A5A5A5A)
+    p.run()
+    assert p.stats()["device_status"] == 0
+    for o, s in zip(outs, streams):
+        want = oracle.run(pipe, s)
+        got = rs.results_to_numpy(o)
+        for k in ("count", "sum"):
+            assert np.array_equal(got[k], want[k]), k
+    p.close()
+
+
 def test_fetch_to_host_and_autotune(rs):
     import torch
     s = wl.cascade_stream(n_total=1 << 18, mean=64, seed=5)
