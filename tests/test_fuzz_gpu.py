@@ -82,6 +82,17 @@ def _draw(rng):
         opts["regions_per_unit"] = int(rng.choice([16, 128, 512] if strategy == "signal" else [64, 1024, 8192]))
     if strategy == "signal" and rng.random() < 0.6:
         opts["boundary_modes"] = _modes(rng, len(stages), stages)
+    if rng.random() < 0.5:
+        # the rest of the option space (the library rejects what does not fit; redrawn)
+        opts["region_cost"] = int(rng.choice([1, 2, 4, 16, 64]))
+        opts["warps_per_block"] = int(rng.choice([0, 1, 2, 3, 4, 8]))
+        opts["grid"] = int(rng.choice([0, 0, 1, 5, 37]))
+        if strategy == "signal":
+            opts["tiles_in_flight"] = int(rng.choice([0, 2, 4]))
+            opts["tile_elements"] = int(rng.choice([128, 256, 1024]))
+            opts["signal_capacity"] = int(rng.choice([4, 8, 32, 256]))
+        if rng.random() < 0.5:
+            opts["queue_capacity"] = int(rng.choice([256, 512, 1024, 2048]))
     return stages, strategy, opts, hashed, emit
 
 
