@@ -286,15 +286,14 @@ def _check_results(got, want, outputs, case):
 
 @pytest.mark.parametrize("seed", range(24))
 def test_random_batch_graph_replay_and_noalloc_match_oracle(rs, seed):
-    """Random linear pipelines over two to six random streams in one launch: the plain run,
-    two replays of a captured CUDA graph (on a side stream, outputs clobbered before) and
-    the workspace-free entry point all give the oracle's results for every stream."""
+    """Random linear pipelines (aggregate or emit sinks) over two to six random streams in one
+    launch: the plain run, two replays of a captured CUDA graph (on a side stream, outputs
+    clobbered before) and the workspace-free entry point all give the oracle's results for
+    every stream."""
     import torch
     rng = np.random.default_rng(17000 + seed)
     for _ in range(50):
         stages, strategy, opts, hashed, emit = _draw(rng)
-        if emit:
-            continue
         try:
             rs.Pipeline(stages, strategy=strategy, **opts).close()
         except rs.RsError:
@@ -302,10 +301,11 @@ def test_random_batch_graph_replay_and_noalloc_match_oracle(rs, seed):
         break
     else:
         pytest.fail("no accepted combination drawn")
-    streams = [_stream(rng, hashed, want_offsets=bool(rng.random() < 0.5)) for _ in range(int(rng.integers(2, 7)))]
-    outputs = ("count", "sum", "min")
+    streams = [_stream(rng, hashed, want_offsets=emit or bool(rng.random() < 0.5))
+               for _ in range(int(rng.integers(2, 7)))]
+    outputs = ("count", "values") if emit else ("count", "sum", "min")
     case = (stages, strategy, opts, len(streams))
-    wants = [oracle.run(stages, s) for s in streams]
+    wants = [oracle.run_emit(stages, s) if emit else oracle.run(stages, s) for s in streams]
     p = rs.Pipeline(stages, strategy=strategy, **opts)
     outs = [p.submit(rs.to_device(s), outputs=outputs) for s in streams]
 
@@ -317,7 +317,16 @@ def test_random_batch_graph_replay_and_noalloc_match_oracle(rs, seed):
     def verify():
         torch.cuda.synchronize()
         for o, want in zip(outs, wants):
-            _check_results(rs.results_to_numpy(o), want, outputs, case)
+            got = rs.results_to_numpy(o)
+            if not emit:
+                _check_results(got, want, outputs, case)
+                continue
+            assert np.array_equal(got["count"], want["count"]), case
+            start = want["start"]
+            for r in np.flatnonzero(want["count"]):
+                a = np.sort(got["values"][start[r]:start[r] + int(want["count"][r])])
+                b = np.sort(want["values"][start[r]:start[r] + int(want["count"][r])])
+                assert np.array_equal(a, b), (case, r)
 
     clobber()
     p.run()
