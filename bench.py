@@ -693,6 +693,33 @@ def run_case(args, rs, torch):
         print(json.dumps({"case": args.case, "n": n, "kernel_ms": kms, "items_per_s": n / (kms * 1e-3),
                           "gbs": 4 * n / (kms * 1e-3) / 1e9, "result": out.cpu().tolist()}), flush=True)
         return
+    if parts[0] == "rsum":
+        # the region-sum pipeline over 2^26 elements in regions of one size: rsum:SIZE:STRATEGY
+        size, strat = int(parts[1]), parts[2]
+        n = N_ELEM
+        L = wl.sized_lengths(n, size, 11, False)
+        el = wl.sized_region_stream(n, 128, seed=11)["elements"]
+        dev = {"R": int(L.shape[0]), "len": torch.from_numpy(L.view(np.int32)).cuda(),
+               "elements": torch.from_numpy(el.view(np.int32)).cuda()}
+        p = rs.Pipeline(wl.pipeline_region_sum(), strategy=strat)
+        out = p.submit(dev, outputs=("count", "sum"))
+        p.timing_enable(args.steps + args.warmup)
+        for _ in range(args.warmup):
+            p.run()
+        torch.cuda.synchronize()
+        p.timing_read()
+        for _ in range(args.steps):
+            p.run()
+        kms = statistics.median(p.timing_read())
+        got = rs.results_to_numpy(out)
+        ok = bool(np.array_equal(got["count"], L) and
+                  int(got["sum"].astype(np.uint64).sum()) == int(el.astype(np.uint64).sum()))
+        print(json.dumps({"case": args.case, "n": n, "regions": int(L.shape[0]), "kernel_ms": kms,
+                          "items_per_s": n / (kms * 1e-3), "opts": p.opts, "invariants_ok": ok}), flush=True)
+        del out
+        if not ok:
+            raise SystemExit("rsum: counts or sums differ from the region lengths and the array's sum")
+        return
     mean, strat = float(parts[0]), parts[1]
     n = 1 << int(parts[2]) if len(parts) > 2 and parts[2] else N_ELEM
     opts = {}
@@ -738,8 +765,9 @@ def main():
                     help="N > 1: split each stream's regions across the ranks (strong scaling) instead of "
                          "running the same five streams on every rank (weak scaling)")
     ap.add_argument("--case", default=None,
-                    help="MEAN:STRATEGY[:N_LOG2[:OPT=V,...]] -- one stream, fixed strategy and options "
-                         "(a small fixed launch sequence for profilers)")
+                    help="MEAN:STRATEGY[:N_LOG2[:OPT=V,...]] -- one cascade stream, fixed strategy and options; "
+                         "calib:N_LOG2 -- the calibration kernel; rsum:SIZE:STRATEGY -- the region-sum pipeline "
+                         "over 2^26 elements in regions of SIZE (small fixed launch sequences for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -141,6 +141,21 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
+// Reductions into global memory that return nothing (red.global: the L2 applies them and
+// sends no value back, where an atomic that returns the old value would)
+__device__ __forceinline__ void red_add_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_min_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.relaxed.gpu.global.min.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 {
 #pragma unroll

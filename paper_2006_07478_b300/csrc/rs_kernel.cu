@@ -2399,6 +2399,8 @@ static const KEntry g_kernels[] = {
     RS_KBOTH(D_ENUM_HASH, D_FILT_MASK, D_MAP_MULADD, 0, 0),
     // loaded elements (edges) -> weight comparison -> aggregate
     RS_KBOTH(D_ENUM_LOAD, D_FILT_WEIGHT, 0, 0, 0),
+    // loaded elements -> aggregate (the region-sum benchmark), 128 items per ensemble
+    RS_KSIG(RS_STRATEGY_SIGNAL, 4, D_ENUM_LOAD, 0, 0, 0, 0),
     // any other stage list
     RS_KBOTH(0, 0, 0, 0, 0),
 };

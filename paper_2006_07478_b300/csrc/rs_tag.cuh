@@ -740,9 +740,9 @@ struct TagEngine {
     __device__ __forceinline__ void fold(uint32_t rr, uint32_t n, unsigned long long s, uint32_t mn) const
     {
         const DevStream &d = D();
-        if (P.want_count) atomicAdd(d.out_count + rr, n);
-        if (P.want_sum) atomicAdd(d.out_sum + rr, s);
-        if (P.want_min) atomicMin(d.out_min + rr, mn);
+        if (P.want_count) red_add_u32(d.out_count + rr, n);
+        if (P.want_sum) red_add_u64(d.out_sum + rr, s);
+        if (P.want_min) red_min_u32(d.out_min + rr, mn);
     }
 
     // One-region ensembles fold into the processor's pending fold (lane 0, shared memory),
@@ -956,6 +956,103 @@ struct TagEngine {
         ++nfast;
     }
 
+    // Enumeration straight into the aggregate (loaded elements, two nodes): a run of full
+    // windows inside the current parent.  Each lane keeps its own 64-bit sum (and minimum)
+    // across the run; the warp reduces them and folds into the pending fold once per run,
+    // not once per window.  Every window of the run is full, so the count is the run's
+    // window count times W.  The run stops where the fast windows end and, while the next
+    // unit is still to be described, 8 windows before the unit's end, as step() does.
+    static constexpr bool RUN = !SG::generic && SG::n == 2 && !SG::emit && SG::template op<0>() == D_ENUM_LOAD;
+
+    template <bool MIN>
+    __device__ __forceinline__ void fast_run()
+    {
+        unsigned long long s = 0;
+        uint32_t mn = NONE, k = 0;
+        do {
+            uint32_t x[V];
+            staged_window(x);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                s += x[j];
+                if (MIN) mn = min(mn, x[j]);
+            }
+            a += W;
+            ++k;
+        } while (a + W <= flim && (nxt_done || a + 8 * W < j1));
+        nfast += k;
+        s = warp_sum_u64(s);
+        if (MIN) mn = __reduce_min_sync(FULLMASK, mn);
+        if (lane == 0) acc_add(r_cur, k * W, s, mn);
+    }
+
+    // Enumeration straight into the aggregate over a window that crosses parent starts
+    // (count and sum; lanes hold consecutive positions): no region id per item.  Inclusive
+    // prefix sums over the window's positions, of the values' low and high 16-bit halves,
+    // go one after the other through the window's staging slot (free until the next copy);
+    // each region's piece of the window, [max(start, lo), min(next start, hi)), is then
+    // the difference of two prefix values, and one lane per piece folds it: one fold per
+    // region and window, not one per lane.  A window with more than 32 pieces is left to
+    // node1's general path: returns false before touching anything.
+    __device__ __forceinline__ bool seg_window(const uint32_t (&x)[V], uint32_t lo, uint32_t hi)
+    {
+        static_assert(NS == 1, "positions a + V lane + i");
+        // lane k: record ord_cur + k, whose piece starts at lo for the current record
+        const uint32_t nrec = ord_loaded - ord_cur, o = ord_cur + lane;
+        const uint32_t st = lane == 0 ? lo : (lane < nrec ? nst()[o & PRM()] : NONE);
+        const bool w = st < hi;
+        const uint32_t bw = __ballot_sync(FULLMASK, w);
+        if (bw >> 31) return false;
+        // inclusive prefixes of both halves at the lane's positions (invalid ones add 0)
+        uint32_t pl[V], ph[V];
+        uint32_t cl = 0, ch = 0;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const uint32_t p = a + V * lane + i;
+            const uint32_t v = (p >= lo && p < hi) ? x[i] : 0u;
+            cl += v & 0xFFFFu;
+            ch += v >> 16;
+            pl[i] = cl;
+            ph[i] = ch;
+        }
+        const uint32_t il = scan_add(cl), ih = scan_add(ch);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            pl[i] += il - cl;
+            ph[i] += ih - ch;
+        }
+        ctr += (lane == 0 || lane == 4 || lane == 7) ? 1u : (lane == 5 ? hi - lo : 0u);
+        const uint32_t s = max(st, lo);
+        const uint32_t e = (w && lane + 1 < nrec) ? min(hi, nst()[(o + 1) & PRM()]) : hi;
+        const bool piece = w && e > s;
+        uint32_t sl = 0, sh = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            __syncwarp();
+            uint32_t q[V];
+#pragma unroll
+            for (int i = 0; i < V; ++i) q[i] = h ? ph[i] : pl[i];
+            if constexpr (V == 4) {
+                reinterpret_cast<uint4 *>(marks().ptr())[lane] = make_uint4(q[0], q[1 % V], q[2 % V], q[3 % V]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) marks()[V * lane + i] = q[i];
+            }
+            __syncwarp();
+            if (piece) {
+                const uint32_t d = marks()[e - 1 - a] - (s > a ? marks()[s - 1 - a] : 0u);
+                if (h) sh = d;
+                else sl = d;
+            }
+        }
+        if (piece) fold((uint32_t)nra()[o & PRM()], e - s, ((unsigned long long)sh << 16) + sl, NONE);
+        __syncwarp();
+        // the last record starting before hi becomes the current one
+        take_record(ord_cur + 31 - __clz(bw));
+        a += W;
+        return true;
+    }
+
     // ---------------------------------------------------------------------------
     // node 1: the window [a, a + W) of the unit (any case: partial windows, parent
     // starts inside the window, parents still to load)
@@ -979,6 +1076,13 @@ struct TagEngine {
         const uint32_t lo = max(a, j0), hi = min(a + W, j1);
         uint32_t r[V], aux[V], st[V], par[V];
         const bool uni = s_nx >= hi;
+        if constexpr (RUN && NS == 1) {
+            // windows whose first region start falls on a lane boundary within the first 32
+            // positions (short regions of lane-multiple lengths, where each lane's items
+            // mostly lie in one region) fold as cheaply per item and stay on the general path
+            const uint32_t d0 = s_nx - a;
+            if (!uni && !P.want_min && ((d0 & (V - 1)) != 0 || d0 >= 32) && seg_window(x, lo, hi)) return;
+        }
         if (uni) {
             // every position of the window lies in the current parent
 #pragma unroll
@@ -1286,8 +1390,16 @@ struct TagEngine {
                 }
             }
         }
-        if (a >= j0 && a + W <= flim) fast_window();
-        else node1();
+        if (a >= j0 && a + W <= flim) {
+            if constexpr (RUN) {
+                if (P.want_min) fast_run<true>();
+                else fast_run<false>();
+            } else {
+                fast_window();
+            }
+        } else {
+            node1();
+        }
         if (!nxt_done && a + 8 * W >= j1) resolve_next();
         pump();
         return true;
@@ -1429,6 +1541,8 @@ struct TagEntry {
      RS_TSIGE(4, CPL, D_ENUM_LOAD, D_FILT_HASH_CTX, D_FILT_HASH_CTX, D_FILT_HASH_CTX, 0),            \
      /* hashed elements -> power-of-two modulus filter -> multiply-add map -> aggregate */          \
      RS_TALLV(CPL, D_ENUM_HASH, D_FILT_MASK, D_MAP_MULADD, 0, 0),                                    \
+     /* loaded elements -> aggregate (the region-sum benchmark), 128 items per ensemble */         \
+     RS_TSIG(4, CPL, D_ENUM_LOAD, 0, 0, 0, 0),                                                       \
      /* loaded elements (edges) -> weight comparison -> aggregate */                                 \
      RS_TALLV(CPL, D_ENUM_LOAD, D_FILT_WEIGHT, 0, 0, 0),                                             \
      /* any other stage list */                                                                      \

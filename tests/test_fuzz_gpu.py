@@ -132,6 +132,58 @@ def test_random_pipeline_matches_oracle(rs, seed):
             assert bad.size == 0, (case, k, bad[:5])
 
 
+@pytest.mark.parametrize("seed", range(48))
+def test_random_region_sum_matches_oracle(rs, seed):
+    """Enumeration straight into the sink (the region-sum pipeline, and its emit form):
+    random region-length mixes from all-short to a few thousand elements, random unit
+    shapes, grids and output subsets (the minimum among them takes the general window
+    path), at the ensemble width the specialised kernels are compiled for and at others."""
+    rng = np.random.default_rng(5000 + seed)
+    emit = bool(rng.random() < 0.2)
+    stages = [("enum_load",), ("emit",) if emit else ("aggregate",)]
+    strategy = str(rng.choice(["tag", "signal"]))
+    widths = [64, 128, 128, 128, 256] if strategy == "tag" else [32, 64, 128, 128, 128]
+    opts = {"ensemble_width": int(rng.choice(widths))}
+    if rng.random() < 0.6:
+        opts["regions_per_unit"] = int(rng.choice([1, 16, 128, 512] if strategy == "signal" else [16, 64, 1024, 8192]))
+        opts["region_cost"] = int(rng.choice([1, 2, 4, 16, 64]))
+        opts["warps_per_block"] = int(rng.choice([0, 1, 2, 4, 8]))
+        opts["grid"] = int(rng.choice([0, 0, 1, 5, 37]))
+        if rng.random() < 0.3:
+            opts["flags"] = rs.FLAG_UNBALANCED_UNITS
+    mean = float(rng.choice([0.5, 3, 16, 127, 600, 2500]))
+    R = int(rng.integers(20, max(40, int(2_000_000 / (mean + 1)))))
+    R = min(R, 20000)
+    L = rng.geometric(1.0 / (1.0 + mean), size=R).astype(np.int64) - 1
+    if rng.random() < 0.3:
+        L = np.full(R, int(rng.choice([1, 31, 128, 129, 1000])), dtype=np.int64)   # fixed sizes
+    L = L.astype(np.uint32)
+    N = int(L.sum())
+    elements = rng.integers(0, 1 << 32, size=max(N, 1), dtype=np.uint64).astype(np.uint32)[:N]
+    case = (stages, strategy, opts, mean, R)
+    if emit:
+        off = np.concatenate(([0], np.cumsum(L.astype(np.int64)))).astype(np.uint32)
+        s = wl.make_stream(offsets=off, elements=elements)
+        want = oracle.run_emit(stages, s)
+        got, st = rs.run_stream(stages, s, strategy=strategy, **opts)
+        assert st["device_status"] == 0, (case, st)
+        assert np.array_equal(got["count"], want["count"]), case
+        start = want["start"]
+        for r in np.flatnonzero(want["count"])[:2000]:
+            a = np.sort(got["values"][start[r]:start[r] + int(want["count"][r])])
+            b = np.sort(want["values"][start[r]:start[r] + int(want["count"][r])])
+            assert np.array_equal(a, b), (case, r)
+        return
+    s = wl.make_stream(L, elements=elements)
+    outputs = [("count", "sum"), ("count", "sum"), ("sum",), ("count", "sum", "min"), ("count",)][int(rng.integers(0, 5))]
+    want = oracle.run(stages, s)
+    got, st = rs.run_stream(stages, s, strategy=strategy, outputs=outputs, **opts)
+    assert st["device_status"] == 0, (case, st)
+    for k in outputs:
+        bad = np.flatnonzero(got[k] != want[k])
+        assert bad.size == 0, (case, k, bad[:5])
+
+
 def _draw_tree(rng):
     """A tree (Figure 1(b)): the enumeration feeds one element stage; below it two
     branches of zero to two element stages each end in an aggregate, forking at a random
