@@ -37,7 +37,12 @@
 //     region's output holds the identity result before its first fold: the planner
 //     writes it for a region two units share (the one a unit starts inside), and the
 //     processor whose unit owns a region writes it when it loads that region's parent,
-//     before any fold into it; this also covers empty regions.
+//     before any fold into it; this also covers empty regions.  Folds are red.global
+//     reductions (no value comes back).
+//   * Enumeration straight into the aggregate (the region-sum stage list, compiled on its
+//     own) needs no tag per item: runs of full windows inside one parent keep per-lane
+//     partials and reduce once per run, and a window crossing parent starts folds each
+//     region's piece as a difference of two warp prefix sums.
 //
 // Rings and the parent stream are drained when a processor moves to a unit of another
 // stream and when it runs out of units.  Nothing waits on another warp: the kernel has
@@ -969,6 +974,10 @@ struct TagEngine {
     {
         unsigned long long s = 0;
         uint32_t mn = NONE, k = 0;
+        // the last window start of the run: a + W <= flim and, while the next unit is
+        // undescribed, a + 8 W < j1 (neither bound moves during the run)
+        uint32_t lim = flim - W;
+        if (!nxt_done) lim = min(lim, j1 > 8 * W ? j1 - 8 * W - 1 : 0u);
         do {
             uint32_t x[V];
             staged_window(x);
@@ -979,7 +988,7 @@ struct TagEngine {
             }
             a += W;
             ++k;
-        } while (a + W <= flim && (nxt_done || a + 8 * W < j1));
+        } while (a <= lim);
         nfast += k;
         s = warp_sum_u64(s);
         if (MIN) mn = __reduce_min_sync(FULLMASK, mn);
