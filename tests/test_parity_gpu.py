@@ -284,6 +284,28 @@ def test_bench_size_sampled(rs, mean):
         assert st["items"][1] == 1 << 26
 
 
+@pytest.mark.parametrize("size,variable", [(16, False), (128, False), (129, False), (2048, False), (64, True)])
+def test_region_sum_bench_size_sampled(rs, size, variable):
+    """The region-sum sweep's full-size shapes (2^26 elements, default options, both
+    strategies), as the bench runs them: every region's count is its length, the sums add
+    up to the array's, and sampled regions' sums equal the oracle's one by one; with the
+    minimum asked for as well (the tag kernel's general window path), sampled minima too."""
+    s = wl.sized_region_stream(1 << 26, size, seed=11, variable=variable)
+    pipe = wl.pipeline_region_sum()
+    rng = np.random.default_rng(size)
+    idx = np.unique(np.concatenate([rng.integers(0, s["R"], 4000), [0, s["R"] - 1]]))
+    want = oracle.run_sampled(pipe, s, idx)
+    total = int(s["elements"].astype(np.uint64).sum())
+    for strategy in STRATEGIES:
+        for outputs in (("count", "sum"), ("count", "sum", "min")):
+            got, st = rs.run_stream(pipe, s, strategy=strategy, outputs=outputs)
+            assert st["device_status"] == 0
+            assert np.array_equal(got["count"], s["len"]), (strategy, outputs)
+            assert int(got["sum"].astype(np.uint64).sum()) == total, (strategy, outputs)
+            for k in outputs:
+                assert np.array_equal(got[k][idx], want[k]), (strategy, outputs, k)
+
+
 def _rand_u32(rng, n):
     return rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
 
