@@ -996,65 +996,87 @@ struct TagEngine {
     }
 
     // Enumeration straight into the aggregate over a window that crosses parent starts
-    // (count and sum; lanes hold consecutive positions): no region id per item.  Inclusive
-    // prefix sums over the window's positions, of the values' low and high 16-bit halves,
-    // go one after the other through the window's staging slot (free until the next copy);
-    // each region's piece of the window, [max(start, lo), min(next start, hi)), is then
-    // the difference of two prefix values, and one lane per piece folds it: one fold per
-    // region and window, not one per lane.  A window with more than 32 pieces is left to
-    // node1's general path: returns false before touching anything.
-    __device__ __forceinline__ bool seg_window(const uint32_t (&x)[V], uint32_t lo, uint32_t hi)
+    // (count and sum; lanes hold consecutive positions): no region id per item.  Lane k
+    // reads the start of record ord_cur + k (the current record's piece starts at lo).
+    //   * Every start on a lane boundary: each lane's V items lie in one region, the
+    //     record of the last start at or below the lane's first position (a count of the
+    //     lanes holding a start, from one OR-reduction of their bits), and the lane folds
+    //     its valid items' count and sum.
+    //   * Otherwise, inclusive prefix sums over the window's positions, of the values' low
+    //     and high 16-bit halves, go one after the other through the window's staging slot
+    //     (free until the next copy); each region's piece of the window,
+    //     [max(start, lo), min(next start, hi)), is the difference of two prefix values,
+    //     and one lane per piece folds it: one fold per region and window.
+    // A window with more than 32 pieces is left to node1's general path: returns false
+    // before touching anything.
+    __device__ __forceinline__ bool agg_window(const uint32_t (&x)[V], uint32_t lo, uint32_t hi)
     {
         static_assert(NS == 1, "positions a + V lane + i");
-        // lane k: record ord_cur + k, whose piece starts at lo for the current record
         const uint32_t nrec = ord_loaded - ord_cur, o = ord_cur + lane;
         const uint32_t st = lane == 0 ? lo : (lane < nrec ? nst()[o & PRM()] : NONE);
         const bool w = st < hi;
         const uint32_t bw = __ballot_sync(FULLMASK, w);
         if (bw >> 31) return false;
-        // inclusive prefixes of both halves at the lane's positions (invalid ones add 0)
-        uint32_t pl[V], ph[V];
-        uint32_t cl = 0, ch = 0;
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const uint32_t p = a + V * lane + i;
-            const uint32_t v = (p >= lo && p < hi) ? x[i] : 0u;
-            cl += v & 0xFFFFu;
-            ch += v >> 16;
-            pl[i] = cl;
-            ph[i] = ch;
-        }
-        const uint32_t il = scan_add(cl), ih = scan_add(ch);
-#pragma unroll
-        for (int i = 0; i < V; ++i) {
-            pl[i] += il - cl;
-            ph[i] += ih - ch;
-        }
         ctr += (lane == 0 || lane == 4 || lane == 7) ? 1u : (lane == 5 ? hi - lo : 0u);
-        const uint32_t s = max(st, lo);
-        const uint32_t e = (w && lane + 1 < nrec) ? min(hi, nst()[(o + 1) & PRM()]) : hi;
-        const bool piece = w && e > s;
-        uint32_t sl = 0, sh = 0;
+        // record k >= 1 starts in (lo, hi): on a lane boundary, at lane (st - a) / V in 1..31
+        const uint32_t d = st - a;
+        if (__all_sync(FULLMASK, !w || lane == 0 || (d & (V - 1)) == 0)) {
+            const uint32_t m = __reduce_or_sync(FULLMASK, (w && lane > 0) ? 1u << (d / V) : 0u);
+            const uint32_t rel = __popc(m & (FULLMASK >> (31 - lane)));
+            uint32_t n = 0;
+            unsigned long long sum = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            __syncwarp();
-            uint32_t q[V];
-#pragma unroll
-            for (int i = 0; i < V; ++i) q[i] = h ? ph[i] : pl[i];
-            if constexpr (V == 4) {
-                reinterpret_cast<uint4 *>(marks().ptr())[lane] = make_uint4(q[0], q[1 % V], q[2 % V], q[3 % V]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < V; ++i) marks()[V * lane + i] = q[i];
+            for (int i = 0; i < V; ++i) {
+                const uint32_t p = a + V * lane + i;
+                const bool in = p >= lo && p < hi;
+                n += in ? 1u : 0u;
+                sum += in ? x[i] : 0u;
             }
-            __syncwarp();
-            if (piece) {
-                const uint32_t d = marks()[e - 1 - a] - (s > a ? marks()[s - 1 - a] : 0u);
-                if (h) sh = d;
-                else sl = d;
+            if (n) fold((uint32_t)nra()[(ord_cur + rel) & PRM()], n, sum, NONE);
+        } else {
+            // inclusive prefixes of both halves at the lane's positions (invalid ones add 0)
+            uint32_t pl[V], ph[V];
+            uint32_t cl = 0, ch = 0;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const uint32_t p = a + V * lane + i;
+                const uint32_t v = (p >= lo && p < hi) ? x[i] : 0u;
+                cl += v & 0xFFFFu;
+                ch += v >> 16;
+                pl[i] = cl;
+                ph[i] = ch;
             }
+            const uint32_t il = scan_add(cl), ih = scan_add(ch);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                pl[i] += il - cl;
+                ph[i] += ih - ch;
+            }
+            const uint32_t s = max(st, lo);
+            const uint32_t e = (w && lane + 1 < nrec) ? min(hi, nst()[(o + 1) & PRM()]) : hi;
+            const bool piece = w && e > s;
+            uint32_t sl = 0, sh = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                __syncwarp();
+                uint32_t q[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) q[i] = h ? ph[i] : pl[i];
+                if constexpr (V == 4) {
+                    reinterpret_cast<uint4 *>(marks().ptr())[lane] = make_uint4(q[0], q[1 % V], q[2 % V], q[3 % V]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) marks()[V * lane + i] = q[i];
+                }
+                __syncwarp();
+                if (piece) {
+                    const uint32_t df = marks()[e - 1 - a] - (s > a ? marks()[s - 1 - a] : 0u);
+                    if (h) sh = df;
+                    else sl = df;
+                }
+            }
+            if (piece) fold((uint32_t)nra()[o & PRM()], e - s, ((unsigned long long)sh << 16) + sl, NONE);
         }
-        if (piece) fold((uint32_t)nra()[o & PRM()], e - s, ((unsigned long long)sh << 16) + sl, NONE);
         __syncwarp();
         // the last record starting before hi becomes the current one
         take_record(ord_cur + 31 - __clz(bw));
@@ -1086,11 +1108,7 @@ struct TagEngine {
         uint32_t r[V], aux[V], st[V], par[V];
         const bool uni = s_nx >= hi;
         if constexpr (RUN && NS == 1) {
-            // windows whose first region start falls on a lane boundary within the first 32
-            // positions (short regions of lane-multiple lengths, where each lane's items
-            // mostly lie in one region) fold as cheaply per item and stay on the general path
-            const uint32_t d0 = s_nx - a;
-            if (!uni && !P.want_min && ((d0 & (V - 1)) != 0 || d0 >= 32) && seg_window(x, lo, hi)) return;
+            if (!uni && !P.want_min && agg_window(x, lo, hi)) return;
         }
         if (uni) {
             // every position of the window lies in the current parent
