@@ -694,10 +694,12 @@ def run_case(args, rs, torch):
                           "gbs": 4 * n / (kms * 1e-3) / 1e9, "result": out.cpu().tolist()}), flush=True)
         return
     if parts[0] == "rsum":
-        # the region-sum pipeline over 2^26 elements in regions of one size: rsum:SIZE:STRATEGY
-        size, strat = int(parts[1]), parts[2]
+        # the region-sum pipeline over 2^26 elements in regions of one size (rsum:SIZE:STRATEGY)
+        # or of sizes uniform on 0..SIZE (rsum:USIZE:STRATEGY), as the region_sizes section cuts them
+        variable = parts[1].startswith("U")
+        size, strat = int(parts[1].lstrip("U")), parts[2]
         n = N_ELEM
-        L = wl.sized_lengths(n, size, 11, False)
+        L = wl.sized_lengths(n, size, 11, variable)
         el = wl.sized_region_stream(n, 128, seed=11)["elements"]
         dev = {"R": int(L.shape[0]), "len": torch.from_numpy(L.view(np.int32)).cuda(),
                "elements": torch.from_numpy(el.view(np.int32)).cuda()}
@@ -766,8 +768,9 @@ def main():
                          "running the same five streams on every rank (weak scaling)")
     ap.add_argument("--case", default=None,
                     help="MEAN:STRATEGY[:N_LOG2[:OPT=V,...]] -- one cascade stream, fixed strategy and options; "
-                         "calib:N_LOG2 -- the calibration kernel; rsum:SIZE:STRATEGY -- the region-sum pipeline "
-                         "over 2^26 elements in regions of SIZE (small fixed launch sequences for profilers)")
+                         "calib:N_LOG2 -- the calibration kernel; rsum:SIZE:STRATEGY or rsum:USIZE:STRATEGY -- the "
+                         "region-sum pipeline over 2^26 elements in regions of SIZE or of sizes U{0..SIZE} "
+                         "(small fixed launch sequences for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
