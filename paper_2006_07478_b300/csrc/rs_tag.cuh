@@ -42,7 +42,8 @@
 //   * Enumeration straight into the aggregate (the region-sum stage list, compiled on its
 //     own) needs no tag per item: runs of full windows inside one parent keep per-lane
 //     partials and reduce once per run, and a window crossing parent starts folds each
-//     region's piece as a difference of two warp prefix sums.
+//     region's piece as a difference of two warp prefix sums, or, when every start in it
+//     falls on a lane boundary, each lane's items (which then lie in one region) at once.
 //
 // Rings and the parent stream are drained when a processor moves to a unit of another
 // stream and when it runs out of units.  Nothing waits on another warp: the kernel has
